@@ -1,0 +1,197 @@
+"""Seeded synthetic inputs shaped like the paper's plasma-mirror workloads.
+
+This module only *generates inputs* (numpy, FP64, seeded with PCG64); it holds
+none of the PSATD or FDTD update arithmetic, so both the CUDA path and the CPU
+oracle can be fed from it.  Every generator is deterministic in its seed.
+
+Workloads (the paper's simulations, Fig. 1 and Sec. II.B, need a PIC code and
+a plasma; these prescribed fields and sources stand in for them):
+
+* ``plane_waves``   -- a sum of on-grid vacuum plane waves (integer mode
+                       numbers, unit-normal amplitudes, random phases,
+                       transverse polarisation so div E = div B = 0).
+* ``current_sheet`` -- the oscillating plasma-mirror surface as a prescribed
+                       current sheet J_y(x, t) = J0 exp(-(x - x0(t))^2 / w^2),
+                       x0(t) = a sin(w0 t)/w0 around the box centre.
+* ``gaussian_charges`` -- moving Gaussian macro-charges whose rho^n, rho^(n+1)
+                       and J^(n+1/2) satisfy discrete continuity exactly.
+* ``random_fields`` -- white-noise component arrays for parity tests.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "rng", "plane_waves", "plane_wave_fields", "current_sheet", "random_fields",
+    "gaussian_charges", "coulomb_field",
+]
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def plane_waves(shape, nwaves=8, seed=1608, polarisations="both"):
+    """Draw ``nwaves`` on-grid plane waves for a 2D grid ``shape = (ny, nx)``.
+
+    Each wave: integer mode numbers (mx, my) with 1 <= |m| < n/2 on at least
+    one axis and |m_i| < n_i/2 on every axis, a random phase, and amplitudes
+    a1 (in-plane, TE: Ex, Ey, Bz) and a2 (out-of-plane, TM: Ez, Bx, By) drawn
+    from N(0, 1).  ``polarisations`` is "both", "te" or "tm".
+    Returns a list of dicts with keys m, phase, a_te, a_tm.
+    """
+    ny, nx = shape
+    g = rng(seed)
+    waves = []
+    while len(waves) < nwaves:
+        mx = int(g.integers(-(nx // 2) + 1, nx // 2))
+        my = int(g.integers(-(ny // 2) + 1, ny // 2))
+        if mx == 0 and my == 0:
+            continue
+        phase = float(g.uniform(0.0, 2.0 * math.pi))
+        a_te, a_tm = (float(v) for v in g.standard_normal(2))
+        if polarisations == "te":
+            a_tm = 0.0
+        elif polarisations == "tm":
+            a_te = 0.0
+        waves.append(dict(m=(mx, my), phase=phase, a_te=a_te, a_tm=a_tm))
+    return waves
+
+
+def plane_wave_fields(waves, shape, d, c=1.0):
+    """Real fields E, B (arrays ``(3, ny, nx)``) of ``waves`` at t = 0, on the nodes.
+
+    Wave: E = (a_te e_te + a_tm z) cos(k.x + phase), B = kappa x E / c,
+    e_te = z x kappa (in-plane, transverse), kappa = k/|k|.
+    """
+    ny, nx = shape
+    x = np.arange(nx) * d[0]
+    y = np.arange(ny) * d[1]
+    X, Y = np.meshgrid(x, y)
+    E = np.zeros((3, ny, nx))
+    B = np.zeros((3, ny, nx))
+    for w in waves:
+        kx = 2.0 * math.pi * w["m"][0] / (nx * d[0])
+        ky = 2.0 * math.pi * w["m"][1] / (ny * d[1])
+        kn = math.hypot(kx, ky)
+        kap = np.array([kx / kn, ky / kn, 0.0])
+        e_te = np.array([-kap[1], kap[0], 0.0])
+        e0 = w["a_te"] * e_te + w["a_tm"] * np.array([0.0, 0.0, 1.0])
+        b0 = np.cross(kap, e0) / c
+        ph = np.cos(kx * X + ky * Y + w["phase"])
+        E += e0[:, None, None] * ph
+        B += b0[:, None, None] * ph
+    return E, B
+
+
+def current_sheet(shape, d, t, *, lam, a, w, J0=1.0, c=1.0):
+    """J = (0, J_y, 0) of the oscillating current sheet at time ``t`` (2D, ``(ny, nx)``).
+
+    J_y(x) = J0 exp(-(x - x0(t))^2 / w^2), x0(t) = xc + a sin(w0 t)/w0,
+    w0 = 2 pi c / lam, xc the box centre; the distance is taken to the nearest
+    periodic image.  Uniform in y, so div J = 0 (rho = 0).
+    """
+    ny, nx = shape
+    Lx = nx * d[0]
+    w0 = 2.0 * math.pi * c / lam
+    x0 = 0.5 * Lx + a * math.sin(w0 * t) / w0
+    x = np.arange(nx) * d[0]
+    dx = (x - x0 + 0.5 * Lx) % Lx - 0.5 * Lx
+    prof = J0 * np.exp(-(dx / w) ** 2)
+    J = np.zeros((3, ny, nx))
+    J[1] = prof[None, :]
+    return J
+
+
+def random_fields(shape, ncomp, seed, scale=1.0):
+    """``ncomp`` white-noise arrays of ``shape`` drawn from N(0, scale^2)."""
+    return scale * rng(seed).standard_normal((ncomp,) + tuple(shape))
+
+
+def _kaxes(shape, d):
+    """Signed discrete wavenumbers per axis (Nyquist entry 0), rfft half along x."""
+    ks = []
+    for ax, n in enumerate(shape):
+        h = d[len(shape) - 1 - ax]
+        if ax == len(shape) - 1:
+            m = np.arange(n // 2 + 1, dtype=np.float64)
+        else:
+            m = np.fft.fftfreq(n) * n
+        k = 2.0 * math.pi * m / (n * h)
+        if n % 2 == 0:
+            k[np.abs(m) == n // 2] = 0.0
+        sh = [1] * len(shape)
+        sh[ax] = k.size
+        ks.append(k.reshape(sh))
+    return ks[::-1]  # (kx, ky[, kz])
+
+
+def gaussian_charges(shape, d, dt, *, n_charges=64, sigma=None, vmax=0.5, c=1.0,
+                     seed=1610, step=0):
+    """rho^n, rho^(n+1) and J^(n+1/2) of moving Gaussian macro-charges.
+
+    Charges q = +1, -1 alternating (net zero), uniform positions, velocities
+    uniform in the ball |v| < vmax c, Gaussian width ``sigma`` (default 3 dx).
+    Built in Fourier space on the discrete wavenumbers (Nyquist entry 0):
+      rho^(k, t)  = (N/V) sum_j q_j exp(-sigma^2 k^2/2) exp(-i k.x_j(t)),
+      J^(k)       = (N/V) sum_j q_j v_j exp(-sigma^2 k^2/2) exp(-i k.x_j(t_n))
+                    * (exp(-i k.v_j dt) - 1)/(-i k.v_j dt),
+    the exact time average of the current over [t_n, t_n+1], so that
+    rho^(n+1) - rho^n = -i dt k.J^ holds to rounding on the discrete k.
+    Returns (rho_n, rho_np1, J) as real arrays (J has shape ``(3, *shape)``).
+    """
+    ndim = len(shape)
+    g = rng(seed)
+    Ls = [shape[ndim - 1 - i] * d[i] for i in range(ndim)]  # (Lx, Ly[, Lz])
+    pos = np.stack([g.uniform(0.0, L, n_charges) for L in Ls], axis=1)
+    dirs = g.standard_normal((n_charges, ndim))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    speed = vmax * c * g.uniform(0.0, 1.0, n_charges) ** (1.0 / ndim)
+    vel = dirs * speed[:, None]
+    q = np.where(np.arange(n_charges) % 2 == 0, 1.0, -1.0)
+    sigma = 3.0 * d[0] if sigma is None else sigma
+    ks = _kaxes(shape, d)
+    k2 = sum(k * k for k in ks)
+    N = float(np.prod(shape))
+    V = float(np.prod(Ls))
+    G = (N / V) * np.exp(-0.5 * sigma * sigma * k2)
+    tn = step * dt
+    rho0 = np.zeros(k2.shape, dtype=np.complex128)
+    rho1 = np.zeros_like(rho0)
+    Jh = [np.zeros_like(rho0) for _ in range(3)]
+    for j in range(n_charges):
+        xn = pos[j] + vel[j] * tn
+        phase = np.exp(-1j * sum(ks[a] * xn[a] for a in range(ndim)))
+        kv = sum(ks[a] * vel[j][a] for a in range(ndim)) * dt
+        e = np.exp(-1j * kv)
+        small = np.abs(kv) < 1e-12
+        kv_safe = np.where(small, 1.0, kv)
+        avg = np.where(small, 1.0 - 0.5j * kv, (e - 1.0) / (-1j * kv_safe))
+        rho0 += q[j] * G * phase
+        rho1 += q[j] * G * phase * e
+        for a in range(ndim):
+            Jh[a] += q[j] * vel[j][a] * G * phase * avg
+    axes = tuple(range(ndim))
+    r0 = np.fft.irfftn(rho0, s=shape, axes=axes)
+    r1 = np.fft.irfftn(rho1, s=shape, axes=axes)
+    J = np.zeros((3,) + tuple(shape))
+    for a in range(ndim):
+        J[a] = np.fft.irfftn(Jh[a], s=shape, axes=axes)
+    return r0, r1, J
+
+
+def coulomb_field(rho, d, eps0=1.0):
+    """Longitudinal E with i k.E^ = rho^/eps0 (Nyquist entries 0), as ``(3, *shape)``."""
+    shape = rho.shape
+    ndim = len(shape)
+    ks = _kaxes(shape, d)
+    k2 = sum(k * k for k in ks)
+    R = np.fft.rfftn(rho, axes=tuple(range(ndim)))
+    k2s = np.where(k2 > 0, k2, 1.0)
+    E = np.zeros((3,) + tuple(shape))
+    for a in range(ndim):
+        Eh = np.where(k2 > 0, -1j * ks[a] * R / (eps0 * k2s), 0.0)
+        E[a] = np.fft.irfftn(Eh, s=shape, axes=tuple(range(ndim)))
+    return E
