@@ -1,0 +1,178 @@
+/*
+ * psatd.h -- C ABI of the GB300 (sm_103a) PSATD Maxwell step and its FDTD
+ * comparators.
+ *
+ * Method (Blaclard, Vincenti, Lehe, Vay 2016, Sec. III.B item 2 and Table 1,
+ * row "PSATD"): Maxwell's equations are solved in (k, t) space on a periodic
+ * grid and integrated analytically over one time step, assuming the sources
+ * J and rho are constant during the step; the scheme is dispersion-free and
+ * has no Courant condition.  One step is: forward FFT of E, B, J (and rho),
+ * the per-mode analytic push with C = cos(c|k|dt), S = sin(c|k|dt), inverse
+ * FFT.  The FDTD comparators are the Yee and Cole-Karkkainen (CKC, beta = 1/4)
+ * schemes of Sec. III.A / Table 1.
+ *
+ * Per-mode update (c, eps0 explicit; kappa = k/|k|; x = c|k|dt):
+ *   E' = C E + (1-C) kappa(kappa.E) + i c S kappa x B - S/(eps0 c k) J
+ *        + (S/(c k) - dt)/eps0 kappa(kappa.J)                       [J-form]
+ *   E' = C E + i c S kappa x B - S/(eps0 c k) J
+ *        + i k/(eps0 k^2) [(S/x - 1) rho_np1 - (S/x - C) rho_n]      [rho-form]
+ *   B' = C B + (1-C) kappa(kappa.B) - i S/(c k) k x E + i (1-C)/(eps0 c^2 k^2) k x J
+ *   k = 0: E' = E - dt J/eps0, B' = B.
+ * The Nyquist index of every even axis is treated as k_i = 0.
+ *
+ * Conventions common to every entry point
+ *   - Arrays are caller-owned DEVICE memory, one array per field component,
+ *     x contiguous: 2D [ny][nx], 3D [nz][ny][nx]; element type double for
+ *     PSATD_FP64 and float for PSATD_FP32; base addresses 16-byte aligned.
+ *   - Staggering: PSATD is collocated (all components on the nodes); the FDTD
+ *     arrays use the Yee positions Ex(i+1/2,j,k) Ey(i,j+1/2,k) Ez(i,j,k+1/2)
+ *     Bx(i,j+1/2,k+1/2) By(i+1/2,j,k+1/2) Bz(i+1/2,j+1/2,k), J with E.
+ *   - Time levels: E, B at t_n in, t_n+1 out (updated in place); J at
+ *     t_n+1/2; rho_n at t_n, rho_np1 at t_n+1.  With nsteps > 1 the sources
+ *     are held constant over the nsteps steps.
+ *   - Every call is asynchronous and stream-ordered on the plan's CUDA stream
+ *     (a cudaStream_t passed as void*; NULL = legacy default stream).  No call
+ *     but psatd_plan_sync and psatd_kernel_times synchronises.
+ *   - Host-side validation happens before any launch; an invalid argument
+ *     returns PSATD_ERR_INVALID_ARG and launches nothing.  No exception crosses
+ *     the ABI.  Message of the last failure: psatd_last_error(plan) (or
+ *     psatd_last_error(NULL) for failures without a plan, thread-local).
+ *   - A plan may be used by one host thread / one stream at a time.
+ */
+#ifndef PSATD_H
+#define PSATD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PSATD_ABI_VERSION 1
+
+typedef enum {
+  PSATD_OK = 0,
+  PSATD_ERR_INVALID_ARG = 1,  /* bad descriptor, null or misaligned pointer, bad count */
+  PSATD_ERR_UNSUPPORTED = 2,  /* valid but not implemented (size, precision, layout)  */
+  PSATD_ERR_OOM = 3,          /* device allocation failed                             */
+  PSATD_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed                 */
+  PSATD_ERR_TIMEOUT = 5,      /* a bounded device-side wait expired                   */
+  PSATD_ERR_NONFINITE = 6     /* reserved: non-finite values detected                 */
+} psatd_status;
+
+typedef enum {
+  PSATD_FP64 = 0,        /* double storage and arithmetic                              */
+  PSATD_FP32 = 1,        /* float storage; twiddles and C, S applied compensated (hi/lo) */
+  PSATD_MIXED_BF16 = 2,  /* reserved (tensor-core split-BF16 DFT passes)              */
+  PSATD_MIXED_FP16 = 3   /* reserved (tensor-core split-FP16 DFT passes)              */
+} psatd_precision;
+
+typedef enum {
+  PSATD_SRC_NONE = 0,    /* vacuum: J = rho = 0                     */
+  PSATD_SRC_J = 1,       /* J-form: uses J                          */
+  PSATD_SRC_J_RHO = 2    /* rho-form: uses J, rho_n and rho_np1     */
+} psatd_source_form;
+
+typedef enum {
+  PSATD_FIELDS_3D6 = 0,   /* 3D, all six components                                 */
+  PSATD_FIELDS_2D6 = 1,   /* 2D (x, y, uniform in z), all six components            */
+  PSATD_FIELDS_2D_TE = 2, /* 2D: Ex, Ey, Bz (sources Jx, Jy, rho)                   */
+  PSATD_FIELDS_2D_TM = 3  /* 2D: Ez, Bx, By (source Jz; no rho-form)                */
+} psatd_layout;
+
+typedef enum { PSATD_FDTD_YEE = 0, PSATD_FDTD_CKC = 1 } psatd_fdtd_scheme;
+
+/* Problem statement (the paper's arguments: grid sizes, cell sizes, dt, c, eps0). */
+typedef struct {
+  int32_t ndim;      /* 2 or 3 (must agree with layout)                           */
+  int32_t layout;    /* psatd_layout                                              */
+  int64_t n[3];      /* cells along x, y, z; n[2] = 1 in 2D                       */
+  double d[3];       /* cell sizes dx, dy, dz (> 0; d[2] ignored in 2D)           */
+  double dt;         /* time step (> 0; PSATD has no Courant limit)               */
+  double c;          /* speed of light (> 0)                                      */
+  double eps0;       /* vacuum permittivity (> 0)                                 */
+  int32_t prec;      /* psatd_precision                                           */
+  int32_t src;       /* psatd_source_form                                         */
+  int32_t flags;     /* reserved, must be 0                                       */
+  int32_t reserved;  /* must be 0                                                 */
+} psatd_desc;
+
+/* Field arrays, updated in place.  Entries of components absent from the
+ * layout must be NULL (TE: E[0], E[1], B[2]; TM: E[2], B[0], B[1]).        */
+typedef struct { void* E[3]; void* B[3]; } psatd_fields;
+
+/* Source arrays, read only.  J entries of absent components must be NULL;
+ * rho_n / rho_np1 are used by PSATD_SRC_J_RHO only.                        */
+typedef struct { const void* J[3]; const void* rho_n; const void* rho_np1; } psatd_sources;
+
+typedef struct psatd_plan_s* psatd_plan;
+
+/* ABI version of the loaded library (PSATD_ABI_VERSION of its build). */
+int32_t psatd_abi_version(void);
+
+/* Create a PSATD plan for `desc` on `cuda_stream`.
+ * Supported (this build): every n[i] a power of two, 16 <= n[0] <= 4096,
+ * 8 <= n[1], n[2] <= 4096; PSATD_FP64 or PSATD_FP32; flags = 0.
+ * Owns: its spectral scratch (about n_in * (n0/2+1) * n1 * n2 complex values,
+ * twice that in 3D), the twiddle tables and the k-space coefficient table,
+ * allocated with cudaMalloc on the current device.  *out is set to NULL on
+ * failure.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA.                   */
+psatd_status psatd_plan_create(const psatd_desc* desc, void* cuda_stream, psatd_plan* out);
+
+/* Fill the plan's tables on the device (FP64 arithmetic, rounded once to the
+ * step precision; FP32 keeps hi/lo pairs of the twiddles and of C and S/|k|):
+ * twiddles exp(-2 pi i j / n) per axis and, per |k|-octant entry,
+ * C, S/|m|, (1-C)/|m|^2, (S/(ck)-dt)/(eps0 |m|^2), (S/x-1)/(eps0 g |m|^2),
+ * (S/x-C)/(eps0 g |m|^2) with their k -> 0 limits, all scaled by 1/N.
+ * Must be called once before psatd_step (psatd_step fails otherwise).     */
+psatd_status psatd_coeffs_init(psatd_plan plan);
+
+/* Advance E, B by nsteps PSATD steps (nsteps >= 1).  `sources` may be NULL
+ * for PSATD_SRC_NONE and must not be NULL otherwise.  Per step: forward
+ * R2C/C2C FFT passes of every input component, the fused per-mode push with
+ * the first inverse pass, the remaining inverse passes (C2R last).  Never
+ * synchronises.  Errors: INVALID_ARG (missing/extra/misaligned pointer,
+ * nsteps < 1, coefficients not initialised), CUDA.                          */
+psatd_status psatd_step(psatd_plan plan, const psatd_fields* fields,
+                        const psatd_sources* sources, int32_t nsteps);
+
+/* Synchronise the plan's stream and report any asynchronous CUDA error. */
+psatd_status psatd_plan_sync(psatd_plan plan);
+
+/* Release the plan and everything it owns (synchronises its stream first).
+ * NULL is accepted and ignored. */
+psatd_status psatd_plan_destroy(psatd_plan plan);
+
+/* Bytes of device memory the plan owns. */
+size_t psatd_plan_workspace_bytes(psatd_plan plan);
+
+/* Per-kernel CUDA-event timing of the plan's launches.  enable != 0 starts
+ * recording an event pair around every launch on the plan's stream (and
+ * clears earlier records).  psatd_kernel_times synchronises, then writes for
+ * each kernel slot i < n_slots: its name (names[i] points into the library,
+ * valid while the plan lives), the number of launches and the summed
+ * milliseconds, and returns the number of slots used.                       */
+psatd_status psatd_plan_set_timing(psatd_plan plan, int32_t enable);
+int32_t psatd_kernel_times(psatd_plan plan, int32_t n_slots, const char** names,
+                           int64_t* launches, double* total_ms);
+
+/* Advance co-temporal E, B (Yee staggering) by nsteps FDTD steps:
+ * B -= (dt/2) curl E;  E += dt (c^2 curl B - J/eps0);  B -= (dt/2) curl E.
+ * scheme: PSATD_FDTD_YEE (2D or 3D) or PSATD_FDTD_CKC (2D only; the Faraday
+ * differences are weighted 1-beta on the centre row and beta/2 on the two
+ * transverse neighbour rows, beta = 1/4).  desc->src must be PSATD_SRC_NONE
+ * or PSATD_SRC_J.  Sizes: any n[i] >= 2.  Launches on `cuda_stream`, no
+ * allocation, no synchronisation.  Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+psatd_status fdtd_step(const psatd_desc* desc, int32_t scheme, const psatd_fields* fields,
+                       const psatd_sources* sources, int32_t nsteps, void* cuda_stream);
+
+/* Message of the last failure on `plan`, or of this thread's last failure
+ * without a plan when plan == NULL.  Never NULL. */
+const char* psatd_last_error(psatd_plan plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSATD_H */

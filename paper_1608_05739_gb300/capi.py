@@ -1,0 +1,234 @@
+"""ctypes binding of the C ABI in ``include/psatd.h`` (argument marshalling only).
+
+Every step of the PSATD/FDTD path runs in the CUDA kernels of ``libpsatd.so``;
+this module only checks tensor arguments, builds the C structs and calls the
+entry points of the same names.  PyTorch supplies device memory and streams.
+There is no CPU fallback: if the library is missing or no GPU is present, the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpsatd.so")
+
+PSATD_OK = 0
+STATUS = {0: "PSATD_OK", 1: "PSATD_ERR_INVALID_ARG", 2: "PSATD_ERR_UNSUPPORTED", 3: "PSATD_ERR_OOM",
+          4: "PSATD_ERR_CUDA", 5: "PSATD_ERR_TIMEOUT", 6: "PSATD_ERR_NONFINITE"}
+PREC = {"fp64": 0, "fp32": 1, "mixed_bf16": 2, "mixed_fp16": 3}
+SRC = {"none": 0, "J": 1, "rho": 2}
+LAYOUT = {"3d6": 0, "2d6": 1, "te": 2, "tm": 3}
+SCHEME = {"yee": 0, "ckc": 1}
+# (E, B, J) components present per layout
+PRESENT = {
+    "3d6": ((1, 1, 1), (1, 1, 1), (1, 1, 1)),
+    "2d6": ((1, 1, 1), (1, 1, 1), (1, 1, 1)),
+    "te": ((1, 1, 0), (0, 0, 1), (1, 1, 0)),
+    "tm": ((0, 0, 1), (1, 1, 0), (0, 0, 1)),
+}
+
+
+class PsatdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class psatd_desc(ct.Structure):
+    _fields_ = [("ndim", ct.c_int32), ("layout", ct.c_int32), ("n", ct.c_int64 * 3),
+                ("d", ct.c_double * 3), ("dt", ct.c_double), ("c", ct.c_double),
+                ("eps0", ct.c_double), ("prec", ct.c_int32), ("src", ct.c_int32),
+                ("flags", ct.c_int32), ("reserved", ct.c_int32)]
+
+
+class psatd_fields(ct.Structure):
+    _fields_ = [("E", ct.c_void_p * 3), ("B", ct.c_void_p * 3)]
+
+
+class psatd_sources(ct.Structure):
+    _fields_ = [("J", ct.c_void_p * 3), ("rho_n", ct.c_void_p), ("rho_np1", ct.c_void_p)]
+
+
+_lib = None
+
+EXPORTS = [
+    ("psatd_abi_version", ct.c_int32, []),
+    ("psatd_plan_create", ct.c_int, [ct.POINTER(psatd_desc), ct.c_void_p, ct.POINTER(ct.c_void_p)]),
+    ("psatd_coeffs_init", ct.c_int, [ct.c_void_p]),
+    ("psatd_step", ct.c_int, [ct.c_void_p, ct.POINTER(psatd_fields), ct.POINTER(psatd_sources), ct.c_int32]),
+    ("psatd_plan_sync", ct.c_int, [ct.c_void_p]),
+    ("psatd_plan_destroy", ct.c_int, [ct.c_void_p]),
+    ("psatd_plan_workspace_bytes", ct.c_size_t, [ct.c_void_p]),
+    ("psatd_plan_set_timing", ct.c_int, [ct.c_void_p, ct.c_int32]),
+    ("psatd_kernel_times", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_char_p),
+                                        ct.POINTER(ct.c_int64), ct.POINTER(ct.c_double)]),
+    ("fdtd_step", ct.c_int, [ct.POINTER(psatd_desc), ct.c_int32, ct.POINTER(psatd_fields),
+                             ct.POINTER(psatd_sources), ct.c_int32, ct.c_void_p]),
+    ("psatd_last_error", ct.c_char_p, [ct.c_void_p]),
+]
+
+
+def load(path: str = LIB_PATH):
+    """Load libpsatd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("%s is missing: build it with paper_1608_05739_gb300.build.build()" % path)
+    lib = ct.CDLL(path)
+    for name, res, args in EXPORTS:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status, plan=None):
+    if status != PSATD_OK:
+        msg = load().psatd_last_error(plan)
+        raise PsatdError(status, msg.decode() if msg else "")
+
+
+def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0):
+    """psatd_desc for grid ``n`` = (nx, ny[, nz]) and cell sizes ``d``."""
+    nd = len(n)
+    desc = psatd_desc()
+    desc.ndim = nd
+    desc.layout = LAYOUT[layout]
+    for i in range(3):
+        desc.n[i] = int(n[i]) if i < nd else 1
+        desc.d[i] = float(d[i]) if i < nd else 1.0
+    desc.dt, desc.c, desc.eps0 = float(dt), float(c), float(eps0)
+    desc.prec = PREC[prec]
+    desc.src = SRC[src]
+    desc.flags = 0
+    desc.reserved = 0
+    return desc
+
+
+def _ptr(t, shape, dtype, what):
+    """Device pointer of tensor ``t`` after checking device, dtype, shape, layout."""
+    if t is None:
+        return None
+    if not getattr(t, "is_cuda", False):
+        raise ValueError("%s must be a CUDA tensor" % what)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s (got %s)" % (what, dtype, t.dtype))
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s (got %s)" % (what, tuple(shape), tuple(t.shape)))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % what)
+    return t.data_ptr()
+
+
+def _grid_shape(n):
+    return tuple(int(v) for v in reversed(n))  # [nz][ny][nx] / [ny][nx]
+
+
+def _fields_struct(layout, shape, dtype, E, B):
+    pe, pb, _ = PRESENT[layout]
+    f = psatd_fields()
+    for i in range(3):
+        e = E[i] if E is not None else None
+        b = B[i] if B is not None else None
+        if bool(pe[i]) != (e is not None) or bool(pb[i]) != (b is not None):
+            raise ValueError("component %d of E/B presence does not match layout %r" % (i, layout))
+        f.E[i] = _ptr(e, shape, dtype, "E[%d]" % i)
+        f.B[i] = _ptr(b, shape, dtype, "B[%d]" % i)
+    return f
+
+
+def _sources_struct(layout, shape, dtype, J, rho_n, rho_np1):
+    _, _, pj = PRESENT[layout]
+    s = psatd_sources()
+    for i in range(3):
+        j = J[i] if J is not None else None
+        if j is not None and not pj[i]:
+            raise ValueError("J[%d] is not used by layout %r" % (i, layout))
+        s.J[i] = _ptr(j, shape, dtype, "J[%d]" % i)
+    s.rho_n = _ptr(rho_n, shape, dtype, "rho_n")
+    s.rho_np1 = _ptr(rho_np1, shape, dtype, "rho_np1")
+    return s
+
+
+def _torch_dtype(prec):
+    import torch
+    return torch.float64 if prec == "fp64" else torch.float32
+
+
+class Plan:
+    """A PSATD plan (psatd_plan_create + psatd_coeffs_init) bound to a CUDA stream.
+
+    ``n`` = (nx, ny[, nz]) cells, ``d`` cell sizes, ``dt`` time step; fields are
+    passed per component as contiguous CUDA tensors of shape [ny, nx] or
+    [nz, ny, nx] (None for components absent from the layout).
+    """
+
+    def __init__(self, n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, stream=None):
+        import torch
+        lib = load()
+        self.n, self.layout, self.prec, self.src = tuple(n), layout, prec, src
+        self.shape = _grid_shape(n)
+        self.dtype = _torch_dtype(prec)
+        self.desc = make_desc(n, d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ct.c_void_p()
+        _check(lib.psatd_plan_create(ct.byref(self.desc), ct.c_void_p(stream.cuda_stream), ct.byref(h)))
+        self.handle = h
+        _check(lib.psatd_coeffs_init(self.handle), self.handle)
+
+    def step(self, E, B, J=None, rho_n=None, rho_np1=None, nsteps=1):
+        f = _fields_struct(self.layout, self.shape, self.dtype, E, B)
+        s = _sources_struct(self.layout, self.shape, self.dtype, J, rho_n, rho_np1) \
+            if self.src != "none" else None
+        _check(load().psatd_step(self.handle, ct.byref(f), ct.byref(s) if s is not None else None,
+                                 int(nsteps)), self.handle)
+
+    def sync(self):
+        _check(load().psatd_plan_sync(self.handle), self.handle)
+
+    def workspace_bytes(self):
+        return int(load().psatd_plan_workspace_bytes(self.handle))
+
+    def set_timing(self, enable=True):
+        _check(load().psatd_plan_set_timing(self.handle, 1 if enable else 0), self.handle)
+
+    def kernel_times(self):
+        """{kernel name: (launches, total ms)} of the launches since set_timing(True)."""
+        names = (ct.c_char_p * 8)()
+        launches = (ct.c_int64 * 8)()
+        ms = (ct.c_double * 8)()
+        k = load().psatd_kernel_times(self.handle, 8, names, launches, ms)
+        return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(k)}
+
+    def destroy(self):
+        if getattr(self, "handle", None) is not None:
+            load().psatd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def fdtd_step(n, d, dt, E, B, J=None, *, scheme="yee", layout="te", prec="fp32", c=1.0, eps0=1.0,
+              nsteps=1, stream=None):
+    """Yee / CKC FDTD steps of co-temporal (E, B) in place (see include/psatd.h)."""
+    import torch
+    lib = load()
+    desc = make_desc(n, d, dt, layout=layout, prec=prec, src="J" if J is not None else "none", c=c, eps0=eps0)
+    shape = _grid_shape(n)
+    dtype = _torch_dtype(prec)
+    f = _fields_struct(layout, shape, dtype, E, B)
+    s = _sources_struct(layout, shape, dtype, J, None, None) if J is not None else None
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib.fdtd_step(ct.byref(desc), SCHEME[scheme], ct.byref(f), ct.byref(s) if s is not None else None,
+                         int(nsteps), ct.c_void_p(stream.cuda_stream)))

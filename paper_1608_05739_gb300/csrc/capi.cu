@@ -1,0 +1,552 @@
+// capi.cu -- the extern "C" boundary declared in include/psatd.h: argument
+// validation, plan ownership (scratch spectra and tables), the pass sequence
+// of a PSATD step, FDTD dispatch, CUDA-event timing of every launch.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/psatd.h"
+#include "launch.h"
+#include "tables.h"
+
+using namespace psatd;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+enum Slot { K_FWD_X = 0, K_FWD_Y = 1, K_PUSH = 2, K_INV_Y = 3, K_INV_X = 4, K_TABLES = 5, K_NSLOTS = 6 };
+const char* kSlotNames[K_NSLOTS] = {"fwd_x_r2c", "fwd_y_c2c", "line_fft_push", "inv_y_c2c", "inv_x_c2r",
+                                    "tables"};
+
+struct EventPair {
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct psatd_plan_s {
+  psatd_desc d;
+  cudaStream_t st = nullptr;
+  int device = 0;
+  bool f32 = true;
+  int ndim = 2, layout = 0, form = 0, n_in = 0, n_out = 0;
+  int64_t nx = 0, ny = 0, nz = 1, nxh = 0, cs = 0;
+  void* spec1 = nullptr;
+  void* spec2 = nullptr;
+  void* tw[3] = {nullptr, nullptr, nullptr};
+  void* tab = nullptr;
+  int64_t tab_e[3] = {1, 1, 1};
+  size_t bytes = 0;
+  bool coeffs_ready = false;
+  double g0 = 0, r[3] = {1, 1, 1};
+  std::string err = "no error";
+  bool timing = false;
+  std::vector<EventPair> ev[K_NSLOTS];
+  std::vector<EventPair> pool;
+};
+
+namespace {
+
+psatd_status fail(psatd_plan p, psatd_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (p) p->err = buf;
+  else g_err = buf;
+  return s;
+}
+
+psatd_status cuda_fail(psatd_plan p, cudaError_t e, const char* what) {
+  return fail(p, PSATD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+bool pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+bool pos_finite(double v) { return std::isfinite(v) && v > 0; }
+
+int layout_ndim(int layout) { return layout == PSATD_FIELDS_3D6 ? 3 : 2; }
+
+// component slots of a layout / source form (see psatd_kernels.cuh)
+void counts(int layout, int form, int* n_in, int* n_out) {
+  const bool six = (layout == PSATD_FIELDS_3D6 || layout == PSATD_FIELDS_2D6);
+  const int nf = six ? 6 : 3;
+  const int nj = six ? 3 : (layout == PSATD_FIELDS_2D_TE ? 2 : 1);
+  *n_out = nf;
+  *n_in = nf + (form >= 1 ? nj : 0) + (form == 2 ? 2 : 0);
+}
+
+// which (E, B, J) components a layout uses
+void present(int layout, bool e[3], bool b[3], bool j[3]) {
+  for (int i = 0; i < 3; ++i) e[i] = b[i] = j[i] = true;
+  if (layout == PSATD_FIELDS_2D_TE) {
+    e[2] = b[0] = b[1] = j[2] = false;
+  } else if (layout == PSATD_FIELDS_2D_TM) {
+    e[0] = e[1] = b[2] = j[0] = j[1] = false;
+  }
+}
+
+psatd_status validate_desc(psatd_plan p, const psatd_desc* d, bool psatd_limits) {
+  if (!d) return fail(p, PSATD_ERR_INVALID_ARG, "desc is NULL");
+  if (d->layout < 0 || d->layout > 3) return fail(p, PSATD_ERR_INVALID_ARG, "unknown layout %d", d->layout);
+  if (d->ndim != layout_ndim(d->layout))
+    return fail(p, PSATD_ERR_INVALID_ARG, "ndim %d does not match layout %d", d->ndim, d->layout);
+  if (d->flags != 0 || d->reserved != 0) return fail(p, PSATD_ERR_INVALID_ARG, "flags/reserved must be 0");
+  if (d->src < 0 || d->src > 2) return fail(p, PSATD_ERR_INVALID_ARG, "unknown source form %d", d->src);
+  if (d->layout == PSATD_FIELDS_2D_TM && d->src == PSATD_SRC_J_RHO)
+    return fail(p, PSATD_ERR_INVALID_ARG, "the TM layout has no rho-form (k.E = 0)");
+  if (d->prec < 0 || d->prec > 3) return fail(p, PSATD_ERR_INVALID_ARG, "unknown precision %d", d->prec);
+  if (d->prec >= PSATD_MIXED_BF16) return fail(p, PSATD_ERR_UNSUPPORTED, "mixed precision not in this build");
+  const int nd = d->ndim;
+  for (int i = 0; i < nd; ++i)
+    if (!pos_finite(d->d[i])) return fail(p, PSATD_ERR_INVALID_ARG, "d[%d] must be finite and > 0", i);
+  if (!pos_finite(d->dt) || !pos_finite(d->c) || !pos_finite(d->eps0))
+    return fail(p, PSATD_ERR_INVALID_ARG, "dt, c and eps0 must be finite and > 0");
+  if (nd == 2 && d->n[2] != 1) return fail(p, PSATD_ERR_INVALID_ARG, "n[2] must be 1 in 2D");
+  for (int i = 0; i < nd; ++i)
+    if (d->n[i] < 2) return fail(p, PSATD_ERR_INVALID_ARG, "n[%d] = %lld too small", i, (long long)d->n[i]);
+  if (psatd_limits) {
+    if (!pow2(d->n[0]) || d->n[0] < 16 || d->n[0] > 4096)
+      return fail(p, PSATD_ERR_UNSUPPORTED, "n[0] must be a power of two in [16, 4096]");
+    for (int i = 1; i < nd; ++i)
+      if (!pow2(d->n[i]) || d->n[i] < 8 || d->n[i] > 4096)
+        return fail(p, PSATD_ERR_UNSUPPORTED, "n[%d] must be a power of two in [8, 4096]", i);
+  } else {
+    for (int i = 0; i < nd; ++i)
+      if (d->n[i] > (1LL << 20)) return fail(p, PSATD_ERR_UNSUPPORTED, "n[%d] too large", i);
+  }
+  return PSATD_OK;
+}
+
+bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
+
+// Collect the input slots of a step in kernel slot order; checks presence,
+// absence and alignment of every pointer.
+psatd_status gather_slots(psatd_plan p, const psatd_fields* f, const psatd_sources* s,
+                          const void* in[kMaxComp], void* out[kMaxComp]) {
+  if (!f) return fail(p, PSATD_ERR_INVALID_ARG, "fields is NULL");
+  bool pe[3], pb[3], pj[3];
+  present(p->layout, pe, pb, pj);
+  const char* names = "xyz";
+  for (int i = 0; i < 3; ++i) {
+    if (pe[i] != (f->E[i] != nullptr))
+      return fail(p, PSATD_ERR_INVALID_ARG, "E%c must be %s for this layout", names[i], pe[i] ? "non-NULL" : "NULL");
+    if (pb[i] != (f->B[i] != nullptr))
+      return fail(p, PSATD_ERR_INVALID_ARG, "B%c must be %s for this layout", names[i], pb[i] ? "non-NULL" : "NULL");
+    if (f->E[i] && !aligned16(f->E[i])) return fail(p, PSATD_ERR_INVALID_ARG, "E%c not 16-byte aligned", names[i]);
+    if (f->B[i] && !aligned16(f->B[i])) return fail(p, PSATD_ERR_INVALID_ARG, "B%c not 16-byte aligned", names[i]);
+  }
+  if (p->form != PSATD_SRC_NONE) {
+    if (!s) return fail(p, PSATD_ERR_INVALID_ARG, "sources is NULL but the plan's source form needs them");
+    for (int i = 0; i < 3; ++i) {
+      if (pj[i] != (s->J[i] != nullptr))
+        return fail(p, PSATD_ERR_INVALID_ARG, "J%c must be %s for this layout", names[i], pj[i] ? "non-NULL" : "NULL");
+      if (s->J[i] && !aligned16(s->J[i])) return fail(p, PSATD_ERR_INVALID_ARG, "J%c not 16-byte aligned", names[i]);
+    }
+    if (p->form == PSATD_SRC_J_RHO) {
+      if (!s->rho_n || !s->rho_np1) return fail(p, PSATD_ERR_INVALID_ARG, "rho-form needs rho_n and rho_np1");
+      if (!aligned16(s->rho_n) || !aligned16(s->rho_np1))
+        return fail(p, PSATD_ERR_INVALID_ARG, "rho arrays not 16-byte aligned");
+    }
+  }
+  int k = 0;
+  for (int i = 0; i < 3; ++i)
+    if (pe[i]) { in[k] = f->E[i]; out[k] = f->E[i]; ++k; }
+  for (int i = 0; i < 3; ++i)
+    if (pb[i]) { in[k] = f->B[i]; out[k] = f->B[i]; ++k; }
+  if (p->form >= 1)
+    for (int i = 0; i < 3; ++i)
+      if (pj[i]) { in[k] = s->J[i]; out[k] = nullptr; ++k; }
+  if (p->form == 2) {
+    in[k] = s->rho_n; out[k] = nullptr; ++k;
+    in[k] = s->rho_np1; out[k] = nullptr; ++k;
+  }
+  return PSATD_OK;
+}
+
+void release(psatd_plan p) {
+  void* bufs[] = {p->spec1, p->spec2, p->tw[0], p->tw[1], p->tw[2], p->tab};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (auto& v : p->ev) v.clear();
+  for (auto& e : p->pool) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  p->pool.clear();
+}
+
+psatd_status alloc(psatd_plan p, void** ptr, size_t bytes, const char* what) {
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return fail(p, PSATD_ERR_OOM, "cudaMalloc of %zu bytes for %s failed: %s", bytes, what, cudaGetErrorString(e));
+  }
+  p->bytes += bytes;
+  return PSATD_OK;
+}
+
+// lines per CTA for a transposing pass of length L with `nb` lines available
+int pick_log_tb(int L, int64_t nb, bool f32) {
+  const int T = L / 8;
+  const int maxthr = f32 ? 512 : 256;
+  int tb = 1;
+  while (tb * 2 * T <= maxthr && tb * 2 <= 32 && tb * 2 <= nb) tb *= 2;
+  int lg = 0;
+  while ((1 << lg) < tb) ++lg;
+  return lg;
+}
+
+size_t tpass_smem(int L, int log_tb, bool r2c, size_t csz) {
+  const int tb = 1 << log_tb;
+  const int kbuf = ((L + L / 8 + 1) / 2) * 2;
+  const size_t nk = r2c ? (size_t)L + 1 : (size_t)L;
+  const size_t a = (size_t)tb * kbuf, b = nk * (size_t)(tb + 1);
+  return (a > b ? a : b) * csz;
+}
+
+struct TimedLaunch {
+  psatd_plan p;
+  int slot;
+  EventPair ep{};
+  TimedLaunch(psatd_plan pl, int s) : p(pl), slot(s) {
+    if (!p->timing) return;
+    if (!p->pool.empty()) {
+      ep = p->pool.back();
+      p->pool.pop_back();
+    } else {
+      cudaEventCreate(&ep.a);
+      cudaEventCreate(&ep.b);
+    }
+    cudaEventRecord(ep.a, p->st);
+  }
+  ~TimedLaunch() {
+    if (!p->timing) return;
+    cudaEventRecord(ep.b, p->st);
+    p->ev[slot].push_back(ep);
+  }
+};
+
+template <typename R>
+psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp]) {
+  typedef typename Types<R>::C C;
+  const size_t csz = sizeof(C);
+  C* s1 = static_cast<C*>(p->spec1);
+  C* s2 = static_cast<C*>(p->spec2);
+  const int64_t nx = p->nx, ny = p->ny, nz = p->nz, nxh = p->nxh, cs = p->cs;
+  const int Lx = (int)(nx / 2);
+  cudaError_t e;
+  LineIO io;
+  std::memset(&io, 0, sizeof io);
+
+  // pass 1: x rows (R2C), b = y, a0 = z -> spec1 [c][kx][z][y]
+  {
+    PassGeom g;
+    g.log_tb = pick_log_tb(Lx, ny, p->f32);
+    g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)nz, (unsigned)p->n_in);
+    g.smem = tpass_smem(Lx, g.log_tb, true, csz);
+    for (int c = 0; c < p->n_in; ++c) {
+      io.in[c] = in[c];
+      io.out[c] = s1 + c * cs;
+    }
+    TimedLaunch tl(p, K_FWD_X);
+    e = launch_fwd_T<R>(Lx, true, g, p->st, io, p->tw[0], ny * nx, nx, ny, nz * ny);
+    if (e != cudaSuccess) return cuda_fail(p, e, "fwd_x_r2c launch");
+  }
+  C* sp = s1;
+  int Lline = (int)ny;
+  int64_t nlines = nxh;
+  if (p->ndim == 3) {
+    // pass 2: y lines (C2C), b = z, a0 = kx: spec1 [c][kx][z][y] -> spec2 [c][kx][ky][z]
+    PassGeom g;
+    g.log_tb = pick_log_tb((int)ny, nz, p->f32);
+    g.grid = dim3((unsigned)(nz >> g.log_tb), (unsigned)nxh, (unsigned)p->n_in);
+    g.smem = tpass_smem((int)ny, g.log_tb, false, csz);
+    for (int c = 0; c < p->n_in; ++c) {
+      io.in[c] = s1 + c * cs;
+      io.out[c] = s2 + c * cs;
+    }
+    TimedLaunch tl(p, K_FWD_Y);
+    e = launch_fwd_T<R>((int)ny, false, g, p->st, io, p->tw[1], nz * ny, ny, ny * nz, nz);
+    if (e != cudaSuccess) return cuda_fail(p, e, "fwd_y_c2c launch");
+    sp = s2;
+    Lline = (int)nz;
+    nlines = nxh * ny;
+  }
+  // fused last-axis pass
+  {
+    PushArgs<R> a;
+    a.spec = sp;
+    a.cs = cs;
+    a.tab = static_cast<const Coef<R>*>(p->tab);
+    a.nlines = (int)nlines;
+    a.n_in = p->n_in;
+    a.n_out = p->n_out;
+    a.form = p->form;
+    a.ndim = p->ndim;
+    a.nx_half = (int)(nx / 2);
+    a.ny = (int)ny;
+    a.tab_row = Lline / 2 + 1;
+    a.rx = (R)p->r[0];
+    a.ry = (R)p->r[1];
+    a.rz = (R)p->r[2];
+    const double c = p->d.c, ic = 1.0 / c;
+    a.c_h = (R)c;
+    a.c_l = (R)(c - (double)a.c_h);
+    a.ic_h = (R)ic;
+    a.ic_l = (R)(ic - (double)a.ic_h);
+    a.s_src = (R)(1.0 / (p->d.eps0 * c * p->g0));
+    a.s_a6 = (R)(1.0 / (p->d.eps0 * c * c * p->g0));
+    const int T = Lline / 8;
+    const int kbuf = ((Lline + Lline / 8 + 1) / 2) * 2;
+    const size_t per_line = ((size_t)p->n_in * Lline + kbuf) * csz;
+    int tb = 1;
+    while (tb * 2 * T <= 256 && (size_t)(tb * 2) * per_line <= 100 * 1024 && tb * 2 <= nlines) tb *= 2;
+    const dim3 grid((unsigned)((nlines + tb - 1) / tb));
+    TimedLaunch tl(p, K_PUSH);
+    e = launch_line_push<R>(Lline, p->layout, grid, tb, tb * per_line, p->st, a, p->tw[p->ndim == 3 ? 2 : 1]);
+    if (e != cudaSuccess) return cuda_fail(p, e, "line_fft_push launch");
+  }
+  if (p->ndim == 3) {
+    // pass 4: inverse y lines: spec2 [c][kx][ky][z] -> spec1 [c][kx][z][y]
+    PassGeom g;
+    g.log_tb = pick_log_tb((int)ny, nz, p->f32);
+    g.grid = dim3((unsigned)(nz >> g.log_tb), (unsigned)nxh, (unsigned)p->n_out);
+    g.smem = tpass_smem((int)ny, g.log_tb, false, csz);
+    for (int c = 0; c < p->n_out; ++c) {
+      io.in[c] = s2 + c * cs;
+      io.out[c] = s1 + c * cs;
+    }
+    TimedLaunch tl(p, K_INV_Y);
+    e = launch_inv_T<R>((int)ny, false, g, p->st, io, p->tw[1], ny * nz, nz, nz * ny, ny);
+    if (e != cudaSuccess) return cuda_fail(p, e, "inv_y_c2c launch");
+  }
+  // last pass: inverse x rows (C2R): spec1 [c][kx][z][y] -> out [z][y][x]
+  {
+    PassGeom g;
+    g.log_tb = pick_log_tb(Lx, ny, p->f32);
+    g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)nz, (unsigned)p->n_out);
+    g.smem = tpass_smem(Lx, g.log_tb, true, csz);
+    for (int c = 0; c < p->n_out; ++c) {
+      io.in[c] = s1 + c * cs;
+      io.out[c] = out[c];
+    }
+    TimedLaunch tl(p, K_INV_X);
+    e = launch_inv_T<R>(Lx, true, g, p->st, io, p->tw[0], ny, nz * ny, ny * nx, nx);
+    if (e != cudaSuccess) return cuda_fail(p, e, "inv_x_c2r launch");
+  }
+  return PSATD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t psatd_abi_version(void) { return PSATD_ABI_VERSION; }
+
+psatd_status psatd_plan_create(const psatd_desc* desc, void* cuda_stream, psatd_plan* out) {
+  if (!out) return fail(nullptr, PSATD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  psatd_status s = validate_desc(nullptr, desc, true);
+  if (s != PSATD_OK) return s;
+  psatd_plan p = new (std::nothrow) psatd_plan_s();
+  if (!p) return fail(nullptr, PSATD_ERR_OOM, "host allocation failed");
+  p->d = *desc;
+  p->st = static_cast<cudaStream_t>(cuda_stream);
+  p->f32 = desc->prec == PSATD_FP32;
+  p->ndim = desc->ndim;
+  p->layout = desc->layout;
+  p->form = desc->src;
+  counts(p->layout, p->form, &p->n_in, &p->n_out);
+  p->nx = desc->n[0];
+  p->ny = desc->n[1];
+  p->nz = p->ndim == 3 ? desc->n[2] : 1;
+  p->nxh = p->nx / 2 + 1;
+  p->cs = p->nxh * p->ny * p->nz;
+  cudaGetDevice(&p->device);
+  // push pass shared memory (one line per CTA at least)
+  {
+    const int L = (int)(p->ndim == 3 ? p->nz : p->ny);
+    const size_t csz = p->f32 ? 8 : 16;
+    const size_t need = ((size_t)p->n_in * L + (size_t)(((L + L / 8 + 1) / 2) * 2)) * csz;
+    int maxsm = 0;
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    if (maxsm > 0 && need > (size_t)maxsm) {
+      psatd_status r = fail(nullptr, PSATD_ERR_UNSUPPORTED,
+                            "last-axis length %d with %d components needs %zu bytes of shared memory (> %d)", L,
+                            p->n_in, need, maxsm);
+      delete p;
+      return r;
+    }
+  }
+  // wavenumber scale: k_i = g0 r_i m_i; FP32 plans use the float-rounded ratios
+  p->g0 = 2.0 * M_PI / ((double)p->nx * desc->d[0]);
+  const int64_t ns[3] = {p->nx, p->ny, p->nz};
+  for (int i = 0; i < 3; ++i) {
+    if (i >= p->ndim) {
+      p->r[i] = 0.0;
+      continue;
+    }
+    const double gi = 2.0 * M_PI / ((double)ns[i] * desc->d[i]);
+    double ri = gi / p->g0;
+    if (p->f32) ri = (double)(float)ri;
+    p->r[i] = ri;
+  }
+  const size_t csz = p->f32 ? 8 : 16;
+  const size_t spec_bytes = (size_t)p->n_in * (size_t)p->cs * csz;
+  psatd_status a = alloc(p, &p->spec1, spec_bytes, "spectra");
+  if (a == PSATD_OK && p->ndim == 3) a = alloc(p, &p->spec2, spec_bytes, "spectra (2)");
+  const size_t wsz = p->f32 ? 16 : 16;
+  for (int i = 0; i < p->ndim && a == PSATD_OK; ++i) a = alloc(p, &p->tw[i], (size_t)ns[i] * wsz, "twiddles");
+  p->tab_e[0] = p->nx / 2 + 1;
+  p->tab_e[1] = p->ny / 2 + 1;
+  p->tab_e[2] = p->ndim == 3 ? p->nz / 2 + 1 : 1;
+  const size_t ent = (size_t)p->tab_e[0] * p->tab_e[1] * p->tab_e[2];
+  if (a == PSATD_OK) a = alloc(p, &p->tab, ent * (p->f32 ? sizeof(Coef<float>) : sizeof(Coef<double>)), "coefficients");
+  if (a != PSATD_OK) {
+    g_err = p->err;
+    release(p);
+    delete p;
+    return a;
+  }
+  *out = p;
+  return PSATD_OK;
+}
+
+psatd_status psatd_coeffs_init(psatd_plan p) {
+  if (!p) return fail(nullptr, PSATD_ERR_INVALID_ARG, "plan is NULL");
+  cudaError_t e;
+  const int64_t ns[3] = {p->nx, p->ny, p->nz};
+  {
+    TimedLaunch tl(p, K_TABLES);
+    for (int i = 0; i < p->ndim; ++i) {
+      e = launch_twiddles(p->tw[i], (int)ns[i], p->f32, p->st);
+      if (e != cudaSuccess) return cuda_fail(p, e, "twiddle table launch");
+    }
+    const double N = (double)p->nx * (double)p->ny * (double)p->nz;
+    e = launch_coefs(p->tab, p->f32, (int)p->tab_e[0], (int)p->tab_e[1], (int)p->tab_e[2], (int)p->nx, (int)p->ny,
+                     (int)p->nz, p->r[0], p->r[1], p->r[2], p->g0, p->d.c, p->d.dt, p->d.eps0, 1.0 / N, p->st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "coefficient table launch");
+  }
+  p->coeffs_ready = true;
+  return PSATD_OK;
+}
+
+psatd_status psatd_step(psatd_plan p, const psatd_fields* fields, const psatd_sources* sources, int32_t nsteps) {
+  if (!p) return fail(nullptr, PSATD_ERR_INVALID_ARG, "plan is NULL");
+  if (nsteps < 1) return fail(p, PSATD_ERR_INVALID_ARG, "nsteps must be >= 1 (got %d)", nsteps);
+  if (!p->coeffs_ready) return fail(p, PSATD_ERR_INVALID_ARG, "psatd_coeffs_init was not called");
+  const void* in[kMaxComp] = {};
+  void* out[kMaxComp] = {};
+  psatd_status s = gather_slots(p, fields, sources, in, out);
+  if (s != PSATD_OK) return s;
+  for (int i = 0; i < nsteps; ++i) {
+    s = p->f32 ? run_step<float>(p, in, out) : run_step<double>(p, in, out);
+    if (s != PSATD_OK) return s;
+  }
+  return PSATD_OK;
+}
+
+psatd_status psatd_plan_sync(psatd_plan p) {
+  if (!p) return fail(nullptr, PSATD_ERR_INVALID_ARG, "plan is NULL");
+  cudaError_t e = cudaStreamSynchronize(p->st);
+  if (e != cudaSuccess) return cuda_fail(p, e, "stream synchronise");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(p, e, "asynchronous error");
+  return PSATD_OK;
+}
+
+psatd_status psatd_plan_destroy(psatd_plan p) {
+  if (!p) return PSATD_OK;
+  cudaStreamSynchronize(p->st);
+  release(p);
+  delete p;
+  return PSATD_OK;
+}
+
+size_t psatd_plan_workspace_bytes(psatd_plan p) { return p ? p->bytes : 0; }
+
+psatd_status psatd_plan_set_timing(psatd_plan p, int32_t enable) {
+  if (!p) return fail(nullptr, PSATD_ERR_INVALID_ARG, "plan is NULL");
+  cudaStreamSynchronize(p->st);
+  for (auto& v : p->ev) {
+    for (auto& e : v) p->pool.push_back(e);
+    v.clear();
+  }
+  p->timing = enable != 0;
+  return PSATD_OK;
+}
+
+int32_t psatd_kernel_times(psatd_plan p, int32_t n_slots, const char** names, int64_t* launches, double* total_ms) {
+  if (!p) return 0;
+  cudaStreamSynchronize(p->st);
+  int used = 0;
+  for (int s = 0; s < K_NSLOTS && used < n_slots; ++s) {
+    if (p->ev[s].empty()) continue;
+    double ms = 0;
+    for (auto& e : p->ev[s]) {
+      float t = 0;
+      if (cudaEventElapsedTime(&t, e.a, e.b) == cudaSuccess) ms += t;
+    }
+    if (names) names[used] = kSlotNames[s];
+    if (launches) launches[used] = (int64_t)p->ev[s].size();
+    if (total_ms) total_ms[used] = ms;
+    ++used;
+  }
+  return used;
+}
+
+psatd_status fdtd_step(const psatd_desc* desc, int32_t scheme, const psatd_fields* fields,
+                       const psatd_sources* sources, int32_t nsteps, void* cuda_stream) {
+  psatd_status s = validate_desc(nullptr, desc, false);
+  if (s != PSATD_OK) return s;
+  if (scheme != PSATD_FDTD_YEE && scheme != PSATD_FDTD_CKC)
+    return fail(nullptr, PSATD_ERR_INVALID_ARG, "unknown FDTD scheme %d", scheme);
+  if (scheme == PSATD_FDTD_CKC && desc->ndim != 2)
+    return fail(nullptr, PSATD_ERR_UNSUPPORTED, "the CKC scheme is provided in 2D only");
+  if (desc->src == PSATD_SRC_J_RHO)
+    return fail(nullptr, PSATD_ERR_INVALID_ARG, "FDTD takes J only (src must be NONE or J)");
+  if (nsteps < 1) return fail(nullptr, PSATD_ERR_INVALID_ARG, "nsteps must be >= 1 (got %d)", nsteps);
+  if (!fields) return fail(nullptr, PSATD_ERR_INVALID_ARG, "fields is NULL");
+  bool pe[3], pb[3], pj[3];
+  present(desc->layout, pe, pb, pj);
+  const void* J[3] = {nullptr, nullptr, nullptr};
+  for (int i = 0; i < 3; ++i) {
+    if (pe[i] != (fields->E[i] != nullptr) || pb[i] != (fields->B[i] != nullptr))
+      return fail(nullptr, PSATD_ERR_INVALID_ARG, "field component %d presence does not match the layout", i);
+    if ((fields->E[i] && !aligned16(fields->E[i])) || (fields->B[i] && !aligned16(fields->B[i])))
+      return fail(nullptr, PSATD_ERR_INVALID_ARG, "field arrays must be 16-byte aligned");
+  }
+  if (desc->src == PSATD_SRC_J) {
+    if (!sources) return fail(nullptr, PSATD_ERR_INVALID_ARG, "sources is NULL");
+    for (int i = 0; i < 3; ++i) {
+      if (pj[i] != (sources->J[i] != nullptr))
+        return fail(nullptr, PSATD_ERR_INVALID_ARG, "J component %d presence does not match the layout", i);
+      if (sources->J[i] && !aligned16(sources->J[i]))
+        return fail(nullptr, PSATD_ERR_INVALID_ARG, "J arrays must be 16-byte aligned");
+      J[i] = sources->J[i];
+    }
+  }
+  const int64_t nz = desc->ndim == 3 ? desc->n[2] : 1;
+  if (desc->n[1] > 65535 || nz > 65535) return fail(nullptr, PSATD_ERR_UNSUPPORTED, "ny, nz must be <= 65535");
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = desc->prec == PSATD_FP32
+                      ? launch_fdtd<float>(desc->ndim, scheme, desc->n[0], desc->n[1], nz, desc->d, desc->dt, desc->c,
+                                           desc->eps0, fields->E, fields->B, J, nsteps, st)
+                      : launch_fdtd<double>(desc->ndim, scheme, desc->n[0], desc->n[1], nz, desc->d, desc->dt, desc->c,
+                                            desc->eps0, fields->E, fields->B, J, nsteps, st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "fdtd launch");
+  return PSATD_OK;
+}
+
+const char* psatd_last_error(psatd_plan p) { return p ? p->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,260 @@
+// fft_core.cuh -- register/shared-memory Stockham FFT building blocks for sm_103a.
+//
+// A length-L transform (L a power of two, 8 <= L <= 4096) is computed by T = L/8
+// threads; thread t holds the eight elements x[t + T*m], m = 0..7, in registers
+// before and after the transform (natural order in both domains).  Stages:
+// one radix-2 or radix-4 stage first (when log2 L is not a multiple of 3),
+// then radix-8 stages.  Between stages the data go through shared memory with
+// a padded layout (one pad slot every eight elements).
+//
+// Forward = Stockham decimation in time: stage (radix R, span Ns) multiplies
+// input r of butterfly j by w^(r*k), w = exp(-2 pi i/(Ns R)), k = j mod Ns,
+// applies the radix-R DFT and writes output r to (j - k) R + k + r Ns.
+// Inverse = the exact adjoint of the forward (stages in reverse order, adjoint
+// butterflies, conjugated twiddles), i.e. the unnormalised inverse DFT.  With
+// the adjoint, a forward/inverse round trip deviates from N*I only through
+// |w| != 1; in FP32 the twiddles and the sqrt(1/2) constant are therefore
+// applied in compensated form (hi + lo parts, FMA), which keeps the round
+// trip free of systematic gain over thousands of steps.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <utility>
+
+namespace psatd {
+
+template <typename R> struct Types;
+template <> struct Types<float> {
+  typedef float2 C;   // complex value
+  typedef float4 W;   // twiddle: (re_hi, im_hi, re_lo, im_lo)
+  static constexpr bool kComp = true;
+};
+template <> struct Types<double> {
+  typedef double2 C;
+  typedef double2 W;  // twiddle: (re, im)
+  static constexpr bool kComp = false;
+};
+
+__device__ __forceinline__ float2 mkc(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mkc(double a, double b) { return make_double2(a, b); }
+
+template <class C> __device__ __forceinline__ C cadd(C a, C b) { return mkc(a.x + b.x, a.y + b.y); }
+template <class C> __device__ __forceinline__ C csub(C a, C b) { return mkc(a.x - b.x, a.y - b.y); }
+template <class C> __device__ __forceinline__ C cmul_mi(C a) { return mkc(a.y, -a.x); }  // * (-i)
+template <class C> __device__ __forceinline__ C cmul_pi(C a) { return mkc(-a.y, a.x); }  // * (+i)
+template <class C> __device__ __forceinline__ C cconj(C a) { return mkc(a.x, -a.y); }
+
+// x * w, compensated: the low parts enter first, the leading product last.
+__device__ __forceinline__ float2 twmul(float2 x, float4 w) {
+  float re = fmaf(x.x, w.z, -x.y * w.w);
+  float im = fmaf(x.x, w.w, x.y * w.z);
+  re = fmaf(-x.y, w.y, re);
+  im = fmaf(x.y, w.x, im);
+  re = fmaf(x.x, w.x, re);
+  im = fmaf(x.x, w.y, im);
+  return make_float2(re, im);
+}
+// x * conj(w), compensated.
+__device__ __forceinline__ float2 twmul_conj(float2 x, float4 w) {
+  float re = fmaf(x.x, w.z, x.y * w.w);
+  float im = fmaf(x.y, w.z, -x.x * w.w);
+  re = fmaf(x.y, w.y, re);
+  im = fmaf(-x.x, w.y, im);
+  re = fmaf(x.x, w.x, re);
+  im = fmaf(x.y, w.x, im);
+  return make_float2(re, im);
+}
+__device__ __forceinline__ double2 twmul(double2 x, double2 w) {
+  return make_double2(fma(x.x, w.x, -x.y * w.y), fma(x.x, w.y, x.y * w.x));
+}
+__device__ __forceinline__ double2 twmul_conj(double2 x, double2 w) {
+  return make_double2(fma(x.x, w.x, x.y * w.y), fma(x.y, w.x, -x.x * w.y));
+}
+
+// v * sqrt(1/2); in float as hi + lo (0.70710677f + 1.2101617e-8f).
+__device__ __forceinline__ float rsqrt2_mul(float v) { return fmaf(v, 0.70710677f, v * 1.2101617e-08f); }
+__device__ __forceinline__ double rsqrt2_mul(double v) { return v * 0.70710678118654752440; }
+
+// ---------------------------------------------------------------- butterflies
+// Radix-4 DFT in place (forward: exp(-2 pi i/4) = -i; adjoint: +i).  Exact
+// operations apart from the additions, so the adjoint is exact.
+template <bool ADJ, class C>
+__device__ __forceinline__ void dft4(C& x0, C& x1, C& x2, C& x3) {
+  C s0 = cadd(x0, x2), d0 = csub(x0, x2), s1 = cadd(x1, x3), t = csub(x1, x3);
+  C d1 = ADJ ? cmul_pi(t) : cmul_mi(t);
+  x0 = cadd(s0, s1);
+  x1 = cadd(d0, d1);
+  x2 = csub(s0, s1);
+  x3 = csub(d0, d1);
+}
+
+// Radix-8 forward DFT, natural order in and out: split a_r +- a_(r+4), rotate
+// the difference half by w8^r, two radix-4 DFTs interleaved.
+template <class C>
+__device__ __forceinline__ void dft8_fwd(C* a) {
+  C b0 = cadd(a[0], a[4]), b1 = cadd(a[1], a[5]), b2 = cadd(a[2], a[6]), b3 = cadd(a[3], a[7]);
+  C c0 = csub(a[0], a[4]), c1 = csub(a[1], a[5]), c2 = csub(a[2], a[6]), c3 = csub(a[3], a[7]);
+  // c1 *= s(1 - i); c2 *= -i; c3 *= s(-1 - i)
+  c1 = mkc(rsqrt2_mul(c1.x + c1.y), rsqrt2_mul(c1.y - c1.x));
+  c2 = cmul_mi(c2);
+  c3 = mkc(rsqrt2_mul(c3.y - c3.x), rsqrt2_mul(-(c3.x + c3.y)));
+  dft4<false>(b0, b1, b2, b3);
+  dft4<false>(c0, c1, c2, c3);
+  a[0] = b0; a[1] = c0; a[2] = b1; a[3] = c1;
+  a[4] = b2; a[5] = c2; a[6] = b3; a[7] = c3;
+}
+
+// Exact adjoint of dft8_fwd (reverse order of its steps, conjugate constants).
+template <class C>
+__device__ __forceinline__ void dft8_adj(C* a) {
+  C b0 = a[0], b1 = a[2], b2 = a[4], b3 = a[6];
+  C c0 = a[1], c1 = a[3], c2 = a[5], c3 = a[7];
+  dft4<true>(b0, b1, b2, b3);
+  dft4<true>(c0, c1, c2, c3);
+  // c1 *= s(1 + i); c2 *= +i; c3 *= s(-1 + i)
+  c1 = mkc(rsqrt2_mul(c1.x - c1.y), rsqrt2_mul(c1.x + c1.y));
+  c2 = cmul_pi(c2);
+  c3 = mkc(rsqrt2_mul(-(c3.x + c3.y)), rsqrt2_mul(c3.x - c3.y));
+  a[0] = cadd(b0, c0); a[1] = cadd(b1, c1); a[2] = cadd(b2, c2); a[3] = cadd(b3, c3);
+  a[4] = csub(b0, c0); a[5] = csub(b1, c1); a[6] = csub(b2, c2); a[7] = csub(b3, c3);
+}
+
+template <int RS, bool ADJ, class C>
+__device__ __forceinline__ void butterfly(C* a) {
+  if constexpr (RS == 2) {
+    C s = cadd(a[0], a[1]), d = csub(a[0], a[1]);
+    a[0] = s;
+    a[1] = d;
+  } else if constexpr (RS == 4) {
+    dft4<ADJ>(a[0], a[1], a[2], a[3]);
+  } else {
+    if constexpr (ADJ) dft8_adj(a); else dft8_fwd(a);
+  }
+}
+
+// ---------------------------------------------------------------- stage plan
+__host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
+
+template <int L>
+struct FFTPlan {
+  static constexpr int kLog = ilog2(L);
+  static constexpr int kR0 = (kLog % 3 == 1) ? 2 : (kLog % 3 == 2) ? 4 : 8;
+  static constexpr int kStages = (kR0 == 8) ? kLog / 3 : kLog / 3 + 1;
+  static constexpr int kT = L / 8;
+  // padded exchange-buffer length (one pad slot per 8 elements), kept even
+  static constexpr int kBuf = ((L + L / 8 + 1) / 2) * 2;
+  __host__ __device__ static constexpr int radix(int s) { return s == 0 ? kR0 : 8; }
+  __host__ __device__ static constexpr int span(int s) {  // Ns of stage s
+    int ns = 1;
+    for (int i = 0; i < s; ++i) ns *= radix(i);
+    return ns;
+  }
+  static_assert(L >= 8 && (L & (L - 1)) == 0, "L must be a power of two >= 8");
+};
+
+__device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
+
+// One forward stage.  tw: twiddle table of an axis of length L*TWS.
+template <typename R, int L, int S, int TWS>
+__device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[8], typename Types<R>::C* buf,
+                                          const typename Types<R>::W* __restrict__ tw, int t) {
+  typedef typename Types<R>::C C;
+  typedef FFTPlan<L> P;
+  constexpr int RS = P::radix(S), NS = P::span(S), Q = 8 / RS, T = P::kT;
+  constexpr bool LAST = (S == P::kStages - 1);
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int j = t + q * T;
+    const int k = j & (NS - 1);
+    C a[RS];
+#pragma unroll
+    for (int r = 0; r < RS; ++r) a[r] = v[q + r * Q];
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < RS; ++r) a[r] = twmul(a[r], __ldg(&tw[(r * k * (L / (NS * RS))) * TWS]));
+    }
+    butterfly<RS, false>(a);
+    if constexpr (LAST) {
+#pragma unroll
+      for (int r = 0; r < RS; ++r) v[q + r * Q] = a[r];
+    } else {
+      const int base = (j - k) * RS + k;
+#pragma unroll
+      for (int r = 0; r < RS; ++r) buf[pad8(base + r * NS)] = a[r];
+    }
+  }
+  if constexpr (!LAST) {
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = buf[pad8(t + T * m)];
+    __syncthreads();
+  }
+}
+
+// Adjoint of fwd_stage<S>.
+template <typename R, int L, int S, int TWS>
+__device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[8], typename Types<R>::C* buf,
+                                          const typename Types<R>::W* __restrict__ tw, int t) {
+  typedef typename Types<R>::C C;
+  typedef FFTPlan<L> P;
+  constexpr int RS = P::radix(S), NS = P::span(S), Q = 8 / RS, T = P::kT;
+  constexpr bool FIRST = (S == P::kStages - 1);
+  if constexpr (!FIRST) {
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 8; ++m) buf[pad8(t + T * m)] = v[m];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int j = t + q * T;
+    const int k = j & (NS - 1);
+    C a[RS];
+    if constexpr (FIRST) {
+#pragma unroll
+      for (int r = 0; r < RS; ++r) a[r] = v[q + r * Q];
+    } else {
+      const int base = (j - k) * RS + k;
+#pragma unroll
+      for (int r = 0; r < RS; ++r) a[r] = buf[pad8(base + r * NS)];
+    }
+    butterfly<RS, true>(a);
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < RS; ++r) a[r] = twmul_conj(a[r], __ldg(&tw[(r * k * (L / (NS * RS))) * TWS]));
+    }
+#pragma unroll
+    for (int r = 0; r < RS; ++r) v[q + r * Q] = a[r];
+  }
+}
+
+template <typename R, int L, int TWS, int... S>
+__device__ __forceinline__ void fft_fwd_seq(typename Types<R>::C (&v)[8], typename Types<R>::C* buf,
+                                            const typename Types<R>::W* tw, int t,
+                                            std::integer_sequence<int, S...>) {
+  (fwd_stage<R, L, S, TWS>(v, buf, tw, t), ...);
+}
+template <typename R, int L, int TWS, int... S>
+__device__ __forceinline__ void fft_inv_seq(typename Types<R>::C (&v)[8], typename Types<R>::C* buf,
+                                            const typename Types<R>::W* tw, int t,
+                                            std::integer_sequence<int, S...>) {
+  (inv_stage<R, L, FFTPlan<L>::kStages - 1 - S, TWS>(v, buf, tw, t), ...);
+}
+
+// Forward DFT of length L: v holds x[t + T m] on entry, X[t + T m] on exit.
+// Every thread of the block must call it (block-wide barriers inside).
+template <typename R, int L, int TWS>
+__device__ __forceinline__ void block_fft_fwd(typename Types<R>::C (&v)[8], typename Types<R>::C* buf,
+                                              const typename Types<R>::W* tw, int t) {
+  fft_fwd_seq<R, L, TWS>(v, buf, tw, t, std::make_integer_sequence<int, FFTPlan<L>::kStages>{});
+}
+// Unnormalised inverse DFT (adjoint of block_fft_fwd).
+template <typename R, int L, int TWS>
+__device__ __forceinline__ void block_fft_inv(typename Types<R>::C (&v)[8], typename Types<R>::C* buf,
+                                              const typename Types<R>::W* tw, int t) {
+  fft_inv_seq<R, L, TWS>(v, buf, tw, t, std::make_integer_sequence<int, FFTPlan<L>::kStages>{});
+}
+
+}  // namespace psatd

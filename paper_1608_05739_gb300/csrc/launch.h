@@ -1,0 +1,36 @@
+// launch.h -- host-side launchers of the PSATD pass kernels, one set per
+// precision (kernels_f32.cu, kernels_f64.cu).  L is the transform length along
+// the pass axis (power of two, 8..4096); every launcher returns the launch's
+// cudaError_t.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "psatd_kernels.cuh"
+
+namespace psatd {
+
+struct PassGeom {
+  dim3 grid;
+  int log_tb;      // lines per CTA = 1 << log_tb
+  size_t smem;     // dynamic shared memory bytes
+};
+
+template <typename R>
+cudaError_t launch_fwd_T(int L, bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io,
+                         const void* tw, int64_t in_sa0, int64_t in_sb, int64_t out_sa0,
+                         int64_t out_sk);
+template <typename R>
+cudaError_t launch_inv_T(int L, bool c2r, const PassGeom& g, cudaStream_t st, const LineIO& io,
+                         const void* tw, int64_t in_sa0, int64_t in_sk, int64_t out_sa0,
+                         int64_t out_sb);
+template <typename R>
+cudaError_t launch_line_push(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
+                             const PushArgs<R>& a, const void* tw);
+
+template <typename R>
+cudaError_t launch_fdtd(int ndim, int scheme, int64_t nx, int64_t ny, int64_t nz, const double* d,
+                        double dt, double c, double eps0, void* const E[3], void* const B[3],
+                        const void* const J[3], int nsteps, cudaStream_t st);
+
+}  // namespace psatd

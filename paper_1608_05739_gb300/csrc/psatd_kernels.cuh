@@ -1,0 +1,461 @@
+// psatd_kernels.cuh -- the PSATD step's pass kernels (templates; instantiated
+// per precision in kernels_f32.cu / kernels_f64.cu).
+//
+// Data flow of one step (2D: passes 1, 3, 5; 3D: passes 1-5):
+//   1  k_fwd_T<R2C>  x-rows of every input array -> R2C -> half spectrum,
+//                    written with the row index b contiguous (tile transpose)
+//   2  k_fwd_T<C2C>  (3D) y-lines -> C2C, written z-contiguous
+//   3  k_line_push   the last axis: forward FFT of every input component,
+//                    the analytic PSATD push per mode (Sec. III.B), inverse FFT
+//                    of the E and B components, in place
+//   4  k_inv_T<C2C>  (3D) inverse y-lines, read z-contiguous
+//   5  k_inv_T<C2R>  inverse x-rows (C2R) into the caller's E and B arrays
+// A CTA handles TB lines (blockDim.y) of T = L/8 threads each (blockDim.x).
+#pragma once
+
+#include "fft_core.cuh"
+
+namespace psatd {
+
+constexpr int kMaxComp = 11;
+
+// Per-component base pointers of a pass (index = grid z = component slot).
+struct LineIO {
+  const void* in[kMaxComp];
+  void* out[kMaxComp];
+};
+
+// k-space coefficient table entry (one per |m|-octant point), see tables.cu.
+template <typename R>
+struct alignas(8 * sizeof(R)) Coef {
+  R C_h, C_l;  // cos(x) / N              (hi, lo)
+  R S_h, S_l;  // sin(x) / |m| / N        (hi, lo)
+  R A1;        // (1 - C) / |m|^2 / N
+  R A4;        // (S/(c k) - dt) / (eps0 |m|^2) / N
+  R B1;        // (S/x - 1) / (eps0 g0 |m|^2) / N
+  R B2;        // (S/x - C) / (eps0 g0 |m|^2) / N
+};
+
+template <typename R>
+struct PushArgs {
+  void* spec;        // spectral scratch, component slot c at spec + c * cs
+  int64_t cs;        // component stride (complex elements)
+  const Coef<R>* tab;
+  int nlines;        // lines along the last axis
+  int n_in, n_out;   // component slots read / written
+  int form;          // 0 vacuum, 1 J, 2 rho
+  int ndim;
+  int nx_half;       // nx/2 (Nyquist index along x)
+  int ny;            // 3D: lines are (kx, ky), ky fastest
+  int tab_row;       // L/2 + 1 entries per table row
+  R rx, ry, rz;      // k_i = g0 * r_i * m_i
+  R c_h, c_l;        // c (hi, lo)
+  R ic_h, ic_l;      // 1/c (hi, lo)
+  R s_src;           // 1 / (eps0 c g0)
+  R s_a6;            // 1 / (eps0 c^2 g0)
+};
+
+// ---------------------------------------------------------------- pass 1 / 2
+// Forward FFT along the contiguous axis of TB consecutive lines b, written out
+// with b contiguous: out[a1] + a0*out_sa0 + k*out_sk + b.  R2C: the input rows
+// are real (length 2L), the output has L+1 bins (half spectrum).
+template <typename R, int L, bool R2C>
+__global__ void __launch_bounds__(512) k_fwd_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
+                                               int64_t in_sa0, int64_t in_sb, int64_t out_sa0,
+                                               int64_t out_sk, int log_tb) {
+  typedef typename Types<R>::C C;
+  typedef FFTPlan<L> P;
+  constexpr int T = P::kT;
+  constexpr int NK = R2C ? L + 1 : L;
+  constexpr int TWS = R2C ? 2 : 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* smem = reinterpret_cast<C*>(smem_raw);
+  const int TB = 1 << log_tb;
+  const int t = threadIdx.x, g = threadIdx.y;
+  const int64_t b = (int64_t)blockIdx.x * TB + g;
+  const int a0 = blockIdx.y, a1 = blockIdx.z;
+  C* buf = smem + g * P::kBuf;
+
+  C v[8];
+  {
+    const C* row;
+    if constexpr (R2C)
+      row = reinterpret_cast<const C*>(static_cast<const R*>(io.in[a1]) + a0 * in_sa0 + b * in_sb);
+    else
+      row = static_cast<const C*>(io.in[a1]) + a0 * in_sa0 + b * in_sb;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = row[t + T * m];
+  }
+  block_fft_fwd<R, L, TWS>(v, buf, tw, t);
+
+  C* tile = smem;  // [NK][TB + 1], aliases the exchange buffers
+  const int tp = TB + 1;
+  if constexpr (R2C) {
+    // X[k] = Fe[k] + W_N^k Fo[k] with Fe = (Z[k] + Z*[L-k])/2, Fo = (Z[k] - Z*[L-k])/(2i)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) buf[pad8(t + T * m)] = v[m];
+    __syncthreads();
+    C X[8];
+    C XL = mkc(R(0), R(0));
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k = t + T * m;
+      const C zk = buf[pad8(k)];
+      const C zm = cconj(buf[pad8((L - k) & (L - 1))]);
+      const C fe = mkc(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y + zm.y));
+      const C fo = mkc(R(0.5) * (zk.y - zm.y), R(-0.5) * (zk.x - zm.x));
+      X[m] = cadd(fe, twmul(fo, __ldg(&tw[k])));
+      if (k == 0) XL = csub(fe, fo);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 8; ++m) tile[(t + T * m) * tp + g] = X[m];
+    if (t == 0) tile[L * tp + g] = XL;
+  } else {
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < 8; ++m) tile[(t + T * m) * tp + g] = v[m];
+  }
+  __syncthreads();
+  C* ob = static_cast<C*>(io.out[a1]) + a0 * out_sa0 + (int64_t)blockIdx.x * TB;
+  const int nthr = T * TB;
+  for (int idx = g * T + t; idx < NK * TB; idx += nthr) {
+    const int k = idx >> log_tb, gg = idx & (TB - 1);
+    ob[(int64_t)k * out_sk + gg] = tile[k * tp + gg];
+  }
+}
+
+// ---------------------------------------------------------------- pass 4 / 5
+// Adjoint data movement of k_fwd_T: read TB consecutive b of every bin k from
+// in[a1] + a0*in_sa0 + k*in_sk + b, inverse FFT along k, write the lines
+// contiguously to out[a1] + a0*out_sa0 + b*out_sb.  C2R: L+1 Hermitian bins
+// in, real rows of length 2L out (unnormalised).
+template <typename R, int L, bool C2R>
+__global__ void __launch_bounds__(512) k_inv_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
+                                               int64_t in_sa0, int64_t in_sk, int64_t out_sa0,
+                                               int64_t out_sb, int log_tb) {
+  typedef typename Types<R>::C C;
+  typedef FFTPlan<L> P;
+  constexpr int T = P::kT;
+  constexpr int NK = C2R ? L + 1 : L;
+  constexpr int TWS = C2R ? 2 : 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* smem = reinterpret_cast<C*>(smem_raw);
+  const int TB = 1 << log_tb;
+  const int t = threadIdx.x, g = threadIdx.y;
+  const int64_t b = (int64_t)blockIdx.x * TB + g;
+  const int a0 = blockIdx.y, a1 = blockIdx.z;
+  C* tile = smem;
+  const int tp = TB + 1;
+  {
+    const C* ib = static_cast<const C*>(io.in[a1]) + a0 * in_sa0 + (int64_t)blockIdx.x * TB;
+    const int nthr = T * TB;
+    for (int idx = g * T + t; idx < NK * TB; idx += nthr) {
+      const int k = idx >> log_tb, gg = idx & (TB - 1);
+      tile[k * tp + gg] = ib[(int64_t)k * in_sk + gg];
+    }
+  }
+  __syncthreads();
+  C v[8];
+  if constexpr (C2R) {
+    // Z[k] = Fe + i Fo, Fe = X[k] + X*[L-k], Fo = (X[k] - X*[L-k]) conj(W_N^k)
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int k = t + T * m;
+      const C xk = tile[k * tp + g];
+      const C xm = cconj(tile[(L - k) * tp + g]);
+      const C fe = cadd(xk, xm);
+      const C fo = twmul_conj(csub(xk, xm), __ldg(&tw[k]));
+      v[m] = cadd(fe, cmul_pi(fo));
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = tile[(t + T * m) * tp + g];
+  }
+  __syncthreads();
+  C* buf = smem + g * P::kBuf;
+  block_fft_inv<R, L, TWS>(v, buf, tw, t);
+  C* row;
+  if constexpr (C2R)
+    row = reinterpret_cast<C*>(static_cast<R*>(io.out[a1]) + a0 * out_sa0 + b * out_sb);
+  else
+    row = static_cast<C*>(io.out[a1]) + a0 * out_sa0 + b * out_sb;
+#pragma unroll
+  for (int m = 0; m < 8; ++m) row[t + T * m] = v[m];
+}
+
+// ---------------------------------------------------------------- the push
+template <typename R>
+struct CoefReg {
+  R C_h, C_l, S_h, S_l, A1, A4, B1, B2;
+};
+
+template <class C, typename R>
+__device__ __forceinline__ C rmul(R a, C z) { return mkc(a * z.x, a * z.y); }
+// z * (h + l), compensated in float
+template <class C, typename R>
+__device__ __forceinline__ C rmul2(R h, R l, C z) {
+  if constexpr (Types<R>::kComp) return mkc(fmaf(z.x, h, z.x * l), fmaf(z.y, h, z.y * l));
+  else return mkc(z.x * h, z.y * h);
+}
+template <class C> __device__ __forceinline__ C iz(C z) { return cmul_pi(z); }
+
+// (h, l) of a*b for hi/lo pairs a = (ah, al), b = (bh, bl)
+template <typename R>
+__device__ __forceinline__ void prod2(R ah, R al, R bh, R bl, R& h, R& l) {
+  h = ah * bh;
+  if constexpr (Types<R>::kComp) l = fmaf(ah, bh, -h) + (ah * bl + al * bh);
+  else l = R(0);
+}
+
+// TE part (Ex, Ey, Bz; Jx, Jy; rho) of a mode with m = (mx, my, 0).
+template <typename R, class C>
+__device__ __forceinline__ void push_te(C& E0, C& E1, C& B2, C J0, C J1, C r0, C r1, R mx, R my,
+                                        const CoefReg<R>& f, R cS_h, R cS_l, R Sc_h, R Sc_l,
+                                        const PushArgs<R>& a, int form) {
+  const C mE = cadd(rmul(mx, E0), rmul(my, E1));
+  const C mxEz = csub(rmul(mx, E1), rmul(my, E0));
+  C e0 = cadd(rmul2(f.C_h, f.C_l, E0), iz(rmul2(cS_h, cS_l, rmul(my, B2))));
+  C e1 = csub(rmul2(f.C_h, f.C_l, E1), iz(rmul2(cS_h, cS_l, rmul(mx, B2))));
+  C b2 = csub(rmul2(f.C_h, f.C_l, B2), iz(rmul2(Sc_h, Sc_l, mxEz)));
+  if (form == 0) {
+    const C l = rmul(f.A1, mE);
+    e0 = cadd(e0, rmul(mx, l));
+    e1 = cadd(e1, rmul(my, l));
+  } else {
+    const R ss = a.s_src * f.S_h;
+    e0 = csub(e0, rmul(ss, J0));
+    e1 = csub(e1, rmul(ss, J1));
+    const C mxJz = csub(rmul(mx, J1), rmul(my, J0));
+    b2 = cadd(b2, iz(rmul(a.s_a6 * f.A1, mxJz)));
+    if (form == 1) {
+      const C mJ = cadd(rmul(mx, J0), rmul(my, J1));
+      const C l = cadd(rmul(f.A1, mE), rmul(f.A4, mJ));
+      e0 = cadd(e0, rmul(mx, l));
+      e1 = cadd(e1, rmul(my, l));
+    } else {
+      const C q = iz(csub(rmul(f.B1, r1), rmul(f.B2, r0)));
+      e0 = cadd(e0, rmul(mx, q));
+      e1 = cadd(e1, rmul(my, q));
+    }
+  }
+  E0 = e0;
+  E1 = e1;
+  B2 = b2;
+}
+
+// TM part (Ez, Bx, By; Jz) of a mode with m = (mx, my, 0); k.E = 0 here.
+template <typename R, class C>
+__device__ __forceinline__ void push_tm(C& E2, C& B0, C& B1, C J2, R mx, R my, const CoefReg<R>& f,
+                                        R cS_h, R cS_l, R Sc_h, R Sc_l, const PushArgs<R>& a,
+                                        int form) {
+  const C mB = cadd(rmul(mx, B0), rmul(my, B1));
+  const C mxBz = csub(rmul(mx, B1), rmul(my, B0));
+  C e2 = cadd(rmul2(f.C_h, f.C_l, E2), iz(rmul2(cS_h, cS_l, mxBz)));
+  const C lb = rmul(f.A1, mB);
+  C b0 = csub(cadd(rmul2(f.C_h, f.C_l, B0), rmul(mx, lb)), iz(rmul2(Sc_h, Sc_l, rmul(my, E2))));
+  C b1 = cadd(cadd(rmul2(f.C_h, f.C_l, B1), rmul(my, lb)), iz(rmul2(Sc_h, Sc_l, rmul(mx, E2))));
+  if (form != 0) {
+    e2 = csub(e2, rmul(a.s_src * f.S_h, J2));
+    const R a6 = a.s_a6 * f.A1;
+    b0 = cadd(b0, iz(rmul(a6, rmul(my, J2))));
+    b1 = csub(b1, iz(rmul(a6, rmul(mx, J2))));
+  }
+  E2 = e2;
+  B0 = b0;
+  B1 = b1;
+}
+
+// Full 3D mode.
+template <typename R, class C>
+__device__ __forceinline__ void push_3d(C (&E)[3], C (&B)[3], const C (&J)[3], C r0, C r1, R mx,
+                                        R my, R mz, const CoefReg<R>& f, R cS_h, R cS_l, R Sc_h,
+                                        R Sc_l, const PushArgs<R>& a, int form) {
+  const R m[3] = {mx, my, mz};
+  const C mE = cadd(cadd(rmul(mx, E[0]), rmul(my, E[1])), rmul(mz, E[2]));
+  const C mB = cadd(cadd(rmul(mx, B[0]), rmul(my, B[1])), rmul(mz, B[2]));
+  C mxB[3], mxE[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+    mxB[i] = csub(rmul(m[i1], B[i2]), rmul(m[i2], B[i1]));
+    mxE[i] = csub(rmul(m[i1], E[i2]), rmul(m[i2], E[i1]));
+  }
+  C e[3], bb[3];
+  const C lb = rmul(f.A1, mB);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    e[i] = cadd(rmul2(f.C_h, f.C_l, E[i]), iz(rmul2(cS_h, cS_l, mxB[i])));
+    bb[i] = csub(cadd(rmul2(f.C_h, f.C_l, B[i]), rmul(m[i], lb)), iz(rmul2(Sc_h, Sc_l, mxE[i])));
+  }
+  if (form == 0) {
+    const C l = rmul(f.A1, mE);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) e[i] = cadd(e[i], rmul(m[i], l));
+  } else {
+    const R ss = a.s_src * f.S_h;
+    const R a6 = a.s_a6 * f.A1;
+    C l;
+    if (form == 1) {
+      const C mJ = cadd(cadd(rmul(mx, J[0]), rmul(my, J[1])), rmul(mz, J[2]));
+      l = cadd(rmul(f.A1, mE), rmul(f.A4, mJ));
+    } else {
+      l = iz(csub(rmul(f.B1, r1), rmul(f.B2, r0)));
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+      const C mxJ = csub(rmul(m[i1], J[i2]), rmul(m[i2], J[i1]));
+      e[i] = cadd(csub(e[i], rmul(ss, J[i])), rmul(m[i], l));
+      bb[i] = cadd(bb[i], iz(rmul(a6, mxJ)));
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    E[i] = e[i];
+    B[i] = bb[i];
+  }
+}
+
+// Layout codes (psatd_layout): 0 3D6, 1 2D6, 2 TE, 3 TM.
+// Slot order: 3D6/2D6: E0 E1 E2 B0 B1 B2 [J0 J1 J2] [rho_n rho_np1]
+//             TE: E0 E1 B2 [J0 J1] [rho_n rho_np1];  TM: E2 B0 B1 [J2]
+template <typename R, int LAYOUT>
+__device__ __forceinline__ void push_slots(typename Types<R>::C* st, int L, int l, const CoefReg<R>& f,
+                                           R mx, R my, R mz, const PushArgs<R>& a) {
+  typedef typename Types<R>::C C;
+  const C Z = mkc(R(0), R(0));
+  const int form = a.form;
+  R cS_h, cS_l, Sc_h, Sc_l;
+  prod2(a.c_h, a.c_l, f.S_h, f.S_l, cS_h, cS_l);
+  prod2(a.ic_h, a.ic_l, f.S_h, f.S_l, Sc_h, Sc_l);
+  auto S = [&](int c) -> C& { return st[c * L + l]; };
+  if constexpr (LAYOUT == 2) {
+    C E0 = S(0), E1 = S(1), B2 = S(2);
+    const C J0 = form ? S(3) : Z, J1 = form ? S(4) : Z;
+    const C r0 = form == 2 ? S(5) : Z, r1 = form == 2 ? S(6) : Z;
+    push_te<R>(E0, E1, B2, J0, J1, r0, r1, mx, my, f, cS_h, cS_l, Sc_h, Sc_l, a, form);
+    S(0) = E0; S(1) = E1; S(2) = B2;
+  } else if constexpr (LAYOUT == 3) {
+    C E2 = S(0), B0 = S(1), B1 = S(2);
+    const C J2 = form ? S(3) : Z;
+    push_tm<R>(E2, B0, B1, J2, mx, my, f, cS_h, cS_l, Sc_h, Sc_l, a, form);
+    S(0) = E2; S(1) = B0; S(2) = B1;
+  } else if constexpr (LAYOUT == 1) {
+    C E0 = S(0), E1 = S(1), E2 = S(2), B0 = S(3), B1 = S(4), B2 = S(5);
+    const C J0 = form ? S(6) : Z, J1 = form ? S(7) : Z, J2 = form ? S(8) : Z;
+    const C r0 = form == 2 ? S(9) : Z, r1 = form == 2 ? S(10) : Z;
+    push_te<R>(E0, E1, B2, J0, J1, r0, r1, mx, my, f, cS_h, cS_l, Sc_h, Sc_l, a, form);
+    push_tm<R>(E2, B0, B1, J2, mx, my, f, cS_h, cS_l, Sc_h, Sc_l, a, form);
+    S(0) = E0; S(1) = E1; S(2) = E2; S(3) = B0; S(4) = B1; S(5) = B2;
+  } else {
+    C E[3] = {S(0), S(1), S(2)}, B[3] = {S(3), S(4), S(5)};
+    const C J[3] = {form ? S(6) : Z, form ? S(7) : Z, form ? S(8) : Z};
+    const C r0 = form == 2 ? S(9) : Z, r1 = form == 2 ? S(10) : Z;
+    push_3d<R>(E, B, J, r0, r1, mx, my, mz, f, cS_h, cS_l, Sc_h, Sc_l, a, form);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      S(i) = E[i];
+      S(3 + i) = B[i];
+    }
+  }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// Fused last-axis pass: for TB lines (kx in 2D, (kx, ky) in 3D), forward FFT
+// of every input slot, per-mode push, inverse FFT of the n_out field slots,
+// written back in place.  Shared memory per line: n_in*L staged spectra
+// (natural order) + one padded exchange buffer.
+template <typename R, int L, int LAYOUT>
+__global__ void __launch_bounds__(FFTPlan<L>::kT > 256 ? FFTPlan<L>::kT : 256)
+k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
+  typedef typename Types<R>::C C;
+  typedef FFTPlan<L> P;
+  constexpr int T = P::kT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int t = threadIdx.x, g = threadIdx.y;
+  const int line = blockIdx.x * blockDim.y + g;
+  const bool valid = line < a.nlines;
+  C* st = reinterpret_cast<C*>(smem_raw) + g * (a.n_in * L + P::kBuf);
+  C* buf = st + a.n_in * L;
+  C* spec = static_cast<C*>(a.spec);
+
+  // stage every input slot of this line (cp.async, 16-byte chunks)
+  {
+    constexpr int CH = (L * (int)sizeof(C)) / 16;  // chunks per slot
+    for (int c = 0; c < a.n_in; ++c) {
+      const char* src = reinterpret_cast<const char*>(spec + c * a.cs + (int64_t)line * L);
+      char* dst = reinterpret_cast<char*>(st + c * L);
+      for (int i = t; i < CH; i += T) {
+        if (valid) cp_async16(dst + 16 * i, src + 16 * i);
+        else reinterpret_cast<float4*>(dst)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  C v[8];
+  for (int c = 0; c < a.n_in; ++c) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = st[c * L + t + T * m];
+    block_fft_fwd<R, L, 1>(v, buf, tw, t);
+#pragma unroll
+    for (int m = 0; m < 8; ++m) st[c * L + t + T * m] = v[m];
+  }
+
+  // mode indices of this line
+  int mxi, myi;  // signed integer modes (Nyquist -> 0) of the line's fixed axes
+  int rowi;      // coefficient-table row
+  if (a.ndim == 2) {
+    mxi = (line == a.nx_half) ? 0 : line;
+    myi = 0;
+    rowi = line;
+  } else {
+    const int kx = line / a.ny, ky = line - kx * a.ny;
+    mxi = (kx == a.nx_half) ? 0 : kx;
+    const int nyh = a.ny >> 1;
+    myi = (ky == nyh) ? 0 : (ky < nyh ? ky : ky - a.ny);
+    rowi = kx * (nyh + 1) + (ky <= nyh ? ky : a.ny - ky);
+  }
+  if (!valid) rowi = 0;
+  const Coef<R>* trow = a.tab + (int64_t)rowi * a.tab_row;
+#pragma unroll 1
+  for (int m = 0; m < 8; ++m) {
+    const int l = t + T * m;
+    const int am = (l <= L / 2) ? l : L - l;             // |m| along the line axis
+    const int ml = (l == L / 2) ? 0 : (l < L / 2 ? l : l - L);
+    CoefReg<R> f;
+    {
+      const Coef<R> q = trow[am];
+      f.C_h = q.C_h; f.C_l = q.C_l; f.S_h = q.S_h; f.S_l = q.S_l;
+      f.A1 = q.A1; f.A4 = q.A4; f.B1 = q.B1; f.B2 = q.B2;
+    }
+    R mx, my, mz;
+    if (a.ndim == 2) {
+      mx = a.rx * R(mxi); my = a.ry * R(ml); mz = R(0);
+    } else {
+      mx = a.rx * R(mxi); my = a.ry * R(myi); mz = a.rz * R(ml);
+    }
+    push_slots<R, LAYOUT>(st, L, l, f, mx, my, mz, a);
+  }
+
+  for (int c = 0; c < a.n_out; ++c) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) v[m] = st[c * L + t + T * m];
+    block_fft_inv<R, L, 1>(v, buf, tw, t);
+    if (valid) {
+      C* dst = spec + c * a.cs + (int64_t)line * L;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) dst[t + T * m] = v[m];
+    }
+  }
+}
+
+}  // namespace psatd

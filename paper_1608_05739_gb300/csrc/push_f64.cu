@@ -1,0 +1,7 @@
+// push_f64.cu -- double instantiation of the fused last-axis FFT + PSATD push pass.
+#include "launch_impl.cuh"
+
+namespace psatd {
+template cudaError_t launch_line_push<double>(int, int, dim3, int, size_t, cudaStream_t,
+                                              const PushArgs<double>&, const void*);
+}  // namespace psatd

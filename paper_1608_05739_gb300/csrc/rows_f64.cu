@@ -1,0 +1,9 @@
+// rows_f64.cu -- double instantiation of the transposing line-FFT passes.
+#include "launch_impl.cuh"
+
+namespace psatd {
+template cudaError_t launch_fwd_T<double>(int, bool, const PassGeom&, cudaStream_t, const LineIO&,
+                                          const void*, int64_t, int64_t, int64_t, int64_t);
+template cudaError_t launch_inv_T<double>(int, bool, const PassGeom&, cudaStream_t, const LineIO&,
+                                          const void*, int64_t, int64_t, int64_t, int64_t);
+}  // namespace psatd

@@ -1,0 +1,134 @@
+// tables.cu -- plan-time tables, computed in FP64 on the GPU and rounded once
+// to the step precision (FP32 keeps hi/lo pairs of the values that multiply
+// the field state every step).
+//
+// Twiddles of an axis of length n: W[j] = exp(-2 pi i j / n), j < n.
+//
+// Coefficient octant: one entry per (|mx|, |my|, |mz|), |m_i| <= n_i/2, with
+// the Nyquist index of each axis taken as m_i = 0.  With the integer-mode
+// vector mt = (rx mx, ry my, rz mz), k = g0 mt, x = c |k| dt (Sec. III.B: the
+// analytic integration over dt with sources constant):
+//   C  = cos x                          S_m = sin x / |mt|       (-> c g0 dt)
+//   A1 = (1 - C) / |mt|^2              (-> (c g0 dt)^2 / 2)
+//   A4 = (S/(c k) - dt) / (eps0 |mt|^2) = dt (c g0 dt)^2 f1(x) / eps0
+//   B1 = (S/x - 1) / (eps0 g0 |mt|^2)   = c^2 g0 dt^2 f1(x) / eps0
+//   B2 = (S/x - C) / (eps0 g0 |mt|^2)   = c^2 g0 dt^2 f2(x) / eps0
+// f1 = (sin x/x - 1)/x^2, f2 = (sin x/x - cos x)/x^2 (Taylor series below 0.5),
+// every entry multiplied by 1/N (the inverse-FFT normalisation).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "psatd_kernels.cuh"
+#include "tables.h"
+
+namespace psatd {
+
+__global__ void k_twiddles(void* out, int n, int f32) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s, c;
+  sincospi(-2.0 * (double)j / (double)n, &s, &c);
+  if (f32) {
+    const float ch = (float)c, sh = (float)s;
+    static_cast<float4*>(out)[j] = make_float4(ch, sh, (float)(c - (double)ch), (float)(s - (double)sh));
+  } else {
+    static_cast<double2*>(out)[j] = make_double2(c, s);
+  }
+}
+
+__device__ double f1_series(double x) {  // sum_{n>=1} (-1)^n x^(2n-2) / (2n+1)!
+  const double x2 = x * x;
+  double t = -1.0 / 6.0, s = t;
+  for (int n = 2; n <= 12; ++n) {
+    t *= -x2 / ((2.0 * n) * (2.0 * n + 1.0));
+    s += t;
+  }
+  return s;
+}
+__device__ double f2_series(double x) {  // sum_{n>=1} (-1)^(n+1) 2n x^(2n-2) / (2n+1)!
+  const double x2 = x * x;
+  double u = 1.0 / 6.0, s = 2.0 * u;
+  for (int n = 2; n <= 12; ++n) {
+    u *= x2 / ((2.0 * n) * (2.0 * n + 1.0));
+    s += ((n & 1) ? 1.0 : -1.0) * 2.0 * n * u;
+  }
+  return s;
+}
+
+__global__ void k_coefs(void* out, int f32, int e0, int e1, int e2, int nx, int ny, int nz,
+                        double rx, double ry, double rz, double g0, double c, double dt,
+                        double eps0, double invN) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)e0 * e1 * e2;
+  if (idx >= total) return;
+  const int iz = (int)(idx % e2);
+  const int iy = (int)((idx / e2) % e1);
+  const int ix = (int)(idx / ((int64_t)e1 * e2));
+  const double mx = (2 * ix == nx) ? 0.0 : ix;
+  const double my = (2 * iy == ny) ? 0.0 : iy;
+  const double mz = (nz > 1 && 2 * iz == nz) ? 0.0 : iz;
+  const double mm = sqrt((rx * mx) * (rx * mx) + (ry * my) * (ry * my) + (rz * mz) * (rz * mz));
+  const double q = c * g0 * dt;  // x = q |mt|
+  const double x = q * mm;
+  double sx, cx;
+  sincos(x, &sx, &cx);
+  double sinc = 1.0, sinc_h = 1.0;
+  if (x > 0.0) {
+    sinc = sx / x;
+    sinc_h = sin(0.5 * x) / (0.5 * x);
+  }
+  double f1, f2;
+  if (x < 0.5) {
+    f1 = f1_series(x);
+    f2 = f2_series(x);
+  } else {
+    f1 = (sinc - 1.0) / (x * x);
+    f2 = (sinc - cx) / (x * x);
+  }
+  const double C = cx * invN;
+  const double Sm = q * sinc * invN;
+  const double A1 = 0.5 * q * q * sinc_h * sinc_h * invN;
+  const double A4 = dt * q * q * f1 / eps0 * invN;
+  const double B1 = c * c * g0 * dt * dt * f1 / eps0 * invN;
+  const double B2 = c * c * g0 * dt * dt * f2 / eps0 * invN;
+  if (f32) {
+    Coef<float> e;
+    e.C_h = (float)C;
+    e.C_l = (float)(C - (double)e.C_h);
+    e.S_h = (float)Sm;
+    e.S_l = (float)(Sm - (double)e.S_h);
+    e.A1 = (float)A1;
+    e.A4 = (float)A4;
+    e.B1 = (float)B1;
+    e.B2 = (float)B2;
+    static_cast<Coef<float>*>(out)[idx] = e;
+  } else {
+    Coef<double> e;
+    e.C_h = C;
+    e.C_l = 0.0;
+    e.S_h = Sm;
+    e.S_l = 0.0;
+    e.A1 = A1;
+    e.A4 = A4;
+    e.B1 = B1;
+    e.B2 = B2;
+    static_cast<Coef<double>*>(out)[idx] = e;
+  }
+}
+
+cudaError_t launch_twiddles(void* out, int n, bool f32, cudaStream_t st) {
+  k_twiddles<<<(n + 255) / 256, 256, 0, st>>>(out, n, f32 ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coefs(void* out, bool f32, int e0, int e1, int e2, int nx, int ny, int nz,
+                         double rx, double ry, double rz, double g0, double c, double dt,
+                         double eps0, double invN, cudaStream_t st) {
+  const int64_t total = (int64_t)e0 * e1 * e2;
+  const unsigned blocks = (unsigned)((total + 255) / 256);
+  k_coefs<<<blocks, 256, 0, st>>>(out, f32 ? 1 : 0, e0, e1, e2, nx, ny, nz, rx, ry, rz, g0, c, dt,
+                                  eps0, invN);
+  return cudaGetLastError();
+}
+
+}  // namespace psatd

@@ -1,0 +1,107 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds, loads,
+exports every function declared in include/psatd.h, and rejects invalid
+arguments before any CUDA call."""
+import ctypes as ct
+import os
+import re
+
+import pytest
+
+from paper_1608_05739_gb300 import build as bld
+from paper_1608_05739_gb300 import capi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    bld.build()
+    return capi.load()
+
+
+def _declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**([A-Za-z_][A-Za-z0-9_]*)\s*\(",
+                            text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert "psatd_step" in names and "fdtd_step" in names and len(names) >= 11
+    for n in names:
+        assert hasattr(lib, n), n
+    assert lib.psatd_abi_version() == 1
+
+
+def test_desc_struct_layout_matches_c():
+    assert ct.sizeof(capi.psatd_desc) == 96
+    assert capi.psatd_desc.n.offset == 8 and capi.psatd_desc.d.offset == 32
+    assert capi.psatd_desc.prec.offset == 80
+    assert ct.sizeof(capi.psatd_fields) == 48 and ct.sizeof(capi.psatd_sources) == 40
+
+
+def _create(lib, desc):
+    h = ct.c_void_p()
+    st = lib.psatd_plan_create(ct.byref(desc) if desc is not None else None, None, ct.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("mutate,expect", [
+    (lambda d: setattr(d, "ndim", 3), 1),                  # ndim does not match a 2D layout
+    (lambda d: d.n.__setitem__(0, 100), 2),                # not a power of two
+    (lambda d: d.n.__setitem__(0, 8192), 2),               # too long
+    (lambda d: d.n.__setitem__(2, 4), 1),                  # n[2] != 1 in 2D
+    (lambda d: setattr(d, "dt", 0.0), 1),
+    (lambda d: setattr(d, "c", -1.0), 1),
+    (lambda d: setattr(d, "eps0", float("nan")), 1),
+    (lambda d: d.d.__setitem__(1, 0.0), 1),
+    (lambda d: setattr(d, "prec", 2), 2),                  # mixed precision: reserved
+    (lambda d: setattr(d, "prec", 9), 1),
+    (lambda d: setattr(d, "src", 7), 1),
+    (lambda d: setattr(d, "flags", 1), 1),
+    (lambda d: (setattr(d, "layout", 3), setattr(d, "src", 2)), 1),  # TM has no rho-form
+    (lambda d: setattr(d, "layout", 9), 1),
+])
+def test_plan_create_rejects_invalid_descriptors(lib, mutate, expect):
+    d = capi.make_desc((64, 32), (1.0, 1.0), 0.5, layout="te", prec="fp32", src="J")
+    mutate(d)
+    st, h = _create(lib, d)
+    assert st == expect
+    assert h.value is None
+    assert len(lib.psatd_last_error(None)) > 0
+
+
+def test_null_arguments(lib):
+    h = ct.c_void_p()
+    assert lib.psatd_plan_create(None, None, ct.byref(h)) == 1
+    d = capi.make_desc((64, 32), (1.0, 1.0), 0.5)
+    assert lib.psatd_plan_create(ct.byref(d), None, None) == 1
+    assert lib.psatd_step(None, None, None, 1) == 1
+    assert lib.psatd_coeffs_init(None) == 1
+    assert lib.psatd_plan_destroy(None) == 0
+    assert lib.psatd_plan_workspace_bytes(None) == 0
+    assert b"NULL" in lib.psatd_last_error(None)
+
+
+def test_fdtd_rejects_invalid_arguments(lib):
+    d = capi.make_desc((64, 32), (1.0, 1.0), 0.5, layout="te", src="J")
+    f = capi.psatd_fields()
+    s = capi.psatd_sources()
+    assert lib.fdtd_step(ct.byref(d), 5, ct.byref(f), ct.byref(s), 1, None) == 1       # scheme
+    d3 = capi.make_desc((16, 16, 16), (1.0, 1.0, 1.0), 0.5, layout="3d6", src="none")
+    assert lib.fdtd_step(ct.byref(d3), 1, ct.byref(f), None, 1, None) == 2             # CKC 3D
+    assert lib.fdtd_step(ct.byref(d), 0, ct.byref(f), ct.byref(s), 0, None) == 1       # nsteps
+    assert lib.fdtd_step(ct.byref(d), 0, None, ct.byref(s), 1, None) == 1              # fields NULL
+    assert lib.fdtd_step(ct.byref(d), 0, ct.byref(f), ct.byref(s), 1, None) == 1       # E missing
+    f.E[0] = 0x1000
+    f.E[1] = 0x2004                                                                     # misaligned
+    f.B[2] = 0x3000
+    assert lib.fdtd_step(ct.byref(d), 0, ct.byref(f), ct.byref(s), 1, None) == 1
+    dr = capi.make_desc((64, 32), (1.0, 1.0), 0.5, layout="te", src="rho")
+    assert lib.fdtd_step(ct.byref(dr), 0, ct.byref(f), ct.byref(s), 1, None) == 1      # rho-form
