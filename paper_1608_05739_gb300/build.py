@@ -41,9 +41,23 @@ def _stale(target, sources):
     return any(os.path.getmtime(s) > t for s in sources)
 
 
+def _arch_stamp():
+    """Objects built on another host architecture are discarded (x86 vs aarch64)."""
+    import platform
+    stamp = os.path.join(BUILD, "ARCH")
+    here = platform.machine()
+    old = open(stamp).read().strip() if os.path.exists(stamp) else None
+    if old != here:
+        for f in glob.glob(os.path.join(BUILD, "*.o")) + glob.glob(os.path.join(BUILD, "*.so")):
+            os.unlink(f)
+        with open(stamp, "w") as fh:
+            fh.write(here)
+
+
 def build(verbose: bool = False, jobs: int | None = None) -> str:
     """Compile and link; returns the path of libpsatd.so."""
     os.makedirs(BUILD, exist_ok=True)
+    _arch_stamp()
     cc = nvcc()
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     deps = _deps()
