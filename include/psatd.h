@@ -167,6 +167,27 @@ int32_t psatd_kernel_times(psatd_plan plan, int32_t n_slots, const char** names,
 psatd_status fdtd_step(const psatd_desc* desc, int32_t scheme, const psatd_fields* fields,
                        const psatd_sources* sources, int32_t nsteps, void* cuda_stream);
 
+/* PSATD step without any device allocation, for callers that cannot call
+ * cudaMalloc (e.g. code running where a foreign allocator owns all device
+ * memory, or a host that must not allocate after start-up).  The paper has no
+ * counterpart: this is a deployment variant of psatd_plan_create +
+ * psatd_coeffs_init + psatd_step + psatd_plan_destroy in one call.
+ *   Scratch: one fixed 16 MiB device array inside the library, held by every
+ *   GPU that loads the library until the process exits.  Grids whose spectra
+ *   and tables need more (for FP32 2D TE J-form, anything above about 512^2)
+ *   are rejected with PSATD_ERR_UNSUPPORTED and a message naming the size.
+ *   The caller still passes (and owns) every field and source array.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (with that device current); make that first call before any stream capture.
+ *   Each call rebuilds the twiddle and coefficient tables in the array (the
+ *   array keeps the previous call's contents; the spectra are overwritten
+ *   before they are read, so nothing needs clearing).
+ *   All calls share the one array: calls whose work overlaps on the GPU (other
+ *   streams, other host threads) race and corrupt each other's results.
+ * Arguments and errors as psatd_plan_create and psatd_step; asynchronous.   */
+psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_fields* fields,
+                                const psatd_sources* sources, int32_t nsteps, void* cuda_stream);
+
 /* Message of the last failure on `plan`, or of this thread's last failure
  * without a plan when plan == NULL.  Never NULL. */
 const char* psatd_last_error(psatd_plan plan);

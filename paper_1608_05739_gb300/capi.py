@@ -232,3 +232,30 @@ def fdtd_step(n, d, dt, E, B, J=None, *, scheme="yee", layout="te", prec="fp32",
         stream = torch.cuda.current_stream()
     _check(lib.fdtd_step(ct.byref(desc), SCHEME[scheme], ct.byref(f), ct.byref(s) if s is not None else None,
                          int(nsteps), ct.c_void_p(stream.cuda_stream)))
+
+
+def step_noalloc(n, d, dt, E, B, J=None, rho_n=None, rho_np1=None, *, layout="te", prec="fp32", src="J",
+                 c=1.0, eps0=1.0, nsteps=1, stream=None):
+    """psatd_step_noalloc: one-call PSATD step that allocates no device memory.
+
+    For callers that cannot allocate on the GPU: the library's scratch is a
+    fixed 16 MiB device array (grids needing more raise PsatdError with
+    PSATD_ERR_UNSUPPORTED).  Calls whose GPU work overlaps share that array
+    and race; the first call on a device must precede any stream capture.
+    Fields and sources are passed as for Plan.step.
+    """
+    import torch
+    lib = load()
+    fn = lib.psatd_step_noalloc
+    fn.restype = ct.c_int
+    fn.argtypes = [ct.POINTER(psatd_desc), ct.POINTER(psatd_fields), ct.POINTER(psatd_sources), ct.c_int32,
+                   ct.c_void_p]
+    desc = make_desc(n, d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0)
+    shape = _grid_shape(n)
+    dtype = _torch_dtype(prec)
+    f = _fields_struct(layout, shape, dtype, E, B)
+    s = _sources_struct(layout, shape, dtype, J, rho_n, rho_np1) if src != "none" else None
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(fn(ct.byref(desc), ct.byref(f), ct.byref(s) if s is not None else None, int(nsteps),
+              ct.c_void_p(stream.cuda_stream)))

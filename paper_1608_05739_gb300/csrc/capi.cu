@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -550,3 +551,135 @@ psatd_status fdtd_step(const psatd_desc* desc, int32_t scheme, const psatd_field
 const char* psatd_last_error(psatd_plan p) { return p ? p->err.c_str() : g_err.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// psatd_step_noalloc: the PSATD step for callers that cannot allocate device
+// memory (see include/psatd.h).  Its scratch (spectra, twiddles, coefficient
+// table) lives in one fixed, file-scope device array of kNoAllocBytes that
+// every GPU loading this library holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(16) << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+std::mutex g_noalloc_mutex;
+
+size_t round256(size_t v) { return (v + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_fields* fields,
+                                           const psatd_sources* sources, int32_t nsteps, void* cuda_stream) {
+  psatd_status s = validate_desc(nullptr, desc, true);
+  if (s != PSATD_OK) return s;
+  if (nsteps < 1) return fail(nullptr, PSATD_ERR_INVALID_ARG, "nsteps must be >= 1 (got %d)", nsteps);
+
+  // a plan-shaped descriptor on the stack whose buffers are carved from the array
+  psatd_plan_s p;
+  p.d = *desc;
+  p.st = static_cast<cudaStream_t>(cuda_stream);
+  p.f32 = desc->prec == PSATD_FP32;
+  p.ndim = desc->ndim;
+  p.layout = desc->layout;
+  p.form = desc->src;
+  counts(p.layout, p.form, &p.n_in, &p.n_out);
+  p.nx = desc->n[0];
+  p.ny = desc->n[1];
+  p.nz = p.ndim == 3 ? desc->n[2] : 1;
+  p.nxh = p.nx / 2 + 1;
+  p.cs = p.nxh * p.ny * p.nz;
+  const size_t csz = p.f32 ? 8 : 16;
+  const int64_t ns[3] = {p.nx, p.ny, p.nz};
+  p.tab_e[0] = p.nx / 2 + 1;
+  p.tab_e[1] = p.ny / 2 + 1;
+  p.tab_e[2] = p.ndim == 3 ? p.nz / 2 + 1 : 1;
+  const size_t spec = round256((size_t)p.n_in * (size_t)p.cs * csz);
+  size_t tw[3] = {0, 0, 0};
+  for (int i = 0; i < p.ndim; ++i) tw[i] = round256((size_t)ns[i] * 16);
+  const size_t tab = round256((size_t)p.tab_e[0] * p.tab_e[1] * p.tab_e[2] *
+                              (p.f32 ? sizeof(Coef<float>) : sizeof(Coef<double>)));
+  const size_t need = spec * (p.ndim == 3 ? 2 : 1) + tw[0] + tw[1] + tw[2] + tab;
+  if (need > kNoAllocBytes)
+    return fail(nullptr, PSATD_ERR_UNSUPPORTED,
+                "psatd_step_noalloc: this grid needs %zu bytes of scratch, more than its fixed %zu-byte "
+                "device array; use psatd_plan_create / psatd_step",
+                need, kNoAllocBytes);
+
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(nullptr, PSATD_ERR_UNSUPPORTED, "device index %d too large", dev);
+  {
+    int maxsm = 0;
+    cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int L = (int)(p.ndim == 3 ? p.nz : p.ny);
+    const size_t smem = ((size_t)p.n_in * L + (size_t)(((L + L / 8 + 1) / 2) * 2)) * csz;
+    if (maxsm > 0 && smem > (size_t)maxsm)
+      return fail(nullptr, PSATD_ERR_UNSUPPORTED, "last-axis length %d needs %zu bytes of shared memory", L, smem);
+  }
+  unsigned char* base = nullptr;
+  {
+    // one-time set-up per device (with that device current): the device address of the array
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress of the no-alloc scratch");
+      g_noalloc_ptr[dev] = ptr;
+    }
+    base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+  }
+  size_t off = 0;
+  p.spec1 = base + off;
+  off += spec;
+  if (p.ndim == 3) {
+    p.spec2 = base + off;
+    off += spec;
+  }
+  for (int i = 0; i < p.ndim; ++i) {
+    p.tw[i] = base + off;
+    off += tw[i];
+  }
+  p.tab = base + off;
+
+  const void* in[kMaxComp] = {};
+  void* out[kMaxComp] = {};
+  s = gather_slots(&p, fields, sources, in, out);
+  if (s != PSATD_OK) {
+    g_err = p.err;
+    return s;
+  }
+  // wavenumber scale as in psatd_plan_create
+  p.g0 = 2.0 * M_PI / ((double)p.nx * desc->d[0]);
+  for (int i = 0; i < 3; ++i) {
+    if (i >= p.ndim) {
+      p.r[i] = 0.0;
+      continue;
+    }
+    double ri = (2.0 * M_PI / ((double)ns[i] * desc->d[i])) / p.g0;
+    if (p.f32) ri = (double)(float)ri;
+    p.r[i] = ri;
+  }
+  // the tables are rebuilt by every call (the array keeps the previous call's contents);
+  // the spectra need no clearing: the first pass overwrites them entirely
+  for (int i = 0; i < p.ndim; ++i) {
+    e = launch_twiddles(p.tw[i], (int)ns[i], p.f32, p.st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "twiddle table launch");
+  }
+  const double N = (double)p.nx * (double)p.ny * (double)p.nz;
+  e = launch_coefs(p.tab, p.f32, (int)p.tab_e[0], (int)p.tab_e[1], (int)p.tab_e[2], (int)p.nx, (int)p.ny, (int)p.nz,
+                   p.r[0], p.r[1], p.r[2], p.g0, desc->c, desc->dt, desc->eps0, 1.0 / N, p.st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "coefficient table launch");
+  p.coeffs_ready = true;
+  for (int i = 0; i < nsteps; ++i) {
+    s = p.f32 ? run_step<float>(&p, in, out) : run_step<double>(&p, in, out);
+    if (s != PSATD_OK) {
+      g_err = p.err;
+      return s;
+    }
+  }
+  return PSATD_OK;
+}
