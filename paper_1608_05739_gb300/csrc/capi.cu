@@ -208,9 +208,8 @@ int pick_log_tb(int L, int64_t nb, bool f32) {
 
 size_t tpass_smem(int L, int log_tb, bool r2c, size_t csz) {
   const int tb = 1 << log_tb;
-  const int kbuf = ((L + L / 8 + 1) / 2) * 2;
   const size_t nk = r2c ? (size_t)L + 1 : (size_t)L;
-  const size_t a = (size_t)tb * kbuf, b = nk * (size_t)(tb + 1);
+  const size_t a = (size_t)tb * 2 * L, b = nk * (size_t)(tb + 1);
   return (a > b ? a : b) * csz;
 }
 
@@ -306,15 +305,17 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     a.ic_l = (R)(ic - (double)a.ic_h);
     a.s_src = (R)(1.0 / (p->d.eps0 * c * p->g0));
     a.s_a6 = (R)(1.0 / (p->d.eps0 * c * c * p->g0));
-    const int T = Lline / 8;
-    const int kbuf = ((Lline + Lline / 8 + 1) / 2) * 2;
-    const size_t per_line = ((size_t)p->n_in * Lline + kbuf) * csz;
-    int tb = 1;
-    while (tb * 2 * T <= 256 && (size_t)(tb * 2) * per_line <= 100 * 1024 && tb * 2 <= nlines) tb *= 2;
-    const dim3 grid((unsigned)((nlines + tb - 1) / tb));
-    TimedLaunch tl(p, K_PUSH);
-    e = launch_line_push<R>(Lline, p->layout, grid, tb, tb * per_line, p->st, a, p->tw[p->ndim == 3 ? 2 : 1]);
-    if (e != cudaSuccess) return cuda_fail(p, e, "line_fft_push launch");
+    const void* twl = p->tw[p->ndim == 3 ? 2 : 1];
+    {
+      const int T = Lline / 8;
+      const size_t per_line = ((size_t)p->n_in + 1) * (size_t)Lline * csz;
+      int tb = 1;
+      while (tb * 2 * T <= 256 && (size_t)(tb * 2) * per_line <= 100 * 1024 && tb * 2 <= nlines) tb *= 2;
+      const dim3 grid((unsigned)((nlines + tb - 1) / tb));
+      TimedLaunch tl(p, K_PUSH);
+      e = launch_line_push<R>(Lline, p->layout, grid, tb, tb * per_line, p->st, a, twl);
+      if (e != cudaSuccess) return cuda_fail(p, e, "line_fft_push launch");
+    }
   }
   if (p->ndim == 3) {
     // pass 4: inverse y lines: spec2 [c][kx][ky][z] -> spec1 [c][kx][z][y]
@@ -377,7 +378,7 @@ psatd_status psatd_plan_create(const psatd_desc* desc, void* cuda_stream, psatd_
   {
     const int L = (int)(p->ndim == 3 ? p->nz : p->ny);
     const size_t csz = p->f32 ? 8 : 16;
-    const size_t need = ((size_t)p->n_in * L + (size_t)(((L + L / 8 + 1) / 2) * 2)) * csz;
+    const size_t need = ((size_t)p->n_in + 1) * (size_t)L * csz;
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
     if (maxsm > 0 && need > (size_t)maxsm) {
@@ -429,7 +430,7 @@ psatd_status psatd_coeffs_init(psatd_plan p) {
   {
     TimedLaunch tl(p, K_TABLES);
     for (int i = 0; i < p->ndim; ++i) {
-      e = launch_twiddles(p->tw[i], (int)ns[i], p->f32, p->st);
+      e = launch_twiddles(p->tw[i], i == 0 ? (int)(ns[0] / 2) : (int)ns[i], i == 0, p->f32, p->st);
       if (e != cudaSuccess) return cuda_fail(p, e, "twiddle table launch");
     }
     const double N = (double)p->nx * (double)p->ny * (double)p->nz;
@@ -616,7 +617,7 @@ extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_f
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int L = (int)(p.ndim == 3 ? p.nz : p.ny);
-    const size_t smem = ((size_t)p.n_in * L + (size_t)(((L + L / 8 + 1) / 2) * 2)) * csz;
+    const size_t smem = ((size_t)p.n_in + 1) * (size_t)L * csz;
     if (maxsm > 0 && smem > (size_t)maxsm)
       return fail(nullptr, PSATD_ERR_UNSUPPORTED, "last-axis length %d needs %zu bytes of shared memory", L, smem);
   }
@@ -666,7 +667,7 @@ extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_f
   // the tables are rebuilt by every call (the array keeps the previous call's contents);
   // the spectra need no clearing: the first pass overwrites them entirely
   for (int i = 0; i < p.ndim; ++i) {
-    e = launch_twiddles(p.tw[i], (int)ns[i], p.f32, p.st);
+    e = launch_twiddles(p.tw[i], i == 0 ? (int)(ns[0] / 2) : (int)ns[i], i == 0, p.f32, p.st);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "twiddle table launch");
   }
   const double N = (double)p.nx * (double)p.ny * (double)p.nz;

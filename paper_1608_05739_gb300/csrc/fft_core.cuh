@@ -4,8 +4,9 @@
 // threads; thread t holds the eight elements x[t + T*m], m = 0..7, in registers
 // before and after the transform (natural order in both domains).  Stages:
 // one radix-2 or radix-4 stage first (when log2 L is not a multiple of 3),
-// then radix-8 stages.  Between stages the data go through shared memory with
-// a padded layout (one pad slot every eight elements).
+// then radix-8 stages.  Between stages the data go through shared memory in
+// rows of 16 elements whose columns are XOR-swizzled per exchange (free of
+// bank conflicts for each stage's write pattern); two buffers alternate.
 //
 // Forward = Stockham decimation in time: stage (radix R, span Ns) multiplies
 // input r of butterfly j by w^(r*k), w = exp(-2 pi i/(Ns R)), k = j mod Ns,
@@ -143,27 +144,74 @@ struct FFTPlan {
   static constexpr int kR0 = (kLog % 3 == 1) ? 2 : (kLog % 3 == 2) ? 4 : 8;
   static constexpr int kStages = (kR0 == 8) ? kLog / 3 : kLog / 3 + 1;
   static constexpr int kT = L / 8;
-  // padded exchange-buffer length (one pad slot per 8 elements), kept even
-  static constexpr int kBuf = ((L + L / 8 + 1) / 2) * 2;
+  static constexpr int kBuf = L;  // exchange buffer (XOR-swizzled, no padding)
   __host__ __device__ static constexpr int radix(int s) { return s == 0 ? kR0 : 8; }
   __host__ __device__ static constexpr int span(int s) {  // Ns of stage s
     int ns = 1;
     for (int i = 0; i < s; ++i) ns *= radix(i);
     return ns;
   }
+  // offset of stage s's twiddle block in the stage table (stages s >= 1)
+  __host__ __device__ static constexpr int tw_off(int s) {
+    int o = 0;
+    for (int i = 1; i < s; ++i) o += (radix(i) - 1) * span(i);
+    return o;
+  }
+  // entries of the stage table: sum over s >= 1 of (R_s - 1) Ns_s = L - R_0
+  static constexpr int kTwEntries = L - kR0;
+  // XOR multiplier of the exchange written by stage s (bank-conflict free for
+  // the Stockham write pattern of that stage and the contiguous reads after it)
+  __host__ __device__ static constexpr int swz(int s) { return span(s) == 1 ? 1 : 10; }
+  // swizzle of the last exchange: forward output / inverse input positions
+  // sw<kLastCX>(t + T m) are each touched by their own thread only
+  static constexpr int kLastCX = (kStages >= 2) ? swz(kStages - 2) : 0;
   static_assert(L >= 8 && (L & (L - 1)) == 0, "L must be a power of two >= 8");
 };
 
-__device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
+// element i of an exchange buffer, rows of 16 elements (128 B) XOR-swizzled
+template <int CX>
+__device__ __forceinline__ int sw(int i) { return i ^ (((i >> 4) * CX) & 15); }
 
-// One forward stage.  tw: twiddle table of an axis of length L*TWS.
-template <typename R, int L, int S, int TWS>
-__device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[8], typename Types<R>::C* buf,
+// Two exchange buffers used alternately: consecutive exchanges never share a
+// buffer, so one barrier per exchange suffices.  `twslot` is a shared-memory
+// word holding the twiddle table's address (written before the kernel's first
+// barrier): each stage reads it back, which ties that stage's twiddle loads to
+// the stage (the compiler cannot prefetch every stage's twiddles of every
+// transform in a kernel into registers).
+template <class C>
+struct ExBuf {
+  C* b[2];
+  int cur;
+  const void* const* twslot;
+  __device__ __forceinline__ C* next() {
+    C* p = b[cur];
+    cur ^= 1;
+    return p;
+  }
+};
+
+template <typename R, class C>
+__device__ __forceinline__ const typename Types<R>::W* stage_tw(const ExBuf<C>& ex) {
+  return reinterpret_cast<const typename Types<R>::W*>(
+      const_cast<const void*>(*reinterpret_cast<const void* const volatile*>(ex.twslot)));
+}
+
+// Twiddle tables of a length-L transform (built in tables.cu): stage s >= 1
+// keeps W_L^(r k L/(Ns R)) at [tw_off(s) + (r-1) Ns + k], k < Ns, 1 <= r < R,
+// so the threads of a warp read consecutive entries.
+
+// One forward stage.
+template <typename R, int L, int S>
+__device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[8], ExBuf<typename Types<R>::C>& ex,
                                           const typename Types<R>::W* __restrict__ tw, int t) {
   typedef typename Types<R>::C C;
   typedef FFTPlan<L> P;
   constexpr int RS = P::radix(S), NS = P::span(S), Q = 8 / RS, T = P::kT;
   constexpr bool LAST = (S == P::kStages - 1);
+  constexpr int CX = P::swz(S);
+  C* buf = nullptr;
+  if constexpr (!LAST) buf = ex.next();
+  asm volatile("" : "+r"(t)::"memory");  // stage boundary for the front end
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int j = t + q * T;
@@ -172,8 +220,9 @@ __device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[8], typename
 #pragma unroll
     for (int r = 0; r < RS; ++r) a[r] = v[q + r * Q];
     if constexpr (NS > 1) {
+      const typename Types<R>::W* tws = stage_tw<R>(ex) + P::tw_off(S) + k;
 #pragma unroll
-      for (int r = 1; r < RS; ++r) a[r] = twmul(a[r], __ldg(&tw[(r * k * (L / (NS * RS))) * TWS]));
+      for (int r = 1; r < RS; ++r) a[r] = twmul(a[r], __ldg(&tws[(r - 1) * NS]));
     }
     butterfly<RS, false>(a);
     if constexpr (LAST) {
@@ -182,31 +231,33 @@ __device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[8], typename
     } else {
       const int base = (j - k) * RS + k;
 #pragma unroll
-      for (int r = 0; r < RS; ++r) buf[pad8(base + r * NS)] = a[r];
+      for (int r = 0; r < RS; ++r) buf[sw<CX>(base + r * NS)] = a[r];
     }
   }
   if constexpr (!LAST) {
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = buf[pad8(t + T * m)];
-    __syncthreads();
+    for (int m = 0; m < 8; ++m) v[m] = buf[sw<CX>(t + T * m)];
   }
 }
 
 // Adjoint of fwd_stage<S>.
-template <typename R, int L, int S, int TWS>
-__device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[8], typename Types<R>::C* buf,
+template <typename R, int L, int S>
+__device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[8], ExBuf<typename Types<R>::C>& ex,
                                           const typename Types<R>::W* __restrict__ tw, int t) {
   typedef typename Types<R>::C C;
   typedef FFTPlan<L> P;
   constexpr int RS = P::radix(S), NS = P::span(S), Q = 8 / RS, T = P::kT;
   constexpr bool FIRST = (S == P::kStages - 1);
+  constexpr int CX = P::swz(S);
+  C* buf = nullptr;
   if constexpr (!FIRST) {
-    __syncthreads();
+    buf = ex.next();
 #pragma unroll
-    for (int m = 0; m < 8; ++m) buf[pad8(t + T * m)] = v[m];
+    for (int m = 0; m < 8; ++m) buf[sw<CX>(t + T * m)] = v[m];
     __syncthreads();
   }
+  asm volatile("" : "+r"(t)::"memory");  // stage boundary (see fwd_stage)
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int j = t + q * T;
@@ -218,43 +269,45 @@ __device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[8], typename
     } else {
       const int base = (j - k) * RS + k;
 #pragma unroll
-      for (int r = 0; r < RS; ++r) a[r] = buf[pad8(base + r * NS)];
+      for (int r = 0; r < RS; ++r) a[r] = buf[sw<CX>(base + r * NS)];
     }
     butterfly<RS, true>(a);
     if constexpr (NS > 1) {
+      const typename Types<R>::W* tws = stage_tw<R>(ex) + P::tw_off(S) + k;
 #pragma unroll
-      for (int r = 1; r < RS; ++r) a[r] = twmul_conj(a[r], __ldg(&tw[(r * k * (L / (NS * RS))) * TWS]));
+      for (int r = 1; r < RS; ++r) a[r] = twmul_conj(a[r], __ldg(&tws[(r - 1) * NS]));
     }
 #pragma unroll
     for (int r = 0; r < RS; ++r) v[q + r * Q] = a[r];
   }
 }
 
-template <typename R, int L, int TWS, int... S>
-__device__ __forceinline__ void fft_fwd_seq(typename Types<R>::C (&v)[8], typename Types<R>::C* buf,
+template <typename R, int L, int... S>
+__device__ __forceinline__ void fft_fwd_seq(typename Types<R>::C (&v)[8], ExBuf<typename Types<R>::C>& ex,
                                             const typename Types<R>::W* tw, int t,
                                             std::integer_sequence<int, S...>) {
-  (fwd_stage<R, L, S, TWS>(v, buf, tw, t), ...);
+  (fwd_stage<R, L, S>(v, ex, tw, t), ...);
 }
-template <typename R, int L, int TWS, int... S>
-__device__ __forceinline__ void fft_inv_seq(typename Types<R>::C (&v)[8], typename Types<R>::C* buf,
+template <typename R, int L, int... S>
+__device__ __forceinline__ void fft_inv_seq(typename Types<R>::C (&v)[8], ExBuf<typename Types<R>::C>& ex,
                                             const typename Types<R>::W* tw, int t,
                                             std::integer_sequence<int, S...>) {
-  (inv_stage<R, L, FFTPlan<L>::kStages - 1 - S, TWS>(v, buf, tw, t), ...);
+  (inv_stage<R, L, FFTPlan<L>::kStages - 1 - S>(v, ex, tw, t), ...);
 }
 
 // Forward DFT of length L: v holds x[t + T m] on entry, X[t + T m] on exit.
-// Every thread of the block must call it (block-wide barriers inside).
-template <typename R, int L, int TWS>
-__device__ __forceinline__ void block_fft_fwd(typename Types<R>::C (&v)[8], typename Types<R>::C* buf,
+// Every thread of the block must call it (block-wide barriers inside); the
+// exchanges alternate between the two buffers of `ex`.
+template <typename R, int L>
+__device__ __forceinline__ void block_fft_fwd(typename Types<R>::C (&v)[8], ExBuf<typename Types<R>::C>& ex,
                                               const typename Types<R>::W* tw, int t) {
-  fft_fwd_seq<R, L, TWS>(v, buf, tw, t, std::make_integer_sequence<int, FFTPlan<L>::kStages>{});
+  fft_fwd_seq<R, L>(v, ex, tw, t, std::make_integer_sequence<int, FFTPlan<L>::kStages>{});
 }
 // Unnormalised inverse DFT (adjoint of block_fft_fwd).
-template <typename R, int L, int TWS>
-__device__ __forceinline__ void block_fft_inv(typename Types<R>::C (&v)[8], typename Types<R>::C* buf,
+template <typename R, int L>
+__device__ __forceinline__ void block_fft_inv(typename Types<R>::C (&v)[8], ExBuf<typename Types<R>::C>& ex,
                                               const typename Types<R>::W* tw, int t) {
-  fft_inv_seq<R, L, TWS>(v, buf, tw, t, std::make_integer_sequence<int, FFTPlan<L>::kStages>{});
+  fft_inv_seq<R, L>(v, ex, tw, t, std::make_integer_sequence<int, FFTPlan<L>::kStages>{});
 }
 
 }  // namespace psatd

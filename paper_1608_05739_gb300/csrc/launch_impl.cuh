@@ -5,9 +5,12 @@
 
 namespace psatd {
 
+// Dynamic shared-memory opt-in (static shared memory adds to the request).  The
+// carveout is left to the driver: a maximal shared carveout shrinks the L1 that
+// holds the twiddle tables and was measured slower.
 template <typename K>
 static cudaError_t set_smem(K kern, size_t smem) {
-  if (smem > 48 * 1024)
+  if (smem > 32 * 1024)
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   return cudaSuccess;
 }

@@ -67,14 +67,15 @@ __global__ void __launch_bounds__(512) k_fwd_T(LineIO io, const typename Types<R
   typedef FFTPlan<L> P;
   constexpr int T = P::kT;
   constexpr int NK = R2C ? L + 1 : L;
-  constexpr int TWS = R2C ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smem = reinterpret_cast<C*>(smem_raw);
   const int TB = 1 << log_tb;
   const int t = threadIdx.x, g = threadIdx.y;
   const int64_t b = (int64_t)blockIdx.x * TB + g;
   const int a0 = blockIdx.y, a1 = blockIdx.z;
-  C* buf = smem + g * P::kBuf;
+  __shared__ const void* twslot;
+  if (t == 0 && g == 0) twslot = tw;
+  ExBuf<C> ex{{smem + g * 2 * L, smem + g * 2 * L + L}, 0, &twslot};
 
   C v[8];
   {
@@ -86,25 +87,28 @@ __global__ void __launch_bounds__(512) k_fwd_T(LineIO io, const typename Types<R
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = row[t + T * m];
   }
-  block_fft_fwd<R, L, TWS>(v, buf, tw, t);
+  if constexpr (P::kStages == 1) __syncthreads();  // twslot visible (else the first exchange's barrier)
+  block_fft_fwd<R, L>(v, ex, tw, t);
 
   C* tile = smem;  // [NK][TB + 1], aliases the exchange buffers
   const int tp = TB + 1;
   if constexpr (R2C) {
     // X[k] = Fe[k] + W_N^k Fo[k] with Fe = (Z[k] + Z*[L-k])/2, Fo = (Z[k] - Z*[L-k])/(2i)
+    C* zb = ex.next();
 #pragma unroll
-    for (int m = 0; m < 8; ++m) buf[pad8(t + T * m)] = v[m];
+    for (int m = 0; m < 8; ++m) zb[sw<1>(t + T * m)] = v[m];
     __syncthreads();
+    const typename Types<R>::W* wn = tw + P::kTwEntries;  // W_N^k, N = 2L
     C X[8];
     C XL = mkc(R(0), R(0));
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const int k = t + T * m;
-      const C zk = buf[pad8(k)];
-      const C zm = cconj(buf[pad8((L - k) & (L - 1))]);
+      const C zk = zb[sw<1>(k)];
+      const C zm = cconj(zb[sw<1>((L - k) & (L - 1))]);
       const C fe = mkc(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y + zm.y));
       const C fo = mkc(R(0.5) * (zk.y - zm.y), R(-0.5) * (zk.x - zm.x));
-      X[m] = cadd(fe, twmul(fo, __ldg(&tw[k])));
+      X[m] = cadd(fe, twmul(fo, __ldg(&wn[k])));
       if (k == 0) XL = csub(fe, fo);
     }
     __syncthreads();
@@ -138,7 +142,6 @@ __global__ void __launch_bounds__(512) k_inv_T(LineIO io, const typename Types<R
   typedef FFTPlan<L> P;
   constexpr int T = P::kT;
   constexpr int NK = C2R ? L + 1 : L;
-  constexpr int TWS = C2R ? 2 : 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smem = reinterpret_cast<C*>(smem_raw);
   const int TB = 1 << log_tb;
@@ -147,6 +150,8 @@ __global__ void __launch_bounds__(512) k_inv_T(LineIO io, const typename Types<R
   const int a0 = blockIdx.y, a1 = blockIdx.z;
   C* tile = smem;
   const int tp = TB + 1;
+  __shared__ const void* twslot;
+  if (t == 0 && g == 0) twslot = tw;
   {
     const C* ib = static_cast<const C*>(io.in[a1]) + a0 * in_sa0 + (int64_t)blockIdx.x * TB;
     const int nthr = T * TB;
@@ -159,13 +164,14 @@ __global__ void __launch_bounds__(512) k_inv_T(LineIO io, const typename Types<R
   C v[8];
   if constexpr (C2R) {
     // Z[k] = Fe + i Fo, Fe = X[k] + X*[L-k], Fo = (X[k] - X*[L-k]) conj(W_N^k)
+    const typename Types<R>::W* wn = tw + P::kTwEntries;
 #pragma unroll
     for (int m = 0; m < 8; ++m) {
       const int k = t + T * m;
       const C xk = tile[k * tp + g];
       const C xm = cconj(tile[(L - k) * tp + g]);
       const C fe = cadd(xk, xm);
-      const C fo = twmul_conj(csub(xk, xm), __ldg(&tw[k]));
+      const C fo = twmul_conj(csub(xk, xm), __ldg(&wn[k]));
       v[m] = cadd(fe, cmul_pi(fo));
     }
   } else {
@@ -173,8 +179,8 @@ __global__ void __launch_bounds__(512) k_inv_T(LineIO io, const typename Types<R
     for (int m = 0; m < 8; ++m) v[m] = tile[(t + T * m) * tp + g];
   }
   __syncthreads();
-  C* buf = smem + g * P::kBuf;
-  block_fft_inv<R, L, TWS>(v, buf, tw, t);
+  ExBuf<C> ex{{smem + g * 2 * L, smem + g * 2 * L + L}, 0, &twslot};
+  block_fft_inv<R, L>(v, ex, tw, t);
   C* row;
   if constexpr (C2R)
     row = reinterpret_cast<C*>(static_cast<R*>(io.out[a1]) + a0 * out_sa0 + b * out_sb);
@@ -361,6 +367,23 @@ __device__ __forceinline__ void push_slots(typename Types<R>::C* st, int L, int 
   }
 }
 
+// Signed integer modes (Nyquist -> 0) of a last-axis line's fixed axes and its
+// coefficient-table row: 2D lines are kx, 3D lines are (kx, ky), ky fastest.
+template <typename R>
+__device__ __forceinline__ void line_modes(const PushArgs<R>& a, int line, int& mxi, int& myi, int& rowi) {
+  if (a.ndim == 2) {
+    mxi = (line == a.nx_half) ? 0 : line;
+    myi = 0;
+    rowi = line;
+  } else {
+    const int kx = line / a.ny, ky = line - kx * a.ny;
+    mxi = (kx == a.nx_half) ? 0 : kx;
+    const int nyh = a.ny >> 1;
+    myi = (ky == nyh) ? 0 : (ky < nyh ? ky : ky - a.ny);
+    rowi = kx * (nyh + 1) + (ky <= nyh ? ky : a.ny - ky);
+  }
+}
+
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
@@ -371,21 +394,27 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // Fused last-axis pass: for TB lines (kx in 2D, (kx, ky) in 3D), forward FFT
 // of every input slot, per-mode push, inverse FFT of the n_out field slots,
-// written back in place.  Shared memory per line: n_in*L staged spectra
-// (natural order) + one padded exchange buffer.
+// written back in place.  Shared memory per line: n_in staged slots of L values
+// and one extra exchange buffer; a slot doubles as the other exchange buffer
+// of its own transforms.  After its forward FFT a slot holds the spectrum at
+// positions sw<kLastCX>(t + T m), so the push and the inverse FFT's first
+// exchange only touch each thread's own positions.
 template <typename R, int L, int LAYOUT>
 __global__ void __launch_bounds__(FFTPlan<L>::kT > 256 ? FFTPlan<L>::kT : 256)
 k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   typedef typename Types<R>::C C;
   typedef FFTPlan<L> P;
   constexpr int T = P::kT;
+  constexpr int CXL = P::kLastCX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int t = threadIdx.x, g = threadIdx.y;
   const int line = blockIdx.x * blockDim.y + g;
   const bool valid = line < a.nlines;
-  C* st = reinterpret_cast<C*>(smem_raw) + g * (a.n_in * L + P::kBuf);
-  C* buf = st + a.n_in * L;
+  C* st = reinterpret_cast<C*>(smem_raw) + g * ((a.n_in + 1) * L);
+  C* bufB = st + a.n_in * L;
   C* spec = static_cast<C*>(a.spec);
+  __shared__ const void* twslot;
+  if (t == 0 && g == 0) twslot = tw;
 
   // stage every input slot of this line (cp.async, 16-byte chunks)
   {
@@ -403,28 +432,18 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   }
   C v[8];
   for (int c = 0; c < a.n_in; ++c) {
+    C* sl = st + c * L;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = st[c * L + t + T * m];
-    block_fft_fwd<R, L, 1>(v, buf, tw, t);
+    for (int m = 0; m < 8; ++m) v[m] = sl[t + T * m];
+    __syncthreads();  // the slot becomes an exchange buffer
+    ExBuf<C> ex{{sl, bufB}, 0, &twslot};
+    block_fft_fwd<R, L>(v, ex, tw, t);
 #pragma unroll
-    for (int m = 0; m < 8; ++m) st[c * L + t + T * m] = v[m];
+    for (int m = 0; m < 8; ++m) sl[sw<CXL>(t + T * m)] = v[m];
   }
 
-  // mode indices of this line
-  int mxi, myi;  // signed integer modes (Nyquist -> 0) of the line's fixed axes
-  int rowi;      // coefficient-table row
-  if (a.ndim == 2) {
-    mxi = (line == a.nx_half) ? 0 : line;
-    myi = 0;
-    rowi = line;
-  } else {
-    const int kx = line / a.ny, ky = line - kx * a.ny;
-    mxi = (kx == a.nx_half) ? 0 : kx;
-    const int nyh = a.ny >> 1;
-    myi = (ky == nyh) ? 0 : (ky < nyh ? ky : ky - a.ny);
-    rowi = kx * (nyh + 1) + (ky <= nyh ? ky : a.ny - ky);
-  }
-  if (!valid) rowi = 0;
+  int mxi, myi, rowi;
+  line_modes(a, valid ? line : 0, mxi, myi, rowi);
   const Coef<R>* trow = a.tab + (int64_t)rowi * a.tab_row;
 #pragma unroll 1
   for (int m = 0; m < 8; ++m) {
@@ -443,13 +462,15 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
     } else {
       mx = a.rx * R(mxi); my = a.ry * R(myi); mz = a.rz * R(ml);
     }
-    push_slots<R, LAYOUT>(st, L, l, f, mx, my, mz, a);
+    push_slots<R, LAYOUT>(st, L, sw<CXL>(l), f, mx, my, mz, a);
   }
 
   for (int c = 0; c < a.n_out; ++c) {
+    C* sl = st + c * L;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = st[c * L + t + T * m];
-    block_fft_inv<R, L, 1>(v, buf, tw, t);
+    for (int m = 0; m < 8; ++m) v[m] = sl[sw<CXL>(t + T * m)];
+    ExBuf<C> ex{{sl, bufB}, 0, &twslot};
+    block_fft_inv<R, L>(v, ex, tw, t);
     if (valid) {
       C* dst = spec + c * a.cs + (int64_t)line * L;
 #pragma unroll

@@ -4,4 +4,5 @@
 namespace psatd {
 template cudaError_t launch_line_push<float>(int, int, dim3, int, size_t, cudaStream_t,
                                               const PushArgs<float>&, const void*);
+
 }  // namespace psatd

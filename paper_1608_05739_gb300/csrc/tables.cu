@@ -2,7 +2,10 @@
 // to the step precision (FP32 keeps hi/lo pairs of the values that multiply
 // the field state every step).
 //
-// Twiddles of an axis of length n: W[j] = exp(-2 pi i j / n), j < n.
+// Twiddles of a length-L transform, in the order the FFT stages read them
+// (fft_core.cuh): for each stage s >= 1 (radix 8, span Ns), entry
+// (r-1) Ns + k holds W_L^(r k L/(8 Ns)); an R2C/C2R axis (N = 2L real points)
+// appends W_N^k, k < L, for the even/odd split.
 //
 // Coefficient octant: one entry per (|mx|, |my|, |mz|), |m_i| <= n_i/2, with
 // the Nyquist index of each axis taken as m_i = 0.  With the integer-mode
@@ -23,16 +26,40 @@
 
 namespace psatd {
 
-__global__ void k_twiddles(void* out, int n, int f32) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+__global__ void k_twiddles(void* out, int L, int r2c, int f32) {
+  int lg = 0;
+  while ((1 << lg) < L) ++lg;
+  const int r0 = (lg % 3 == 1) ? 2 : (lg % 3 == 2) ? 4 : 8;
+  const int nstage = L - r0;
+  const int total = nstage + (r2c ? L : 0);
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  double num, den;  // W = exp(-2 pi i num/den)
+  if (e < nstage) {
+    int off = 0, ns = r0;
+    num = 0.0;
+    den = (double)L;
+    while (true) {
+      const int size = 7 * ns;
+      if (e < off + size) {
+        const int r = (e - off) / ns + 1, k = (e - off) % ns;
+        num = (double)((long long)r * k * (L / (8 * ns)));
+        break;
+      }
+      off += size;
+      ns *= 8;
+    }
+  } else {
+    num = (double)(e - nstage);
+    den = 2.0 * (double)L;
+  }
   double s, c;
-  sincospi(-2.0 * (double)j / (double)n, &s, &c);
+  sincospi(-2.0 * num / den, &s, &c);
   if (f32) {
     const float ch = (float)c, sh = (float)s;
-    static_cast<float4*>(out)[j] = make_float4(ch, sh, (float)(c - (double)ch), (float)(s - (double)sh));
+    static_cast<float4*>(out)[e] = make_float4(ch, sh, (float)(c - (double)ch), (float)(s - (double)sh));
   } else {
-    static_cast<double2*>(out)[j] = make_double2(c, s);
+    static_cast<double2*>(out)[e] = make_double2(c, s);
   }
 }
 
@@ -116,8 +143,9 @@ __global__ void k_coefs(void* out, int f32, int e0, int e1, int e2, int nx, int 
   }
 }
 
-cudaError_t launch_twiddles(void* out, int n, bool f32, cudaStream_t st) {
-  k_twiddles<<<(n + 255) / 256, 256, 0, st>>>(out, n, f32 ? 1 : 0);
+cudaError_t launch_twiddles(void* out, int L, bool r2c, bool f32, cudaStream_t st) {
+  const int total = 2 * L;
+  k_twiddles<<<(total + 255) / 256, 256, 0, st>>>(out, L, r2c ? 1 : 0, f32 ? 1 : 0);
   return cudaGetLastError();
 }
 
