@@ -197,7 +197,7 @@ psatd_status alloc(psatd_plan p, void** ptr, size_t bytes, const char* what) {
 
 // lines per CTA for a transposing pass of length L with `nb` lines available
 int pick_log_tb(int L, int64_t nb, bool f32) {
-  const int T = L / 8;
+  const int T = L / row_ept(L);
   const int maxthr = f32 ? 512 : 256;
   int tb = 1;
   while (tb * 2 * T <= maxthr && tb * 2 <= 32 && tb * 2 <= nb) tb *= 2;
@@ -209,7 +209,7 @@ int pick_log_tb(int L, int64_t nb, bool f32) {
 size_t tpass_smem(int L, int log_tb, bool r2c, size_t csz) {
   const int tb = 1 << log_tb;
   const size_t nk = r2c ? (size_t)L + 1 : (size_t)L;
-  const size_t a = (size_t)tb * 2 * L, b = nk * (size_t)(tb + 1);
+  const size_t a = (size_t)tb * L, b = nk * (size_t)(tb + 1);
   return (a > b ? a : b) * csz;
 }
 
@@ -307,7 +307,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     a.s_a6 = (R)(1.0 / (p->d.eps0 * c * c * p->g0));
     const void* twl = p->tw[p->ndim == 3 ? 2 : 1];
     {
-      const int T = Lline / 8;
+      const int T = Lline / kPushEPT;
       const size_t per_line = ((size_t)p->n_in + 1) * (size_t)Lline * csz;
       int tb = 1;
       while (tb * 2 * T <= 256 && (size_t)(tb * 2) * per_line <= 100 * 1024 && tb * 2 <= nlines) tb *= 2;
@@ -430,7 +430,9 @@ psatd_status psatd_coeffs_init(psatd_plan p) {
   {
     TimedLaunch tl(p, K_TABLES);
     for (int i = 0; i < p->ndim; ++i) {
-      e = launch_twiddles(p->tw[i], i == 0 ? (int)(ns[0] / 2) : (int)ns[i], i == 0, p->f32, p->st);
+      const int L = i == 0 ? (int)(ns[0] / 2) : (int)ns[i];
+      const bool push_axis = (i == p->ndim - 1) && i > 0;
+      e = launch_twiddles(p->tw[i], L, push_axis ? kPushEPT : row_ept(L), i == 0, p->f32, p->st);
       if (e != cudaSuccess) return cuda_fail(p, e, "twiddle table launch");
     }
     const double N = (double)p->nx * (double)p->ny * (double)p->nz;
@@ -667,7 +669,9 @@ extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_f
   // the tables are rebuilt by every call (the array keeps the previous call's contents);
   // the spectra need no clearing: the first pass overwrites them entirely
   for (int i = 0; i < p.ndim; ++i) {
-    e = launch_twiddles(p.tw[i], i == 0 ? (int)(ns[0] / 2) : (int)ns[i], i == 0, p.f32, p.st);
+    const int L = i == 0 ? (int)(ns[0] / 2) : (int)ns[i];
+    const bool push_axis = (i == p.ndim - 1) && i > 0;
+    e = launch_twiddles(p.tw[i], L, push_axis ? kPushEPT : row_ept(L), i == 0, p.f32, p.st);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "twiddle table launch");
   }
   const double N = (double)p.nx * (double)p.ny * (double)p.nz;

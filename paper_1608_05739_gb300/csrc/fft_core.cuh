@@ -122,6 +122,102 @@ __device__ __forceinline__ void dft8_adj(C* a) {
   a[4] = csub(b0, c0); a[5] = csub(b1, c1); a[6] = csub(b2, c2); a[7] = csub(b3, c3);
 }
 
+// Multiplication by constants of the radix-16 DFT: z (p + i q) with p, q the
+// double-precision values, applied as hi + lo pairs in float.
+template <class C> struct KMul;
+template <> struct KMul<float2> {
+  template <int P_NUM>
+  static __device__ __forceinline__ float2 mul(float2 z, double p, double q) {
+    const float ph = (float)p, pl = (float)(p - (double)ph), qh = (float)q, ql = (float)(q - (double)qh);
+    float re = z.x * pl;
+    re = fmaf(-z.y, ql, re);
+    re = fmaf(-z.y, qh, re);
+    re = fmaf(z.x, ph, re);
+    float im = z.x * ql;
+    im = fmaf(z.y, pl, im);
+    im = fmaf(z.y, ph, im);
+    im = fmaf(z.x, qh, im);
+    return make_float2(re, im);
+  }
+};
+template <> struct KMul<double2> {
+  template <int P_NUM>
+  static __device__ __forceinline__ double2 mul(double2 z, double p, double q) {
+    return make_double2(fma(z.x, p, -z.y * q), fma(z.x, q, z.y * p));
+  }
+};
+constexpr double kCos8 = 0.92387953251128675613;  // cos(pi/8)
+constexpr double kSin8 = 0.38268343236508977173;  // sin(pi/8)
+
+// z * w16^e (forward, w16 = exp(-2 pi i/16)) or z * conj(w16^e) (adjoint), e in {1,2,3,4,6,9}
+template <int E, bool ADJ, class C>
+__device__ __forceinline__ C w16mul(C z) {
+  constexpr double sg = ADJ ? 1.0 : -1.0;  // sign of the imaginary part of the constant
+  if constexpr (E == 1) return KMul<C>::template mul<1>(z, kCos8, sg * kSin8);
+  else if constexpr (E == 3) return KMul<C>::template mul<3>(z, kSin8, sg * kCos8);
+  else if constexpr (E == 9) { const C u = KMul<C>::template mul<1>(z, kCos8, sg * kSin8); return mkc(-u.x, -u.y); }
+  else if constexpr (E == 4) return ADJ ? cmul_pi(z) : cmul_mi(z);
+  else if constexpr (E == 2) {
+    if constexpr (ADJ) return mkc(rsqrt2_mul(z.x - z.y), rsqrt2_mul(z.x + z.y));
+    else return mkc(rsqrt2_mul(z.x + z.y), rsqrt2_mul(z.y - z.x));
+  } else {  // E == 6
+    if constexpr (ADJ) return mkc(rsqrt2_mul(-(z.x + z.y)), rsqrt2_mul(z.x - z.y));
+    else return mkc(rsqrt2_mul(z.y - z.x), rsqrt2_mul(-(z.x + z.y)));
+  }
+}
+
+// Radix-16 forward DFT, natural order in and out: 4 x 4 decomposition
+// (radix-4 DFTs over the stride-4 columns, twiddles w16^(r1 k2), radix-4 DFTs
+// over the rows, transposed read-out).
+template <class C>
+__device__ __forceinline__ void dft16_fwd(C* a) {
+#pragma unroll
+  for (int r1 = 0; r1 < 4; ++r1) dft4<false>(a[r1], a[r1 + 4], a[r1 + 8], a[r1 + 12]);
+  a[5] = w16mul<1, false>(a[5]);
+  a[9] = w16mul<2, false>(a[9]);
+  a[13] = w16mul<3, false>(a[13]);
+  a[6] = w16mul<2, false>(a[6]);
+  a[10] = w16mul<4, false>(a[10]);
+  a[14] = w16mul<6, false>(a[14]);
+  a[7] = w16mul<3, false>(a[7]);
+  a[11] = w16mul<6, false>(a[11]);
+  a[15] = w16mul<9, false>(a[15]);
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2) dft4<false>(a[4 * k2], a[4 * k2 + 1], a[4 * k2 + 2], a[4 * k2 + 3]);
+  C y[16];
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2)
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) y[k2 + 4 * k1] = a[4 * k2 + k1];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = y[i];
+}
+
+// Exact adjoint of dft16_fwd.
+template <class C>
+__device__ __forceinline__ void dft16_adj(C* a) {
+  C x[16];
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2)
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) x[4 * k2 + k1] = a[k2 + 4 * k1];
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2) dft4<true>(x[4 * k2], x[4 * k2 + 1], x[4 * k2 + 2], x[4 * k2 + 3]);
+  x[5] = w16mul<1, true>(x[5]);
+  x[9] = w16mul<2, true>(x[9]);
+  x[13] = w16mul<3, true>(x[13]);
+  x[6] = w16mul<2, true>(x[6]);
+  x[10] = w16mul<4, true>(x[10]);
+  x[14] = w16mul<6, true>(x[14]);
+  x[7] = w16mul<3, true>(x[7]);
+  x[11] = w16mul<6, true>(x[11]);
+  x[15] = w16mul<9, true>(x[15]);
+#pragma unroll
+  for (int r1 = 0; r1 < 4; ++r1) dft4<true>(x[r1], x[r1 + 4], x[r1 + 8], x[r1 + 12]);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) a[i] = x[i];
+}
+
 template <int RS, bool ADJ, class C>
 __device__ __forceinline__ void butterfly(C* a) {
   if constexpr (RS == 2) {
@@ -130,22 +226,32 @@ __device__ __forceinline__ void butterfly(C* a) {
     a[1] = d;
   } else if constexpr (RS == 4) {
     dft4<ADJ>(a[0], a[1], a[2], a[3]);
-  } else {
+  } else if constexpr (RS == 8) {
     if constexpr (ADJ) dft8_adj(a); else dft8_fwd(a);
+  } else {
+    if constexpr (ADJ) dft16_adj(a); else dft16_fwd(a);
   }
 }
 
 // ---------------------------------------------------------------- stage plan
 __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v >> 1); }
 
+// Elements per thread of the transposing row/line passes (16 from L = 16 on)
+// and of the fused last-axis pass (8).
 template <int L>
+struct RowEPT { static constexpr int value = L >= 16 ? 16 : 8; };
+
+template <int L, int EPT = 8>
 struct FFTPlan {
+  static constexpr int kEPT = EPT;
   static constexpr int kLog = ilog2(L);
-  static constexpr int kR0 = (kLog % 3 == 1) ? 2 : (kLog % 3 == 2) ? 4 : 8;
-  static constexpr int kStages = (kR0 == 8) ? kLog / 3 : kLog / 3 + 1;
-  static constexpr int kT = L / 8;
+  static constexpr int kB = ilog2(EPT);
+  static constexpr int kRem = kLog % kB;
+  static constexpr int kR0 = kRem ? (1 << kRem) : EPT;
+  static constexpr int kStages = kRem ? kLog / kB + 1 : kLog / kB;
+  static constexpr int kT = L / EPT;
   static constexpr int kBuf = L;  // exchange buffer (XOR-swizzled, no padding)
-  __host__ __device__ static constexpr int radix(int s) { return s == 0 ? kR0 : 8; }
+  __host__ __device__ static constexpr int radix(int s) { return s == 0 ? kR0 : EPT; }
   __host__ __device__ static constexpr int span(int s) {  // Ns of stage s
     int ns = 1;
     for (int i = 0; i < s; ++i) ns *= radix(i);
@@ -161,11 +267,11 @@ struct FFTPlan {
   static constexpr int kTwEntries = L - kR0;
   // XOR multiplier of the exchange written by stage s (bank-conflict free for
   // the Stockham write pattern of that stage and the contiguous reads after it)
-  __host__ __device__ static constexpr int swz(int s) { return span(s) == 1 ? 1 : 10; }
+  __host__ __device__ static constexpr int swz(int s) { return EPT == 16 ? 1 : (span(s) == 1 ? 1 : 10); }
   // swizzle of the last exchange: forward output / inverse input positions
   // sw<kLastCX>(t + T m) are each touched by their own thread only
   static constexpr int kLastCX = (kStages >= 2) ? swz(kStages - 2) : 0;
-  static_assert(L >= 8 && (L & (L - 1)) == 0, "L must be a power of two >= 8");
+  static_assert(L >= EPT && (L & (L - 1)) == 0, "L must be a power of two >= EPT");
 };
 
 // element i of an exchange buffer, rows of 16 elements (128 B) XOR-swizzled
@@ -178,14 +284,18 @@ __device__ __forceinline__ int sw(int i) { return i ^ (((i >> 4) * CX) & 15); }
 // barrier): each stage reads it back, which ties that stage's twiddle loads to
 // the stage (the compiler cannot prefetch every stage's twiddles of every
 // transform in a kernel into registers).
+// With b[0] == b[1] (one buffer, `single`), next() adds the barrier that lets
+// the previous exchange's reads finish before the buffer is overwritten.
 template <class C>
 struct ExBuf {
   C* b[2];
   int cur;
   const void* const* twslot;
+  bool single;
   __device__ __forceinline__ C* next() {
     C* p = b[cur];
     cur ^= 1;
+    if (single) __syncthreads();
     return p;
   }
 };
@@ -201,12 +311,12 @@ __device__ __forceinline__ const typename Types<R>::W* stage_tw(const ExBuf<C>& 
 // so the threads of a warp read consecutive entries.
 
 // One forward stage.
-template <typename R, int L, int S>
-__device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[8], ExBuf<typename Types<R>::C>& ex,
+template <typename R, int L, int EPT, int S>
+__device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
                                           const typename Types<R>::W* __restrict__ tw, int t) {
   typedef typename Types<R>::C C;
-  typedef FFTPlan<L> P;
-  constexpr int RS = P::radix(S), NS = P::span(S), Q = 8 / RS, T = P::kT;
+  typedef FFTPlan<L, EPT> P;
+  constexpr int RS = P::radix(S), NS = P::span(S), Q = EPT / RS, T = P::kT;
   constexpr bool LAST = (S == P::kStages - 1);
   constexpr int CX = P::swz(S);
   C* buf = nullptr;
@@ -237,24 +347,24 @@ __device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[8], ExBuf<ty
   if constexpr (!LAST) {
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = buf[sw<CX>(t + T * m)];
+    for (int m = 0; m < EPT; ++m) v[m] = buf[sw<CX>(t + T * m)];
   }
 }
 
 // Adjoint of fwd_stage<S>.
-template <typename R, int L, int S>
-__device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[8], ExBuf<typename Types<R>::C>& ex,
+template <typename R, int L, int EPT, int S>
+__device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
                                           const typename Types<R>::W* __restrict__ tw, int t) {
   typedef typename Types<R>::C C;
-  typedef FFTPlan<L> P;
-  constexpr int RS = P::radix(S), NS = P::span(S), Q = 8 / RS, T = P::kT;
+  typedef FFTPlan<L, EPT> P;
+  constexpr int RS = P::radix(S), NS = P::span(S), Q = EPT / RS, T = P::kT;
   constexpr bool FIRST = (S == P::kStages - 1);
   constexpr int CX = P::swz(S);
   C* buf = nullptr;
   if constexpr (!FIRST) {
     buf = ex.next();
 #pragma unroll
-    for (int m = 0; m < 8; ++m) buf[sw<CX>(t + T * m)] = v[m];
+    for (int m = 0; m < EPT; ++m) buf[sw<CX>(t + T * m)] = v[m];
     __syncthreads();
   }
   asm volatile("" : "+r"(t)::"memory");  // stage boundary (see fwd_stage)
@@ -282,32 +392,32 @@ __device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[8], ExBuf<ty
   }
 }
 
-template <typename R, int L, int... S>
-__device__ __forceinline__ void fft_fwd_seq(typename Types<R>::C (&v)[8], ExBuf<typename Types<R>::C>& ex,
+template <typename R, int L, int EPT, int... S>
+__device__ __forceinline__ void fft_fwd_seq(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
                                             const typename Types<R>::W* tw, int t,
                                             std::integer_sequence<int, S...>) {
-  (fwd_stage<R, L, S>(v, ex, tw, t), ...);
+  (fwd_stage<R, L, EPT, S>(v, ex, tw, t), ...);
 }
-template <typename R, int L, int... S>
-__device__ __forceinline__ void fft_inv_seq(typename Types<R>::C (&v)[8], ExBuf<typename Types<R>::C>& ex,
+template <typename R, int L, int EPT, int... S>
+__device__ __forceinline__ void fft_inv_seq(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
                                             const typename Types<R>::W* tw, int t,
                                             std::integer_sequence<int, S...>) {
-  (inv_stage<R, L, FFTPlan<L>::kStages - 1 - S>(v, ex, tw, t), ...);
+  (inv_stage<R, L, EPT, FFTPlan<L, EPT>::kStages - 1 - S>(v, ex, tw, t), ...);
 }
 
-// Forward DFT of length L: v holds x[t + T m] on entry, X[t + T m] on exit.
-// Every thread of the block must call it (block-wide barriers inside); the
-// exchanges alternate between the two buffers of `ex`.
-template <typename R, int L>
-__device__ __forceinline__ void block_fft_fwd(typename Types<R>::C (&v)[8], ExBuf<typename Types<R>::C>& ex,
+// Forward DFT of length L: v holds x[t + T m] on entry, X[t + T m] on exit
+// (T = L/EPT, m < EPT).  Every thread of the block must call it (block-wide
+// barriers inside); the exchanges alternate between the two buffers of `ex`.
+template <typename R, int L, int EPT>
+__device__ __forceinline__ void block_fft_fwd(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
                                               const typename Types<R>::W* tw, int t) {
-  fft_fwd_seq<R, L>(v, ex, tw, t, std::make_integer_sequence<int, FFTPlan<L>::kStages>{});
+  fft_fwd_seq<R, L, EPT>(v, ex, tw, t, std::make_integer_sequence<int, FFTPlan<L, EPT>::kStages>{});
 }
 // Unnormalised inverse DFT (adjoint of block_fft_fwd).
-template <typename R, int L>
-__device__ __forceinline__ void block_fft_inv(typename Types<R>::C (&v)[8], ExBuf<typename Types<R>::C>& ex,
+template <typename R, int L, int EPT>
+__device__ __forceinline__ void block_fft_inv(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
                                               const typename Types<R>::W* tw, int t) {
-  fft_inv_seq<R, L>(v, ex, tw, t, std::make_integer_sequence<int, FFTPlan<L>::kStages>{});
+  fft_inv_seq<R, L, EPT>(v, ex, tw, t, std::make_integer_sequence<int, FFTPlan<L, EPT>::kStages>{});
 }
 
 }  // namespace psatd

@@ -19,7 +19,7 @@ template <typename R, int L>
 static cudaError_t fwd_T_L(bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io,
                            const void* tw, int64_t a, int64_t b, int64_t c, int64_t d) {
   typedef typename Types<R>::W W;
-  const dim3 block(FFTPlan<L>::kT, 1u << g.log_tb);
+  const dim3 block(FFTPlan<L, RowEPT<L>::value>::kT, 1u << g.log_tb);
   cudaError_t e;
   if (r2c) {
     if constexpr (L <= 2048) {
@@ -41,7 +41,7 @@ template <typename R, int L>
 static cudaError_t inv_T_L(bool c2r, const PassGeom& g, cudaStream_t st, const LineIO& io,
                            const void* tw, int64_t a, int64_t b, int64_t c, int64_t d) {
   typedef typename Types<R>::W W;
-  const dim3 block(FFTPlan<L>::kT, 1u << g.log_tb);
+  const dim3 block(FFTPlan<L, RowEPT<L>::value>::kT, 1u << g.log_tb);
   cudaError_t e;
   if (c2r) {
     if constexpr (L <= 2048) {
@@ -63,7 +63,7 @@ template <typename R, int L>
 static cudaError_t push_L(int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
                           const PushArgs<R>& a, const void* tw) {
   typedef typename Types<R>::W W;
-  const dim3 block(FFTPlan<L>::kT, tb);
+  const dim3 block(FFTPlan<L, 8>::kT, tb);
   cudaError_t e;
 #define PSATD_PUSH_CASE(LAY)                                                   \
   case LAY: {                                                                  \

@@ -60,11 +60,12 @@ struct PushArgs {
 // with b contiguous: out[a1] + a0*out_sa0 + k*out_sk + b.  R2C: the input rows
 // are real (length 2L), the output has L+1 bins (half spectrum).
 template <typename R, int L, bool R2C>
-__global__ void __launch_bounds__(512) k_fwd_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
                                                int64_t in_sa0, int64_t in_sb, int64_t out_sa0,
                                                int64_t out_sk, int log_tb) {
   typedef typename Types<R>::C C;
-  typedef FFTPlan<L> P;
+  constexpr int EPT = RowEPT<L>::value;
+  typedef FFTPlan<L, EPT> P;
   constexpr int T = P::kT;
   constexpr int NK = R2C ? L + 1 : L;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -75,9 +76,9 @@ __global__ void __launch_bounds__(512) k_fwd_T(LineIO io, const typename Types<R
   const int a0 = blockIdx.y, a1 = blockIdx.z;
   __shared__ const void* twslot;
   if (t == 0 && g == 0) twslot = tw;
-  ExBuf<C> ex{{smem + g * 2 * L, smem + g * 2 * L + L}, 0, &twslot};
+  ExBuf<C> ex{{smem + g * L, smem + g * L}, 0, &twslot, true};  // one exchange buffer per line
 
-  C v[8];
+  C v[EPT];
   {
     const C* row;
     if constexpr (R2C)
@@ -85,10 +86,10 @@ __global__ void __launch_bounds__(512) k_fwd_T(LineIO io, const typename Types<R
     else
       row = static_cast<const C*>(io.in[a1]) + a0 * in_sa0 + b * in_sb;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = row[t + T * m];
+    for (int m = 0; m < EPT; ++m) v[m] = row[t + T * m];
   }
   if constexpr (P::kStages == 1) __syncthreads();  // twslot visible (else the first exchange's barrier)
-  block_fft_fwd<R, L>(v, ex, tw, t);
+  block_fft_fwd<R, L, EPT>(v, ex, tw, t);
 
   C* tile = smem;  // [NK][TB + 1], aliases the exchange buffers
   const int tp = TB + 1;
@@ -96,13 +97,13 @@ __global__ void __launch_bounds__(512) k_fwd_T(LineIO io, const typename Types<R
     // X[k] = Fe[k] + W_N^k Fo[k] with Fe = (Z[k] + Z*[L-k])/2, Fo = (Z[k] - Z*[L-k])/(2i)
     C* zb = ex.next();
 #pragma unroll
-    for (int m = 0; m < 8; ++m) zb[sw<1>(t + T * m)] = v[m];
+    for (int m = 0; m < EPT; ++m) zb[sw<1>(t + T * m)] = v[m];
     __syncthreads();
     const typename Types<R>::W* wn = tw + P::kTwEntries;  // W_N^k, N = 2L
-    C X[8];
+    C X[EPT];
     C XL = mkc(R(0), R(0));
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
+    for (int m = 0; m < EPT; ++m) {
       const int k = t + T * m;
       const C zk = zb[sw<1>(k)];
       const C zm = cconj(zb[sw<1>((L - k) & (L - 1))]);
@@ -113,12 +114,12 @@ __global__ void __launch_bounds__(512) k_fwd_T(LineIO io, const typename Types<R
     }
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 8; ++m) tile[(t + T * m) * tp + g] = X[m];
+    for (int m = 0; m < EPT; ++m) tile[(t + T * m) * tp + g] = X[m];
     if (t == 0) tile[L * tp + g] = XL;
   } else {
     __syncthreads();
 #pragma unroll
-    for (int m = 0; m < 8; ++m) tile[(t + T * m) * tp + g] = v[m];
+    for (int m = 0; m < EPT; ++m) tile[(t + T * m) * tp + g] = v[m];
   }
   __syncthreads();
   C* ob = static_cast<C*>(io.out[a1]) + a0 * out_sa0 + (int64_t)blockIdx.x * TB;
@@ -135,11 +136,12 @@ __global__ void __launch_bounds__(512) k_fwd_T(LineIO io, const typename Types<R
 // contiguously to out[a1] + a0*out_sa0 + b*out_sb.  C2R: L+1 Hermitian bins
 // in, real rows of length 2L out (unnormalised).
 template <typename R, int L, bool C2R>
-__global__ void __launch_bounds__(512) k_inv_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_inv_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
                                                int64_t in_sa0, int64_t in_sk, int64_t out_sa0,
                                                int64_t out_sb, int log_tb) {
   typedef typename Types<R>::C C;
-  typedef FFTPlan<L> P;
+  constexpr int EPT = RowEPT<L>::value;
+  typedef FFTPlan<L, EPT> P;
   constexpr int T = P::kT;
   constexpr int NK = C2R ? L + 1 : L;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -161,12 +163,12 @@ __global__ void __launch_bounds__(512) k_inv_T(LineIO io, const typename Types<R
     }
   }
   __syncthreads();
-  C v[8];
+  C v[EPT];
   if constexpr (C2R) {
     // Z[k] = Fe + i Fo, Fe = X[k] + X*[L-k], Fo = (X[k] - X*[L-k]) conj(W_N^k)
     const typename Types<R>::W* wn = tw + P::kTwEntries;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
+    for (int m = 0; m < EPT; ++m) {
       const int k = t + T * m;
       const C xk = tile[k * tp + g];
       const C xm = cconj(tile[(L - k) * tp + g]);
@@ -176,18 +178,18 @@ __global__ void __launch_bounds__(512) k_inv_T(LineIO io, const typename Types<R
     }
   } else {
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = tile[(t + T * m) * tp + g];
+    for (int m = 0; m < EPT; ++m) v[m] = tile[(t + T * m) * tp + g];
   }
   __syncthreads();
-  ExBuf<C> ex{{smem + g * 2 * L, smem + g * 2 * L + L}, 0, &twslot};
-  block_fft_inv<R, L>(v, ex, tw, t);
+  ExBuf<C> ex{{smem + g * L, smem + g * L}, 0, &twslot, true};  // one exchange buffer per line
+  block_fft_inv<R, L, EPT>(v, ex, tw, t);
   C* row;
   if constexpr (C2R)
     row = reinterpret_cast<C*>(static_cast<R*>(io.out[a1]) + a0 * out_sa0 + b * out_sb);
   else
     row = static_cast<C*>(io.out[a1]) + a0 * out_sa0 + b * out_sb;
 #pragma unroll
-  for (int m = 0; m < 8; ++m) row[t + T * m] = v[m];
+  for (int m = 0; m < EPT; ++m) row[t + T * m] = v[m];
 }
 
 // ---------------------------------------------------------------- the push
@@ -400,10 +402,10 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // positions sw<kLastCX>(t + T m), so the push and the inverse FFT's first
 // exchange only touch each thread's own positions.
 template <typename R, int L, int LAYOUT>
-__global__ void __launch_bounds__(FFTPlan<L>::kT > 256 ? FFTPlan<L>::kT : 256)
+__global__ void __launch_bounds__(FFTPlan<L, 8>::kT > 256 ? FFTPlan<L, 8>::kT : 256)
 k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   typedef typename Types<R>::C C;
-  typedef FFTPlan<L> P;
+  typedef FFTPlan<L, 8> P;
   constexpr int T = P::kT;
   constexpr int CXL = P::kLastCX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -436,8 +438,8 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = sl[t + T * m];
     __syncthreads();  // the slot becomes an exchange buffer
-    ExBuf<C> ex{{sl, bufB}, 0, &twslot};
-    block_fft_fwd<R, L>(v, ex, tw, t);
+    ExBuf<C> ex{{sl, bufB}, 0, &twslot, false};
+    block_fft_fwd<R, L, 8>(v, ex, tw, t);
 #pragma unroll
     for (int m = 0; m < 8; ++m) sl[sw<CXL>(t + T * m)] = v[m];
   }
@@ -469,8 +471,8 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
     C* sl = st + c * L;
 #pragma unroll
     for (int m = 0; m < 8; ++m) v[m] = sl[sw<CXL>(t + T * m)];
-    ExBuf<C> ex{{sl, bufB}, 0, &twslot};
-    block_fft_inv<R, L>(v, ex, tw, t);
+    ExBuf<C> ex{{sl, bufB}, 0, &twslot, false};
+    block_fft_inv<R, L, 8>(v, ex, tw, t);
     if (valid) {
       C* dst = spec + c * a.cs + (int64_t)line * L;
 #pragma unroll

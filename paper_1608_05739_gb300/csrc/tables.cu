@@ -2,10 +2,10 @@
 // to the step precision (FP32 keeps hi/lo pairs of the values that multiply
 // the field state every step).
 //
-// Twiddles of a length-L transform, in the order the FFT stages read them
-// (fft_core.cuh): for each stage s >= 1 (radix 8, span Ns), entry
-// (r-1) Ns + k holds W_L^(r k L/(8 Ns)); an R2C/C2R axis (N = 2L real points)
-// appends W_N^k, k < L, for the even/odd split.
+// Twiddles of a length-L transform with EPT elements per thread, in the order
+// the FFT stages read them (fft_core.cuh): for each stage s >= 1 (radix EPT,
+// span Ns), entry (r-1) Ns + k holds W_L^(r k L/(EPT Ns)); an R2C/C2R axis
+// (N = 2L real points) appends W_N^k, k < L, for the even/odd split.
 //
 // Coefficient octant: one entry per (|mx|, |my|, |mz|), |m_i| <= n_i/2, with
 // the Nyquist index of each axis taken as m_i = 0.  With the integer-mode
@@ -26,10 +26,12 @@
 
 namespace psatd {
 
-__global__ void k_twiddles(void* out, int L, int r2c, int f32) {
-  int lg = 0;
+__global__ void k_twiddles(void* out, int L, int ept, int r2c, int f32) {
+  int lg = 0, b = 0;
   while ((1 << lg) < L) ++lg;
-  const int r0 = (lg % 3 == 1) ? 2 : (lg % 3 == 2) ? 4 : 8;
+  while ((1 << b) < ept) ++b;
+  const int rem = lg % b;
+  const int r0 = rem ? (1 << rem) : ept;
   const int nstage = L - r0;
   const int total = nstage + (r2c ? L : 0);
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -40,14 +42,14 @@ __global__ void k_twiddles(void* out, int L, int r2c, int f32) {
     num = 0.0;
     den = (double)L;
     while (true) {
-      const int size = 7 * ns;
+      const int size = (ept - 1) * ns;
       if (e < off + size) {
         const int r = (e - off) / ns + 1, k = (e - off) % ns;
-        num = (double)((long long)r * k * (L / (8 * ns)));
+        num = (double)((long long)r * k * (L / (ept * ns)));
         break;
       }
       off += size;
-      ns *= 8;
+      ns *= ept;
     }
   } else {
     num = (double)(e - nstage);
@@ -143,9 +145,9 @@ __global__ void k_coefs(void* out, int f32, int e0, int e1, int e2, int nx, int 
   }
 }
 
-cudaError_t launch_twiddles(void* out, int L, bool r2c, bool f32, cudaStream_t st) {
+cudaError_t launch_twiddles(void* out, int L, int ept, bool r2c, bool f32, cudaStream_t st) {
   const int total = 2 * L;
-  k_twiddles<<<(total + 255) / 256, 256, 0, st>>>(out, L, r2c ? 1 : 0, f32 ? 1 : 0);
+  k_twiddles<<<(total + 255) / 256, 256, 0, st>>>(out, L, ept, r2c ? 1 : 0, f32 ? 1 : 0);
   return cudaGetLastError();
 }
 
