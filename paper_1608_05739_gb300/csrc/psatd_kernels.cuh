@@ -418,6 +418,16 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   __shared__ const void* twslot;
   if (t == 0 && g == 0) twslot = tw;
 
+  int mxi, myi, rowi;
+  line_modes(a, valid ? line : 0, mxi, myi, rowi);
+  const Coef<R>* trow = a.tab + (int64_t)rowi * a.tab_row;
+  // the push needs eight coefficient entries per thread: start bringing them
+  // into L2 now, so that its loads do not wait on DRAM one mode after another
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int l = t + T * m;
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(trow + ((l <= L / 2) ? l : L - l)));
+  }
   // stage every input slot of this line (cp.async, 16-byte chunks)
   {
     constexpr int CH = (L * (int)sizeof(C)) / 16;  // chunks per slot
@@ -444,27 +454,30 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
     for (int m = 0; m < 8; ++m) sl[sw<CXL>(t + T * m)] = v[m];
   }
 
-  int mxi, myi, rowi;
-  line_modes(a, valid ? line : 0, mxi, myi, rowi);
-  const Coef<R>* trow = a.tab + (int64_t)rowi * a.tab_row;
+  // push, two modes per iteration (both coefficient loads issued together)
 #pragma unroll 1
-  for (int m = 0; m < 8; ++m) {
-    const int l = t + T * m;
-    const int am = (l <= L / 2) ? l : L - l;             // |m| along the line axis
-    const int ml = (l == L / 2) ? 0 : (l < L / 2 ? l : l - L);
-    CoefReg<R> f;
-    {
-      const Coef<R> q = trow[am];
-      f.C_h = q.C_h; f.C_l = q.C_l; f.S_h = q.S_h; f.S_l = q.S_l;
-      f.A1 = q.A1; f.A4 = q.A4; f.B1 = q.B1; f.B2 = q.B2;
+  for (int m0 = 0; m0 < 8; m0 += 2) {
+    Coef<R> q[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int l = t + T * (m0 + h);
+      q[h] = trow[(l <= L / 2) ? l : L - l];  // |m| along the line axis
     }
-    R mx, my, mz;
-    if (a.ndim == 2) {
-      mx = a.rx * R(mxi); my = a.ry * R(ml); mz = R(0);
-    } else {
-      mx = a.rx * R(mxi); my = a.ry * R(myi); mz = a.rz * R(ml);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int l = t + T * (m0 + h);
+      const int ml = (l == L / 2) ? 0 : (l < L / 2 ? l : l - L);
+      CoefReg<R> f;
+      f.C_h = q[h].C_h; f.C_l = q[h].C_l; f.S_h = q[h].S_h; f.S_l = q[h].S_l;
+      f.A1 = q[h].A1; f.A4 = q[h].A4; f.B1 = q[h].B1; f.B2 = q[h].B2;
+      R mx, my, mz;
+      if (a.ndim == 2) {
+        mx = a.rx * R(mxi); my = a.ry * R(ml); mz = R(0);
+      } else {
+        mx = a.rx * R(mxi); my = a.ry * R(myi); mz = a.rz * R(ml);
+      }
+      push_slots<R, LAYOUT>(st, L, sw<CXL>(l), f, mx, my, mz, a);
     }
-    push_slots<R, LAYOUT>(st, L, sw<CXL>(l), f, mx, my, mz, a);
   }
 
   for (int c = 0; c < a.n_out; ++c) {
@@ -480,5 +493,6 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
     }
   }
 }
+
 
 }  // namespace psatd
