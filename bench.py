@@ -38,21 +38,27 @@ NX = NY = 2048
 LAM_CELLS = 64
 WORKLOAD = ("2D TE PSATD 2048x2048 FP32, J-form current-sheet drive J_y(x,t), dx=lambda/64, "
             "c dt=dx/sqrt(2), a=0.9c, w=2dx")
-# algorithmic bytes per cell and launch (2D TE J-form, FP32: 5 input components,
-# 3 outputs, complex half spectrum of (nx/2+1) x ny 8-byte values per component,
-# coefficient table of (nx/2+1) x (ny/2+1) 32-byte entries)
+# algorithmic bytes per launch of each PSATD pass: every input component read
+# once and every output written once per pass, complex half spectra of
+# (nx/2+1) ny nz values (8 B in FP32), plus the coefficient table (one 32-byte
+# entry per (nx/2+1)(ny/2+1)(nz/2+1) octant point) read by the fused pass.
 N_IN, N_OUT = 5, 3
 
 
-def algorithmic_bytes():
-    cells = NX * NY
-    half = (NX // 2 + 1) * NY
-    tab = (NX // 2 + 1) * (NY // 2 + 1) * 32
-    return {
-        "fwd_x_r2c": N_IN * cells * 4 + N_IN * half * 8,
-        "line_fft_push": N_IN * half * 8 + N_OUT * half * 8 + tab,
-        "inv_x_c2r": N_OUT * half * 8 + N_OUT * cells * 4,
+def algorithmic_bytes(nx=NX, ny=NY, nz=1, n_in=N_IN, n_out=N_OUT, real=4):
+    cells = nx * ny * nz
+    half = (nx // 2 + 1) * ny * nz
+    cplx = 2 * real
+    tab = (nx // 2 + 1) * (ny // 2 + 1) * (nz // 2 + 1 if nz > 1 else 1) * 8 * real
+    out = {
+        "fwd_x_r2c": n_in * cells * real + n_in * half * cplx,
+        "line_fft_push": n_in * half * cplx + n_out * half * cplx + tab,
+        "inv_x_c2r": n_out * half * cplx + n_out * cells * real,
     }
+    if nz > 1:
+        out["fwd_y_c2c"] = 2 * n_in * half * cplx
+        out["inv_y_c2c"] = 2 * n_out * half * cplx
+    return out
 
 
 def sheet_profile(n, dt, dx):
@@ -196,10 +202,15 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=30.0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="te2048", choices=["te2048", "3d256", "fdtd-yee", "fdtd-ckc"],
+                    help="te2048 (default) is the metric's configuration; the others are side measurements")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+        return
+    if args.workload != "te2048":
+        run_side_workload(args)
         return
 
     import torch
@@ -334,6 +345,94 @@ def main():
     plan.destroy()
     if world > 1:
         dist.destroy_process_group()
+
+
+def timed_steps(step, steps, warmup, flush, stream):
+    """Run ``warmup`` untimed steps, then ``steps`` steps each preceded by an L2
+    flush and bracketed by CUDA events on ``stream``; returns total ms and clocks."""
+    import torch
+    for n in range(warmup):
+        step(n)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    for s in range(steps):
+        flush.zero_()
+        starts[s].record(stream)
+        step(warmup + s)
+        ends[s].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    return sum(starts[s].elapsed_time(ends[s]) for s in range(steps)), clk
+
+
+def run_side_workload(args):
+    """Side measurements (not the metric's line): the 3D step of the Gaussian-charge
+    workload and the FDTD comparators on the 2048^2 TE grid."""
+    import torch
+    from paper_1608_05739_gb300 import build as bld
+    from paper_1608_05739_gb300 import capi, synth
+    bld.build()
+    capi.load()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    line = {"metric": METRIC + " (side measurement)", "unit": "cell-steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f32", "data": "synthetic"}
+    if args.workload == "3d256":
+        n = 256
+        d = 1.0
+        dt = 0.5 * d
+        r0, r1, J, E = synth.gaussian_charges_torch((n, n, n), (d, d, d), dt, n_charges=64, seed=1610, device=dev)
+        E = [E[i].contiguous() for i in range(3)]
+        B = [torch.zeros(n, n, n, device=dev) for _ in range(3)]
+        J = [J[i].contiguous() for i in range(3)]
+        plan = capi.Plan((n, n, n), (d, d, d), dt, layout="3d6", prec="fp32", src="rho", stream=stream)
+        plan.set_timing(True)
+        ms, clk = timed_steps(lambda i: plan.step(E, B, J, r0, r1), args.steps, args.warmup, flush, stream)
+        kt = plan.kernel_times()
+        alg = algorithmic_bytes(n, n, n, 11, 6)
+        cells = n ** 3
+        per = {k: v[1] / v[0] for k, v in kt.items()}
+        line.update({
+            "value": cells * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+            "config": {"workload": "3D PSATD 256^3 FP32, rho-form, 64 moving Gaussian charges (sigma = 3 dx, "
+                                   "|v| < 0.5c), c dt = 0.5 dx, sources held over the run",
+                       "l2": "flushed before every timed step"},
+            "per_kernel_ms": per,
+            "per_kernel_gbs": {k: alg[k] / (per[k] * 1e-3) / 1e9 for k in per},
+            "step_algorithmic_bytes_per_cell": sum(alg.values()) / cells,
+            "hbm_gbs_peak": hbm, "clocks": clk, "gpu_launches": sum(v[0] for v in kt.values()),
+        })
+        plan.destroy()
+    else:
+        scheme = args.workload.split("-")[1]
+        dx = 1.0 / LAM_CELLS
+        dt = dx / math.sqrt(2.0)
+        Ex, Ey, Bz, Jx = (torch.zeros(NY, NX, device=dev) for _ in range(4))
+        total = args.warmup + args.steps
+        prof = torch.from_numpy(np.stack([sheet_profile(k, dt, dx) for k in range(total)])).float().to(dev)
+        Jy = [prof[k].expand(NY, NX).contiguous() for k in range(total)]
+        ms, clk = timed_steps(lambda i: capi.fdtd_step((NX, NY), (dx, dx), dt, [Ex, Ey, None], [None, None, Bz],
+                                                       [Jx, Jy[i], None], scheme=scheme, layout="te", prec="fp32",
+                                                       stream=stream), args.steps, args.warmup, flush, stream)
+        cells = NX * NY
+        # per step: two B half steps (read Ex, Ey, Bz, write Bz) and one E step
+        # (read Ex, Ey, Bz, Jx, Jy, write Ex, Ey), 4-byte values, neighbours from cache
+        bytes_step = cells * 4 * (2 * (3 + 1) + (5 + 2))
+        line.update({
+            "value": cells * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+            "config": {"workload": "2D TE %s FDTD 2048x2048 FP32, current-sheet J, dx=lambda/64, c dt=dx/sqrt(2)"
+                                   % scheme.upper(), "l2": "flushed before every timed step"},
+            "step_gbs": bytes_step / (ms / args.steps * 1e-3) / 1e9, "hbm_gbs_peak": hbm, "clocks": clk,
+            "gpu_launches": 3 * args.steps,
+        })
+    print(json.dumps(line), flush=True)
 
 
 def source_hash():

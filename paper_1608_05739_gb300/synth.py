@@ -195,3 +195,56 @@ def coulomb_field(rho, d, eps0=1.0):
         Eh = np.where(k2 > 0, -1j * ks[a] * R / (eps0 * k2s), 0.0)
         E[a] = np.fft.irfftn(Eh, s=shape, axes=tuple(range(ndim)))
     return E
+
+
+def gaussian_charges_torch(shape, d, dt, *, n_charges=64, sigma=None, vmax=0.5, c=1.0, seed=1610,
+                           step=0, device="cuda"):
+    """GPU twin of :func:`gaussian_charges` (same seeded draws and formulas, evaluated with
+    torch on ``device``; for large grids).  Returns float32 CUDA tensors
+    (rho_n, rho_np1, J) with J of shape ``(3, *shape)``, and the Coulomb field E of rho_n."""
+    import torch
+
+    ndim = len(shape)
+    g = rng(seed)
+    Ls = [shape[ndim - 1 - i] * d[i] for i in range(ndim)]
+    pos = np.stack([g.uniform(0.0, L, n_charges) for L in Ls], axis=1)
+    dirs = g.standard_normal((n_charges, ndim))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    speed = vmax * c * g.uniform(0.0, 1.0, n_charges) ** (1.0 / ndim)
+    vel = dirs * speed[:, None]
+    q = np.where(np.arange(n_charges) % 2 == 0, 1.0, -1.0)
+    sigma = 3.0 * d[0] if sigma is None else sigma
+    ks = [torch.from_numpy(np.ascontiguousarray(k)).to(device) for k in _kaxes(shape, d)]
+    k2 = sum(k * k for k in ks)
+    N = float(np.prod(shape))
+    V = float(np.prod(Ls))
+    G = (N / V) * torch.exp(-0.5 * sigma * sigma * k2)
+    tn = step * dt
+    rho0 = torch.zeros(k2.shape, dtype=torch.complex128, device=device)
+    rho1 = torch.zeros_like(rho0)
+    Jh = [torch.zeros_like(rho0) for _ in range(3)]
+    for j in range(n_charges):
+        xn = pos[j] + vel[j] * tn
+        phase = torch.exp(-1j * sum(ks[a] * float(xn[a]) for a in range(ndim)))
+        kv = sum(ks[a] * float(vel[j][a]) for a in range(ndim)) * dt
+        e = torch.exp(-1j * kv)
+        small = kv.abs() < 1e-12
+        kv_safe = torch.where(small, torch.ones_like(kv), kv)
+        avg = torch.where(small, 1.0 - 0.5j * kv, (e - 1.0) / (-1j * kv_safe))
+        base = q[j] * G * phase
+        rho0 += base
+        rho1 += base * e
+        for a in range(ndim):
+            Jh[a] += float(vel[j][a]) * base * avg
+    dims = tuple(range(ndim))
+    r0 = torch.fft.irfftn(rho0, s=shape, dim=dims)
+    r1 = torch.fft.irfftn(rho1, s=shape, dim=dims)
+    J = torch.zeros((3,) + tuple(shape), dtype=torch.float64, device=device)
+    for a in range(ndim):
+        J[a] = torch.fft.irfftn(Jh[a], s=shape, dim=dims)
+    k2s = torch.where(k2 > 0, k2, torch.ones_like(k2))
+    E = torch.zeros_like(J)
+    for a in range(ndim):
+        Eh = torch.where(k2 > 0, -1j * ks[a] * rho0 / k2s, torch.zeros_like(rho0))
+        E[a] = torch.fft.irfftn(Eh, s=shape, dim=dims)
+    return r0.float(), r1.float(), J.float(), E.float()

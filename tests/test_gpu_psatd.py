@@ -207,3 +207,14 @@ def test_step_argument_errors_raise():
     assert all(v[0] == 3 and v[1] > 0 for v in t.values())
     assert plan.workspace_bytes() > 5 * 17 * 32 * 8
     plan.destroy()
+
+
+def test_config3_full_size_one_step_fp32():
+    """3D 256^3 FP32 rho-form (all five passes at the size the 3D side bench times):
+    one step from seeded white-noise fields and sources vs the FP64 oracle."""
+    shape = (256, 256, 256)
+    d, dt = (1.0, 1.0, 1.0), 0.5
+    E, B, J, r0, r1 = _inputs(shape, "3d6", "rho", 2024, d, dt, "fp32")
+    Eg, Bg = psatd_gpu(shape, d, dt, E, B, J, r0, r1, layout="3d6", prec="fp32", src="rho")
+    Eo, Bo = _oracle(E, B, J, r0, r1, d, dt, "rho")
+    assert rel_l2_fields(Eg, Bg, Eo, Bo) < TOL["fp32"]
