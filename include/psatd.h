@@ -167,6 +167,38 @@ int32_t psatd_kernel_times(psatd_plan plan, int32_t n_slots, const char** names,
 psatd_status fdtd_step(const psatd_desc* desc, int32_t scheme, const psatd_fields* fields,
                        const psatd_sources* sources, int32_t nsteps, void* cuda_stream);
 
+/* ---- batches of 2D patches --------------------------------------------
+ * The paper advances many subdomains, each with its own local FFT
+ * (Sec. II.A.3).  A batch holds npatch independent periodic 2D patches sharing
+ * the base descriptor's layout (2D6, TE or TM), precision, source form, cell
+ * sizes, dt, c and eps0; patch i has n[2i] x n[2i+1] cells (powers of two,
+ * limits as psatd_plan_create).  Fields and sources of all patches are packed
+ * per component: one array per component holding patch 0, patch 1, ... back
+ * to back (patch i at element offset sum_{j<i} n[2j] n[2j+1]).
+ * Patches of equal size form a class advanced with one launch per pass; a
+ * call with nsteps > 1 on a non-default stream records one step of all
+ * classes into a CUDA graph (re-recorded when the field/source pointers
+ * change) and replays it nsteps times.  Guard cells are part of each patch
+ * (the caller fills them; no exchange between patches is done here).      */
+typedef struct psatd_batch_s* psatd_batch;
+
+/* Create a batch (allocates each class's spectra, tables and offset table
+ * and fills the tables; synchronous).  *out = NULL on failure.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA (message: psatd_last_error(NULL)). */
+psatd_status psatd_batch_create(const psatd_desc* base, int32_t npatch, const int64_t* n,
+                                void* cuda_stream, psatd_batch* out);
+
+/* Advance every patch by nsteps PSATD steps (sources held constant), as
+ * psatd_step does for one grid.  Asynchronous. */
+psatd_status psatd_batch_step(psatd_batch batch, const psatd_fields* fields,
+                              const psatd_sources* sources, int32_t nsteps);
+
+/* Total cells of the batch (sum over patches). */
+int64_t psatd_batch_cells(psatd_batch batch);
+
+/* Release the batch (synchronises its stream).  NULL is accepted. */
+psatd_status psatd_batch_destroy(psatd_batch batch);
+
 /* PSATD step without any device allocation, for callers that cannot call
  * cudaMalloc (e.g. code running where a foreign allocator owns all device
  * memory, or a host that must not allocate after start-up).  The paper has no

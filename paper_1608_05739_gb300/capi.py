@@ -67,6 +67,11 @@ EXPORTS = [
     ("fdtd_step", ct.c_int, [ct.POINTER(psatd_desc), ct.c_int32, ct.POINTER(psatd_fields),
                              ct.POINTER(psatd_sources), ct.c_int32, ct.c_void_p]),
     ("psatd_last_error", ct.c_char_p, [ct.c_void_p]),
+    ("psatd_batch_create", ct.c_int, [ct.POINTER(psatd_desc), ct.c_int32, ct.POINTER(ct.c_int64), ct.c_void_p,
+                                      ct.POINTER(ct.c_void_p)]),
+    ("psatd_batch_step", ct.c_int, [ct.c_void_p, ct.POINTER(psatd_fields), ct.POINTER(psatd_sources), ct.c_int32]),
+    ("psatd_batch_cells", ct.c_int64, [ct.c_void_p]),
+    ("psatd_batch_destroy", ct.c_int, [ct.c_void_p]),
 ]
 
 
@@ -209,6 +214,58 @@ class Plan:
     def destroy(self):
         if getattr(self, "handle", None) is not None:
             load().psatd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A batch of independent 2D periodic patches (psatd_batch_create) on a CUDA stream.
+
+    ``sizes`` = [(nx, ny), ...] (powers of two).  Fields and sources are passed
+    per component as one contiguous CUDA tensor of ``total`` elements holding
+    the patches back to back, patch i being its (ny_i, nx_i) row-major block.
+    """
+
+    def __init__(self, sizes, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, stream=None):
+        import torch
+        lib = load()
+        self.sizes = [(int(a), int(b)) for a, b in sizes]
+        self.layout, self.prec, self.src = layout, prec, src
+        self.dtype = _torch_dtype(prec)
+        self.total = sum(a * b for a, b in self.sizes)
+        self.offsets = []
+        acc = 0
+        for a, b in self.sizes:
+            self.offsets.append(acc)
+            acc += a * b
+        desc = make_desc(self.sizes[0], d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0)
+        arr = (ct.c_int64 * (2 * len(self.sizes)))(*[v for ab in self.sizes for v in ab])
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ct.c_void_p()
+        _check(lib.psatd_batch_create(ct.byref(desc), len(self.sizes), arr, ct.c_void_p(stream.cuda_stream),
+                                      ct.byref(h)))
+        self.handle = h
+
+    def step(self, E, B, J=None, rho_n=None, rho_np1=None, nsteps=1):
+        shape = (self.total,)
+        f = _fields_struct(self.layout, shape, self.dtype, E, B)
+        s = _sources_struct(self.layout, shape, self.dtype, J, rho_n, rho_np1) if self.src != "none" else None
+        _check(load().psatd_batch_step(self.handle, ct.byref(f), ct.byref(s) if s is not None else None,
+                                       int(nsteps)))
+
+    def cells(self):
+        return int(load().psatd_batch_cells(self.handle))
+
+    def destroy(self):
+        if getattr(self, "handle", None) is not None:
+            load().psatd_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

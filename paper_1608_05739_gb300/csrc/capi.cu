@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -51,6 +52,8 @@ struct psatd_plan_s {
   bool timing = false;
   std::vector<EventPair> ev[K_NSLOTS];
   std::vector<EventPair> pool;
+  int npatch = 1;             // 2D batches: patches of this size class
+  int64_t* d_off = nullptr;   // their element offsets in the caller's packed arrays (device)
 };
 
 namespace {
@@ -173,7 +176,7 @@ psatd_status gather_slots(psatd_plan p, const psatd_fields* f, const psatd_sourc
 }
 
 void release(psatd_plan p) {
-  void* bufs[] = {p->spec1, p->spec2, p->tw[0], p->tw[1], p->tw[2], p->tab};
+  void* bufs[] = {p->spec1, p->spec2, p->tw[0], p->tw[1], p->tw[2], p->tab, p->d_off};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (auto& v : p->ev) v.clear();
@@ -247,23 +250,27 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
   LineIO io;
   std::memset(&io, 0, sizeof io);
 
-  // pass 1: x rows (R2C), b = y, a0 = z -> spec1 [c][kx][z][y]
+  // a0: z in 3D (strided), the patch in a 2D batch (offset table; spectra [c][patch][kx][y])
+  const bool d3 = p->ndim == 3;
+  const int64_t na0 = d3 ? nz : p->npatch;
+  // pass 1: x rows (R2C), b = y -> spec1 [c][kx][z][y] (3D) / [c][patch][kx][y] (2D)
   {
     PassGeom g;
     g.log_tb = pick_log_tb(Lx, ny, p->f32);
-    g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)nz, (unsigned)p->n_in);
+    g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)na0, (unsigned)p->n_in);
     g.smem = tpass_smem(Lx, g.log_tb, true, csz);
     for (int c = 0; c < p->n_in; ++c) {
       io.in[c] = in[c];
       io.out[c] = s1 + c * cs;
     }
     TimedLaunch tl(p, K_FWD_X);
-    e = launch_fwd_T<R>(Lx, true, g, p->st, io, p->tw[0], ny * nx, nx, ny, nz * ny);
+    e = launch_fwd_T<R>(Lx, true, g, p->st, io, p->tw[0], d3 ? ny * nx : 0, nx, d3 ? ny : nxh * ny, nz * ny,
+                        d3 ? nullptr : p->d_off);
     if (e != cudaSuccess) return cuda_fail(p, e, "fwd_x_r2c launch");
   }
   C* sp = s1;
   int Lline = (int)ny;
-  int64_t nlines = nxh;
+  int64_t nlines = nxh * p->npatch;
   if (p->ndim == 3) {
     // pass 2: y lines (C2C), b = z, a0 = kx: spec1 [c][kx][z][y] -> spec2 [c][kx][ky][z]
     PassGeom g;
@@ -293,6 +300,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     a.form = p->form;
     a.ndim = p->ndim;
     a.nx_half = (int)(nx / 2);
+    a.lines_per_patch = (int)nxh;
     a.ny = (int)ny;
     a.tab_row = Lline / 2 + 1;
     a.rx = (R)p->r[0];
@@ -331,18 +339,19 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     e = launch_inv_T<R>((int)ny, false, g, p->st, io, p->tw[1], ny * nz, nz, nz * ny, ny);
     if (e != cudaSuccess) return cuda_fail(p, e, "inv_y_c2c launch");
   }
-  // last pass: inverse x rows (C2R): spec1 [c][kx][z][y] -> out [z][y][x]
+  // last pass: inverse x rows (C2R): spec1 -> out [z][y][x] (3D) / packed patches (2D)
   {
     PassGeom g;
     g.log_tb = pick_log_tb(Lx, ny, p->f32);
-    g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)nz, (unsigned)p->n_out);
+    g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)na0, (unsigned)p->n_out);
     g.smem = tpass_smem(Lx, g.log_tb, true, csz);
     for (int c = 0; c < p->n_out; ++c) {
       io.in[c] = s1 + c * cs;
       io.out[c] = out[c];
     }
     TimedLaunch tl(p, K_INV_X);
-    e = launch_inv_T<R>(Lx, true, g, p->st, io, p->tw[0], ny, nz * ny, ny * nx, nx);
+    e = launch_inv_T<R>(Lx, true, g, p->st, io, p->tw[0], d3 ? ny : nxh * ny, nz * ny, d3 ? ny * nx : 0, nx,
+                        d3 ? nullptr : p->d_off);
     if (e != cudaSuccess) return cuda_fail(p, e, "inv_x_c2r launch");
   }
   return PSATD_OK;
@@ -354,8 +363,7 @@ extern "C" {
 
 int32_t psatd_abi_version(void) { return PSATD_ABI_VERSION; }
 
-psatd_status psatd_plan_create(const psatd_desc* desc, void* cuda_stream, psatd_plan* out) {
-  if (!out) return fail(nullptr, PSATD_ERR_INVALID_ARG, "out is NULL");
+static psatd_status plan_create_n(const psatd_desc* desc, void* cuda_stream, int npatch, psatd_plan* out) {
   *out = nullptr;
   psatd_status s = validate_desc(nullptr, desc, true);
   if (s != PSATD_OK) return s;
@@ -372,7 +380,8 @@ psatd_status psatd_plan_create(const psatd_desc* desc, void* cuda_stream, psatd_
   p->ny = desc->n[1];
   p->nz = p->ndim == 3 ? desc->n[2] : 1;
   p->nxh = p->nx / 2 + 1;
-  p->cs = p->nxh * p->ny * p->nz;
+  p->npatch = npatch;
+  p->cs = p->nxh * p->ny * p->nz * npatch;
   cudaGetDevice(&p->device);
   // push pass shared memory (one line per CTA at least)
   {
@@ -421,6 +430,11 @@ psatd_status psatd_plan_create(const psatd_desc* desc, void* cuda_stream, psatd_
   }
   *out = p;
   return PSATD_OK;
+}
+
+psatd_status psatd_plan_create(const psatd_desc* desc, void* cuda_stream, psatd_plan* out) {
+  if (!out) return fail(nullptr, PSATD_ERR_INVALID_ARG, "out is NULL");
+  return plan_create_n(desc, cuda_stream, 1, out);
 }
 
 psatd_status psatd_coeffs_init(psatd_plan p) {
@@ -686,5 +700,178 @@ extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_f
       return s;
     }
   }
+  return PSATD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches of 2D patches (the paper's local-FFT subdomains, Sec. II.A.3): each
+// patch is its own periodic domain; patches of one size form a class advanced
+// with one launch per pass (patch index on the grid); a multi-step call is
+// replayed from a CUDA graph of one step.
+// ---------------------------------------------------------------------------
+struct psatd_batch_s {
+  cudaStream_t st = nullptr;
+  int npatch = 0;
+  bool f32 = true;
+  std::vector<psatd_plan> cls;  // one plan per patch size class
+  int64_t total_cells = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[2 * kMaxComp] = {};
+};
+
+namespace {
+
+void batch_release(psatd_batch b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  for (psatd_plan p : b->cls) {
+    release(p);
+    delete p;
+  }
+  b->cls.clear();
+}
+
+psatd_status batch_launch_all(psatd_batch b, const void* in[kMaxComp], void* out[kMaxComp]) {
+  for (psatd_plan p : b->cls) {
+    psatd_status s = b->f32 ? run_step<float>(p, in, out) : run_step<double>(p, in, out);
+    if (s != PSATD_OK) {
+      g_err = p->err;
+      return s;
+    }
+  }
+  return PSATD_OK;
+}
+
+}  // namespace
+
+extern "C" psatd_status psatd_batch_create(const psatd_desc* base, int32_t npatch, const int64_t* n,
+                                           void* cuda_stream, psatd_batch* out) {
+  if (!out) return fail(nullptr, PSATD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!base) return fail(nullptr, PSATD_ERR_INVALID_ARG, "base desc is NULL");
+  if (base->ndim != 2 || base->layout == PSATD_FIELDS_3D6)
+    return fail(nullptr, PSATD_ERR_INVALID_ARG, "batches hold 2D patches (layouts 2D6, TE, TM)");
+  if (npatch < 1 || !n) return fail(nullptr, PSATD_ERR_INVALID_ARG, "npatch must be >= 1 and n non-NULL");
+  std::vector<int64_t> off(npatch);
+  std::vector<std::pair<int64_t, int64_t>> dims(npatch);
+  int64_t acc = 0;
+  for (int i = 0; i < npatch; ++i) {
+    psatd_desc d = *base;
+    d.n[0] = n[2 * i];
+    d.n[1] = n[2 * i + 1];
+    d.n[2] = 1;
+    psatd_status s = validate_desc(nullptr, &d, true);
+    if (s != PSATD_OK) {
+      g_err = "patch " + std::to_string(i) + ": " + g_err;
+      return s;
+    }
+    dims[i] = {d.n[0], d.n[1]};
+    off[i] = acc;
+    acc += d.n[0] * d.n[1];
+  }
+  psatd_batch b = new (std::nothrow) psatd_batch_s();
+  if (!b) return fail(nullptr, PSATD_ERR_OOM, "host allocation failed");
+  b->st = static_cast<cudaStream_t>(cuda_stream);
+  b->npatch = npatch;
+  b->f32 = base->prec == PSATD_FP32;
+  b->total_cells = acc;
+  std::vector<std::pair<int64_t, int64_t>> classes;
+  for (auto& dd : dims)
+    if (std::find(classes.begin(), classes.end(), dd) == classes.end()) classes.push_back(dd);
+  for (auto& cl : classes) {
+    std::vector<int64_t> offs;
+    for (int i = 0; i < npatch; ++i)
+      if (dims[i] == cl) offs.push_back(off[i]);
+    psatd_desc d = *base;
+    d.n[0] = cl.first;
+    d.n[1] = cl.second;
+    d.n[2] = 1;
+    psatd_plan p = nullptr;
+    psatd_status s = plan_create_n(&d, cuda_stream, (int)offs.size(), &p);
+    if (s == PSATD_OK) {
+      s = alloc(p, reinterpret_cast<void**>(&p->d_off), offs.size() * sizeof(int64_t), "patch offsets");
+      if (s == PSATD_OK) {
+        cudaError_t e = cudaMemcpy(p->d_off, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) s = cuda_fail(p, e, "patch offset upload");
+      }
+      if (s == PSATD_OK) s = psatd_coeffs_init(p);
+      if (s != PSATD_OK) g_err = p->err;
+    }
+    if (s != PSATD_OK) {
+      if (p) {
+        release(p);
+        delete p;
+      }
+      batch_release(b);
+      delete b;
+      return s;
+    }
+    b->cls.push_back(p);
+  }
+  *out = b;
+  return PSATD_OK;
+}
+
+extern "C" psatd_status psatd_batch_step(psatd_batch b, const psatd_fields* fields, const psatd_sources* sources,
+                                         int32_t nsteps) {
+  if (!b) return fail(nullptr, PSATD_ERR_INVALID_ARG, "batch is NULL");
+  if (nsteps < 1) return fail(nullptr, PSATD_ERR_INVALID_ARG, "nsteps must be >= 1 (got %d)", nsteps);
+  const void* in[kMaxComp] = {};
+  void* out[kMaxComp] = {};
+  psatd_status s = gather_slots(b->cls[0], fields, sources, in, out);
+  if (s != PSATD_OK) {
+    g_err = b->cls[0]->err;
+    return s;
+  }
+  if (nsteps == 1 || b->st == nullptr) {  // the legacy stream cannot be captured
+    for (int i = 0; i < nsteps; ++i)
+      if ((s = batch_launch_all(b, in, out)) != PSATD_OK) return s;
+    return PSATD_OK;
+  }
+  const void* key[2 * kMaxComp];
+  for (int i = 0; i < kMaxComp; ++i) {
+    key[i] = in[i];
+    key[kMaxComp + i] = out[i];
+  }
+  if (!b->gexec || std::memcmp(key, b->gkey, sizeof key) != 0) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "begin graph capture");
+    s = batch_launch_all(b, in, out);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->st, &g);
+    if (s != PSATD_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "end graph capture");
+    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_fail(nullptr, e, "graph instantiate");
+    }
+    b->graph = g;
+    std::memcpy(b->gkey, key, sizeof key);
+  }
+  for (int i = 0; i < nsteps; ++i) {
+    cudaError_t e = cudaGraphLaunch(b->gexec, b->st);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "graph launch");
+  }
+  return PSATD_OK;
+}
+
+extern "C" int64_t psatd_batch_cells(psatd_batch b) { return b ? b->total_cells : 0; }
+
+extern "C" psatd_status psatd_batch_destroy(psatd_batch b) {
+  if (!b) return PSATD_OK;
+  cudaStreamSynchronize(b->st);
+  batch_release(b);
+  delete b;
   return PSATD_OK;
 }

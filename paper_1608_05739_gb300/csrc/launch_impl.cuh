@@ -17,7 +17,7 @@ static cudaError_t set_smem(K kern, size_t smem) {
 
 template <typename R, int L>
 static cudaError_t fwd_T_L(bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io,
-                           const void* tw, int64_t a, int64_t b, int64_t c, int64_t d) {
+                           const void* tw, int64_t a, int64_t b, int64_t c, int64_t d, const int64_t* off) {
   typedef typename Types<R>::W W;
   const dim3 block(FFTPlan<L, RowEPT<L>::value>::kT, 1u << g.log_tb);
   cudaError_t e;
@@ -25,21 +25,21 @@ static cudaError_t fwd_T_L(bool r2c, const PassGeom& g, cudaStream_t st, const L
     if constexpr (L <= 2048) {
       auto kern = k_fwd_T<R, L, true>;
       if ((e = set_smem(kern, g.smem)) != cudaSuccess) return e;
-      kern<<<g.grid, block, g.smem, st>>>(io, static_cast<const W*>(tw), a, b, c, d, g.log_tb);
+      kern<<<g.grid, block, g.smem, st>>>(io, static_cast<const W*>(tw), a, b, c, d, g.log_tb, off);
     } else {
       return cudaErrorInvalidValue;
     }
   } else {
     auto kern = k_fwd_T<R, L, false>;
     if ((e = set_smem(kern, g.smem)) != cudaSuccess) return e;
-    kern<<<g.grid, block, g.smem, st>>>(io, static_cast<const W*>(tw), a, b, c, d, g.log_tb);
+    kern<<<g.grid, block, g.smem, st>>>(io, static_cast<const W*>(tw), a, b, c, d, g.log_tb, off);
   }
   return cudaGetLastError();
 }
 
 template <typename R, int L>
 static cudaError_t inv_T_L(bool c2r, const PassGeom& g, cudaStream_t st, const LineIO& io,
-                           const void* tw, int64_t a, int64_t b, int64_t c, int64_t d) {
+                           const void* tw, int64_t a, int64_t b, int64_t c, int64_t d, const int64_t* off) {
   typedef typename Types<R>::W W;
   const dim3 block(FFTPlan<L, RowEPT<L>::value>::kT, 1u << g.log_tb);
   cudaError_t e;
@@ -47,14 +47,14 @@ static cudaError_t inv_T_L(bool c2r, const PassGeom& g, cudaStream_t st, const L
     if constexpr (L <= 2048) {
       auto kern = k_inv_T<R, L, true>;
       if ((e = set_smem(kern, g.smem)) != cudaSuccess) return e;
-      kern<<<g.grid, block, g.smem, st>>>(io, static_cast<const W*>(tw), a, b, c, d, g.log_tb);
+      kern<<<g.grid, block, g.smem, st>>>(io, static_cast<const W*>(tw), a, b, c, d, g.log_tb, off);
     } else {
       return cudaErrorInvalidValue;
     }
   } else {
     auto kern = k_inv_T<R, L, false>;
     if ((e = set_smem(kern, g.smem)) != cudaSuccess) return e;
-    kern<<<g.grid, block, g.smem, st>>>(io, static_cast<const W*>(tw), a, b, c, d, g.log_tb);
+    kern<<<g.grid, block, g.smem, st>>>(io, static_cast<const W*>(tw), a, b, c, d, g.log_tb, off);
   }
   return cudaGetLastError();
 }
@@ -102,15 +102,15 @@ static cudaError_t push_L(int layout, dim3 grid, int tb, size_t smem, cudaStream
 template <typename R>
 cudaError_t launch_fwd_T(int L, bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io,
                          const void* tw, int64_t in_sa0, int64_t in_sb, int64_t out_sa0,
-                         int64_t out_sk) {
-  PSATD_L_SWITCH(fwd_T_L, r2c, g, st, io, tw, in_sa0, in_sb, out_sa0, out_sk)
+                         int64_t out_sk, const int64_t* a0_off) {
+  PSATD_L_SWITCH(fwd_T_L, r2c, g, st, io, tw, in_sa0, in_sb, out_sa0, out_sk, a0_off)
 }
 
 template <typename R>
 cudaError_t launch_inv_T(int L, bool c2r, const PassGeom& g, cudaStream_t st, const LineIO& io,
                          const void* tw, int64_t in_sa0, int64_t in_sk, int64_t out_sa0,
-                         int64_t out_sb) {
-  PSATD_L_SWITCH(inv_T_L, c2r, g, st, io, tw, in_sa0, in_sk, out_sa0, out_sb)
+                         int64_t out_sb, const int64_t* a0_off) {
+  PSATD_L_SWITCH(inv_T_L, c2r, g, st, io, tw, in_sa0, in_sk, out_sa0, out_sb, a0_off)
 }
 
 template <typename R>

@@ -46,6 +46,7 @@ struct PushArgs {
   int form;          // 0 vacuum, 1 J, 2 rho
   int ndim;
   int nx_half;       // nx/2 (Nyquist index along x)
+  int lines_per_patch;  // 2D: nx/2 + 1 lines per patch of a batch (line = patch * lpp + kx)
   int ny;            // 3D: lines are (kx, ky), ky fastest
   int tab_row;       // L/2 + 1 entries per table row
   R rx, ry, rz;      // k_i = g0 * r_i * m_i
@@ -62,7 +63,7 @@ struct PushArgs {
 template <typename R, int L, bool R2C>
 __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
                                                int64_t in_sa0, int64_t in_sb, int64_t out_sa0,
-                                               int64_t out_sk, int log_tb) {
+                                               int64_t out_sk, int log_tb, const int64_t* __restrict__ in_off) {
   typedef typename Types<R>::C C;
   constexpr int EPT = RowEPT<L>::value;
   typedef FFTPlan<L, EPT> P;
@@ -81,10 +82,11 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO 
   C v[EPT];
   {
     const C* row;
+    const int64_t o0 = in_off ? in_off[a0] : a0 * in_sa0;  // per-patch offsets of a batch
     if constexpr (R2C)
-      row = reinterpret_cast<const C*>(static_cast<const R*>(io.in[a1]) + a0 * in_sa0 + b * in_sb);
+      row = reinterpret_cast<const C*>(static_cast<const R*>(io.in[a1]) + o0 + b * in_sb);
     else
-      row = static_cast<const C*>(io.in[a1]) + a0 * in_sa0 + b * in_sb;
+      row = static_cast<const C*>(io.in[a1]) + o0 + b * in_sb;
 #pragma unroll
     for (int m = 0; m < EPT; ++m) v[m] = row[t + T * m];
   }
@@ -138,7 +140,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO 
 template <typename R, int L, bool C2R>
 __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_inv_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
                                                int64_t in_sa0, int64_t in_sk, int64_t out_sa0,
-                                               int64_t out_sb, int log_tb) {
+                                               int64_t out_sb, int log_tb, const int64_t* __restrict__ out_off) {
   typedef typename Types<R>::C C;
   constexpr int EPT = RowEPT<L>::value;
   typedef FFTPlan<L, EPT> P;
@@ -184,10 +186,11 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_inv_T(LineIO 
   ExBuf<C> ex{{smem + g * L, smem + g * L}, 0, &twslot, true};  // one exchange buffer per line
   block_fft_inv<R, L, EPT>(v, ex, tw, t);
   C* row;
+  const int64_t o0 = out_off ? out_off[a0] : a0 * out_sa0;  // per-patch offsets of a batch
   if constexpr (C2R)
-    row = reinterpret_cast<C*>(static_cast<R*>(io.out[a1]) + a0 * out_sa0 + b * out_sb);
+    row = reinterpret_cast<C*>(static_cast<R*>(io.out[a1]) + o0 + b * out_sb);
   else
-    row = static_cast<C*>(io.out[a1]) + a0 * out_sa0 + b * out_sb;
+    row = static_cast<C*>(io.out[a1]) + o0 + b * out_sb;
 #pragma unroll
   for (int m = 0; m < EPT; ++m) row[t + T * m] = v[m];
 }
@@ -374,9 +377,10 @@ __device__ __forceinline__ void push_slots(typename Types<R>::C* st, int L, int 
 template <typename R>
 __device__ __forceinline__ void line_modes(const PushArgs<R>& a, int line, int& mxi, int& myi, int& rowi) {
   if (a.ndim == 2) {
-    mxi = (line == a.nx_half) ? 0 : line;
+    const int kx = line % a.lines_per_patch;
+    mxi = (kx == a.nx_half) ? 0 : kx;
     myi = 0;
-    rowi = line;
+    rowi = kx;
   } else {
     const int kx = line / a.ny, ky = line - kx * a.ny;
     mxi = (kx == a.nx_half) ? 0 : kx;

@@ -3,7 +3,9 @@
 
 namespace psatd {
 template cudaError_t launch_fwd_T<float>(int, bool, const PassGeom&, cudaStream_t, const LineIO&,
-                                          const void*, int64_t, int64_t, int64_t, int64_t);
+                                          const void*, int64_t, int64_t, int64_t, int64_t,
+                                          const int64_t*);
 template cudaError_t launch_inv_T<float>(int, bool, const PassGeom&, cudaStream_t, const LineIO&,
-                                          const void*, int64_t, int64_t, int64_t, int64_t);
+                                          const void*, int64_t, int64_t, int64_t, int64_t,
+                                          const int64_t*);
 }  // namespace psatd

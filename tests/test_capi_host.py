@@ -105,3 +105,18 @@ def test_fdtd_rejects_invalid_arguments(lib):
     assert lib.fdtd_step(ct.byref(d), 0, ct.byref(f), ct.byref(s), 1, None) == 1
     dr = capi.make_desc((64, 32), (1.0, 1.0), 0.5, layout="te", src="rho")
     assert lib.fdtd_step(ct.byref(dr), 0, ct.byref(f), ct.byref(s), 1, None) == 1      # rho-form
+
+
+def test_batch_create_rejects_invalid_arguments(lib):
+    d = capi.make_desc((64, 64), (1.0, 1.0), 0.5, layout="te", src="J")
+    h = ct.c_void_p()
+    n = (ct.c_int64 * 4)(64, 64, 100, 64)
+    assert lib.psatd_batch_create(ct.byref(d), 2, n, None, ct.byref(h)) == 2       # 100 not a power of two
+    assert b"patch 1" in lib.psatd_last_error(None)
+    assert lib.psatd_batch_create(ct.byref(d), 0, n, None, ct.byref(h)) == 1       # no patch
+    assert lib.psatd_batch_create(ct.byref(d), 1, None, None, ct.byref(h)) == 1
+    d3 = capi.make_desc((16, 16, 16), (1.0, 1.0, 1.0), 0.5, layout="3d6", src="J")
+    assert lib.psatd_batch_create(ct.byref(d3), 1, n, None, ct.byref(h)) == 1      # 3D
+    assert lib.psatd_batch_step(None, None, None, 1) == 1
+    assert lib.psatd_batch_destroy(None) == 0
+    assert lib.psatd_batch_cells(None) == 0
