@@ -202,7 +202,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=30.0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="te2048", choices=["te2048", "3d256", "fdtd-yee", "fdtd-ckc"],
+    ap.add_argument("--workload", default="te2048", choices=["te2048", "3d256", "fdtd-yee", "fdtd-ckc", "batch512"],
                     help="te2048 (default) is the metric's configuration; the others are side measurements")
     args = ap.parse_args()
     world, rank, local = dist_setup()
@@ -410,6 +410,58 @@ def run_side_workload(args):
             "hbm_gbs_peak": hbm, "clocks": clk, "gpu_launches": sum(v[0] for v in kt.values()),
         })
         plan.destroy()
+    elif args.workload == "batch512":
+        # 512 local-FFT patches (Sec. II.A.3): interior n ~ U{64..512} per side, guard g ~ U{8..16},
+        # each patch a periodic domain of side next_pow2(n + 2g) (this build's transforms are
+        # power-of-two); TE J-form FP32, smooth random J; the whole run is one psatd_batch_step
+        # call (a CUDA graph of one step replayed `steps` times)
+        g = synth.rng(1612)
+        sizes, interior = [], 0
+        for _ in range(512):
+            n = g.integers(64, 513, size=2)
+            gg = g.integers(8, 17, size=2)
+            side = [1 << int(math.ceil(math.log2(int(a) + 2 * int(b)))) for a, b in zip(n, gg)]
+            sizes.append((side[0], side[1]))
+            interior += int(n[0]) * int(n[1])
+        dx = 1.0 / LAM_CELLS
+        dt = dx / math.sqrt(2.0)
+        side_stream = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        b = capi.Batch(sizes, (dx, dx), dt, layout="te", prec="fp32", src="J", stream=side_stream)
+        tot = b.total
+        Ex, Ey, Bz = (torch.zeros(tot, device=dev) for _ in range(3))
+        Jx = torch.randn(tot, device=dev, generator=torch.Generator(device=dev).manual_seed(1613)) * 0.01
+        Jy = torch.randn(tot, device=dev, generator=torch.Generator(device=dev).manual_seed(1614)) * 0.01
+        torch.cuda.synchronize()
+        with torch.cuda.stream(side_stream):
+            b.step([Ex, Ey, None], [None, None, Bz], [Jx, Jy, None], nsteps=args.warmup)  # records the graph
+            side_stream.synchronize()
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            clocks = ClockSampler(0)
+            clocks.start()
+            time.sleep(0.3)
+            e0.record(side_stream)
+            b.step([Ex, Ey, None], [None, None, Bz], [Jx, Jy, None], nsteps=args.steps)
+            e1.record(side_stream)
+            side_stream.synchronize()
+            clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        classes = len(set(sizes))
+        alg = float(sum(sum(algorithmic_bytes(nx, ny, 1, 5, 3).values()) for (nx, ny) in sizes))
+        line.update({
+            "value": tot * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+            "interior_cell_steps_per_s": interior * args.steps / (ms * 1e-3),
+            "config": {"workload": "512 2D TE FP32 patches, interior U{64..512}^2, guards U{8..16}, periodic domain "
+                                   "next_pow2(n+2g) per side, J-form, one CUDA graph of one step replayed",
+                       "cells": tot, "interior_cells": interior, "size_classes": classes,
+                       "l2": "inputs %.1f GB >> L2, flushed once before the run" % (tot * 5 * 4 / 1e9)},
+            "step_gbs": alg / (ms / args.steps * 1e-3) / 1e9, "hbm_gbs_peak": hbm, "clocks": clk,
+            "gpu_launches": 3 * classes * args.steps,
+        })
+        b.destroy()
     else:
         scheme = args.workload.split("-")[1]
         dx = 1.0 / LAM_CELLS
