@@ -127,6 +127,19 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+def replica_throughput(ms_local, cells, steps, world, device):
+    """Whole-job cell-steps/s of `world` independent replicas: every rank advanced
+    `cells` cells by `steps` steps; the job's time is the slowest rank's (max over
+    ranks of the summed CUDA-event milliseconds).  Returns (value, max ms)."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    return world * cells * steps / (t_max * 1e-3), t_max
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -293,12 +306,8 @@ def main():
     e2e_ms = e0.elapsed_time(e1)
     e2e_value = NX * NY * e2e_steps / (e2e_ms * 1e-3)
 
-    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    t_max = float(t_local.item())
     cells = NX * NY
-    value = world * cells * args.steps / (t_max * 1e-3)
+    value, t_max = replica_throughput(ms, cells, args.steps, world, dev)
 
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
