@@ -315,7 +315,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     a.s_a6 = (R)(1.0 / (p->d.eps0 * c * c * p->g0));
     const void* twl = p->tw[p->ndim == 3 ? 2 : 1];
     {
-      const int T = Lline / kPushEPT;
+      const int T = Lline / push_ept(Lline);
       const size_t per_line = ((size_t)p->n_in + 1) * (size_t)Lline * csz;
       int tb = 1;
       while (tb * 2 * T <= 256 && (size_t)(tb * 2) * per_line <= 100 * 1024 && tb * 2 <= nlines) tb *= 2;
@@ -446,7 +446,7 @@ psatd_status psatd_coeffs_init(psatd_plan p) {
     for (int i = 0; i < p->ndim; ++i) {
       const int L = i == 0 ? (int)(ns[0] / 2) : (int)ns[i];
       const bool push_axis = (i == p->ndim - 1) && i > 0;
-      e = launch_twiddles(p->tw[i], L, push_axis ? kPushEPT : row_ept(L), i == 0, p->f32, p->st);
+      e = launch_twiddles(p->tw[i], L, push_axis ? push_ept(L) : row_ept(L), i == 0, p->f32, p->st);
       if (e != cudaSuccess) return cuda_fail(p, e, "twiddle table launch");
     }
     const double N = (double)p->nx * (double)p->ny * (double)p->nz;
@@ -685,7 +685,7 @@ extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_f
   for (int i = 0; i < p.ndim; ++i) {
     const int L = i == 0 ? (int)(ns[0] / 2) : (int)ns[i];
     const bool push_axis = (i == p.ndim - 1) && i > 0;
-    e = launch_twiddles(p.tw[i], L, push_axis ? kPushEPT : row_ept(L), i == 0, p.f32, p.st);
+    e = launch_twiddles(p.tw[i], L, push_axis ? push_ept(L) : row_ept(L), i == 0, p.f32, p.st);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "twiddle table launch");
   }
   const double N = (double)p.nx * (double)p.ny * (double)p.nz;

@@ -240,6 +240,11 @@ __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v
 // and of the fused last-axis pass (8).
 template <int L>
 struct RowEPT { static constexpr int value = L >= 16 ? 16 : 8; };
+// The fused pass keeps 8 elements per thread: with 16 a 2048-point line has
+// half the threads and, its shared memory being fixed per line, the SM half
+// the warps (measured slower).
+template <int L>
+struct PushEPT { static constexpr int value = 8; };
 
 template <int L, int EPT = 8>
 struct FFTPlan {

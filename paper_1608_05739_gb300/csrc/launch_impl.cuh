@@ -63,7 +63,7 @@ template <typename R, int L>
 static cudaError_t push_L(int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
                           const PushArgs<R>& a, const void* tw) {
   typedef typename Types<R>::W W;
-  const dim3 block(FFTPlan<L, 8>::kT, tb);
+  const dim3 block(FFTPlan<L, PushEPT<L>::value>::kT, tb);
   cudaError_t e;
 #define PSATD_PUSH_CASE(LAY)                                                   \
   case LAY: {                                                                  \

@@ -406,10 +406,11 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // positions sw<kLastCX>(t + T m), so the push and the inverse FFT's first
 // exchange only touch each thread's own positions.
 template <typename R, int L, int LAYOUT>
-__global__ void __launch_bounds__(FFTPlan<L, 8>::kT > 256 ? FFTPlan<L, 8>::kT : 256)
+__global__ void __launch_bounds__(FFTPlan<L, PushEPT<L>::value>::kT > 256 ? FFTPlan<L, PushEPT<L>::value>::kT : 256)
 k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   typedef typename Types<R>::C C;
-  typedef FFTPlan<L, 8> P;
+  constexpr int EPT = PushEPT<L>::value;
+  typedef FFTPlan<L, EPT> P;
   constexpr int T = P::kT;
   constexpr int CXL = P::kLastCX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -425,10 +426,10 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   int mxi, myi, rowi;
   line_modes(a, valid ? line : 0, mxi, myi, rowi);
   const Coef<R>* trow = a.tab + (int64_t)rowi * a.tab_row;
-  // the push needs eight coefficient entries per thread: start bringing them
+  // the push needs EPT coefficient entries per thread: start bringing them
   // into L2 now, so that its loads do not wait on DRAM one mode after another
 #pragma unroll
-  for (int m = 0; m < 8; ++m) {
+  for (int m = 0; m < EPT; ++m) {
     const int l = t + T * m;
     asm volatile("prefetch.global.L2 [%0];" ::"l"(trow + ((l <= L / 2) ? l : L - l)));
   }
@@ -446,21 +447,21 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
     cp_async_wait_all();
     __syncthreads();
   }
-  C v[8];
+  C v[EPT];
   for (int c = 0; c < a.n_in; ++c) {
     C* sl = st + c * L;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = sl[t + T * m];
+    for (int m = 0; m < EPT; ++m) v[m] = sl[t + T * m];
     __syncthreads();  // the slot becomes an exchange buffer
     ExBuf<C> ex{{sl, bufB}, 0, &twslot, false};
-    block_fft_fwd<R, L, 8>(v, ex, tw, t);
+    block_fft_fwd<R, L, EPT>(v, ex, tw, t);
 #pragma unroll
-    for (int m = 0; m < 8; ++m) sl[sw<CXL>(t + T * m)] = v[m];
+    for (int m = 0; m < EPT; ++m) sl[sw<CXL>(t + T * m)] = v[m];
   }
 
   // push, two modes per iteration (both coefficient loads issued together)
 #pragma unroll 1
-  for (int m0 = 0; m0 < 8; m0 += 2) {
+  for (int m0 = 0; m0 < EPT; m0 += 2) {
     Coef<R> q[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -487,13 +488,13 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   for (int c = 0; c < a.n_out; ++c) {
     C* sl = st + c * L;
 #pragma unroll
-    for (int m = 0; m < 8; ++m) v[m] = sl[sw<CXL>(t + T * m)];
+    for (int m = 0; m < EPT; ++m) v[m] = sl[sw<CXL>(t + T * m)];
     ExBuf<C> ex{{sl, bufB}, 0, &twslot, false};
-    block_fft_inv<R, L, 8>(v, ex, tw, t);
+    block_fft_inv<R, L, EPT>(v, ex, tw, t);
     if (valid) {
       C* dst = spec + c * a.cs + (int64_t)line * L;
 #pragma unroll
-      for (int m = 0; m < 8; ++m) dst[t + T * m] = v[m];
+      for (int m = 0; m < EPT; ++m) dst[t + T * m] = v[m];
     }
   }
 }
