@@ -209,9 +209,10 @@ int pick_log_tb(int L, int64_t nb, bool f32) {
   return lg;
 }
 
-size_t tpass_smem(int L, int log_tb, bool r2c, size_t csz) {
+// shared memory of a transposing pass: one L-element buffer per line, or the
+// [nk][tb + 1] transpose tile when the pass uses one (nk = 0: no tile)
+size_t tpass_smem(int L, int log_tb, size_t nk, size_t csz) {
   const int tb = 1 << log_tb;
-  const size_t nk = r2c ? (size_t)L + 1 : (size_t)L;
   const size_t a = (size_t)tb * L, b = nk * (size_t)(tb + 1);
   return (a > b ? a : b) * csz;
 }
@@ -258,7 +259,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     PassGeom g;
     g.log_tb = pick_log_tb(Lx, ny, p->f32);
     g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)na0, (unsigned)p->n_in);
-    g.smem = tpass_smem(Lx, g.log_tb, true, csz);
+    g.smem = tpass_smem(Lx, g.log_tb, 0, csz);
     for (int c = 0; c < p->n_in; ++c) {
       io.in[c] = in[c];
       io.out[c] = s1 + c * cs;
@@ -276,7 +277,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     PassGeom g;
     g.log_tb = pick_log_tb((int)ny, nz, p->f32);
     g.grid = dim3((unsigned)(nz >> g.log_tb), (unsigned)nxh, (unsigned)p->n_in);
-    g.smem = tpass_smem((int)ny, g.log_tb, false, csz);
+    g.smem = tpass_smem((int)ny, g.log_tb, (size_t)ny, csz);
     for (int c = 0; c < p->n_in; ++c) {
       io.in[c] = s1 + c * cs;
       io.out[c] = s2 + c * cs;
@@ -330,7 +331,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     PassGeom g;
     g.log_tb = pick_log_tb((int)ny, nz, p->f32);
     g.grid = dim3((unsigned)(nz >> g.log_tb), (unsigned)nxh, (unsigned)p->n_out);
-    g.smem = tpass_smem((int)ny, g.log_tb, false, csz);
+    g.smem = tpass_smem((int)ny, g.log_tb, (size_t)ny, csz);
     for (int c = 0; c < p->n_out; ++c) {
       io.in[c] = s2 + c * cs;
       io.out[c] = s1 + c * cs;
@@ -344,7 +345,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     PassGeom g;
     g.log_tb = pick_log_tb(Lx, ny, p->f32);
     g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)na0, (unsigned)p->n_out);
-    g.smem = tpass_smem(Lx, g.log_tb, true, csz);
+    g.smem = tpass_smem(Lx, g.log_tb, (size_t)Lx + 1, csz);
     for (int c = 0; c < p->n_out; ++c) {
       io.in[c] = s1 + c * cs;
       io.out[c] = out[c];

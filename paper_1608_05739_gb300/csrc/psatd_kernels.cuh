@@ -93,42 +93,46 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO 
   if constexpr (P::kStages == 1) __syncthreads();  // twslot visible (else the first exchange's barrier)
   block_fft_fwd<R, L, EPT>(v, ex, tw, t);
 
-  C* tile = smem;  // [NK][TB + 1], aliases the exchange buffers
-  const int tp = TB + 1;
   if constexpr (R2C) {
-    // X[k] = Fe[k] + W_N^k Fo[k] with Fe = (Z[k] + Z*[L-k])/2, Fo = (Z[k] - Z*[L-k])/(2i)
+    // X[k] = Fe[k] + W_N^k Fo[k], Fe = (Z[k] + Z*[L-k])/2, Fo = (Z[k] - Z*[L-k])/(2i), k = 0..L,
+    // computed straight into the transposed store: Z of row g goes to this line's buffer
+    // (XOR-ed by a row-dependent mask so that the column-wise reads hit distinct banks),
+    // then each thread produces whole output elements (k, row) and stores them.
     C* zb = ex.next();
+    const int xg = (g * (16 >> log_tb)) & 15 & (L - 1);  // stays inside the line for L < 16
 #pragma unroll
-    for (int m = 0; m < EPT; ++m) zb[sw<1>(t + T * m)] = v[m];
+    for (int m = 0; m < EPT; ++m) zb[(t + T * m) ^ xg] = v[m];
     __syncthreads();
     const typename Types<R>::W* wn = tw + P::kTwEntries;  // W_N^k, N = 2L
-    C X[EPT];
-    C XL = mkc(R(0), R(0));
-#pragma unroll
-    for (int m = 0; m < EPT; ++m) {
-      const int k = t + T * m;
-      const C zk = zb[sw<1>(k)];
-      const C zm = cconj(zb[sw<1>((L - k) & (L - 1))]);
+    const int nthr = T * TB;
+    const int tid = g * T + t;
+    const int kstep = nthr >> log_tb;
+    const int gg = tid & (TB - 1);
+    const int xgg = (gg * (16 >> log_tb)) & 15 & (L - 1);
+    const C* zr = smem + gg * L;
+    int k = tid >> log_tb;
+    C* o = static_cast<C*>(io.out[a1]) + a0 * out_sa0 + (int64_t)blockIdx.x * TB + (int64_t)k * out_sk + gg;
+    const int64_t ostep = (int64_t)kstep * out_sk;
+    for (; k <= L; k += kstep, o += ostep) {
+      const C zk = zr[(k & (L - 1)) ^ xgg];
+      const C zm = cconj(zr[((L - k) & (L - 1)) ^ xgg]);
       const C fe = mkc(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y + zm.y));
       const C fo = mkc(R(0.5) * (zk.y - zm.y), R(-0.5) * (zk.x - zm.x));
-      X[m] = cadd(fe, twmul(fo, __ldg(&wn[k])));
-      if (k == 0) XL = csub(fe, fo);
+      *o = (k < L) ? cadd(fe, twmul(fo, __ldg(&wn[k]))) : csub(fe, fo);
     }
-    __syncthreads();
-#pragma unroll
-    for (int m = 0; m < EPT; ++m) tile[(t + T * m) * tp + g] = X[m];
-    if (t == 0) tile[L * tp + g] = XL;
   } else {
+    C* tile = smem;  // [NK][TB + 1], aliases the exchange buffers
+    const int tp = TB + 1;
     __syncthreads();
 #pragma unroll
     for (int m = 0; m < EPT; ++m) tile[(t + T * m) * tp + g] = v[m];
-  }
-  __syncthreads();
-  C* ob = static_cast<C*>(io.out[a1]) + a0 * out_sa0 + (int64_t)blockIdx.x * TB;
-  const int nthr = T * TB;
-  for (int idx = g * T + t; idx < NK * TB; idx += nthr) {
-    const int k = idx >> log_tb, gg = idx & (TB - 1);
-    ob[(int64_t)k * out_sk + gg] = tile[k * tp + gg];
+    __syncthreads();
+    C* ob = static_cast<C*>(io.out[a1]) + a0 * out_sa0 + (int64_t)blockIdx.x * TB;
+    const int nthr = T * TB;
+    for (int idx = g * T + t; idx < NK * TB; idx += nthr) {
+      const int k = idx >> log_tb, gg = idx & (TB - 1);
+      ob[(int64_t)k * out_sk + gg] = tile[k * tp + gg];
+    }
   }
 }
 
