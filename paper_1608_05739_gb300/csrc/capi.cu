@@ -345,7 +345,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     PassGeom g;
     g.log_tb = pick_log_tb(Lx, ny, p->f32);
     g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)na0, (unsigned)p->n_out);
-    g.smem = tpass_smem(Lx, g.log_tb, (size_t)Lx + 1, csz);
+    g.smem = tpass_smem(Lx, g.log_tb, 0, csz);
     for (int c = 0; c < p->n_out; ++c) {
       io.in[c] = s1 + c * cs;
       io.out[c] = out[c];

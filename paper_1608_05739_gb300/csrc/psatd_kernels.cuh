@@ -156,37 +156,52 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_inv_T(LineIO 
   const int t = threadIdx.x, g = threadIdx.y;
   const int64_t b = (int64_t)blockIdx.x * TB + g;
   const int a0 = blockIdx.y, a1 = blockIdx.z;
-  C* tile = smem;
-  const int tp = TB + 1;
   __shared__ const void* twslot;
   if (t == 0 && g == 0) twslot = tw;
-  {
-    const C* ib = static_cast<const C*>(io.in[a1]) + a0 * in_sa0 + (int64_t)blockIdx.x * TB;
-    const int nthr = T * TB;
-    for (int idx = g * T + t; idx < NK * TB; idx += nthr) {
-      const int k = idx >> log_tb, gg = idx & (TB - 1);
-      tile[k * tp + gg] = ib[(int64_t)k * in_sk + gg];
-    }
-  }
-  __syncthreads();
   C v[EPT];
   if constexpr (C2R) {
-    // Z[k] = Fe + i Fo, Fe = X[k] + X*[L-k], Fo = (X[k] - X*[L-k]) conj(W_N^k)
+    // Z[k] = Fe + i Fo, Fe = X[k] + X*[L-k], Fo = (X[k] - X*[L-k]) conj(W_N^k), read straight
+    // from the transposed spectrum: each thread takes a bin pair (k, L-k) of one line, which
+    // also gives Z[L-k] = Fe* + i Fo* (as W_N^(L-k) = -conj(W_N^k)), and writes both into the
+    // line's buffer under the row-dependent XOR mask of the forward pass.
     const typename Types<R>::W* wn = tw + P::kTwEntries;
-#pragma unroll
-    for (int m = 0; m < EPT; ++m) {
-      const int k = t + T * m;
-      const C xk = tile[k * tp + g];
-      const C xm = cconj(tile[(L - k) * tp + g]);
+    const int nthr = T * TB;
+    const int tid = g * T + t;
+    const int pstep = nthr >> log_tb;
+    const int gg = tid & (TB - 1);
+    const int xgg = (gg * (16 >> log_tb)) & 15 & (L - 1);
+    C* zr = smem + gg * L;
+    const C* ib = static_cast<const C*>(io.in[a1]) + a0 * in_sa0 + (int64_t)blockIdx.x * TB + gg;
+    for (int pp = tid >> log_tb; pp <= L / 2; pp += pstep) {
+      const C xk = ib[(int64_t)pp * in_sk];
+      const C xm = cconj(ib[(int64_t)(L - pp) * in_sk]);
       const C fe = cadd(xk, xm);
-      const C fo = twmul_conj(csub(xk, xm), __ldg(&wn[k]));
-      v[m] = cadd(fe, cmul_pi(fo));
+      const C d = csub(xk, xm);
+      const C fo = (pp == 0) ? d : twmul_conj(d, __ldg(&wn[pp]));
+      zr[pp ^ xgg] = cadd(fe, cmul_pi(fo));
+      if (pp > 0 && pp < L / 2) zr[(L - pp) ^ xgg] = cadd(cconj(fe), cmul_pi(cconj(fo)));
     }
+    __syncthreads();
+    const int xg = (g * (16 >> log_tb)) & 15 & (L - 1);
+    const C* zb = smem + g * L;
+#pragma unroll
+    for (int m = 0; m < EPT; ++m) v[m] = zb[(t + T * m) ^ xg];
   } else {
+    C* tile = smem;
+    const int tp = TB + 1;
+    {
+      const C* ib = static_cast<const C*>(io.in[a1]) + a0 * in_sa0 + (int64_t)blockIdx.x * TB;
+      const int nthr = T * TB;
+      for (int idx = g * T + t; idx < NK * TB; idx += nthr) {
+        const int k = idx >> log_tb, gg = idx & (TB - 1);
+        tile[k * tp + gg] = ib[(int64_t)k * in_sk + gg];
+      }
+    }
+    __syncthreads();
 #pragma unroll
     for (int m = 0; m < EPT; ++m) v[m] = tile[(t + T * m) * tp + g];
+    __syncthreads();
   }
-  __syncthreads();
   ExBuf<C> ex{{smem + g * L, smem + g * L}, 0, &twslot, true};  // one exchange buffer per line
   block_fft_inv<R, L, EPT>(v, ex, tw, t);
   C* row;
