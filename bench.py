@@ -45,6 +45,13 @@ WORKLOAD = ("2D TE PSATD 2048x2048 FP32, J-form current-sheet drive J_y(x,t), dx
 N_IN, N_OUT = 5, 3
 
 
+PREC_NOTE = {
+    "fp32": "fp32 (compensated twiddles and C, S)",
+    "mixed_fp16": "mixed: radix-16 stages as tcgen05 DFT-matrix MMAs, split-FP16 operands, FP32 accumulate; "
+                  "rest fp32 as the plain path",
+}
+
+
 def algorithmic_bytes(nx=NX, ny=NY, nz=1, n_in=N_IN, n_out=N_OUT, real=4):
     cells = nx * ny * nz
     half = (nx // 2 + 1) * ny * nz
@@ -215,6 +222,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=30.0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed_fp16"],
+                    help="te2048 arithmetic: plain FP32, or tensor-core split-FP16 radix-16 stages")
     ap.add_argument("--workload", default="te2048", choices=["te2048", "3d256", "fdtd-yee", "fdtd-ckc", "batch512"],
                     help="te2048 (default) is the metric's configuration; the others are side measurements")
     args = ap.parse_args()
@@ -244,7 +253,7 @@ def main():
     dx = 1.0 / LAM_CELLS
     dt = dx / math.sqrt(2.0)
     stream = torch.cuda.current_stream()
-    plan = capi.Plan((NX, NY), (dx, dx), dt, layout="te", prec="fp32", src="J", stream=stream)
+    plan = capi.Plan((NX, NY), (dx, dx), dt, layout="te", prec=args.precision, src="J", stream=stream)
     Ex = torch.zeros(NY, NX, device=dev)
     Ey = torch.zeros(NY, NX, device=dev)
     Bz = torch.zeros(NY, NX, device=dev)
@@ -279,6 +288,7 @@ def main():
     ms = sum(starts[s].elapsed_time(ends[s]) for s in range(args.steps))
     ktimes = plan.kernel_times()
     plan.set_timing(False)
+    plan.sync()  # raises if a tensor-core pass reported an expired wait
     if not bool(torch.isfinite(Ey).all()):
         raise RuntimeError("non-finite field after the timed steps")
 
@@ -338,8 +348,9 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": [NX, NY], "precision": "fp32 (compensated twiddles and C, S)",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f16x2-split tensor + f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [NX, NY], "precision": PREC_NOTE[args.precision],
                        "l2": "flushed before every timed step (256 MiB write), step alone inside the events",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "e2e": {"value": e2e_value, "unit": "cell-steps/s", "h2d_bytes_per_step": 5 * cells * 4,

@@ -65,7 +65,11 @@ typedef enum {
   PSATD_FP64 = 0,        /* double storage and arithmetic                              */
   PSATD_FP32 = 1,        /* float storage; twiddles and C, S applied compensated (hi/lo) */
   PSATD_MIXED_BF16 = 2,  /* reserved (tensor-core split-BF16 DFT passes)              */
-  PSATD_MIXED_FP16 = 3   /* reserved (tensor-core split-FP16 DFT passes)              */
+  PSATD_MIXED_FP16 = 3   /* float storage; every radix-16 FFT stage is a 16 x 16 DFT-
+                            matrix contraction on the tensor cores (tcgen05) with
+                            split-FP16 operands (hi + lo, per-row power-of-two scale,
+                            three products) accumulated in FP32; the other stages,
+                            twiddles and the push as PSATD_FP32.  PSATD step only. */
 } psatd_precision;
 
 typedef enum {
@@ -113,7 +117,10 @@ int32_t psatd_abi_version(void);
 
 /* Create a PSATD plan for `desc` on `cuda_stream`.
  * Supported (this build): every n[i] a power of two, 16 <= n[0] <= 4096,
- * 8 <= n[1], n[2] <= 4096; PSATD_FP64 or PSATD_FP32; flags = 0.
+ * 8 <= n[1], n[2] <= 4096; PSATD_FP64, PSATD_FP32 or PSATD_MIXED_FP16;
+ * flags = 0.  PSATD_MIXED_FP16 also needs n[0] >= 32, n[1], n[2] >= 16 and
+ * at least 128 threads per CTA in every pass (n[0]/32 * min(32, n[1]) >= 128
+ * for the x pass; UNSUPPORTED otherwise).
  * Owns: its spectral scratch (about n_in * (n0/2+1) * n1 * n2 complex values,
  * twice that in 3D), the twiddle tables and the k-space coefficient table,
  * allocated with cudaMalloc on the current device.  *out is set to NULL on
@@ -137,7 +144,10 @@ psatd_status psatd_coeffs_init(psatd_plan plan);
 psatd_status psatd_step(psatd_plan plan, const psatd_fields* fields,
                         const psatd_sources* sources, int32_t nsteps);
 
-/* Synchronise the plan's stream and report any asynchronous CUDA error. */
+/* Synchronise the plan's stream and report any asynchronous CUDA error, or
+ * PSATD_ERR_TIMEOUT when a tensor-core pass (PSATD_MIXED_FP16) gave up a
+ * bounded wait for its MMAs since the last sync (the step's output is then
+ * not valid; the flag is cleared).                                          */
 psatd_status psatd_plan_sync(psatd_plan plan);
 
 /* Release the plan and everything it owns (synchronises its stream first).
@@ -216,6 +226,7 @@ psatd_status psatd_batch_destroy(psatd_batch batch);
  *   before they are read, so nothing needs clearing).
  *   All calls share the one array: calls whose work overlaps on the GPU (other
  *   streams, other host threads) race and corrupt each other's results.
+ * Precision: PSATD_FP32 or PSATD_FP64 (others: PSATD_ERR_UNSUPPORTED).
  * Arguments and errors as psatd_plan_create and psatd_step; asynchronous.   */
 psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_fields* fields,
                                 const psatd_sources* sources, int32_t nsteps, void* cuda_stream);

@@ -54,6 +54,9 @@ struct psatd_plan_s {
   std::vector<EventPair> pool;
   int npatch = 1;             // 2D batches: patches of this size class
   int64_t* d_off = nullptr;   // their element offsets in the caller's packed arrays (device)
+  bool tc = false;            // split-FP16 tensor-core radix-16 stages (PSATD_MIXED_FP16)
+  void* gmat = nullptr;       // their split DFT matrices (kTcTail image, device)
+  int* d_err = nullptr;       // device error word of the tensor-core passes
 };
 
 namespace {
@@ -107,7 +110,10 @@ psatd_status validate_desc(psatd_plan p, const psatd_desc* d, bool psatd_limits)
   if (d->layout == PSATD_FIELDS_2D_TM && d->src == PSATD_SRC_J_RHO)
     return fail(p, PSATD_ERR_INVALID_ARG, "the TM layout has no rho-form (k.E = 0)");
   if (d->prec < 0 || d->prec > 3) return fail(p, PSATD_ERR_INVALID_ARG, "unknown precision %d", d->prec);
-  if (d->prec >= PSATD_MIXED_BF16) return fail(p, PSATD_ERR_UNSUPPORTED, "mixed precision not in this build");
+  if (d->prec == PSATD_MIXED_BF16)
+    return fail(p, PSATD_ERR_UNSUPPORTED, "split-BF16 is not in this build (PSATD_MIXED_FP16 is)");
+  if (d->prec == PSATD_MIXED_FP16 && !psatd_limits)
+    return fail(p, PSATD_ERR_UNSUPPORTED, "mixed precision applies to the PSATD step only");
   const int nd = d->ndim;
   for (int i = 0; i < nd; ++i)
     if (!pos_finite(d->d[i])) return fail(p, PSATD_ERR_INVALID_ARG, "d[%d] must be finite and > 0", i);
@@ -176,7 +182,7 @@ psatd_status gather_slots(psatd_plan p, const psatd_fields* f, const psatd_sourc
 }
 
 void release(psatd_plan p) {
-  void* bufs[] = {p->spec1, p->spec2, p->tw[0], p->tw[1], p->tw[2], p->tab, p->d_off};
+  void* bufs[] = {p->spec1, p->spec2, p->tw[0], p->tw[1], p->tw[2], p->tab, p->d_off, p->gmat, p->d_err};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (auto& v : p->ev) v.clear();
@@ -217,6 +223,18 @@ size_t tpass_smem(int L, int log_tb, size_t nk, size_t csz) {
   return (a > b ? a : b) * csz;
 }
 
+// lines per CTA of the fused last-axis pass: up to 256 threads and 100 KB of
+// line buffers; the tensor-core variant needs a multiple of 128 threads
+int push_lines_per_cta(int L, int n_in, int64_t nlines, bool tc, bool f32) {
+  const int T = L / push_ept(L, tc);
+  const size_t per_line = ((size_t)n_in + 1) * (size_t)L * (f32 ? 8 : 16);
+  int tb = 1;
+  while (tb * 2 * T <= 256 && (size_t)(tb * 2) * per_line <= 100 * 1024 && tb * 2 <= nlines) tb *= 2;
+  if (tc)
+    while (tb * T < 128) tb *= 2;
+  return tb;
+}
+
 struct TimedLaunch {
   psatd_plan p;
   int slot;
@@ -239,7 +257,7 @@ struct TimedLaunch {
   }
 };
 
-template <typename R>
+template <typename R, bool TC>
 psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp]) {
   typedef typename Types<R>::C C;
   const size_t csz = sizeof(C);
@@ -250,6 +268,9 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
   cudaError_t e;
   LineIO io;
   std::memset(&io, 0, sizeof io);
+  io.gmat = p->gmat;
+  io.err = p->d_err;
+  const size_t tail = TC ? (size_t)kTcTail : 0;  // tensor-core passes: matrices + mbarrier first
 
   // a0: z in 3D (strided), the patch in a 2D batch (offset table; spectra [c][patch][kx][y])
   const bool d3 = p->ndim == 3;
@@ -259,13 +280,13 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     PassGeom g;
     g.log_tb = pick_log_tb(Lx, ny, p->f32);
     g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)na0, (unsigned)p->n_in);
-    g.smem = tpass_smem(Lx, g.log_tb, 0, csz);
+    g.smem = tail + tpass_smem(Lx, g.log_tb, 0, csz);
     for (int c = 0; c < p->n_in; ++c) {
       io.in[c] = in[c];
       io.out[c] = s1 + c * cs;
     }
     TimedLaunch tl(p, K_FWD_X);
-    e = launch_fwd_T<R>(Lx, true, g, p->st, io, p->tw[0], d3 ? ny * nx : 0, nx, d3 ? ny : nxh * ny, nz * ny,
+    e = launch_fwd_T<R, TC>(Lx, true, g, p->st, io, p->tw[0], d3 ? ny * nx : 0, nx, d3 ? ny : nxh * ny, nz * ny,
                         d3 ? nullptr : p->d_off);
     if (e != cudaSuccess) return cuda_fail(p, e, "fwd_x_r2c launch");
   }
@@ -277,13 +298,13 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     PassGeom g;
     g.log_tb = pick_log_tb((int)ny, nz, p->f32);
     g.grid = dim3((unsigned)(nz >> g.log_tb), (unsigned)nxh, (unsigned)p->n_in);
-    g.smem = tpass_smem((int)ny, g.log_tb, (size_t)ny, csz);
+    g.smem = tail + tpass_smem((int)ny, g.log_tb, (size_t)ny, csz);
     for (int c = 0; c < p->n_in; ++c) {
       io.in[c] = s1 + c * cs;
       io.out[c] = s2 + c * cs;
     }
     TimedLaunch tl(p, K_FWD_Y);
-    e = launch_fwd_T<R>((int)ny, false, g, p->st, io, p->tw[1], nz * ny, ny, ny * nz, nz);
+    e = launch_fwd_T<R, TC>((int)ny, false, g, p->st, io, p->tw[1], nz * ny, ny, ny * nz, nz);
     if (e != cudaSuccess) return cuda_fail(p, e, "fwd_y_c2c launch");
     sp = s2;
     Lline = (int)nz;
@@ -314,15 +335,15 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     a.ic_l = (R)(ic - (double)a.ic_h);
     a.s_src = (R)(1.0 / (p->d.eps0 * c * p->g0));
     a.s_a6 = (R)(1.0 / (p->d.eps0 * c * c * p->g0));
+    a.gmat = p->gmat;
+    a.err = p->d_err;
     const void* twl = p->tw[p->ndim == 3 ? 2 : 1];
     {
-      const int T = Lline / push_ept(Lline);
+      const int tb = push_lines_per_cta(Lline, p->n_in, nlines, TC, p->f32);
       const size_t per_line = ((size_t)p->n_in + 1) * (size_t)Lline * csz;
-      int tb = 1;
-      while (tb * 2 * T <= 256 && (size_t)(tb * 2) * per_line <= 100 * 1024 && tb * 2 <= nlines) tb *= 2;
       const dim3 grid((unsigned)((nlines + tb - 1) / tb));
       TimedLaunch tl(p, K_PUSH);
-      e = launch_line_push<R>(Lline, p->layout, grid, tb, tb * per_line, p->st, a, twl);
+      e = launch_line_push<R, TC>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl);
       if (e != cudaSuccess) return cuda_fail(p, e, "line_fft_push launch");
     }
   }
@@ -331,13 +352,13 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     PassGeom g;
     g.log_tb = pick_log_tb((int)ny, nz, p->f32);
     g.grid = dim3((unsigned)(nz >> g.log_tb), (unsigned)nxh, (unsigned)p->n_out);
-    g.smem = tpass_smem((int)ny, g.log_tb, (size_t)ny, csz);
+    g.smem = tail + tpass_smem((int)ny, g.log_tb, (size_t)ny, csz);
     for (int c = 0; c < p->n_out; ++c) {
       io.in[c] = s2 + c * cs;
       io.out[c] = s1 + c * cs;
     }
     TimedLaunch tl(p, K_INV_Y);
-    e = launch_inv_T<R>((int)ny, false, g, p->st, io, p->tw[1], ny * nz, nz, nz * ny, ny);
+    e = launch_inv_T<R, TC>((int)ny, false, g, p->st, io, p->tw[1], ny * nz, nz, nz * ny, ny);
     if (e != cudaSuccess) return cuda_fail(p, e, "inv_y_c2c launch");
   }
   // last pass: inverse x rows (C2R): spec1 -> out [z][y][x] (3D) / packed patches (2D)
@@ -345,16 +366,45 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     PassGeom g;
     g.log_tb = pick_log_tb(Lx, ny, p->f32);
     g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)na0, (unsigned)p->n_out);
-    g.smem = tpass_smem(Lx, g.log_tb, 0, csz);
+    g.smem = tail + tpass_smem(Lx, g.log_tb, 0, csz);
     for (int c = 0; c < p->n_out; ++c) {
       io.in[c] = s1 + c * cs;
       io.out[c] = out[c];
     }
     TimedLaunch tl(p, K_INV_X);
-    e = launch_inv_T<R>(Lx, true, g, p->st, io, p->tw[0], d3 ? ny : nxh * ny, nz * ny, d3 ? ny * nx : 0, nx,
+    e = launch_inv_T<R, TC>(Lx, true, g, p->st, io, p->tw[0], d3 ? ny : nxh * ny, nz * ny, d3 ? ny * nx : 0, nx,
                         d3 ? nullptr : p->d_off);
     if (e != cudaSuccess) return cuda_fail(p, e, "inv_x_c2r launch");
   }
+  return PSATD_OK;
+}
+
+psatd_status step_once(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp]) {
+  if (p->tc) return run_step<float, true>(p, in, out);
+  return p->f32 ? run_step<float, false>(p, in, out) : run_step<double, false>(p, in, out);
+}
+
+// Shape checks of the tensor-core variant: every transposing pass and the fused
+// pass run with a multiple of 128 threads per CTA (one MMA row per thread).
+psatd_status check_tc_shape(psatd_plan p, int maxsm) {
+  const int Lx = (int)(p->nx / 2);
+  const int Ll = (int)(p->ndim == 3 ? p->nz : p->ny);
+  if (Lx < 16 || Ll < 16 || (p->ndim == 3 && p->ny < 16))
+    return fail(nullptr, PSATD_ERR_UNSUPPORTED, "mixed precision needs nx >= 32 and ny, nz >= 16");
+  struct { int L; int64_t nb; } rows[2] = {{Lx, p->ny}, {(int)p->ny, p->nz}};
+  for (int i = 0; i < (p->ndim == 3 ? 2 : 1); ++i) {
+    const int T = rows[i].L / row_ept(rows[i].L);
+    if ((T << pick_log_tb(rows[i].L, rows[i].nb, true)) < 128)
+      return fail(nullptr, PSATD_ERR_UNSUPPORTED,
+                  "mixed precision: a line pass of length %d over %lld lines has fewer than 128 threads per CTA",
+                  rows[i].L, (long long)rows[i].nb);
+  }
+  const int64_t nlines = p->ndim == 3 ? p->nxh * p->ny : p->nxh * p->npatch;
+  const int tb = push_lines_per_cta(Ll, p->n_in, nlines, true, true);
+  const size_t smem = (size_t)kTcTail + (size_t)tb * ((size_t)p->n_in + 1) * (size_t)Ll * 8;
+  if (maxsm > 0 && smem > (size_t)maxsm)
+    return fail(nullptr, PSATD_ERR_UNSUPPORTED, "mixed precision: last-axis length %d needs %zu bytes of shared memory",
+                Ll, smem);
   return PSATD_OK;
 }
 
@@ -372,7 +422,8 @@ static psatd_status plan_create_n(const psatd_desc* desc, void* cuda_stream, int
   if (!p) return fail(nullptr, PSATD_ERR_OOM, "host allocation failed");
   p->d = *desc;
   p->st = static_cast<cudaStream_t>(cuda_stream);
-  p->f32 = desc->prec == PSATD_FP32;
+  p->f32 = desc->prec == PSATD_FP32 || desc->prec == PSATD_MIXED_FP16;
+  p->tc = desc->prec == PSATD_MIXED_FP16;
   p->ndim = desc->ndim;
   p->layout = desc->layout;
   p->form = desc->src;
@@ -397,6 +448,13 @@ static psatd_status plan_create_n(const psatd_desc* desc, void* cuda_stream, int
                             p->n_in, need, maxsm);
       delete p;
       return r;
+    }
+    if (p->tc) {
+      psatd_status r = check_tc_shape(p, maxsm);
+      if (r != PSATD_OK) {
+        delete p;
+        return r;
+      }
     }
   }
   // wavenumber scale: k_i = g0 r_i m_i; FP32 plans use the float-rounded ratios
@@ -423,6 +481,12 @@ static psatd_status plan_create_n(const psatd_desc* desc, void* cuda_stream, int
   p->tab_e[2] = p->ndim == 3 ? p->nz / 2 + 1 : 1;
   const size_t ent = (size_t)p->tab_e[0] * p->tab_e[1] * p->tab_e[2];
   if (a == PSATD_OK) a = alloc(p, &p->tab, ent * (p->f32 ? sizeof(Coef<float>) : sizeof(Coef<double>)), "coefficients");
+  if (a == PSATD_OK && p->tc) a = alloc(p, &p->gmat, 2 * TcGeom<16>::kGDir, "tensor-core DFT matrices");
+  if (a == PSATD_OK && p->tc) a = alloc(p, reinterpret_cast<void**>(&p->d_err), sizeof(int), "error word");
+  if (a == PSATD_OK && p->tc) {
+    cudaError_t e = cudaMemset(p->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) a = cuda_fail(p, e, "error word clear");
+  }
   if (a != PSATD_OK) {
     g_err = p->err;
     release(p);
@@ -447,8 +511,12 @@ psatd_status psatd_coeffs_init(psatd_plan p) {
     for (int i = 0; i < p->ndim; ++i) {
       const int L = i == 0 ? (int)(ns[0] / 2) : (int)ns[i];
       const bool push_axis = (i == p->ndim - 1) && i > 0;
-      e = launch_twiddles(p->tw[i], L, push_axis ? push_ept(L) : row_ept(L), i == 0, p->f32, p->st);
+      e = launch_twiddles(p->tw[i], L, push_axis ? push_ept(L, p->tc) : row_ept(L), i == 0, p->f32, p->st);
       if (e != cudaSuccess) return cuda_fail(p, e, "twiddle table launch");
+    }
+    if (p->tc) {
+      e = launch_tc_dftmat(p->gmat, p->st);
+      if (e != cudaSuccess) return cuda_fail(p, e, "tensor-core DFT matrix launch");
     }
     const double N = (double)p->nx * (double)p->ny * (double)p->nz;
     e = launch_coefs(p->tab, p->f32, (int)p->tab_e[0], (int)p->tab_e[1], (int)p->tab_e[2], (int)p->nx, (int)p->ny,
@@ -468,7 +536,7 @@ psatd_status psatd_step(psatd_plan p, const psatd_fields* fields, const psatd_so
   psatd_status s = gather_slots(p, fields, sources, in, out);
   if (s != PSATD_OK) return s;
   for (int i = 0; i < nsteps; ++i) {
-    s = p->f32 ? run_step<float>(p, in, out) : run_step<double>(p, in, out);
+    s = step_once(p, in, out);
     if (s != PSATD_OK) return s;
   }
   return PSATD_OK;
@@ -480,6 +548,15 @@ psatd_status psatd_plan_sync(psatd_plan p) {
   if (e != cudaSuccess) return cuda_fail(p, e, "stream synchronise");
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(p, e, "asynchronous error");
+  if (p->d_err) {
+    int w = 0;
+    e = cudaMemcpy(&w, p->d_err, sizeof w, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(p, e, "error word read");
+    if (w != 0) {
+      cudaMemset(p->d_err, 0, sizeof(int));
+      return fail(p, PSATD_ERR_TIMEOUT, "a tensor-core pass gave up waiting for its MMAs (error word %d)", w);
+    }
+  }
   return PSATD_OK;
 }
 
@@ -594,6 +671,8 @@ extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_f
   psatd_status s = validate_desc(nullptr, desc, true);
   if (s != PSATD_OK) return s;
   if (nsteps < 1) return fail(nullptr, PSATD_ERR_INVALID_ARG, "nsteps must be >= 1 (got %d)", nsteps);
+  if (desc->prec != PSATD_FP32 && desc->prec != PSATD_FP64)
+    return fail(nullptr, PSATD_ERR_UNSUPPORTED, "psatd_step_noalloc runs PSATD_FP32 and PSATD_FP64 only");
 
   // a plan-shaped descriptor on the stack whose buffers are carved from the array
   psatd_plan_s p;
@@ -695,7 +774,7 @@ extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_f
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "coefficient table launch");
   p.coeffs_ready = true;
   for (int i = 0; i < nsteps; ++i) {
-    s = p.f32 ? run_step<float>(&p, in, out) : run_step<double>(&p, in, out);
+    s = step_once(&p, in, out);
     if (s != PSATD_OK) {
       g_err = p.err;
       return s;
@@ -737,7 +816,7 @@ void batch_release(psatd_batch b) {
 
 psatd_status batch_launch_all(psatd_batch b, const void* in[kMaxComp], void* out[kMaxComp]) {
   for (psatd_plan p : b->cls) {
-    psatd_status s = b->f32 ? run_step<float>(p, in, out) : run_step<double>(p, in, out);
+    psatd_status s = step_once(p, in, out);
     if (s != PSATD_OK) {
       g_err = p->err;
       return s;
@@ -777,7 +856,7 @@ extern "C" psatd_status psatd_batch_create(const psatd_desc* base, int32_t npatc
   if (!b) return fail(nullptr, PSATD_ERR_OOM, "host allocation failed");
   b->st = static_cast<cudaStream_t>(cuda_stream);
   b->npatch = npatch;
-  b->f32 = base->prec == PSATD_FP32;
+  b->f32 = base->prec != PSATD_FP64;
   b->total_cells = acc;
   std::vector<std::pair<int64_t, int64_t>> classes;
   for (auto& dd : dims)

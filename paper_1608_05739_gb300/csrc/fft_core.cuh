@@ -24,6 +24,8 @@
 
 #include <utility>
 
+#include "tc_dft.cuh"
+
 namespace psatd {
 
 template <typename R> struct Types;
@@ -242,9 +244,10 @@ template <int L>
 struct RowEPT { static constexpr int value = L >= 16 ? 16 : 8; };
 // The fused pass keeps 8 elements per thread: with 16 a 2048-point line has
 // half the threads and, its shared memory being fixed per line, the SM half
-// the warps (measured slower).
-template <int L>
-struct PushEPT { static constexpr int value = 8; };
+// the warps (measured slower).  The tensor-core variant (TC) takes 16, so that
+// its stages are radix-16 DFT-matrix contractions.
+template <int L, bool TC = false>
+struct PushEPT { static constexpr int value = TC ? 16 : 8; };
 
 template <int L, int EPT = 8>
 struct FFTPlan {
@@ -316,9 +319,9 @@ __device__ __forceinline__ const typename Types<R>::W* stage_tw(const ExBuf<C>& 
 // so the threads of a warp read consecutive entries.
 
 // One forward stage.
-template <typename R, int L, int EPT, int S>
+template <typename R, int L, int EPT, int S, bool TC>
 __device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
-                                          const typename Types<R>::W* __restrict__ tw, int t) {
+                                          const typename Types<R>::W* __restrict__ tw, int t, TcCtx* tc) {
   typedef typename Types<R>::C C;
   typedef FFTPlan<L, EPT> P;
   constexpr int RS = P::radix(S), NS = P::span(S), Q = EPT / RS, T = P::kT;
@@ -339,7 +342,8 @@ __device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[EPT], ExBuf<
 #pragma unroll
       for (int r = 1; r < RS; ++r) a[r] = twmul(a[r], __ldg(&tws[(r - 1) * NS]));
     }
-    butterfly<RS, false>(a);
+    if constexpr (TC && RS == 16) tc_dft<16, false>(a, *tc);
+    else butterfly<RS, false>(a);
     if constexpr (LAST) {
 #pragma unroll
       for (int r = 0; r < RS; ++r) v[q + r * Q] = a[r];
@@ -357,9 +361,9 @@ __device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[EPT], ExBuf<
 }
 
 // Adjoint of fwd_stage<S>.
-template <typename R, int L, int EPT, int S>
+template <typename R, int L, int EPT, int S, bool TC>
 __device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
-                                          const typename Types<R>::W* __restrict__ tw, int t) {
+                                          const typename Types<R>::W* __restrict__ tw, int t, TcCtx* tc) {
   typedef typename Types<R>::C C;
   typedef FFTPlan<L, EPT> P;
   constexpr int RS = P::radix(S), NS = P::span(S), Q = EPT / RS, T = P::kT;
@@ -386,7 +390,8 @@ __device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[EPT], ExBuf<
 #pragma unroll
       for (int r = 0; r < RS; ++r) a[r] = buf[sw<CX>(base + r * NS)];
     }
-    butterfly<RS, true>(a);
+    if constexpr (TC && RS == 16) tc_dft<16, true>(a, *tc);
+    else butterfly<RS, true>(a);
     if constexpr (NS > 1) {
       const typename Types<R>::W* tws = stage_tw<R>(ex) + P::tw_off(S) + k;
 #pragma unroll
@@ -397,32 +402,35 @@ __device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[EPT], ExBuf<
   }
 }
 
-template <typename R, int L, int EPT, int... S>
+template <typename R, int L, int EPT, bool TC, int... S>
 __device__ __forceinline__ void fft_fwd_seq(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
-                                            const typename Types<R>::W* tw, int t,
+                                            const typename Types<R>::W* tw, int t, TcCtx* tc,
                                             std::integer_sequence<int, S...>) {
-  (fwd_stage<R, L, EPT, S>(v, ex, tw, t), ...);
+  (fwd_stage<R, L, EPT, S, TC>(v, ex, tw, t, tc), ...);
 }
-template <typename R, int L, int EPT, int... S>
+template <typename R, int L, int EPT, bool TC, int... S>
 __device__ __forceinline__ void fft_inv_seq(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
-                                            const typename Types<R>::W* tw, int t,
+                                            const typename Types<R>::W* tw, int t, TcCtx* tc,
                                             std::integer_sequence<int, S...>) {
-  (inv_stage<R, L, EPT, FFTPlan<L, EPT>::kStages - 1 - S>(v, ex, tw, t), ...);
+  (inv_stage<R, L, EPT, FFTPlan<L, EPT>::kStages - 1 - S, TC>(v, ex, tw, t, tc), ...);
 }
 
 // Forward DFT of length L: v holds x[t + T m] on entry, X[t + T m] on exit
 // (T = L/EPT, m < EPT).  Every thread of the block must call it (block-wide
 // barriers inside); the exchanges alternate between the two buffers of `ex`.
-template <typename R, int L, int EPT>
+// TC: the radix-16 stages run on the tensor cores (tc_dft.cuh, context *tc).
+template <typename R, int L, int EPT, bool TC = false>
 __device__ __forceinline__ void block_fft_fwd(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
-                                              const typename Types<R>::W* tw, int t) {
-  fft_fwd_seq<R, L, EPT>(v, ex, tw, t, std::make_integer_sequence<int, FFTPlan<L, EPT>::kStages>{});
+                                              const typename Types<R>::W* tw, int t, TcCtx* tc = nullptr) {
+  static_assert(!TC || sizeof(R) == 4, "tensor-core stages take float data");
+  fft_fwd_seq<R, L, EPT, TC>(v, ex, tw, t, tc, std::make_integer_sequence<int, FFTPlan<L, EPT>::kStages>{});
 }
 // Unnormalised inverse DFT (adjoint of block_fft_fwd).
-template <typename R, int L, int EPT>
+template <typename R, int L, int EPT, bool TC = false>
 __device__ __forceinline__ void block_fft_inv(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
-                                              const typename Types<R>::W* tw, int t) {
-  fft_inv_seq<R, L, EPT>(v, ex, tw, t, std::make_integer_sequence<int, FFTPlan<L, EPT>::kStages>{});
+                                              const typename Types<R>::W* tw, int t, TcCtx* tc = nullptr) {
+  static_assert(!TC || sizeof(R) == 4, "tensor-core stages take float data");
+  fft_inv_seq<R, L, EPT, TC>(v, ex, tw, t, tc, std::make_integer_sequence<int, FFTPlan<L, EPT>::kStages>{});
 }
 
 }  // namespace psatd

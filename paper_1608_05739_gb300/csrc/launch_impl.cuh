@@ -15,7 +15,7 @@ static cudaError_t set_smem(K kern, size_t smem) {
   return cudaSuccess;
 }
 
-template <typename R, int L>
+template <typename R, bool TC, int L>
 static cudaError_t fwd_T_L(bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io,
                            const void* tw, int64_t a, int64_t b, int64_t c, int64_t d, const int64_t* off) {
   typedef typename Types<R>::W W;
@@ -23,21 +23,21 @@ static cudaError_t fwd_T_L(bool r2c, const PassGeom& g, cudaStream_t st, const L
   cudaError_t e;
   if (r2c) {
     if constexpr (L <= 2048) {
-      auto kern = k_fwd_T<R, L, true>;
+      auto kern = k_fwd_T<R, L, true, TC>;
       if ((e = set_smem(kern, g.smem)) != cudaSuccess) return e;
       kern<<<g.grid, block, g.smem, st>>>(io, static_cast<const W*>(tw), a, b, c, d, g.log_tb, off);
     } else {
       return cudaErrorInvalidValue;
     }
   } else {
-    auto kern = k_fwd_T<R, L, false>;
+    auto kern = k_fwd_T<R, L, false, TC>;
     if ((e = set_smem(kern, g.smem)) != cudaSuccess) return e;
     kern<<<g.grid, block, g.smem, st>>>(io, static_cast<const W*>(tw), a, b, c, d, g.log_tb, off);
   }
   return cudaGetLastError();
 }
 
-template <typename R, int L>
+template <typename R, bool TC, int L>
 static cudaError_t inv_T_L(bool c2r, const PassGeom& g, cudaStream_t st, const LineIO& io,
                            const void* tw, int64_t a, int64_t b, int64_t c, int64_t d, const int64_t* off) {
   typedef typename Types<R>::W W;
@@ -45,29 +45,29 @@ static cudaError_t inv_T_L(bool c2r, const PassGeom& g, cudaStream_t st, const L
   cudaError_t e;
   if (c2r) {
     if constexpr (L <= 2048) {
-      auto kern = k_inv_T<R, L, true>;
+      auto kern = k_inv_T<R, L, true, TC>;
       if ((e = set_smem(kern, g.smem)) != cudaSuccess) return e;
       kern<<<g.grid, block, g.smem, st>>>(io, static_cast<const W*>(tw), a, b, c, d, g.log_tb, off);
     } else {
       return cudaErrorInvalidValue;
     }
   } else {
-    auto kern = k_inv_T<R, L, false>;
+    auto kern = k_inv_T<R, L, false, TC>;
     if ((e = set_smem(kern, g.smem)) != cudaSuccess) return e;
     kern<<<g.grid, block, g.smem, st>>>(io, static_cast<const W*>(tw), a, b, c, d, g.log_tb, off);
   }
   return cudaGetLastError();
 }
 
-template <typename R, int L>
+template <typename R, bool TC, int L>
 static cudaError_t push_L(int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
                           const PushArgs<R>& a, const void* tw) {
   typedef typename Types<R>::W W;
-  const dim3 block(FFTPlan<L, PushEPT<L>::value>::kT, tb);
+  const dim3 block(FFTPlan<L, PushEPT<L, TC>::value>::kT, tb);
   cudaError_t e;
 #define PSATD_PUSH_CASE(LAY)                                                   \
   case LAY: {                                                                  \
-    auto kern = k_line_push<R, L, LAY>;                                        \
+    auto kern = k_line_push<R, L, LAY, TC>;                                    \
     if ((e = set_smem(kern, smem)) != cudaSuccess) return e;                   \
     kern<<<grid, block, smem, st>>>(a, static_cast<const W*>(tw));             \
     break;                                                                     \
@@ -84,36 +84,38 @@ static cudaError_t push_L(int layout, dim3 grid, int tb, size_t smem, cudaStream
   return cudaGetLastError();
 }
 
-#define PSATD_L_SWITCH(FN, ...)                     \
-  switch (L) {                                      \
-    case 8: return FN<R, 8>(__VA_ARGS__);           \
-    case 16: return FN<R, 16>(__VA_ARGS__);         \
-    case 32: return FN<R, 32>(__VA_ARGS__);         \
-    case 64: return FN<R, 64>(__VA_ARGS__);         \
-    case 128: return FN<R, 128>(__VA_ARGS__);       \
-    case 256: return FN<R, 256>(__VA_ARGS__);       \
-    case 512: return FN<R, 512>(__VA_ARGS__);       \
-    case 1024: return FN<R, 1024>(__VA_ARGS__);     \
-    case 2048: return FN<R, 2048>(__VA_ARGS__);     \
-    case 4096: return FN<R, 4096>(__VA_ARGS__);     \
-    default: return cudaErrorInvalidValue;          \
+// The tensor-core variants exist from L = 16 on (their first radix-16 stage).
+#define PSATD_L_SWITCH(FN, ...)                                   \
+  switch (L) {                                                    \
+    case 8: if constexpr (!TC) return FN<R, TC, 8>(__VA_ARGS__);  \
+            else return cudaErrorInvalidValue;                    \
+    case 16: return FN<R, TC, 16>(__VA_ARGS__);                   \
+    case 32: return FN<R, TC, 32>(__VA_ARGS__);                   \
+    case 64: return FN<R, TC, 64>(__VA_ARGS__);                   \
+    case 128: return FN<R, TC, 128>(__VA_ARGS__);                 \
+    case 256: return FN<R, TC, 256>(__VA_ARGS__);                 \
+    case 512: return FN<R, TC, 512>(__VA_ARGS__);                 \
+    case 1024: return FN<R, TC, 1024>(__VA_ARGS__);               \
+    case 2048: return FN<R, TC, 2048>(__VA_ARGS__);               \
+    case 4096: return FN<R, TC, 4096>(__VA_ARGS__);               \
+    default: return cudaErrorInvalidValue;                        \
   }
 
-template <typename R>
+template <typename R, bool TC>
 cudaError_t launch_fwd_T(int L, bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io,
                          const void* tw, int64_t in_sa0, int64_t in_sb, int64_t out_sa0,
                          int64_t out_sk, const int64_t* a0_off) {
   PSATD_L_SWITCH(fwd_T_L, r2c, g, st, io, tw, in_sa0, in_sb, out_sa0, out_sk, a0_off)
 }
 
-template <typename R>
+template <typename R, bool TC>
 cudaError_t launch_inv_T(int L, bool c2r, const PassGeom& g, cudaStream_t st, const LineIO& io,
                          const void* tw, int64_t in_sa0, int64_t in_sk, int64_t out_sa0,
                          int64_t out_sb, const int64_t* a0_off) {
   PSATD_L_SWITCH(inv_T_L, c2r, g, st, io, tw, in_sa0, in_sk, out_sa0, out_sb, a0_off)
 }
 
-template <typename R>
+template <typename R, bool TC>
 cudaError_t launch_line_push(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
                              const PushArgs<R>& a, const void* tw) {
   PSATD_L_SWITCH(push_L, layout, grid, tb, smem, st, a, tw)

@@ -23,6 +23,8 @@ constexpr int kMaxComp = 11;
 struct LineIO {
   const void* in[kMaxComp];
   void* out[kMaxComp];
+  const void* gmat;  // tensor-core passes: split DFT matrices (kTcTail image)
+  int* err;          // tensor-core passes: device error word
 };
 
 // k-space coefficient table entry (one per |m|-octant point), see tables.cu.
@@ -54,13 +56,17 @@ struct PushArgs {
   R ic_h, ic_l;      // 1/c (hi, lo)
   R s_src;           // 1 / (eps0 c g0)
   R s_a6;            // 1 / (eps0 c^2 g0)
+  const void* gmat;  // tensor-core pass: split DFT matrices (kTcTail image)
+  int* err;          // tensor-core pass: device error word
 };
 
 // ---------------------------------------------------------------- pass 1 / 2
 // Forward FFT along the contiguous axis of TB consecutive lines b, written out
 // with b contiguous: out[a1] + a0*out_sa0 + k*out_sk + b.  R2C: the input rows
 // are real (length 2L), the output has L+1 bins (half spectrum).
-template <typename R, int L, bool R2C>
+// TC: radix-16 stages on the tensor cores; the dynamic shared memory then
+// starts with the kTcTail block and the A tiles alias the line buffers.
+template <typename R, int L, bool R2C, bool TC = false>
 __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
                                                int64_t in_sa0, int64_t in_sb, int64_t out_sa0,
                                                int64_t out_sk, int log_tb, const int64_t* __restrict__ in_off) {
@@ -70,13 +76,15 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO 
   constexpr int T = P::kT;
   constexpr int NK = R2C ? L + 1 : L;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* smem = reinterpret_cast<C*>(smem_raw);
+  C* smem = reinterpret_cast<C*>(smem_raw + (TC ? kTcTail : 0));
   const int TB = 1 << log_tb;
   const int t = threadIdx.x, g = threadIdx.y;
   const int64_t b = (int64_t)blockIdx.x * TB + g;
   const int a0 = blockIdx.y, a1 = blockIdx.z;
   __shared__ const void* twslot;
   if (t == 0 && g == 0) twslot = tw;
+  TcCtx tc;
+  if constexpr (TC) tc_setup(tc, smem_raw, io.gmat, smem_u32(smem), io.err);
   ExBuf<C> ex{{smem + g * L, smem + g * L}, 0, &twslot, true};  // one exchange buffer per line
 
   C v[EPT];
@@ -91,7 +99,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO 
     for (int m = 0; m < EPT; ++m) v[m] = row[t + T * m];
   }
   if constexpr (P::kStages == 1) __syncthreads();  // twslot visible (else the first exchange's barrier)
-  block_fft_fwd<R, L, EPT>(v, ex, tw, t);
+  block_fft_fwd<R, L, EPT, TC>(v, ex, tw, t, &tc);
 
   if constexpr (R2C) {
     // X[k] = Fe[k] + W_N^k Fo[k], Fe = (Z[k] + Z*[L-k])/2, Fo = (Z[k] - Z*[L-k])/(2i), k = 0..L,
@@ -134,6 +142,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO 
       ob[(int64_t)k * out_sk + gg] = tile[k * tp + gg];
     }
   }
+  if constexpr (TC) tc_teardown(tc);
 }
 
 // ---------------------------------------------------------------- pass 4 / 5
@@ -141,7 +150,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO 
 // in[a1] + a0*in_sa0 + k*in_sk + b, inverse FFT along k, write the lines
 // contiguously to out[a1] + a0*out_sa0 + b*out_sb.  C2R: L+1 Hermitian bins
 // in, real rows of length 2L out (unnormalised).
-template <typename R, int L, bool C2R>
+template <typename R, int L, bool C2R, bool TC = false>
 __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_inv_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
                                                int64_t in_sa0, int64_t in_sk, int64_t out_sa0,
                                                int64_t out_sb, int log_tb, const int64_t* __restrict__ out_off) {
@@ -151,13 +160,15 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_inv_T(LineIO 
   constexpr int T = P::kT;
   constexpr int NK = C2R ? L + 1 : L;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* smem = reinterpret_cast<C*>(smem_raw);
+  C* smem = reinterpret_cast<C*>(smem_raw + (TC ? kTcTail : 0));
   const int TB = 1 << log_tb;
   const int t = threadIdx.x, g = threadIdx.y;
   const int64_t b = (int64_t)blockIdx.x * TB + g;
   const int a0 = blockIdx.y, a1 = blockIdx.z;
   __shared__ const void* twslot;
   if (t == 0 && g == 0) twslot = tw;
+  TcCtx tc;
+  if constexpr (TC) tc_setup(tc, smem_raw, io.gmat, smem_u32(smem), io.err);
   C v[EPT];
   if constexpr (C2R) {
     // Z[k] = Fe + i Fo, Fe = X[k] + X*[L-k], Fo = (X[k] - X*[L-k]) conj(W_N^k), read straight
@@ -203,7 +214,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_inv_T(LineIO 
     __syncthreads();
   }
   ExBuf<C> ex{{smem + g * L, smem + g * L}, 0, &twslot, true};  // one exchange buffer per line
-  block_fft_inv<R, L, EPT>(v, ex, tw, t);
+  block_fft_inv<R, L, EPT, TC>(v, ex, tw, t, &tc);
   C* row;
   const int64_t o0 = out_off ? out_off[a0] : a0 * out_sa0;  // per-patch offsets of a batch
   if constexpr (C2R)
@@ -212,6 +223,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_inv_T(LineIO 
     row = static_cast<C*>(io.out[a1]) + o0 + b * out_sb;
 #pragma unroll
   for (int m = 0; m < EPT; ++m) row[t + T * m] = v[m];
+  if constexpr (TC) tc_teardown(tc);
 }
 
 // ---------------------------------------------------------------- the push
@@ -419,16 +431,18 @@ __device__ __forceinline__ void cp_async_wait_all() {
 
 // Fused last-axis pass: for TB lines (kx in 2D, (kx, ky) in 3D), forward FFT
 // of every input slot, per-mode push, inverse FFT of the n_out field slots,
-// written back in place.  Shared memory per line: n_in staged slots of L values
-// and one extra exchange buffer; a slot doubles as the other exchange buffer
-// of its own transforms.  After its forward FFT a slot holds the spectrum at
-// positions sw<kLastCX>(t + T m), so the push and the inverse FFT's first
-// exchange only touch each thread's own positions.
-template <typename R, int L, int LAYOUT>
-__global__ void __launch_bounds__(FFTPlan<L, PushEPT<L>::value>::kT > 256 ? FFTPlan<L, PushEPT<L>::value>::kT : 256)
+// written back in place.  Shared memory: n_in staged slots of L values per
+// line, then one extra exchange buffer per line (contiguous, so that in the
+// tensor-core variant TC they hold the A tiles of the CTA's 128-row groups);
+// a slot doubles as the other exchange buffer of its own transforms.  After
+// its forward FFT a slot holds the spectrum at positions sw<kLastCX>(t + T m),
+// so the push and the inverse FFT's first exchange only touch each thread's
+// own positions.
+template <typename R, int L, int LAYOUT, bool TC = false>
+__global__ void __launch_bounds__(FFTPlan<L, PushEPT<L, TC>::value>::kT > 256 ? FFTPlan<L, PushEPT<L, TC>::value>::kT : 256)
 k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   typedef typename Types<R>::C C;
-  constexpr int EPT = PushEPT<L>::value;
+  constexpr int EPT = PushEPT<L, TC>::value;
   typedef FFTPlan<L, EPT> P;
   constexpr int T = P::kT;
   constexpr int CXL = P::kLastCX;
@@ -436,11 +450,14 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   const int t = threadIdx.x, g = threadIdx.y;
   const int line = blockIdx.x * blockDim.y + g;
   const bool valid = line < a.nlines;
-  C* st = reinterpret_cast<C*>(smem_raw) + g * ((a.n_in + 1) * L);
-  C* bufB = st + a.n_in * L;
+  C* base = reinterpret_cast<C*>(smem_raw + (TC ? kTcTail : 0));
+  C* st = base + g * (a.n_in * L);
+  C* bufB = base + (int)blockDim.y * a.n_in * L + g * L;
   C* spec = static_cast<C*>(a.spec);
   __shared__ const void* twslot;
   if (t == 0 && g == 0) twslot = tw;
+  TcCtx tc;
+  if constexpr (TC) tc_setup(tc, smem_raw, a.gmat, smem_u32(base + (int)blockDim.y * a.n_in * L), a.err);
 
   int mxi, myi, rowi;
   line_modes(a, valid ? line : 0, mxi, myi, rowi);
@@ -473,7 +490,7 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
     for (int m = 0; m < EPT; ++m) v[m] = sl[t + T * m];
     __syncthreads();  // the slot becomes an exchange buffer
     ExBuf<C> ex{{sl, bufB}, 0, &twslot, false};
-    block_fft_fwd<R, L, EPT>(v, ex, tw, t);
+    block_fft_fwd<R, L, EPT, TC>(v, ex, tw, t, &tc);
 #pragma unroll
     for (int m = 0; m < EPT; ++m) sl[sw<CXL>(t + T * m)] = v[m];
   }
@@ -509,13 +526,14 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
 #pragma unroll
     for (int m = 0; m < EPT; ++m) v[m] = sl[sw<CXL>(t + T * m)];
     ExBuf<C> ex{{sl, bufB}, 0, &twslot, false};
-    block_fft_inv<R, L, EPT>(v, ex, tw, t);
+    block_fft_inv<R, L, EPT, TC>(v, ex, tw, t, &tc);
     if (valid) {
       C* dst = spec + c * a.cs + (int64_t)line * L;
 #pragma unroll
       for (int m = 0; m < EPT; ++m) dst[t + T * m] = v[m];
     }
   }
+  if constexpr (TC) tc_teardown(tc);
 }
 
 

@@ -145,6 +145,36 @@ __global__ void k_coefs(void* out, int f32, int e0, int e1, int e2, int nx, int 
   }
 }
 
+// Split radix-16 DFT matrices for the tensor-core stages (tc_dft.cuh): for
+// direction dir (0: F_rq = exp(-2 pi i rq/16), 1: its conjugate) the real
+// 32 x 32 form G[n][k], n = 2r + d, k = 2q + c, as G = G_h + G_l + G_ll:
+// G_h = G rounded to the 2^-8 grid (exact in FP16), G_l = FP16 of G - G_h,
+// G_ll = FP16 of G - G_h - G_l (all from the FP64 value); each piece stored as
+// 8-row x 16-byte core matrices (LBO 128 B, SBO 512 B).
+__global__ void k_tc_dftmat(unsigned short* out) {
+  typedef TcGeom<16> G;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * 32 * 32) return;
+  const int dir = e >> 10, n = (e >> 5) & 31, k = e & 31;
+  const int r = n >> 1, d = n & 1, q = k >> 1, c = k & 1;
+  double sn, cs;
+  sincospi((dir ? 2.0 : -2.0) * (double)((r * q) & 15) / 16.0, &sn, &cs);
+  const double v = d == 0 ? (c == 0 ? cs : -sn) : (c == 0 ? sn : cs);
+  const double vh = rint(v * 256.0) / 256.0;
+  const __half h = __float2half_rn((float)vh);
+  const __half l = __float2half_rn((float)(v - vh));
+  const __half ll = __float2half_rn((float)(v - vh - (double)__half2float(l)));
+  const int off = (n >> 3) * G::kSBO + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
+  out[(dir * G::kGDir + off) / 2] = __half_as_ushort(h);
+  out[(dir * G::kGDir + G::kGPiece + off) / 2] = __half_as_ushort(l);
+  out[(dir * G::kGDir + 2 * G::kGPiece + off) / 2] = __half_as_ushort(ll);
+}
+
+cudaError_t launch_tc_dftmat(void* out, cudaStream_t st) {
+  k_tc_dftmat<<<8, 256, 0, st>>>(static_cast<unsigned short*>(out));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_twiddles(void* out, int L, int ept, bool r2c, bool f32, cudaStream_t st) {
   const int total = 2 * L;
   k_twiddles<<<(total + 255) / 256, 256, 0, st>>>(out, L, ept, r2c ? 1 : 0, f32 ? 1 : 0);

@@ -25,7 +25,7 @@ def torch_dev(a, prec):
 def rounded(a, prec):
     """Inputs as the GPU sees them (FP32 paths read float32-rounded arrays)."""
     a = np.asarray(a, dtype=np.float64)
-    return a.astype(np.float32).astype(np.float64) if prec == "fp32" else a
+    return a.astype(np.float32).astype(np.float64) if prec != "fp64" else a
 
 
 def grid_n(shape):

@@ -61,7 +61,7 @@ def _create(lib, desc):
     (lambda d: setattr(d, "c", -1.0), 1),
     (lambda d: setattr(d, "eps0", float("nan")), 1),
     (lambda d: d.d.__setitem__(1, 0.0), 1),
-    (lambda d: setattr(d, "prec", 2), 2),                  # mixed precision: reserved
+    (lambda d: setattr(d, "prec", 2), 2),                  # split-BF16: not in this build
     (lambda d: setattr(d, "prec", 9), 1),
     (lambda d: setattr(d, "src", 7), 1),
     (lambda d: setattr(d, "flags", 1), 1),
@@ -120,3 +120,22 @@ def test_batch_create_rejects_invalid_arguments(lib):
     assert lib.psatd_batch_step(None, None, None, 1) == 1
     assert lib.psatd_batch_destroy(None) == 0
     assert lib.psatd_batch_cells(None) == 0
+
+
+@pytest.mark.parametrize("n,why", [((64, 32), b"128 threads"), ((16, 64), b"nx >= 32"), ((64, 8), b"ny, nz >= 16")])
+def test_mixed_fp16_shape_limits(lib, n, why):
+    """The tensor-core passes need one MMA row per thread in groups of 128:
+    grids too small for that are refused before any allocation."""
+    d = capi.make_desc(n, (1.0, 1.0), 0.5, layout="te", prec="mixed_fp16", src="J")
+    st, h = _create(lib, d)
+    assert st == 2 and h.value is None
+    assert why in lib.psatd_last_error(None)
+
+
+def test_mixed_fp16_only_for_the_psatd_step(lib):
+    d = capi.make_desc((64, 64), (1.0, 1.0), 0.5, layout="te", prec="mixed_fp16", src="J")
+    f = capi.psatd_fields()
+    s = capi.psatd_sources()
+    assert lib.fdtd_step(ct.byref(d), 0, ct.byref(f), ct.byref(s), 1, None) == 2
+    assert lib.psatd_step_noalloc(ct.byref(d), ct.byref(f), ct.byref(s), 1, None) == 2
+    assert b"FP32" in lib.psatd_last_error(None)
