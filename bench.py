@@ -213,6 +213,49 @@ def cpu_baseline(seconds):
                       % (steps, el)}
 
 
+def time_te2048(capi, torch, prec, args, dev, dt, dx, Jy_all, flush, stream, world, sample_clocks):
+    """W untimed + K timed steps of the 2048^2 TE workload at precision `prec`
+    from zero fields, L2 flushed before every timed step; returns the summed
+    CUDA-event ms of the K steps, the per-kernel times, the clock record and the
+    plan (kept for the end-to-end leg)."""
+    plan = capi.Plan((NX, NY), (dx, dx), dt, layout="te", prec=prec, src="J", stream=stream)
+    Ex = torch.zeros(NY, NX, device=dev)
+    Ey = torch.zeros(NY, NX, device=dev)
+    Bz = torch.zeros(NY, NX, device=dev)
+    Jx = torch.zeros(NY, NX, device=dev)
+    for n in range(args.warmup):
+        plan.step([Ex, Ey, None], [None, None, Bz], [Jx, Jy_all[n], None])
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device()) if sample_clocks else None
+    plan.set_timing(True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    for s in range(args.steps):
+        flush.zero_()
+        starts[s].record(stream)
+        plan.step([Ex, Ey, None], [None, None, Bz], [Jx, Jy_all[args.warmup + s], None])
+        ends[s].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    ms = sum(starts[s].elapsed_time(ends[s]) for s in range(args.steps))
+    ktimes = plan.kernel_times()
+    plan.set_timing(False)
+    plan.sync()  # raises if a tensor-core pass reported an expired wait
+    if not bool(torch.isfinite(Ey).all()):
+        raise RuntimeError("non-finite field after the timed steps")
+    return ms, ktimes, clk, plan
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -223,7 +266,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed_fp16"],
-                    help="te2048 arithmetic: plain FP32, or tensor-core split-FP16 radix-16 stages")
+                    help="te2048 arithmetic of the headline line: plain FP32, or tensor-core split-FP16 "
+                         "radix-16 stages (the other one is timed too and reported under 'other_precision')")
+    ap.add_argument("--no-side-precision", action="store_true", help="skip timing the other precision")
     ap.add_argument("--workload", default="te2048", choices=["te2048", "3d256", "fdtd-yee", "fdtd-ckc", "batch512"],
                     help="te2048 (default) is the metric's configuration; the others are side measurements")
     args = ap.parse_args()
@@ -253,44 +298,22 @@ def main():
     dx = 1.0 / LAM_CELLS
     dt = dx / math.sqrt(2.0)
     stream = torch.cuda.current_stream()
-    plan = capi.Plan((NX, NY), (dx, dx), dt, layout="te", prec=args.precision, src="J", stream=stream)
-    Ex = torch.zeros(NY, NX, device=dev)
-    Ey = torch.zeros(NY, NX, device=dev)
-    Bz = torch.zeros(NY, NX, device=dev)
-    Jx = torch.zeros(NY, NX, device=dev)
     total = args.warmup + args.steps
     prof = torch.from_numpy(np.stack([sheet_profile(n, dt, dx) for n in range(total)])).float().to(dev)
     Jy_all = [prof[n].expand(NY, NX).contiguous() for n in range(total)]  # resident before timing
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    for n in range(args.warmup):
-        plan.step([Ex, Ey, None], [None, None, Bz], [Jx, Jy_all[n], None])
-    torch.cuda.synchronize()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    plan.set_timing(True)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.3)
-    for s in range(args.steps):
-        flush.zero_()
-        starts[s].record(stream)
-        plan.step([Ex, Ey, None], [None, None, Bz], [Jx, Jy_all[args.warmup + s], None])
-        ends[s].record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    if world > 1:
-        dist.barrier()
-    ms = sum(starts[s].elapsed_time(ends[s]) for s in range(args.steps))
-    ktimes = plan.kernel_times()
-    plan.set_timing(False)
-    plan.sync()  # raises if a tensor-core pass reported an expired wait
-    if not bool(torch.isfinite(Ey).all()):
-        raise RuntimeError("non-finite field after the timed steps")
+    other = "mixed_fp16" if args.precision == "fp32" else "fp32"
+    side = None
+    if not args.no_side_precision:
+        side_ms, side_kt, _, side_plan = time_te2048(capi, torch, other, args, dev, dt, dx, Jy_all, flush, stream,
+                                                     world, sample_clocks=False)
+        side_plan.destroy()
+        side = {"precision": PREC_NOTE[other], "value": NX * NY * args.steps / (side_ms * 1e-3),
+                "unit": "cell-steps/s", "ms_per_step": side_ms / args.steps,
+                "per_kernel_ms": {k: v[1] / v[0] for k, v in side_kt.items()}}
+    ms, ktimes, clk, plan = time_te2048(capi, torch, args.precision, args, dev, dt, dx, Jy_all, flush, stream,
+                                        world, sample_clocks=True)
 
     # end to end through the C ABI from pinned host buffers
     hE = [torch.zeros(NY, NX).pin_memory() for _ in range(3)]
@@ -359,6 +382,8 @@ def main():
             "roofline": roof,
             "clocks": clk,
         }
+        if side is not None:
+            line["other_precision"] = side
         if world == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
         print(json.dumps(line), flush=True)

@@ -87,6 +87,13 @@ typedef enum {
 
 typedef enum { PSATD_FDTD_YEE = 0, PSATD_FDTD_CKC = 1 } psatd_fdtd_scheme;
 
+/* psatd_desc.flags bits.  PSATD_FLAG_AUTOTUNE: psatd_coeffs_init also picks
+ * the launch shapes with the autotuner (psatd_plan_autotune with 5 timed
+ * steps), or reuses the shapes found earlier in this process for the same
+ * precision, layout, source form and sizes.  PSATD plans and batches only;
+ * fdtd_step rejects it and psatd_step_noalloc ignores it. */
+#define PSATD_FLAG_AUTOTUNE 1
+
 /* Problem statement (the paper's arguments: grid sizes, cell sizes, dt, c, eps0). */
 typedef struct {
   int32_t ndim;      /* 2 or 3 (must agree with layout)                           */
@@ -98,7 +105,7 @@ typedef struct {
   double eps0;       /* vacuum permittivity (> 0)                                 */
   int32_t prec;      /* psatd_precision                                           */
   int32_t src;       /* psatd_source_form                                         */
-  int32_t flags;     /* reserved, must be 0                                       */
+  int32_t flags;     /* PSATD_FLAG_* bits (0: none)                               */
   int32_t reserved;  /* must be 0                                                 */
 } psatd_desc;
 
@@ -132,8 +139,38 @@ psatd_status psatd_plan_create(const psatd_desc* desc, void* cuda_stream, psatd_
  * twiddles exp(-2 pi i j / n) per axis and, per |k|-octant entry,
  * C, S/|m|, (1-C)/|m|^2, (S/(ck)-dt)/(eps0 |m|^2), (S/x-1)/(eps0 g |m|^2),
  * (S/x-C)/(eps0 g |m|^2) with their k -> 0 limits, all scaled by 1/N.
- * Must be called once before psatd_step (psatd_step fails otherwise).     */
+ * Must be called once before psatd_step (psatd_step fails otherwise).
+ * With PSATD_FLAG_AUTOTUNE it then runs (or recalls) the autotuner and is
+ * synchronous.                                                              */
 psatd_status psatd_coeffs_init(psatd_plan plan);
+
+/* Autotuner (no counterpart in the paper; the launch shapes of the passes).
+ * Times every valid candidate of each knob with CUDA events on the plan's
+ * stream over `reps` steps (1..1000) of zero-filled scratch fields it
+ * allocates and frees, keeps the fastest, and caches it for the process:
+ *   lines per CTA of each transposing pass (x forward/inverse, y in 3D), and
+ *   the fused pass's radix schedule (radix-8 or radix-16 stages, i.e. 8 or 16
+ *   elements per thread; radix 16 only for PSATD_MIXED_FP16) with its lines
+ *   per CTA.
+ * Results do not depend on the choice (same arithmetic, same order per line).
+ * `report` (may be NULL) receives a one-line summary of the times, the chosen
+ * ones marked '*', truncated to report_len - 1 bytes.  Synchronous.
+ * Errors: INVALID_ARG (NULL plan, tables not initialised, reps out of range),
+ * OOM (scratch), UNSUPPORTED, CUDA.                                         */
+psatd_status psatd_plan_autotune(psatd_plan plan, int32_t reps, char* report, size_t report_len);
+
+/* Launch shapes of the plan, as int32_t cfg[6]:
+ *   cfg[0..3] log2(lines per CTA) of the x forward, y forward (3D), y inverse
+ *             (3D) and x inverse passes (-1 / unused: 2D y passes);
+ *   cfg[4]    lines per CTA of the fused pass;
+ *   cfg[5]    its elements per thread: 8 (radix-8 stages) or 16 (radix-16).
+ * psatd_plan_get_launch reports the shapes the next step will use.
+ * psatd_plan_set_launch sets them (-1 entries: the built-in choice) after
+ * checking each against the shapes the autotuner would consider
+ * (INVALID_ARG otherwise); it rebuilds the fused axis's twiddle table when
+ * cfg[5] changes, so it needs psatd_coeffs_init first.                    */
+psatd_status psatd_plan_set_launch(psatd_plan plan, const int32_t cfg[6]);
+psatd_status psatd_plan_get_launch(psatd_plan plan, int32_t cfg[6]);
 
 /* Advance E, B by nsteps PSATD steps (nsteps >= 1).  `sources` may be NULL
  * for PSATD_SRC_NONE and must not be NULL otherwise.  Per step: forward

@@ -72,7 +72,12 @@ EXPORTS = [
     ("psatd_batch_step", ct.c_int, [ct.c_void_p, ct.POINTER(psatd_fields), ct.POINTER(psatd_sources), ct.c_int32]),
     ("psatd_batch_cells", ct.c_int64, [ct.c_void_p]),
     ("psatd_batch_destroy", ct.c_int, [ct.c_void_p]),
+    ("psatd_plan_autotune", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_char_p, ct.c_size_t]),
+    ("psatd_plan_set_launch", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32)]),
+    ("psatd_plan_get_launch", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32)]),
 ]
+
+FLAG_AUTOTUNE = 1
 
 
 def load(path: str = LIB_PATH):
@@ -97,7 +102,7 @@ def _check(status, plan=None):
         raise PsatdError(status, msg.decode() if msg else "")
 
 
-def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0):
+def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, autotune=False):
     """psatd_desc for grid ``n`` = (nx, ny[, nz]) and cell sizes ``d``."""
     nd = len(n)
     desc = psatd_desc()
@@ -109,7 +114,7 @@ def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0):
     desc.dt, desc.c, desc.eps0 = float(dt), float(c), float(eps0)
     desc.prec = PREC[prec]
     desc.src = SRC[src]
-    desc.flags = 0
+    desc.flags = FLAG_AUTOTUNE if autotune else 0
     desc.reserved = 0
     return desc
 
@@ -172,13 +177,14 @@ class Plan:
     [nz, ny, nx] (None for components absent from the layout).
     """
 
-    def __init__(self, n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, stream=None):
+    def __init__(self, n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, stream=None,
+                 autotune=False):
         import torch
         lib = load()
         self.n, self.layout, self.prec, self.src = tuple(n), layout, prec, src
         self.shape = _grid_shape(n)
         self.dtype = _torch_dtype(prec)
-        self.desc = make_desc(n, d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0)
+        self.desc = make_desc(n, d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0, autotune=autotune)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -196,6 +202,22 @@ class Plan:
 
     def sync(self):
         _check(load().psatd_plan_sync(self.handle), self.handle)
+
+    def get_launch(self):
+        """[log2 tb fwd_x, fwd_y, inv_y, inv_x, push lines per CTA, push elements per thread]."""
+        cfg = (ct.c_int32 * 6)()
+        _check(load().psatd_plan_get_launch(self.handle, cfg), self.handle)
+        return list(cfg)
+
+    def set_launch(self, cfg):
+        arr = (ct.c_int32 * 6)(*[int(v) for v in cfg])
+        _check(load().psatd_plan_set_launch(self.handle, arr), self.handle)
+
+    def autotune(self, reps=5):
+        """psatd_plan_autotune: time the launch shapes, keep the fastest; returns the report."""
+        buf = ct.create_string_buffer(4096)
+        _check(load().psatd_plan_autotune(self.handle, int(reps), buf, len(buf)), self.handle)
+        return buf.value.decode()
 
     def workspace_bytes(self):
         return int(load().psatd_plan_workspace_bytes(self.handle))
@@ -231,7 +253,8 @@ class Batch:
     the patches back to back, patch i being its (ny_i, nx_i) row-major block.
     """
 
-    def __init__(self, sizes, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, stream=None):
+    def __init__(self, sizes, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, stream=None,
+                 autotune=False):
         import torch
         lib = load()
         self.sizes = [(int(a), int(b)) for a, b in sizes]
@@ -243,7 +266,8 @@ class Batch:
         for a, b in self.sizes:
             self.offsets.append(acc)
             acc += a * b
-        desc = make_desc(self.sizes[0], d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0)
+        desc = make_desc(self.sizes[0], d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0,
+                         autotune=autotune)
         arr = (ct.c_int64 * (2 * len(self.sizes)))(*[v for ab in self.sizes for v in ab])
         if stream is None:
             stream = torch.cuda.current_stream()

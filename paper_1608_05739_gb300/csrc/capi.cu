@@ -55,6 +55,12 @@ struct psatd_plan_s {
   int npatch = 1;             // 2D batches: patches of this size class
   int64_t* d_off = nullptr;   // their element offsets in the caller's packed arrays (device)
   bool tc = false;            // split-FP16 tensor-core radix-16 stages (PSATD_MIXED_FP16)
+  // launch configuration: lines per CTA of the passes fwd_x, fwd_y, inv_y, inv_x and of the
+  // fused pass (-1: the built-in heuristic), and the fused pass's elements per thread
+  // (8: radix-8 stages, 16: radix-16); set by psatd_plan_autotune
+  int cfg_log_tb[4] = {-1, -1, -1, -1};
+  int cfg_push_tb = -1;
+  int push_ept = 8;
   void* gmat = nullptr;       // their split DFT matrices (kTcTail image, device)
   int* d_err = nullptr;       // device error word of the tensor-core passes
 };
@@ -105,7 +111,8 @@ psatd_status validate_desc(psatd_plan p, const psatd_desc* d, bool psatd_limits)
   if (d->layout < 0 || d->layout > 3) return fail(p, PSATD_ERR_INVALID_ARG, "unknown layout %d", d->layout);
   if (d->ndim != layout_ndim(d->layout))
     return fail(p, PSATD_ERR_INVALID_ARG, "ndim %d does not match layout %d", d->ndim, d->layout);
-  if (d->flags != 0 || d->reserved != 0) return fail(p, PSATD_ERR_INVALID_ARG, "flags/reserved must be 0");
+  if ((d->flags & ~(psatd_limits ? PSATD_FLAG_AUTOTUNE : 0)) != 0 || d->reserved != 0)
+    return fail(p, PSATD_ERR_INVALID_ARG, "unknown flags (or reserved != 0)");
   if (d->src < 0 || d->src > 2) return fail(p, PSATD_ERR_INVALID_ARG, "unknown source form %d", d->src);
   if (d->layout == PSATD_FIELDS_2D_TM && d->src == PSATD_SRC_J_RHO)
     return fail(p, PSATD_ERR_INVALID_ARG, "the TM layout has no rho-form (k.E = 0)");
@@ -225,8 +232,8 @@ size_t tpass_smem(int L, int log_tb, size_t nk, size_t csz) {
 
 // lines per CTA of the fused last-axis pass: up to 256 threads and 100 KB of
 // line buffers; the tensor-core variant needs a multiple of 128 threads
-int push_lines_per_cta(int L, int n_in, int64_t nlines, bool tc, bool f32) {
-  const int T = L / push_ept(L, tc);
+int push_lines_per_cta(int L, int n_in, int64_t nlines, bool tc, bool f32, int ept) {
+  const int T = L / ept;
   const size_t per_line = ((size_t)n_in + 1) * (size_t)L * (f32 ? 8 : 16);
   int tb = 1;
   while (tb * 2 * T <= 256 && (size_t)(tb * 2) * per_line <= 100 * 1024 && tb * 2 <= nlines) tb *= 2;
@@ -278,7 +285,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
   // pass 1: x rows (R2C), b = y -> spec1 [c][kx][z][y] (3D) / [c][patch][kx][y] (2D)
   {
     PassGeom g;
-    g.log_tb = pick_log_tb(Lx, ny, p->f32);
+    g.log_tb = p->cfg_log_tb[0] >= 0 ? p->cfg_log_tb[0] : pick_log_tb(Lx, ny, p->f32);
     g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)na0, (unsigned)p->n_in);
     g.smem = tail + tpass_smem(Lx, g.log_tb, 0, csz);
     for (int c = 0; c < p->n_in; ++c) {
@@ -296,7 +303,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
   if (p->ndim == 3) {
     // pass 2: y lines (C2C), b = z, a0 = kx: spec1 [c][kx][z][y] -> spec2 [c][kx][ky][z]
     PassGeom g;
-    g.log_tb = pick_log_tb((int)ny, nz, p->f32);
+    g.log_tb = p->cfg_log_tb[1] >= 0 ? p->cfg_log_tb[1] : pick_log_tb((int)ny, nz, p->f32);
     g.grid = dim3((unsigned)(nz >> g.log_tb), (unsigned)nxh, (unsigned)p->n_in);
     g.smem = tail + tpass_smem((int)ny, g.log_tb, (size_t)ny, csz);
     for (int c = 0; c < p->n_in; ++c) {
@@ -339,18 +346,24 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     a.err = p->d_err;
     const void* twl = p->tw[p->ndim == 3 ? 2 : 1];
     {
-      const int tb = push_lines_per_cta(Lline, p->n_in, nlines, TC, p->f32);
+      const int tb = p->cfg_push_tb > 0 ? p->cfg_push_tb
+                                        : push_lines_per_cta(Lline, p->n_in, nlines, TC, p->f32, p->push_ept);
       const size_t per_line = ((size_t)p->n_in + 1) * (size_t)Lline * csz;
       const dim3 grid((unsigned)((nlines + tb - 1) / tb));
       TimedLaunch tl(p, K_PUSH);
-      e = launch_line_push<R, TC>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl);
+      if (p->push_ept == 16) {
+        e = launch_line_push<R, TC, 16>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl);
+      } else {
+        if constexpr (TC) e = cudaErrorInvalidValue;
+        else e = launch_line_push<R, false, 8>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl);
+      }
       if (e != cudaSuccess) return cuda_fail(p, e, "line_fft_push launch");
     }
   }
   if (p->ndim == 3) {
     // pass 4: inverse y lines: spec2 [c][kx][ky][z] -> spec1 [c][kx][z][y]
     PassGeom g;
-    g.log_tb = pick_log_tb((int)ny, nz, p->f32);
+    g.log_tb = p->cfg_log_tb[2] >= 0 ? p->cfg_log_tb[2] : pick_log_tb((int)ny, nz, p->f32);
     g.grid = dim3((unsigned)(nz >> g.log_tb), (unsigned)nxh, (unsigned)p->n_out);
     g.smem = tail + tpass_smem((int)ny, g.log_tb, (size_t)ny, csz);
     for (int c = 0; c < p->n_out; ++c) {
@@ -364,7 +377,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
   // last pass: inverse x rows (C2R): spec1 -> out [z][y][x] (3D) / packed patches (2D)
   {
     PassGeom g;
-    g.log_tb = pick_log_tb(Lx, ny, p->f32);
+    g.log_tb = p->cfg_log_tb[3] >= 0 ? p->cfg_log_tb[3] : pick_log_tb(Lx, ny, p->f32);
     g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)na0, (unsigned)p->n_out);
     g.smem = tail + tpass_smem(Lx, g.log_tb, 0, csz);
     for (int c = 0; c < p->n_out; ++c) {
@@ -400,11 +413,241 @@ psatd_status check_tc_shape(psatd_plan p, int maxsm) {
                   rows[i].L, (long long)rows[i].nb);
   }
   const int64_t nlines = p->ndim == 3 ? p->nxh * p->ny : p->nxh * p->npatch;
-  const int tb = push_lines_per_cta(Ll, p->n_in, nlines, true, true);
+  const int tb = push_lines_per_cta(Ll, p->n_in, nlines, true, true, 16);
   const size_t smem = (size_t)kTcTail + (size_t)tb * ((size_t)p->n_in + 1) * (size_t)Ll * 8;
   if (maxsm > 0 && smem > (size_t)maxsm)
     return fail(nullptr, PSATD_ERR_UNSUPPORTED, "mixed precision: last-axis length %d needs %zu bytes of shared memory",
                 Ll, smem);
+  return PSATD_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+// Knobs: lines per CTA of each transposing pass (fwd_x, fwd_y, inv_y, inv_x)
+// and, for the fused pass, its radix schedule (8 or 16 elements per thread:
+// radix-8 or radix-16 stages) with its lines per CTA.  Every valid candidate
+// of every knob is timed on the plan's stream (CUDA events around each launch)
+// over `reps` steps on zero-filled scratch fields; the passes are independent,
+// so round i sets every knob to its i-th candidate and one series of steps
+// times them all.  Results are cached per (precision, layout, source form,
+// sizes, patch count) for the process.
+struct TuneCfg {
+  int log_tb[4];
+  int push_tb, push_ept;
+};
+struct TuneKey {
+  int prec, layout, form, npatch;
+  int64_t n[3];
+  bool operator==(const TuneKey& o) const {
+    return prec == o.prec && layout == o.layout && form == o.form && npatch == o.npatch && n[0] == o.n[0] &&
+           n[1] == o.n[1] && n[2] == o.n[2];
+  }
+};
+std::mutex g_tune_mutex;
+std::vector<std::pair<TuneKey, TuneCfg>> g_tune_cache;
+
+TuneKey tune_key(psatd_plan p) {
+  return TuneKey{p->d.prec, p->layout, p->form, p->npatch, {p->nx, p->ny, p->nz}};
+}
+void apply_cfg(psatd_plan p, const TuneCfg& c) {
+  for (int i = 0; i < 4; ++i) p->cfg_log_tb[i] = c.log_tb[i];
+  p->cfg_push_tb = c.push_tb;
+  p->push_ept = c.push_ept;
+}
+
+psatd_status regen_push_twiddles(psatd_plan p) {
+  if (p->ndim < 2) return PSATD_OK;
+  const int i = p->ndim - 1;
+  const int L = (int)(i == 2 ? p->nz : p->ny);
+  cudaError_t e = launch_twiddles(p->tw[i], L, p->push_ept, false, p->f32, p->st);
+  return e == cudaSuccess ? PSATD_OK : cuda_fail(p, e, "twiddle table launch");
+}
+
+// Valid launch shapes of every knob: rows[k] = log2(lines per CTA) of
+// transposing pass k (empty if the pass does not exist), push = (elements per
+// thread, lines per CTA) of the fused pass.
+struct TuneSpace {
+  std::vector<int> rows[4];
+  std::vector<std::pair<int, int>> push;
+  int rowL[4];
+  int Ll;
+};
+
+TuneSpace tune_space(psatd_plan p) {
+  TuneSpace ts;
+  int maxsm = 0;
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+  const size_t csz = p->f32 ? 8 : 16;
+  const size_t tail = p->tc ? (size_t)kTcTail : 0;
+  const int maxthr = p->f32 ? 512 : 256;
+  const int Lx = (int)(p->nx / 2);
+  ts.Ll = (int)(p->ndim == 3 ? p->nz : p->ny);
+  const int64_t nlines = p->ndim == 3 ? p->nxh * p->ny : p->nxh * p->npatch;
+  const int rowL[4] = {Lx, (int)p->ny, (int)p->ny, Lx};
+  const int64_t rowNb[4] = {p->ny, p->nz, p->nz, p->ny};
+  const size_t rowNk[4] = {0, (size_t)p->ny, (size_t)p->ny, 0};
+  const bool rowOn[4] = {true, p->ndim == 3, p->ndim == 3, true};
+  for (int k = 0; k < 4; ++k) {
+    ts.rowL[k] = rowL[k];
+    if (!rowOn[k]) continue;
+    const int T = rowL[k] / row_ept(rowL[k]);
+    for (int lg = 0; (1 << lg) <= 32 && (1 << lg) <= rowNb[k] && (T << lg) <= maxthr; ++lg) {
+      if (p->tc && (T << lg) < 128) continue;
+      if (maxsm > 0 && tail + tpass_smem(rowL[k], lg, rowNk[k], csz) > (size_t)maxsm) continue;
+      ts.rows[k].push_back(lg);
+    }
+  }
+  for (int ept : {8, 16}) {
+    if ((p->tc && ept != 16) || ts.Ll < ept) continue;
+    const int T = ts.Ll / ept;
+    const size_t per_line = ((size_t)p->n_in + 1) * (size_t)ts.Ll * csz;
+    for (int tb = 1; tb * T <= (T > 256 ? T : 256); tb *= 2) {
+      if (p->tc && (tb * T) % 128 != 0) continue;
+      if (maxsm > 0 && tail + tb * per_line > (size_t)maxsm) continue;
+      if (tb > 1 && tb / 2 >= nlines) break;
+      ts.push.push_back({ept, tb});
+    }
+  }
+  return ts;
+}
+
+psatd_status autotune(psatd_plan p, int reps, std::string* report) {
+  if (reps < 1) reps = 1;
+  const size_t rsz = p->f32 ? 4 : 8;
+  TuneSpace ts = tune_space(p);
+  std::vector<int>* rows = ts.rows;
+  std::vector<std::pair<int, int>>& push = ts.push;
+  const int* rowL = ts.rowL;
+  const int Ll = ts.Ll;
+  const bool rowOn[4] = {true, p->ndim == 3, p->ndim == 3, true};
+  for (int k = 0; k < 4; ++k)
+    if (rowOn[k] && rows[k].empty())
+      return fail(p, PSATD_ERR_UNSUPPORTED, "autotune: no valid launch shape for pass %d", k);
+  if (push.empty()) return fail(p, PSATD_ERR_UNSUPPORTED, "autotune: no valid launch shape for the fused pass");
+  // scratch fields (zero) and, for a batch class, contiguous patch offsets
+  const size_t cells = (size_t)p->nx * p->ny * p->nz * p->npatch;
+  void* fbuf = nullptr;
+  cudaError_t e = cudaMalloc(&fbuf, (size_t)p->n_in * cells * rsz);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(p, PSATD_ERR_OOM, "autotune: scratch fields of %zu bytes", (size_t)p->n_in * cells * rsz);
+  }
+  int64_t* d_off2 = nullptr;
+  int64_t* saved_off = p->d_off;
+  psatd_status st = PSATD_OK;
+  if (p->d_off) {
+    std::vector<int64_t> offs(p->npatch);
+    for (int i = 0; i < p->npatch; ++i) offs[i] = (int64_t)i * p->nx * p->ny;
+    e = cudaMalloc(&d_off2, offs.size() * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMemcpy(d_off2, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) st = cuda_fail(p, e, "autotune: offset table");
+    else p->d_off = d_off2;
+  }
+  if (st == PSATD_OK) {
+    e = cudaMemsetAsync(fbuf, 0, (size_t)p->n_in * cells * rsz, p->st);
+    if (e != cudaSuccess) st = cuda_fail(p, e, "autotune: clear");
+  }
+  const void* in[kMaxComp] = {};
+  void* out[kMaxComp] = {};
+  for (int c = 0; c < p->n_in; ++c) {
+    in[c] = static_cast<char*>(fbuf) + c * cells * rsz;
+    if (c < p->n_out) out[c] = const_cast<void*>(in[c]);
+  }
+  size_t rounds = push.size();
+  for (int k = 0; k < 4; ++k) rounds = std::max(rounds, rows[k].size());
+  std::vector<double> trow[4], tpush(push.size(), 1e30);
+  for (int k = 0; k < 4; ++k) trow[k].assign(rows[k].size(), 1e30);
+  const int slot_of[4] = {K_FWD_X, K_FWD_Y, K_INV_Y, K_INV_X};
+  const bool was_timing = p->timing;
+  const int saved_ept = p->push_ept;
+  for (size_t r = 0; r < rounds && st == PSATD_OK; ++r) {
+    for (int k = 0; k < 4; ++k)
+      if (!rows[k].empty()) p->cfg_log_tb[k] = rows[k][std::min(r, rows[k].size() - 1)];
+    const auto pc = push[std::min(r, push.size() - 1)];
+    if (pc.first != p->push_ept) {
+      p->push_ept = pc.first;
+      if ((st = regen_push_twiddles(p)) != PSATD_OK) break;
+    }
+    p->cfg_push_tb = pc.second;
+    if ((st = step_once(p, in, out)) != PSATD_OK) break;  // warm-up
+    cudaStreamSynchronize(p->st);
+    for (auto& v : p->ev) {
+      for (auto& ev : v) p->pool.push_back(ev);
+      v.clear();
+    }
+    p->timing = true;
+    for (int i = 0; i < reps && st == PSATD_OK; ++i) st = step_once(p, in, out);
+    p->timing = false;
+    e = cudaStreamSynchronize(p->st);
+    if (e != cudaSuccess && st == PSATD_OK) st = cuda_fail(p, e, "autotune: synchronise");
+    auto avg = [&](int slot) {
+      double ms = 0;
+      for (auto& ev : p->ev[slot]) {
+        float t = 0;
+        if (cudaEventElapsedTime(&t, ev.a, ev.b) == cudaSuccess) ms += t;
+      }
+      return p->ev[slot].empty() ? 1e30 : ms / p->ev[slot].size();
+    };
+    for (int k = 0; k < 4; ++k)
+      if (r < rows[k].size()) trow[k][r] = avg(slot_of[k]);
+    if (r < push.size()) tpush[r] = avg(K_PUSH);
+    for (auto& v : p->ev) {
+      for (auto& ev : v) p->pool.push_back(ev);
+      v.clear();
+    }
+  }
+  p->timing = was_timing;
+  p->d_off = saved_off;
+  cudaStreamSynchronize(p->st);
+  cudaFree(fbuf);
+  if (d_off2) cudaFree(d_off2);
+  if (st != PSATD_OK) {
+    for (int k = 0; k < 4; ++k) p->cfg_log_tb[k] = -1;
+    p->cfg_push_tb = -1;
+    if (p->push_ept != saved_ept) {
+      p->push_ept = saved_ept;
+      regen_push_twiddles(p);
+    }
+    return st;
+  }
+  TuneCfg best{{-1, -1, -1, -1}, -1, p->push_ept};
+  const char* names[4] = {"fwd_x", "fwd_y", "inv_y", "inv_x"};
+  char buf[160];
+  for (int k = 0; k < 4; ++k) {
+    if (rows[k].empty()) continue;
+    size_t b = std::min_element(trow[k].begin(), trow[k].end()) - trow[k].begin();
+    best.log_tb[k] = rows[k][b];
+    if (report) {
+      std::snprintf(buf, sizeof buf, "%s L=%d:", names[k], rowL[k]);
+      *report += buf;
+      for (size_t i = 0; i < rows[k].size(); ++i) {
+        std::snprintf(buf, sizeof buf, " tb=%d %.4fms%s", 1 << rows[k][i], trow[k][i], i == b ? "*" : "");
+        *report += buf;
+      }
+      *report += "; ";
+    }
+  }
+  size_t b = std::min_element(tpush.begin(), tpush.end()) - tpush.begin();
+  best.push_ept = push[b].first;
+  best.push_tb = push[b].second;
+  if (report) {
+    std::snprintf(buf, sizeof buf, "push L=%d:", Ll);
+    *report += buf;
+    for (size_t i = 0; i < push.size(); ++i) {
+      std::snprintf(buf, sizeof buf, " radix%d tb=%d %.4fms%s", push[i].first, push[i].second, tpush[i],
+                    i == b ? "*" : "");
+      *report += buf;
+    }
+  }
+  apply_cfg(p, best);
+  if ((st = regen_push_twiddles(p)) != PSATD_OK) return st;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  const TuneKey key = tune_key(p);
+  for (auto& kv : g_tune_cache)
+    if (kv.first == key) {
+      kv.second = best;
+      return PSATD_OK;
+    }
+  g_tune_cache.push_back({key, best});
   return PSATD_OK;
 }
 
@@ -424,6 +667,7 @@ static psatd_status plan_create_n(const psatd_desc* desc, void* cuda_stream, int
   p->st = static_cast<cudaStream_t>(cuda_stream);
   p->f32 = desc->prec == PSATD_FP32 || desc->prec == PSATD_MIXED_FP16;
   p->tc = desc->prec == PSATD_MIXED_FP16;
+  p->push_ept = p->tc ? 16 : 8;
   p->ndim = desc->ndim;
   p->layout = desc->layout;
   p->form = desc->src;
@@ -511,7 +755,7 @@ psatd_status psatd_coeffs_init(psatd_plan p) {
     for (int i = 0; i < p->ndim; ++i) {
       const int L = i == 0 ? (int)(ns[0] / 2) : (int)ns[i];
       const bool push_axis = (i == p->ndim - 1) && i > 0;
-      e = launch_twiddles(p->tw[i], L, push_axis ? push_ept(L, p->tc) : row_ept(L), i == 0, p->f32, p->st);
+      e = launch_twiddles(p->tw[i], L, push_axis ? p->push_ept : row_ept(L), i == 0, p->f32, p->st);
       if (e != cudaSuccess) return cuda_fail(p, e, "twiddle table launch");
     }
     if (p->tc) {
@@ -524,6 +768,70 @@ psatd_status psatd_coeffs_init(psatd_plan p) {
     if (e != cudaSuccess) return cuda_fail(p, e, "coefficient table launch");
   }
   p->coeffs_ready = true;
+  if (p->d.flags & PSATD_FLAG_AUTOTUNE) {
+    bool cached = false;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mutex);
+      const TuneKey key = tune_key(p);
+      for (auto& kv : g_tune_cache)
+        if (kv.first == key) {
+          apply_cfg(p, kv.second);
+          cached = true;
+        }
+    }
+    if (cached) return regen_push_twiddles(p);
+    return autotune(p, 5, nullptr);
+  }
+  return PSATD_OK;
+}
+
+psatd_status psatd_plan_autotune(psatd_plan p, int32_t reps, char* report, size_t report_len) {
+  if (!p) return fail(nullptr, PSATD_ERR_INVALID_ARG, "plan is NULL");
+  if (!p->coeffs_ready) return fail(p, PSATD_ERR_INVALID_ARG, "psatd_coeffs_init was not called");
+  if (reps < 1 || reps > 1000) return fail(p, PSATD_ERR_INVALID_ARG, "reps must be in [1, 1000] (got %d)", reps);
+  std::string rep;
+  psatd_status s = autotune(p, reps, &rep);
+  if (report && report_len > 0) {
+    std::strncpy(report, rep.c_str(), report_len - 1);
+    report[report_len - 1] = 0;
+  }
+  return s;
+}
+
+psatd_status psatd_plan_set_launch(psatd_plan p, const int32_t cfg[6]) {
+  if (!p || !cfg) return fail(p, PSATD_ERR_INVALID_ARG, "plan or cfg is NULL");
+  if (!p->coeffs_ready) return fail(p, PSATD_ERR_INVALID_ARG, "psatd_coeffs_init was not called");
+  TuneSpace ts = tune_space(p);
+  TuneCfg c{{-1, -1, -1, -1}, -1, p->tc ? 16 : 8};
+  for (int k = 0; k < 4; ++k) {
+    if (cfg[k] < 0) continue;
+    if (cfg[k] > 30 || std::find(ts.rows[k].begin(), ts.rows[k].end(), cfg[k]) == ts.rows[k].end())
+      return fail(p, PSATD_ERR_INVALID_ARG, "cfg[%d] = %d is not a valid launch shape of that pass", k, cfg[k]);
+    c.log_tb[k] = cfg[k];
+  }
+  if (cfg[5] >= 0) {
+    if (cfg[5] != 8 && cfg[5] != 16) return fail(p, PSATD_ERR_INVALID_ARG, "cfg[5] must be 8, 16 or -1");
+    c.push_ept = cfg[5];
+  }
+  bool ok = false;
+  for (auto& pt : ts.push) ok |= pt.first == c.push_ept && (cfg[4] < 0 || pt.second == cfg[4]);
+  if (!ok) return fail(p, PSATD_ERR_INVALID_ARG, "fused pass: %d elements per thread and %d lines per CTA not valid",
+                       c.push_ept, cfg[4]);
+  c.push_tb = cfg[4];
+  apply_cfg(p, c);
+  return regen_push_twiddles(p);
+}
+
+psatd_status psatd_plan_get_launch(psatd_plan p, int32_t cfg[6]) {
+  if (!p || !cfg) return fail(p, PSATD_ERR_INVALID_ARG, "plan or cfg is NULL");
+  const int Lx = (int)(p->nx / 2);
+  const int64_t nlines = p->ndim == 3 ? p->nxh * p->ny : p->nxh * p->npatch;
+  const int Ll = (int)(p->ndim == 3 ? p->nz : p->ny);
+  const int dflt[4] = {pick_log_tb(Lx, p->ny, p->f32), p->ndim == 3 ? pick_log_tb((int)p->ny, p->nz, p->f32) : -1,
+                       p->ndim == 3 ? pick_log_tb((int)p->ny, p->nz, p->f32) : -1, pick_log_tb(Lx, p->ny, p->f32)};
+  for (int k = 0; k < 4; ++k) cfg[k] = p->cfg_log_tb[k] >= 0 ? p->cfg_log_tb[k] : dflt[k];
+  cfg[4] = p->cfg_push_tb > 0 ? p->cfg_push_tb : push_lines_per_cta(Ll, p->n_in, nlines, p->tc, p->f32, p->push_ept);
+  cfg[5] = p->push_ept;
   return PSATD_OK;
 }
 

@@ -27,7 +27,8 @@ template <typename R, bool TC = false>
 cudaError_t launch_inv_T(int L, bool c2r, const PassGeom& g, cudaStream_t st, const LineIO& io,
                          const void* tw, int64_t in_sa0, int64_t in_sk, int64_t out_sa0,
                          int64_t out_sb, const int64_t* a0_off = nullptr);
-template <typename R, bool TC = false>
+// EPT: 8 or 16 elements per thread (radix-8 / radix-16 stages); TC needs 16.
+template <typename R, bool TC, int EPT>
 cudaError_t launch_line_push(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
                              const PushArgs<R>& a, const void* tw);
 

@@ -59,29 +59,33 @@ static cudaError_t inv_T_L(bool c2r, const PassGeom& g, cudaStream_t st, const L
   return cudaGetLastError();
 }
 
-template <typename R, bool TC, int L>
+template <typename R, bool TC, int EPT, int L>
 static cudaError_t push_L(int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
                           const PushArgs<R>& a, const void* tw) {
   typedef typename Types<R>::W W;
-  const dim3 block(FFTPlan<L, PushEPT<L, TC>::value>::kT, tb);
-  cudaError_t e;
+  if constexpr (L < EPT) {
+    return cudaErrorInvalidValue;
+  } else {
+    const dim3 block(FFTPlan<L, EPT>::kT, tb);
+    cudaError_t e;
 #define PSATD_PUSH_CASE(LAY)                                                   \
   case LAY: {                                                                  \
-    auto kern = k_line_push<R, L, LAY, TC>;                                    \
+    auto kern = k_line_push<R, L, LAY, TC, EPT>;                               \
     if ((e = set_smem(kern, smem)) != cudaSuccess) return e;                   \
     kern<<<grid, block, smem, st>>>(a, static_cast<const W*>(tw));             \
     break;                                                                     \
   }
-  switch (layout) {
-    PSATD_PUSH_CASE(0)
-    PSATD_PUSH_CASE(1)
-    PSATD_PUSH_CASE(2)
-    PSATD_PUSH_CASE(3)
-    default:
-      return cudaErrorInvalidValue;
-  }
+    switch (layout) {
+      PSATD_PUSH_CASE(0)
+      PSATD_PUSH_CASE(1)
+      PSATD_PUSH_CASE(2)
+      PSATD_PUSH_CASE(3)
+      default:
+        return cudaErrorInvalidValue;
+    }
 #undef PSATD_PUSH_CASE
-  return cudaGetLastError();
+    return cudaGetLastError();
+  }
 }
 
 // The tensor-core variants exist from L = 16 on (their first radix-16 stage).
@@ -115,10 +119,31 @@ cudaError_t launch_inv_T(int L, bool c2r, const PassGeom& g, cudaStream_t st, co
   PSATD_L_SWITCH(inv_T_L, c2r, g, st, io, tw, in_sa0, in_sk, out_sa0, out_sb, a0_off)
 }
 
-template <typename R, bool TC>
+template <typename R, bool TC, int EPT>
+static cudaError_t push_L_e(int layout, dim3 grid, int tb, size_t smem, cudaStream_t st, const PushArgs<R>& a,
+                            const void* tw, int L) {
+#define PUSH_E(LL) push_L<R, TC, EPT, LL>
+  switch (L) {
+    case 8: if constexpr (!TC) return PUSH_E(8)(layout, grid, tb, smem, st, a, tw);
+            else return cudaErrorInvalidValue;
+    case 16: return PUSH_E(16)(layout, grid, tb, smem, st, a, tw);
+    case 32: return PUSH_E(32)(layout, grid, tb, smem, st, a, tw);
+    case 64: return PUSH_E(64)(layout, grid, tb, smem, st, a, tw);
+    case 128: return PUSH_E(128)(layout, grid, tb, smem, st, a, tw);
+    case 256: return PUSH_E(256)(layout, grid, tb, smem, st, a, tw);
+    case 512: return PUSH_E(512)(layout, grid, tb, smem, st, a, tw);
+    case 1024: return PUSH_E(1024)(layout, grid, tb, smem, st, a, tw);
+    case 2048: return PUSH_E(2048)(layout, grid, tb, smem, st, a, tw);
+    case 4096: return PUSH_E(4096)(layout, grid, tb, smem, st, a, tw);
+    default: return cudaErrorInvalidValue;
+  }
+#undef PUSH_E
+}
+
+template <typename R, bool TC, int EPT>
 cudaError_t launch_line_push(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
                              const PushArgs<R>& a, const void* tw) {
-  PSATD_L_SWITCH(push_L, layout, grid, tb, smem, st, a, tw)
+  return push_L_e<R, TC, EPT>(layout, grid, tb, smem, st, a, tw, L);
 }
 
 }  // namespace psatd

@@ -438,11 +438,13 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // its forward FFT a slot holds the spectrum at positions sw<kLastCX>(t + T m),
 // so the push and the inverse FFT's first exchange only touch each thread's
 // own positions.
-template <typename R, int L, int LAYOUT, bool TC = false>
-__global__ void __launch_bounds__(FFTPlan<L, PushEPT<L, TC>::value>::kT > 256 ? FFTPlan<L, PushEPT<L, TC>::value>::kT : 256)
+// EPT: elements per thread, 8 (radix-8 stages) or 16 (radix-16 stages; the
+// only choice of the tensor-core variant).
+template <typename R, int L, int LAYOUT, bool TC = false, int EPT = PushEPT<L, TC>::value>
+__global__ void __launch_bounds__(FFTPlan<L, EPT>::kT > 256 ? FFTPlan<L, EPT>::kT : 256)
 k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   typedef typename Types<R>::C C;
-  constexpr int EPT = PushEPT<L, TC>::value;
+  static_assert(!TC || EPT == 16, "tensor-core stages are radix 16");
   typedef FFTPlan<L, EPT> P;
   constexpr int T = P::kT;
   constexpr int CXL = P::kLastCX;

@@ -64,7 +64,7 @@ def _create(lib, desc):
     (lambda d: setattr(d, "prec", 2), 2),                  # split-BF16: not in this build
     (lambda d: setattr(d, "prec", 9), 1),
     (lambda d: setattr(d, "src", 7), 1),
-    (lambda d: setattr(d, "flags", 1), 1),
+    (lambda d: setattr(d, "flags", 2), 1),                 # unknown flag bit
     (lambda d: (setattr(d, "layout", 3), setattr(d, "src", 2)), 1),  # TM has no rho-form
     (lambda d: setattr(d, "layout", 9), 1),
 ])
@@ -139,3 +139,17 @@ def test_mixed_fp16_only_for_the_psatd_step(lib):
     assert lib.fdtd_step(ct.byref(d), 0, ct.byref(f), ct.byref(s), 1, None) == 2
     assert lib.psatd_step_noalloc(ct.byref(d), ct.byref(f), ct.byref(s), 1, None) == 2
     assert b"FP32" in lib.psatd_last_error(None)
+
+
+def test_autotune_argument_errors(lib):
+    buf = ct.create_string_buffer(64)
+    assert lib.psatd_plan_autotune(None, 5, buf, 64) == 1
+    assert b"NULL" in lib.psatd_last_error(None)
+
+
+def test_autotune_flag_is_psatd_only(lib):
+    d = capi.make_desc((64, 32), (1.0, 1.0), 0.5, layout="te", src="J", autotune=True)
+    f = capi.psatd_fields()
+    s = capi.psatd_sources()
+    assert lib.fdtd_step(ct.byref(d), 0, ct.byref(f), ct.byref(s), 1, None) == 1
+    assert b"flags" in lib.psatd_last_error(None)
