@@ -212,11 +212,16 @@ psatd_status alloc(psatd_plan p, void** ptr, size_t bytes, const char* what) {
 }
 
 // lines per CTA for a transposing pass of length L with `nb` lines available
-int pick_log_tb(int L, int64_t nb, bool f32) {
+// (at most 16 lines: the row-dependent XOR of the transposed store spreads 16
+// lines over the banks, 32 would read one bank twice; the tensor-core variant
+// goes to 32 where it needs that for 128 threads)
+int pick_log_tb(int L, int64_t nb, bool f32, bool tc = false) {
   const int T = L / row_ept(L);
   const int maxthr = f32 ? 512 : 256;
   int tb = 1;
-  while (tb * 2 * T <= maxthr && tb * 2 <= 32 && tb * 2 <= nb) tb *= 2;
+  while (tb * 2 * T <= maxthr && tb * 2 <= 16 && tb * 2 <= nb) tb *= 2;
+  if (tc)
+    while (tb * T < 128 && tb * 2 * T <= maxthr && tb * 2 <= 32 && tb * 2 <= nb) tb *= 2;
   int lg = 0;
   while ((1 << lg) < tb) ++lg;
   return lg;
@@ -285,7 +290,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
   // pass 1: x rows (R2C), b = y -> spec1 [c][kx][z][y] (3D) / [c][patch][kx][y] (2D)
   {
     PassGeom g;
-    g.log_tb = p->cfg_log_tb[0] >= 0 ? p->cfg_log_tb[0] : pick_log_tb(Lx, ny, p->f32);
+    g.log_tb = p->cfg_log_tb[0] >= 0 ? p->cfg_log_tb[0] : pick_log_tb(Lx, ny, p->f32, TC);
     g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)na0, (unsigned)p->n_in);
     g.smem = tail + tpass_smem(Lx, g.log_tb, 0, csz);
     for (int c = 0; c < p->n_in; ++c) {
@@ -303,7 +308,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
   if (p->ndim == 3) {
     // pass 2: y lines (C2C), b = z, a0 = kx: spec1 [c][kx][z][y] -> spec2 [c][kx][ky][z]
     PassGeom g;
-    g.log_tb = p->cfg_log_tb[1] >= 0 ? p->cfg_log_tb[1] : pick_log_tb((int)ny, nz, p->f32);
+    g.log_tb = p->cfg_log_tb[1] >= 0 ? p->cfg_log_tb[1] : pick_log_tb((int)ny, nz, p->f32, TC);
     g.grid = dim3((unsigned)(nz >> g.log_tb), (unsigned)nxh, (unsigned)p->n_in);
     g.smem = tail + tpass_smem((int)ny, g.log_tb, (size_t)ny, csz);
     for (int c = 0; c < p->n_in; ++c) {
@@ -363,7 +368,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
   if (p->ndim == 3) {
     // pass 4: inverse y lines: spec2 [c][kx][ky][z] -> spec1 [c][kx][z][y]
     PassGeom g;
-    g.log_tb = p->cfg_log_tb[2] >= 0 ? p->cfg_log_tb[2] : pick_log_tb((int)ny, nz, p->f32);
+    g.log_tb = p->cfg_log_tb[2] >= 0 ? p->cfg_log_tb[2] : pick_log_tb((int)ny, nz, p->f32, TC);
     g.grid = dim3((unsigned)(nz >> g.log_tb), (unsigned)nxh, (unsigned)p->n_out);
     g.smem = tail + tpass_smem((int)ny, g.log_tb, (size_t)ny, csz);
     for (int c = 0; c < p->n_out; ++c) {
@@ -377,7 +382,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
   // last pass: inverse x rows (C2R): spec1 -> out [z][y][x] (3D) / packed patches (2D)
   {
     PassGeom g;
-    g.log_tb = p->cfg_log_tb[3] >= 0 ? p->cfg_log_tb[3] : pick_log_tb(Lx, ny, p->f32);
+    g.log_tb = p->cfg_log_tb[3] >= 0 ? p->cfg_log_tb[3] : pick_log_tb(Lx, ny, p->f32, TC);
     g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)na0, (unsigned)p->n_out);
     g.smem = tail + tpass_smem(Lx, g.log_tb, 0, csz);
     for (int c = 0; c < p->n_out; ++c) {
@@ -407,7 +412,7 @@ psatd_status check_tc_shape(psatd_plan p, int maxsm) {
   struct { int L; int64_t nb; } rows[2] = {{Lx, p->ny}, {(int)p->ny, p->nz}};
   for (int i = 0; i < (p->ndim == 3 ? 2 : 1); ++i) {
     const int T = rows[i].L / row_ept(rows[i].L);
-    if ((T << pick_log_tb(rows[i].L, rows[i].nb, true)) < 128)
+    if ((T << pick_log_tb(rows[i].L, rows[i].nb, true, true)) < 128)
       return fail(nullptr, PSATD_ERR_UNSUPPORTED,
                   "mixed precision: a line pass of length %d over %lld lines has fewer than 128 threads per CTA",
                   rows[i].L, (long long)rows[i].nb);
@@ -827,8 +832,10 @@ psatd_status psatd_plan_get_launch(psatd_plan p, int32_t cfg[6]) {
   const int Lx = (int)(p->nx / 2);
   const int64_t nlines = p->ndim == 3 ? p->nxh * p->ny : p->nxh * p->npatch;
   const int Ll = (int)(p->ndim == 3 ? p->nz : p->ny);
-  const int dflt[4] = {pick_log_tb(Lx, p->ny, p->f32), p->ndim == 3 ? pick_log_tb((int)p->ny, p->nz, p->f32) : -1,
-                       p->ndim == 3 ? pick_log_tb((int)p->ny, p->nz, p->f32) : -1, pick_log_tb(Lx, p->ny, p->f32)};
+  const bool tc = p->tc;
+  const int dflt[4] = {pick_log_tb(Lx, p->ny, p->f32, tc),
+                       p->ndim == 3 ? pick_log_tb((int)p->ny, p->nz, p->f32, tc) : -1,
+                       p->ndim == 3 ? pick_log_tb((int)p->ny, p->nz, p->f32, tc) : -1, pick_log_tb(Lx, p->ny, p->f32, tc)};
   for (int k = 0; k < 4; ++k) cfg[k] = p->cfg_log_tb[k] >= 0 ? p->cfg_log_tb[k] : dflt[k];
   cfg[4] = p->cfg_push_tb > 0 ? p->cfg_push_tb : push_lines_per_cta(Ll, p->n_in, nlines, p->tc, p->f32, p->push_ept);
   cfg[5] = p->push_ept;

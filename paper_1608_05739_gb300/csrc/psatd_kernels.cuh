@@ -111,22 +111,37 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO 
 #pragma unroll
     for (int m = 0; m < EPT; ++m) zb[(t + T * m) ^ xg] = v[m];
     __syncthreads();
+    // Thread (k0, gg) produces bins k = k0 + j T, j < EPT (all below L), and thread
+    // k0 = 0 also bin L; twiddles are loaded in groups of four before their use.
     const typename Types<R>::W* wn = tw + P::kTwEntries;  // W_N^k, N = 2L
-    const int nthr = T * TB;
     const int tid = g * T + t;
-    const int kstep = nthr >> log_tb;
     const int gg = tid & (TB - 1);
+    const int k0 = tid >> log_tb;  // in [0, T)
     const int xgg = (gg * (16 >> log_tb)) & 15 & (L - 1);
     const C* zr = smem + gg * L;
-    int k = tid >> log_tb;
-    C* o = static_cast<C*>(io.out[a1]) + a0 * out_sa0 + (int64_t)blockIdx.x * TB + (int64_t)k * out_sk + gg;
-    const int64_t ostep = (int64_t)kstep * out_sk;
-    for (; k <= L; k += kstep, o += ostep) {
-      const C zk = zr[(k & (L - 1)) ^ xgg];
-      const C zm = cconj(zr[((L - k) & (L - 1)) ^ xgg]);
-      const C fe = mkc(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y + zm.y));
-      const C fo = mkc(R(0.5) * (zk.y - zm.y), R(-0.5) * (zk.x - zm.x));
-      *o = (k < L) ? cadd(fe, twmul(fo, __ldg(&wn[k]))) : csub(fe, fo);
+    C* o = static_cast<C*>(io.out[a1]) + a0 * out_sa0 + (int64_t)blockIdx.x * TB + (int64_t)k0 * out_sk + gg;
+    const int64_t ostep = (int64_t)T * out_sk;
+#pragma unroll
+    for (int j0 = 0; j0 < EPT; j0 += 4) {
+      typename Types<R>::W w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[j] = __ldg(&wn[k0 + (j0 + j) * T]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = k0 + (j0 + j) * T;
+        const C zk = zr[k ^ xgg];
+        const C zm = cconj(zr[((L - k) & (L - 1)) ^ xgg]);
+        const C fe = mkc(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y + zm.y));
+        const C fo = mkc(R(0.5) * (zk.y - zm.y), R(-0.5) * (zk.x - zm.x));
+        o[(j0 + j) * ostep] = cadd(fe, twmul(fo, w[j]));
+      }
+    }
+    if (k0 == 0) {  // k = L: X[L] = Fe[0] - Fo[0]
+      const C z0 = zr[0 ^ xgg];
+      const C zm = cconj(z0);
+      const C fe = mkc(R(0.5) * (z0.x + zm.x), R(0.5) * (z0.y + zm.y));
+      const C fo = mkc(R(0.5) * (z0.y - zm.y), R(-0.5) * (z0.x - zm.x));
+      o[EPT * ostep] = csub(fe, fo);
     }
   } else {
     C* tile = smem;  // [NK][TB + 1], aliases the exchange buffers
@@ -175,22 +190,43 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_inv_T(LineIO 
     // from the transposed spectrum: each thread takes a bin pair (k, L-k) of one line, which
     // also gives Z[L-k] = Fe* + i Fo* (as W_N^(L-k) = -conj(W_N^k)), and writes both into the
     // line's buffer under the row-dependent XOR mask of the forward pass.
+    // Thread (p0, gg) takes the pairs pp = p0 + j T, j < EPT/2 (all below L/2), and
+    // thread p0 = 0 also the self-paired bin L/2; every load is issued before the first use.
     const typename Types<R>::W* wn = tw + P::kTwEntries;
-    const int nthr = T * TB;
     const int tid = g * T + t;
-    const int pstep = nthr >> log_tb;
     const int gg = tid & (TB - 1);
+    const int p0 = tid >> log_tb;  // in [0, T)
     const int xgg = (gg * (16 >> log_tb)) & 15 & (L - 1);
     C* zr = smem + gg * L;
     const C* ib = static_cast<const C*>(io.in[a1]) + a0 * in_sa0 + (int64_t)blockIdx.x * TB + gg;
-    for (int pp = tid >> log_tb; pp <= L / 2; pp += pstep) {
-      const C xk = ib[(int64_t)pp * in_sk];
-      const C xm = cconj(ib[(int64_t)(L - pp) * in_sk]);
-      const C fe = cadd(xk, xm);
-      const C d = csub(xk, xm);
-      const C fo = (pp == 0) ? d : twmul_conj(d, __ldg(&wn[pp]));
-      zr[pp ^ xgg] = cadd(fe, cmul_pi(fo));
-      if (pp > 0 && pp < L / 2) zr[(L - pp) ^ xgg] = cadd(cconj(fe), cmul_pi(cconj(fo)));
+    constexpr int NP = EPT / 2;  // 4 or 8 pairs, taken four at a time
+#pragma unroll
+    for (int j0 = 0; j0 < NP; j0 += 4) {
+      C xk[4], xm[4];
+      typename Types<R>::W w[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int pp = p0 + (j0 + j) * T;
+        xk[j] = ib[(int64_t)pp * in_sk];
+        xm[j] = ib[(int64_t)(L - pp) * in_sk];
+        w[j] = __ldg(&wn[pp]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int pp = p0 + (j0 + j) * T;
+        const C xmc = cconj(xm[j]);
+        const C fe = cadd(xk[j], xmc);
+        const C d = csub(xk[j], xmc);
+        const C fo = (pp == 0) ? d : twmul_conj(d, w[j]);
+        zr[pp ^ xgg] = cadd(fe, cmul_pi(fo));
+        if (pp > 0) zr[(L - pp) ^ xgg] = cadd(cconj(fe), cmul_pi(cconj(fo)));
+      }
+    }
+    if (p0 == 0) {  // pp = L/2: X[L/2] pairs with itself
+      const C x = ib[(int64_t)(L / 2) * in_sk];
+      const C fe = cadd(x, cconj(x));
+      const C fo = twmul_conj(csub(x, cconj(x)), __ldg(&wn[L / 2]));
+      zr[(L / 2) ^ xgg] = cadd(fe, cmul_pi(fo));
     }
     __syncthreads();
     const int xg = (g * (16 >> log_tb)) & 15 & (L - 1);
