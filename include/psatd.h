@@ -246,6 +246,39 @@ int64_t psatd_batch_cells(psatd_batch batch);
 /* Release the batch (synchronises its stream).  NULL is accepted. */
 psatd_status psatd_batch_destroy(psatd_batch batch);
 
+/* Local-FFT decomposition of one periodic 2D grid (Sec. II.A.3): the grid of
+ * global->n[0] x global->n[1] cells is split into px x py patches of
+ * ix = n[0]/px by iy = n[1]/py interior cells; every patch is extended by
+ * `guard` cells on each side, which hold copies of the neighbouring cells
+ * (periodic wrap at the grid's edges) refreshed before every step; each
+ * extended patch is advanced by one PSATD step as a periodic domain of its own
+ * (its own FFTs, all patches batched in one launch per pass), and the interiors
+ * are written back.  The result differs from the global step by the truncation
+ * error of the local transforms, which falls with the guard width.
+ * global: layout 2D6, TE or TM; precision, source form, cell sizes, dt, c and
+ * eps0 as in psatd_plan_create; n[0], n[1] need not be powers of two, but the
+ * extended sizes ix + 2 guard and iy + 2 guard must satisfy psatd_plan_create's
+ * limits.  Owns a plan of the extended size (px*py patches) and the packed
+ * patch arrays (n_in * px*py * (ix+2g) * (iy+2g) values).
+ * Errors: INVALID_ARG (NULL, px/py not dividing the grid, guard < 0),
+ * UNSUPPORTED (3D, extended sizes out of range), OOM, CUDA.                 */
+typedef struct psatd_local_s* psatd_local;
+psatd_status psatd_local_create(const psatd_desc* global, int32_t px, int32_t py, int32_t guard,
+                                void* cuda_stream, psatd_local* out);
+
+/* Advance the global fields by nsteps local-FFT steps (sources held constant;
+ * arrays as for psatd_step, of the global size).  Per step: guard refresh of
+ * the fields (sources once per call), the batched patch step, write-back of the
+ * interiors.  Asynchronous.  Errors as psatd_step.                           */
+psatd_status psatd_local_step(psatd_local local, const psatd_fields* fields,
+                              const psatd_sources* sources, int32_t nsteps);
+
+/* The plan of the extended patches (timing, autotuning, launch shapes). */
+psatd_plan psatd_local_plan(psatd_local local);
+
+/* Release the decomposition (synchronises its stream).  NULL is accepted. */
+psatd_status psatd_local_destroy(psatd_local local);
+
 /* PSATD step without any device allocation, for callers that cannot call
  * cudaMalloc (e.g. code running where a foreign allocator owns all device
  * memory, or a host that must not allocate after start-up).  The paper has no

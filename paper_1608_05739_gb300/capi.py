@@ -75,6 +75,11 @@ EXPORTS = [
     ("psatd_plan_autotune", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_char_p, ct.c_size_t]),
     ("psatd_plan_set_launch", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32)]),
     ("psatd_plan_get_launch", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32)]),
+    ("psatd_local_create", ct.c_int, [ct.POINTER(psatd_desc), ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p,
+                                      ct.POINTER(ct.c_void_p)]),
+    ("psatd_local_step", ct.c_int, [ct.c_void_p, ct.POINTER(psatd_fields), ct.POINTER(psatd_sources), ct.c_int32]),
+    ("psatd_local_plan", ct.c_void_p, [ct.c_void_p]),
+    ("psatd_local_destroy", ct.c_int, [ct.c_void_p]),
 ]
 
 FLAG_AUTOTUNE = 1
@@ -290,6 +295,51 @@ class Batch:
     def destroy(self):
         if getattr(self, "handle", None) is not None:
             load().psatd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Local:
+    """Local-FFT decomposition of one periodic 2D grid (psatd_local_create): ``px`` x ``py``
+    patches with ``guard`` cells, each advanced by its own FFTs.  Fields and sources are
+    the global arrays, shape [ny, nx], as for Plan."""
+
+    def __init__(self, n, d, dt, *, px, py, guard, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0,
+                 stream=None, autotune=False):
+        import torch
+        lib = load()
+        self.n, self.layout, self.prec, self.src = tuple(n), layout, prec, src
+        self.shape = _grid_shape(n)
+        self.dtype = _torch_dtype(prec)
+        desc = make_desc(n, d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0, autotune=autotune)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ct.c_void_p()
+        _check(lib.psatd_local_create(ct.byref(desc), int(px), int(py), int(guard), ct.c_void_p(stream.cuda_stream),
+                                      ct.byref(h)))
+        self.handle = h
+
+    def step(self, E, B, J=None, rho_n=None, rho_np1=None, nsteps=1):
+        f = _fields_struct(self.layout, self.shape, self.dtype, E, B)
+        s = _sources_struct(self.layout, self.shape, self.dtype, J, rho_n, rho_np1) \
+            if self.src != "none" else None
+        lib = load()
+        _check(lib.psatd_local_step(self.handle, ct.byref(f), ct.byref(s) if s is not None else None, int(nsteps)),
+               lib.psatd_local_plan(self.handle))
+
+    def sync(self):
+        lib = load()
+        _check(lib.psatd_plan_sync(lib.psatd_local_plan(self.handle)), lib.psatd_local_plan(self.handle))
+
+    def destroy(self):
+        if getattr(self, "handle", None) is not None:
+            load().psatd_local_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

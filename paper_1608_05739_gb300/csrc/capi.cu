@@ -15,6 +15,7 @@
 
 #include "../../include/psatd.h"
 #include "launch.h"
+#include "local.h"
 #include "tables.h"
 
 using namespace psatd;
@@ -235,13 +236,17 @@ size_t tpass_smem(int L, int log_tb, size_t nk, size_t csz) {
   return (a > b ? a : b) * csz;
 }
 
-// lines per CTA of the fused last-axis pass: up to 256 threads and 100 KB of
-// line buffers; the tensor-core variant needs a multiple of 128 threads
+// lines per CTA of the fused last-axis pass: as few as make a whole warp (the
+// autotuner found one line per CTA fastest at 256^3, 512^2 and 2048^2: the lines
+// of a CTA only add barriers to each other); the tensor-core variant needs a
+// multiple of 128 threads
 int push_lines_per_cta(int L, int n_in, int64_t nlines, bool tc, bool f32, int ept) {
+  (void)n_in;
+  (void)nlines;
+  (void)f32;
   const int T = L / ept;
-  const size_t per_line = ((size_t)n_in + 1) * (size_t)L * (f32 ? 8 : 16);
   int tb = 1;
-  while (tb * 2 * T <= 256 && (size_t)(tb * 2) * per_line <= 100 * 1024 && tb * 2 <= nlines) tb *= 2;
+  while (tb * T < 32) tb *= 2;
   if (tc)
     while (tb * T < 128) tb *= 2;
   return tb;
@@ -1268,5 +1273,131 @@ extern "C" psatd_status psatd_batch_destroy(psatd_batch b) {
   cudaStreamSynchronize(b->st);
   batch_release(b);
   delete b;
+  return PSATD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Local-FFT decomposition of one periodic 2D grid (Sec. II.A.3): patches with
+// guard cells, refreshed from the neighbours every step, each advanced by its
+// own FFTs (a batch of one size class), interiors written back.
+// ---------------------------------------------------------------------------
+struct psatd_local_s {
+  psatd_plan plan = nullptr;  // px * py extended patches of one size
+  cudaStream_t st = nullptr;
+  int px = 1, py = 1, g = 0;
+  int64_t nx = 0, ny = 0;
+  void* fbuf = nullptr;       // packed extended patches, one array per input slot
+  size_t comp_bytes = 0;
+};
+
+extern "C" psatd_status psatd_local_create(const psatd_desc* global, int32_t px, int32_t py, int32_t guard,
+                                           void* cuda_stream, psatd_local* out) {
+  if (!out) return fail(nullptr, PSATD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!global) return fail(nullptr, PSATD_ERR_INVALID_ARG, "desc is NULL");
+  if (global->ndim != 2 || global->layout == PSATD_FIELDS_3D6)
+    return fail(nullptr, PSATD_ERR_UNSUPPORTED, "the local decomposition is 2D (TE, TM, 2D6)");
+  if (global->n[0] < 1 || global->n[1] < 1) return fail(nullptr, PSATD_ERR_INVALID_ARG, "grid sizes must be >= 1");
+  psatd_status s;
+  if (px < 1 || py < 1 || guard < 0) return fail(nullptr, PSATD_ERR_INVALID_ARG, "px, py >= 1 and guard >= 0 needed");
+  if (global->n[0] % px || global->n[1] % py)
+    return fail(nullptr, PSATD_ERR_INVALID_ARG, "px = %d, py = %d must divide the grid %lld x %lld", px, py,
+                (long long)global->n[0], (long long)global->n[1]);
+  psatd_desc pd = *global;
+  pd.n[0] = global->n[0] / px + 2 * (int64_t)guard;
+  pd.n[1] = global->n[1] / py + 2 * (int64_t)guard;
+  s = validate_desc(nullptr, &pd, true);
+  if (s != PSATD_OK) {
+    g_err = "extended patch " + std::to_string(pd.n[0]) + " x " + std::to_string(pd.n[1]) + ": " + g_err;
+    return s;
+  }
+  psatd_local L = new (std::nothrow) psatd_local_s();
+  if (!L) return fail(nullptr, PSATD_ERR_OOM, "host allocation failed");
+  L->st = static_cast<cudaStream_t>(cuda_stream);
+  L->px = px;
+  L->py = py;
+  L->g = guard;
+  L->nx = global->n[0];
+  L->ny = global->n[1];
+  const int npatch = px * py;
+  s = plan_create_n(&pd, cuda_stream, npatch, &L->plan);
+  psatd_plan p = L->plan;
+  if (s == PSATD_OK) {
+    std::vector<int64_t> offs(npatch);
+    for (int i = 0; i < npatch; ++i) offs[i] = (int64_t)i * pd.n[0] * pd.n[1];
+    s = alloc(p, reinterpret_cast<void**>(&p->d_off), offs.size() * sizeof(int64_t), "patch offsets");
+    if (s == PSATD_OK) {
+      cudaError_t e = cudaMemcpy(p->d_off, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) s = cuda_fail(p, e, "patch offset upload");
+    }
+    L->comp_bytes = (size_t)npatch * pd.n[0] * pd.n[1] * (p->f32 ? 4 : 8);
+    if (s == PSATD_OK) s = alloc(p, &L->fbuf, (size_t)p->n_in * L->comp_bytes, "patch fields");
+    if (s == PSATD_OK) s = psatd_coeffs_init(p);
+    if (s != PSATD_OK) g_err = p->err;
+  }
+  if (s != PSATD_OK) {
+    if (L->fbuf) cudaFree(L->fbuf);
+    if (p) {
+      release(p);
+      delete p;
+    }
+    delete L;
+    return s;
+  }
+  *out = L;
+  return PSATD_OK;
+}
+
+extern "C" psatd_status psatd_local_step(psatd_local L, const psatd_fields* fields, const psatd_sources* sources,
+                                         int32_t nsteps) {
+  if (!L) return fail(nullptr, PSATD_ERR_INVALID_ARG, "local decomposition is NULL");
+  psatd_plan p = L->plan;
+  if (nsteps < 1) return fail(p, PSATD_ERR_INVALID_ARG, "nsteps must be >= 1 (got %d)", nsteps);
+  const void* in[kMaxComp] = {};
+  void* out[kMaxComp] = {};
+  psatd_status s = gather_slots(p, fields, sources, in, out);
+  if (s != PSATD_OK) return s;
+  const void* pin[kMaxComp] = {};
+  void* pout[kMaxComp] = {};
+  for (int c = 0; c < p->n_in; ++c) {
+    pin[c] = static_cast<char*>(L->fbuf) + c * L->comp_bytes;
+    if (c < p->n_out) pout[c] = const_cast<void*>(pin[c]);
+  }
+  LocalComps fc{}, sc{};
+  for (int c = 0; c < p->n_out; ++c) {
+    fc.global[c] = in[c];
+    fc.global_out[c] = out[c];
+    fc.patch[c] = pout[c];
+  }
+  for (int c = p->n_out; c < p->n_in; ++c) {
+    sc.global[c - p->n_out] = in[c];
+    sc.patch[c - p->n_out] = const_cast<void*>(pin[c]);
+  }
+  cudaError_t e;
+  if (p->n_in > p->n_out) {  // sources: held constant over the call, refreshed once
+    e = launch_guard_gather(p->f32, sc, p->n_in - p->n_out, L->nx, L->ny, L->px, L->py, L->g, p->st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "guard gather (sources)");
+  }
+  for (int i = 0; i < nsteps; ++i) {
+    e = launch_guard_gather(p->f32, fc, p->n_out, L->nx, L->ny, L->px, L->py, L->g, p->st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "guard gather");
+    if ((s = step_once(p, pin, pout)) != PSATD_OK) return s;
+    e = launch_guard_scatter(p->f32, fc, p->n_out, L->nx, L->ny, L->px, L->py, L->g, p->st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "guard scatter");
+  }
+  return PSATD_OK;
+}
+
+extern "C" psatd_plan psatd_local_plan(psatd_local L) { return L ? L->plan : nullptr; }
+
+extern "C" psatd_status psatd_local_destroy(psatd_local L) {
+  if (!L) return PSATD_OK;
+  cudaStreamSynchronize(L->st);
+  if (L->fbuf) cudaFree(L->fbuf);
+  if (L->plan) {
+    release(L->plan);
+    delete L->plan;
+  }
+  delete L;
   return PSATD_OK;
 }

@@ -237,11 +237,19 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_inv_T(LineIO 
     C* tile = smem;
     const int tp = TB + 1;
     {
+      // L * TB values over T * TB threads: EPT each, all loads issued before the stores
       const C* ib = static_cast<const C*>(io.in[a1]) + a0 * in_sa0 + (int64_t)blockIdx.x * TB;
       const int nthr = T * TB;
-      for (int idx = g * T + t; idx < NK * TB; idx += nthr) {
-        const int k = idx >> log_tb, gg = idx & (TB - 1);
-        tile[k * tp + gg] = ib[(int64_t)k * in_sk + gg];
+      C tv[EPT];
+#pragma unroll
+      for (int j = 0; j < EPT; ++j) {
+        const int idx = g * T + t + j * nthr;
+        tv[j] = ib[(int64_t)(idx >> log_tb) * in_sk + (idx & (TB - 1))];
+      }
+#pragma unroll
+      for (int j = 0; j < EPT; ++j) {
+        const int idx = g * T + t + j * nthr;
+        tile[(idx >> log_tb) * tp + (idx & (TB - 1))] = tv[j];
       }
     }
     __syncthreads();

@@ -153,3 +153,20 @@ def test_autotune_flag_is_psatd_only(lib):
     s = capi.psatd_sources()
     assert lib.fdtd_step(ct.byref(d), 0, ct.byref(f), ct.byref(s), 1, None) == 1
     assert b"flags" in lib.psatd_last_error(None)
+
+
+def test_local_create_rejects_invalid_arguments(lib):
+    h = ct.c_void_p()
+    d = capi.make_desc((240, 120), (1.0, 1.0), 0.5, layout="te", src="J")
+    assert lib.psatd_local_create(None, 2, 2, 8, None, ct.byref(h)) == 1
+    assert lib.psatd_local_create(ct.byref(d), 7, 2, 8, None, ct.byref(h)) == 1       # 7 does not divide 240
+    assert b"divide" in lib.psatd_last_error(None)
+    assert lib.psatd_local_create(ct.byref(d), 2, 2, -1, None, ct.byref(h)) == 1      # guard < 0
+    assert lib.psatd_local_create(ct.byref(d), 2, 2, 4, None, ct.byref(h)) == 2       # 128 x 68: not a power of two
+    assert b"extended patch 128 x 68" in lib.psatd_last_error(None)
+    d3 = capi.make_desc((64, 64, 64), (1.0, 1.0, 1.0), 0.5, layout="3d6", src="J")
+    assert lib.psatd_local_create(ct.byref(d3), 2, 2, 8, None, ct.byref(h)) == 2
+    assert lib.psatd_local_create(ct.byref(d), 2, 2, 8, None, None) == 1
+    assert lib.psatd_local_step(None, None, None, 1) == 1
+    assert lib.psatd_local_destroy(None) == 0
+    assert lib.psatd_local_plan(None) is None
