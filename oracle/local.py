@@ -17,7 +17,7 @@ side:
      ((x0 - g + i) mod nx, (y0 - g + j) mod ny), 0 <= i < ix + 2g,
      0 <= j < iy + 2g, for every field and source component (the guard refresh);
   2. advance each extended patch by one PSATD step as a periodic domain of its
-     own (``psatd.psatd_step``);
+     own (``psatd.psatd_step``, any stencil order);
   3. keep the interior of every patch (the guards are discarded).
 
 With one patch and g = 0 this is the global step.
@@ -37,7 +37,7 @@ def extract(f, px, py, g, p, q):
 
 
 def local_step(E, B, J=None, rho0=None, rho1=None, *, d, dt, px, py, guard, c=1.0, eps0=1.0,
-               form="none", nsteps=1):
+               form="none", nsteps=1, order=0):
     """``nsteps`` local-FFT PSATD steps of the 2D fields E, B (arrays ``(3, ny, nx)``)
     on px x py patches with ``guard`` cells; sources held constant over the steps."""
     E = np.array(E, dtype=np.float64)
@@ -58,7 +58,8 @@ def local_step(E, B, J=None, rho0=None, rho1=None, *, d, dt, px, py, guard, c=1.
                 Jp = np.stack([ext(J[i]) for i in range(3)]) if J is not None else None
                 r0 = ext(rho0) if rho0 is not None else None
                 r1 = ext(rho1) if rho1 is not None else None
-                Eo, Bo = psatd.psatd_step(Ep, Bp, Jp, r0, r1, d=d, dt=dt, c=c, eps0=eps0, form=form)
+                Eo, Bo = psatd.psatd_step(Ep, Bp, Jp, r0, r1, d=d, dt=dt, c=c, eps0=eps0, form=form,
+                                          order=order)
                 En[:, q * iy:(q + 1) * iy, p * ix:(p + 1) * ix] = Eo[:, g:g + iy, g:g + ix]
                 Bn[:, q * iy:(q + 1) * iy, p * ix:(p + 1) * ix] = Bo[:, g:g + iy, g:g + ix]
         E, B = En, Bn

@@ -101,6 +101,20 @@ def spectral_grid(shape, d):
     return kx, ky, kz
 
 
+def _raw_grid(shape, d):
+    """As :func:`spectral_grid` but with the Nyquist wavenumbers kept (+pi/d on the
+    half x axis, -pi/d at index n/2 of a full axis, numpy's ``fftfreq`` order)."""
+    def ax(n, dd, half):
+        m = np.arange(n // 2 + 1, dtype=np.float64) if half else np.fft.fftfreq(n) * n
+        return 2.0 * math.pi * m / (n * dd)
+    if len(shape) == 2:
+        ny, nx = shape
+        return ax(nx, d[0], True)[None, :], ax(ny, d[1], False)[:, None], np.zeros((1, 1))
+    nz, ny, nx = shape
+    return (ax(nx, d[0], True)[None, None, :], ax(ny, d[1], False)[None, :, None],
+            ax(nz, d[2], False)[:, None, None])
+
+
 def forward(f: np.ndarray) -> np.ndarray:
     """Unnormalised forward DFT of a real grid array (half spectrum along x)."""
     return np.fft.rfftn(f, axes=tuple(range(f.ndim)))
@@ -214,27 +228,75 @@ def push_modes(k, E, B, J=None, rho0=None, rho1=None, *, dt, c=1.0, eps0=1.0,
     raise ValueError("unknown source form %r" % form)
 
 
+# Staggered (Yee) positions: the axes along which each component sits half a
+# cell from the nodes.  Ex(i+1/2, j, k) Ey(i, j+1/2, k) Ez(i, j, k+1/2),
+# Bx(i, j+1/2, k+1/2) By(i+1/2, j, k+1/2) Bz(i+1/2, j+1/2, k); J as E; rho on nodes.
+STAGGER_E = ((0,), (1,), (2,))
+STAGGER_B = ((1, 2), (0, 2), (0, 1))
+
+
+def staggered_operators(shape, d, order):
+    """(k_p, phases) of the order-``order`` staggered scheme on the rfftn spectrum.
+
+    Sec. III.B / Table 1 row PSATD-p: the exact wavenumber of PSATD is replaced by
+    that of the order-p centred staggered difference,
+    k_p,i = (2/d_i) sum_l C_l^p sin((2l-1) k_i d_i / 2)  (Fornberg weights).
+    A component stored at index j but located at x_j + d_i/2 along axis i has the
+    true-position spectrum exp(-i k_i d_i / 2) times its array spectrum; in those
+    spectra the order-p difference is multiplication by i k_p,i, so the push is the
+    collocated one with k -> k_p.  Every product the push forms of a k_p,i with the
+    phases of the two components it couples is the staggered difference's own
+    symbol, 2 pi/d_i-periodic in k_i, so the Nyquist index needs no special
+    reading here: it keeps k_i = +-pi/d_i (unlike the collocated scheme, whose
+    i k_i is not periodic there and is set to 0).
+    """
+    from . import dispersion
+    k = _raw_grid(shape, d)
+    kp = tuple(dispersion._kp_axis(k[i], d[i], order) if i < len(shape) else np.zeros_like(k[i])
+               for i in range(3))
+    dd = tuple(d) + (1.0,) * (3 - len(d))
+    ph = tuple(np.exp(-0.5j * k[i] * dd[i]) for i in range(3))
+    return kp, ph
+
+
+def _shift(F, axes, ph, sign):
+    for a in axes:
+        F = F * (ph[a] if sign > 0 else np.conj(ph[a]))
+    return F
+
+
 def psatd_step(E, B, J=None, rho0=None, rho1=None, *, d, dt, c=1.0, eps0=1.0,
-               form="none", nsteps=1):
+               form="none", nsteps=1, order=0):
     """``nsteps`` PSATD steps of real fields E, B (arrays ``(3, *grid)``).
 
     Sources (J at t+dt/2; rho at t and t+dt) are held constant over the
     ``nsteps`` steps, each step being: forward DFT of every component, the
     per-mode push of :func:`push_modes`, inverse DFT.  Returns new (E, B).
+
+    ``order`` = 0: all components on the nodes, exact wavenumbers.  ``order`` = p
+    (even, >= 2): components at their staggered (Yee) positions and the order-p
+    wavenumbers of :func:`staggered_operators`; each step shifts the spectra to
+    true positions, pushes with k_p, and shifts back.
     """
     E = np.asarray(E, dtype=np.float64)
     B = np.asarray(B, dtype=np.float64)
     shape = E.shape[1:]
-    k = spectral_grid(shape, d)
-    Jh = [forward(np.asarray(J[i], dtype=np.float64)) for i in range(3)] if J is not None else None
+    if order:
+        k, ph = staggered_operators(shape, d, order)
+    else:
+        k, ph = spectral_grid(shape, d), None
+    sE = STAGGER_E if order else ((), (), ())
+    sB = STAGGER_B if order else ((), (), ())
+    Jh = [_shift(forward(np.asarray(J[i], dtype=np.float64)), sE[i], ph, +1) for i in range(3)] \
+        if J is not None else None
     r0 = forward(np.asarray(rho0, dtype=np.float64)) if rho0 is not None else None
     r1 = forward(np.asarray(rho1, dtype=np.float64)) if rho1 is not None else None
     for _ in range(nsteps):
-        Eh = [forward(E[i]) for i in range(3)]
-        Bh = [forward(B[i]) for i in range(3)]
+        Eh = [_shift(forward(E[i]), sE[i], ph, +1) for i in range(3)]
+        Bh = [_shift(forward(B[i]), sB[i], ph, +1) for i in range(3)]
         Eh, Bh = push_modes(k, Eh, Bh, Jh, r0, r1, dt=dt, c=c, eps0=eps0, form=form)
-        E = np.stack([inverse(Eh[i], shape) for i in range(3)])
-        B = np.stack([inverse(Bh[i], shape) for i in range(3)])
+        E = np.stack([inverse(_shift(Eh[i], sE[i], ph, -1), shape) for i in range(3)])
+        B = np.stack([inverse(_shift(Bh[i], sB[i], ph, -1), shape) for i in range(3)])
     return E, B
 
 
