@@ -11,6 +11,13 @@
  * FFT.  The FDTD comparators are the Yee and Cole-Karkkainen (CKC, beta = 1/4)
  * schemes of Sec. III.A / Table 1.
  *
+ * PSATD-p (desc.order = p): on the staggered grid each component's spectrum
+ * is first shifted to its true position (times exp(-i k_i d_i/2) per
+ * staggered axis i), the update below is applied with k replaced by k_p,
+ * k_p,i = (2/d_i) sum_{l=1}^{p/2} C_l sin((2l-1) k_i d_i/2) (C_l the staggered
+ * Fornberg weights), and the spectra are shifted back; the Nyquist index keeps
+ * k_i = +-pi/d_i there (the scheme propagates it).
+ *
  * Per-mode update (c, eps0 explicit; kappa = k/|k|; x = c|k|dt):
  *   E' = C E + (1-C) kappa(kappa.E) + i c S kappa x B - S/(eps0 c k) J
  *        + (S/(c k) - dt)/eps0 kappa(kappa.J)                       [J-form]
@@ -106,7 +113,11 @@ typedef struct {
   int32_t prec;      /* psatd_precision                                           */
   int32_t src;       /* psatd_source_form                                         */
   int32_t flags;     /* PSATD_FLAG_* bits (0: none)                               */
-  int32_t reserved;  /* must be 0                                                 */
+  int32_t order;     /* 0: all components on the nodes, exact wavenumbers k;
+                        p (even, 2..256): PSATD-p (Table 1) on the staggered
+                        (Yee) grid - components at the FDTD positions listed
+                        above, k replaced by the order-p staggered-stencil
+                        wavenumbers k_p (PSATD step only)                        */
 } psatd_desc;
 
 /* Field arrays, updated in place.  Entries of components absent from the

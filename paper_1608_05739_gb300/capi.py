@@ -40,7 +40,7 @@ class psatd_desc(ct.Structure):
     _fields_ = [("ndim", ct.c_int32), ("layout", ct.c_int32), ("n", ct.c_int64 * 3),
                 ("d", ct.c_double * 3), ("dt", ct.c_double), ("c", ct.c_double),
                 ("eps0", ct.c_double), ("prec", ct.c_int32), ("src", ct.c_int32),
-                ("flags", ct.c_int32), ("reserved", ct.c_int32)]
+                ("flags", ct.c_int32), ("order", ct.c_int32)]
 
 
 class psatd_fields(ct.Structure):
@@ -107,7 +107,7 @@ def _check(status, plan=None):
         raise PsatdError(status, msg.decode() if msg else "")
 
 
-def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, autotune=False):
+def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, autotune=False, order=0):
     """psatd_desc for grid ``n`` = (nx, ny[, nz]) and cell sizes ``d``."""
     nd = len(n)
     desc = psatd_desc()
@@ -120,7 +120,7 @@ def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, a
     desc.prec = PREC[prec]
     desc.src = SRC[src]
     desc.flags = FLAG_AUTOTUNE if autotune else 0
-    desc.reserved = 0
+    desc.order = int(order)
     return desc
 
 
@@ -183,13 +183,14 @@ class Plan:
     """
 
     def __init__(self, n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, stream=None,
-                 autotune=False):
+                 autotune=False, order=0):
         import torch
         lib = load()
         self.n, self.layout, self.prec, self.src = tuple(n), layout, prec, src
         self.shape = _grid_shape(n)
         self.dtype = _torch_dtype(prec)
-        self.desc = make_desc(n, d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0, autotune=autotune)
+        self.desc = make_desc(n, d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0, autotune=autotune,
+                              order=order)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -259,7 +260,7 @@ class Batch:
     """
 
     def __init__(self, sizes, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, stream=None,
-                 autotune=False):
+                 autotune=False, order=0):
         import torch
         lib = load()
         self.sizes = [(int(a), int(b)) for a, b in sizes]
@@ -272,7 +273,7 @@ class Batch:
             self.offsets.append(acc)
             acc += a * b
         desc = make_desc(self.sizes[0], d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0,
-                         autotune=autotune)
+                         autotune=autotune, order=order)
         arr = (ct.c_int64 * (2 * len(self.sizes)))(*[v for ab in self.sizes for v in ab])
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -310,13 +311,14 @@ class Local:
     the global arrays, shape [ny, nx], as for Plan."""
 
     def __init__(self, n, d, dt, *, px, py, guard, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0,
-                 stream=None, autotune=False):
+                 stream=None, autotune=False, order=0):
         import torch
         lib = load()
         self.n, self.layout, self.prec, self.src = tuple(n), layout, prec, src
         self.shape = _grid_shape(n)
         self.dtype = _torch_dtype(prec)
-        desc = make_desc(n, d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0, autotune=autotune)
+        desc = make_desc(n, d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0, autotune=autotune,
+                         order=order)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -62,6 +62,10 @@ struct psatd_plan_s {
   int cfg_log_tb[4] = {-1, -1, -1, -1};
   int cfg_push_tb = -1;
   int push_ept = 8;
+  int order = 0;                        // 0: nodes, exact k; p: staggered PSATD-p
+  double* kp_d[3] = {nullptr, nullptr, nullptr};  // per axis k_p / g0 (n_i/2+1 entries)
+  void* ph_d[3] = {nullptr, nullptr, nullptr};    // per axis half-cell phases (twiddle type)
+  double* cw_d = nullptr;               // staggered Fornberg weights (p/2)
   void* gmat = nullptr;       // their split DFT matrices (kTcTail image, device)
   int* d_err = nullptr;       // device error word of the tensor-core passes
 };
@@ -112,8 +116,14 @@ psatd_status validate_desc(psatd_plan p, const psatd_desc* d, bool psatd_limits)
   if (d->layout < 0 || d->layout > 3) return fail(p, PSATD_ERR_INVALID_ARG, "unknown layout %d", d->layout);
   if (d->ndim != layout_ndim(d->layout))
     return fail(p, PSATD_ERR_INVALID_ARG, "ndim %d does not match layout %d", d->ndim, d->layout);
-  if ((d->flags & ~(psatd_limits ? PSATD_FLAG_AUTOTUNE : 0)) != 0 || d->reserved != 0)
-    return fail(p, PSATD_ERR_INVALID_ARG, "unknown flags (or reserved != 0)");
+  if ((d->flags & ~(psatd_limits ? PSATD_FLAG_AUTOTUNE : 0)) != 0)
+    return fail(p, PSATD_ERR_INVALID_ARG, "unknown flags");
+  if (d->order != 0) {
+    if (!psatd_limits)
+      return fail(p, PSATD_ERR_INVALID_ARG, "order applies to the PSATD step only (the FDTD schemes are order 2)");
+    if (d->order < 2 || d->order > 256 || (d->order & 1))
+      return fail(p, PSATD_ERR_INVALID_ARG, "order must be 0 or an even number in [2, 256] (got %d)", d->order);
+  }
   if (d->src < 0 || d->src > 2) return fail(p, PSATD_ERR_INVALID_ARG, "unknown source form %d", d->src);
   if (d->layout == PSATD_FIELDS_2D_TM && d->src == PSATD_SRC_J_RHO)
     return fail(p, PSATD_ERR_INVALID_ARG, "the TM layout has no rho-form (k.E = 0)");
@@ -190,7 +200,8 @@ psatd_status gather_slots(psatd_plan p, const psatd_fields* f, const psatd_sourc
 }
 
 void release(psatd_plan p) {
-  void* bufs[] = {p->spec1, p->spec2, p->tw[0], p->tw[1], p->tw[2], p->tab, p->d_off, p->gmat, p->d_err};
+  void* bufs[] = {p->spec1, p->spec2, p->tw[0], p->tw[1], p->tw[2], p->tab, p->d_off, p->gmat, p->d_err,
+                  p->kp_d[0], p->kp_d[1], p->kp_d[2], p->ph_d[0], p->ph_d[1], p->ph_d[2], p->cw_d};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (auto& v : p->ev) v.clear();
@@ -354,6 +365,11 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     a.s_a6 = (R)(1.0 / (p->d.eps0 * c * c * p->g0));
     a.gmat = p->gmat;
     a.err = p->d_err;
+    a.stag = p->order > 0 ? 1 : 0;
+    for (int i = 0; i < 3; ++i) {
+      a.kp[i] = p->kp_d[i];
+      a.ph[i] = p->ph_d[i];
+    }
     const void* twl = p->tw[p->ndim == 3 ? 2 : 1];
     {
       const int tb = p->cfg_push_tb > 0 ? p->cfg_push_tb
@@ -445,10 +461,11 @@ struct TuneCfg {
   int push_tb, push_ept;
 };
 struct TuneKey {
-  int prec, layout, form, npatch;
+  int prec, layout, form, npatch, order;
   int64_t n[3];
   bool operator==(const TuneKey& o) const {
-    return prec == o.prec && layout == o.layout && form == o.form && npatch == o.npatch && n[0] == o.n[0] &&
+    return prec == o.prec && layout == o.layout && form == o.form && npatch == o.npatch && order == o.order &&
+           n[0] == o.n[0] &&
            n[1] == o.n[1] && n[2] == o.n[2];
   }
 };
@@ -456,7 +473,7 @@ std::mutex g_tune_mutex;
 std::vector<std::pair<TuneKey, TuneCfg>> g_tune_cache;
 
 TuneKey tune_key(psatd_plan p) {
-  return TuneKey{p->d.prec, p->layout, p->form, p->npatch, {p->nx, p->ny, p->nz}};
+  return TuneKey{p->d.prec, p->layout, p->form, p->npatch, p->order, {p->nx, p->ny, p->nz}};
 }
 void apply_cfg(psatd_plan p, const TuneCfg& c) {
   for (int i = 0; i < 4; ++i) p->cfg_log_tb[i] = c.log_tb[i];
@@ -678,6 +695,7 @@ static psatd_status plan_create_n(const psatd_desc* desc, void* cuda_stream, int
   p->f32 = desc->prec == PSATD_FP32 || desc->prec == PSATD_MIXED_FP16;
   p->tc = desc->prec == PSATD_MIXED_FP16;
   p->push_ept = p->tc ? 16 : 8;
+  p->order = desc->order;
   p->ndim = desc->ndim;
   p->layout = desc->layout;
   p->form = desc->src;
@@ -736,6 +754,12 @@ static psatd_status plan_create_n(const psatd_desc* desc, void* cuda_stream, int
   const size_t ent = (size_t)p->tab_e[0] * p->tab_e[1] * p->tab_e[2];
   if (a == PSATD_OK) a = alloc(p, &p->tab, ent * (p->f32 ? sizeof(Coef<float>) : sizeof(Coef<double>)), "coefficients");
   if (a == PSATD_OK && p->tc) a = alloc(p, &p->gmat, 2 * TcGeom<16>::kGDir, "tensor-core DFT matrices");
+  for (int i = 0; i < p->ndim && a == PSATD_OK && p->order > 0; ++i) {
+    a = alloc(p, reinterpret_cast<void**>(&p->kp_d[i]), (size_t)(ns[i] / 2 + 1) * sizeof(double), "k_p table");
+    if (a == PSATD_OK) a = alloc(p, &p->ph_d[i], (size_t)(ns[i] / 2 + 1) * 16, "staggering phases");
+  }
+  if (a == PSATD_OK && p->order > 0)
+    a = alloc(p, reinterpret_cast<void**>(&p->cw_d), (size_t)(p->order / 2) * sizeof(double), "stencil weights");
   if (a == PSATD_OK && p->tc) a = alloc(p, reinterpret_cast<void**>(&p->d_err), sizeof(int), "error word");
   if (a == PSATD_OK && p->tc) {
     cudaError_t e = cudaMemset(p->d_err, 0, sizeof(int));
@@ -772,9 +796,24 @@ psatd_status psatd_coeffs_init(psatd_plan p) {
       e = launch_tc_dftmat(p->gmat, p->st);
       if (e != cudaSuccess) return cuda_fail(p, e, "tensor-core DFT matrix launch");
     }
+    if (p->order > 0) {
+      std::vector<double> C(p->order / 2);
+      staggered_weights(p->order, C.data());
+      e = cudaMemcpyAsync(p->cw_d, C.data(), C.size() * sizeof(double), cudaMemcpyHostToDevice, p->st);
+      if (e != cudaSuccess) return cuda_fail(p, e, "stencil weight upload");
+      for (int i = 0; i < p->ndim; ++i) {
+        e = launch_kp_tables(p->kp_d[i], p->ph_d[i], p->cw_d, p->order / 2, (int)ns[i], p->d.d[i], p->g0, p->f32,
+                             p->st);
+        if (e != cudaSuccess) return cuda_fail(p, e, "k_p table launch");
+      }
+      e = cudaStreamSynchronize(p->st);  // the host weights are read by the copy above
+      if (e != cudaSuccess) return cuda_fail(p, e, "stencil weight upload");
+    }
     const double N = (double)p->nx * (double)p->ny * (double)p->nz;
+    const double* kp[3] = {p->kp_d[0], p->kp_d[1], p->kp_d[2]};
     e = launch_coefs(p->tab, p->f32, (int)p->tab_e[0], (int)p->tab_e[1], (int)p->tab_e[2], (int)p->nx, (int)p->ny,
-                     (int)p->nz, p->r[0], p->r[1], p->r[2], p->g0, p->d.c, p->d.dt, p->d.eps0, 1.0 / N, p->st);
+                     (int)p->nz, p->r[0], p->r[1], p->r[2], p->g0, p->d.c, p->d.dt, p->d.eps0, 1.0 / N, p->st,
+                     p->order > 0 ? kp : nullptr);
     if (e != cudaSuccess) return cuda_fail(p, e, "coefficient table launch");
   }
   p->coeffs_ready = true;
@@ -993,6 +1032,8 @@ extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_f
   if (nsteps < 1) return fail(nullptr, PSATD_ERR_INVALID_ARG, "nsteps must be >= 1 (got %d)", nsteps);
   if (desc->prec != PSATD_FP32 && desc->prec != PSATD_FP64)
     return fail(nullptr, PSATD_ERR_UNSUPPORTED, "psatd_step_noalloc runs PSATD_FP32 and PSATD_FP64 only");
+  if (desc->order != 0)
+    return fail(nullptr, PSATD_ERR_UNSUPPORTED, "psatd_step_noalloc runs the collocated exact-k step (order 0) only");
 
   // a plan-shaped descriptor on the stack whose buffers are carved from the array
   psatd_plan_s p;

@@ -58,6 +58,9 @@ struct PushArgs {
   R s_a6;            // 1 / (eps0 c^2 g0)
   const void* gmat;  // tensor-core pass: split DFT matrices (kTcTail image)
   int* err;          // tensor-core pass: device error word
+  int stag;          // staggered order-p plan (PSATD-p): k_p and half-cell phases below
+  const double* kp[3];  // per axis, k_p / g0 for |m| = 0..n/2
+  const void* ph[3];    // per axis, exp(-i pi m/n) for m = 0..n/2 (twiddle type)
 };
 
 // ---------------------------------------------------------------- pass 1 / 2
@@ -406,16 +409,51 @@ __device__ __forceinline__ void push_3d(C (&E)[3], C (&B)[3], const C (&J)[3], C
 // Layout codes (psatd_layout): 0 3D6, 1 2D6, 2 TE, 3 TM.
 // Slot order: 3D6/2D6: E0 E1 E2 B0 B1 B2 [J0 J1 J2] [rho_n rho_np1]
 //             TE: E0 E1 B2 [J0 J1] [rho_n rho_np1];  TM: E2 B0 B1 [J2]
+// Staggered axes of each slot (bit 0 x, 1 y, 2 z): the Yee positions Ex(x),
+// Ey(y), Ez(z), Bx(y,z), By(x,z), Bz(x,y), J as E, rho on the nodes.
+template <int LAYOUT>
+__device__ __forceinline__ int slot_stagger(int c) {
+  if constexpr (LAYOUT == 2) return c == 0 ? 1 : c == 1 ? 2 : c == 2 ? 3 : c == 3 ? 1 : c == 4 ? 2 : 0;
+  else if constexpr (LAYOUT == 3) return c == 0 ? 4 : c == 1 ? 6 : c == 2 ? 5 : 4;
+  else return c == 0 ? 1 : c == 1 ? 2 : c == 2 ? 4 : c == 3 ? 6 : c == 4 ? 5 : c == 5 ? 3 : c == 6 ? 1 : c == 7 ? 2 : c == 8 ? 4 : 0;
+}
+
 template <typename R, int LAYOUT>
 __device__ __forceinline__ void push_slots(typename Types<R>::C* st, int L, int l, const CoefReg<R>& f,
-                                           R mx, R my, R mz, const PushArgs<R>& a) {
+                                           R mx, R my, R mz, const PushArgs<R>& a,
+                                           const typename Types<R>::W* P) {
   typedef typename Types<R>::C C;
   const C Z = mkc(R(0), R(0));
   const int form = a.form;
   R cS_h, cS_l, Sc_h, Sc_l;
   prod2(a.c_h, a.c_l, f.S_h, f.S_l, cS_h, cS_l);
   prod2(a.ic_h, a.ic_l, f.S_h, f.S_l, Sc_h, Sc_l);
-  auto S = [&](int c) -> C& { return st[c * L + l]; };
+  // staggered plans (P != NULL): slot values to true positions on the way in, back on the way out
+  const int zmask = a.ndim == 3 ? 7 : 3;
+  struct Ref {
+    C* p;
+    int m;
+    const typename Types<R>::W* P;
+    __device__ __forceinline__ operator C() const {
+      C v = *p;
+      if (P) {
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+          if (m & (1 << ax)) v = twmul(v, P[ax]);
+      }
+      return v;
+    }
+    __device__ __forceinline__ Ref& operator=(C v) {
+      if (P) {
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+          if (m & (1 << ax)) v = twmul_conj(v, P[ax]);
+      }
+      *p = v;
+      return *this;
+    }
+  };
+  auto S = [&](int c) -> Ref { return Ref{&st[c * L + l], slot_stagger<LAYOUT>(c) & zmask, P}; };
   if constexpr (LAYOUT == 2) {
     C E0 = S(0), E1 = S(1), B2 = S(2);
     const C J0 = form ? S(3) : Z, J1 = form ? S(4) : Z;
@@ -449,20 +487,35 @@ __device__ __forceinline__ void push_slots(typename Types<R>::C* st, int L, int 
 
 // Signed integer modes (Nyquist -> 0) of a last-axis line's fixed axes and its
 // coefficient-table row: 2D lines are kx, 3D lines are (kx, ky), ky fastest.
+// Staggered plans keep the Nyquist index (+nx/2 on the half axis, -ny/2 on a full one).
 template <typename R>
 __device__ __forceinline__ void line_modes(const PushArgs<R>& a, int line, int& mxi, int& myi, int& rowi) {
   if (a.ndim == 2) {
     const int kx = line % a.lines_per_patch;
-    mxi = (kx == a.nx_half) ? 0 : kx;
+    mxi = (kx == a.nx_half && !a.stag) ? 0 : kx;
     myi = 0;
     rowi = kx;
   } else {
     const int kx = line / a.ny, ky = line - kx * a.ny;
-    mxi = (kx == a.nx_half) ? 0 : kx;
+    mxi = (kx == a.nx_half && !a.stag) ? 0 : kx;
     const int nyh = a.ny >> 1;
-    myi = (ky == nyh) ? 0 : (ky < nyh ? ky : ky - a.ny);
+    myi = (ky == nyh && !a.stag) ? 0 : (ky < nyh ? ky : ky - a.ny);
     rowi = kx * (nyh + 1) + (ky <= nyh ? ky : a.ny - ky);
   }
+}
+
+template <class W> __device__ __forceinline__ W wconj(W w);
+template <> __device__ __forceinline__ float4 wconj(float4 w) { return make_float4(w.x, -w.y, w.z, -w.w); }
+template <> __device__ __forceinline__ double2 wconj(double2 w) { return make_double2(w.x, -w.y); }
+// k_p / g0 and phase of signed mode m along axis ax of a staggered plan (k_p odd, phase conjugate for m < 0)
+template <typename R>
+__device__ __forceinline__ void stag_axis(const PushArgs<R>& a, int ax, int m, R& k, typename Types<R>::W& w) {
+  typedef typename Types<R>::W W;
+  const int am = m < 0 ? -m : m;
+  const R v = (R)__ldg(&a.kp[ax][am]);
+  const W p = __ldg(&static_cast<const W*>(a.ph[ax])[am]);
+  k = m < 0 ? -v : v;
+  w = m < 0 ? wconj(p) : p;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
@@ -507,6 +560,13 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
 
   int mxi, myi, rowi;
   line_modes(a, valid ? line : 0, mxi, myi, rowi);
+  typedef typename Types<R>::W Wt;
+  R kpx = R(0), kpy = R(0);
+  Wt phx{}, phy{};
+  if (a.stag) {
+    stag_axis(a, 0, mxi, kpx, phx);
+    if (a.ndim == 3) stag_axis(a, 1, myi, kpy, phy);
+  }
   const Coef<R>* trow = a.tab + (int64_t)rowi * a.tab_row;
   // the push needs EPT coefficient entries per thread: start bringing them
   // into L2 now, so that its loads do not wait on DRAM one mode after another
@@ -553,17 +613,36 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int l = t + T * (m0 + h);
-      const int ml = (l == L / 2) ? 0 : (l < L / 2 ? l : l - L);
       CoefReg<R> f;
       f.C_h = q[h].C_h; f.C_l = q[h].C_l; f.S_h = q[h].S_h; f.S_l = q[h].S_l;
       f.A1 = q[h].A1; f.A4 = q[h].A4; f.B1 = q[h].B1; f.B2 = q[h].B2;
       R mx, my, mz;
-      if (a.ndim == 2) {
-        mx = a.rx * R(mxi); my = a.ry * R(ml); mz = R(0);
+      if (a.stag) {
+        const int ml = l < L / 2 ? l : l - L;
+        R kl;
+        Wt pl;
+        stag_axis(a, a.ndim == 2 ? 1 : 2, ml, kl, pl);
+        Wt P[3];
+        P[0] = phx;
+        if (a.ndim == 2) {
+          mx = kpx; my = kl; mz = R(0);
+          P[1] = pl;
+          P[2] = phy;
+        } else {
+          mx = kpx; my = kpy; mz = kl;
+          P[1] = phy;
+          P[2] = pl;
+        }
+        push_slots<R, LAYOUT>(st, L, sw<CXL>(l), f, mx, my, mz, a, P);
       } else {
-        mx = a.rx * R(mxi); my = a.ry * R(myi); mz = a.rz * R(ml);
+        const int ml = (l == L / 2) ? 0 : (l < L / 2 ? l : l - L);
+        if (a.ndim == 2) {
+          mx = a.rx * R(mxi); my = a.ry * R(ml); mz = R(0);
+        } else {
+          mx = a.rx * R(mxi); my = a.ry * R(myi); mz = a.rz * R(ml);
+        }
+        push_slots<R, LAYOUT>(st, L, sw<CXL>(l), f, mx, my, mz, a, nullptr);
       }
-      push_slots<R, LAYOUT>(st, L, sw<CXL>(l), f, mx, my, mz, a);
     }
   }
 

@@ -84,19 +84,50 @@ __device__ double f2_series(double x) {  // sum_{n>=1} (-1)^(n+1) 2n x^(2n-2) / 
   return s;
 }
 
+// Order-p staggered wavenumbers and half-cell phases of one axis of n cells of
+// size d (PSATD-p, Table 1): for m = 0..n/2,
+//   kp[m] = (2/d) sum_{l=1}^{p/2} C_l sin((2l-1) pi m/n) / g0   (in units of g0),
+//   ph[m] = exp(-i pi m/n) (the shift of a component sitting half a cell along
+//   the axis; negative m take the conjugate), rounded to the step precision
+//   (FP32: hi/lo pairs).  The Nyquist entry m = n/2 is kept (k = pi/d).
+__global__ void k_kp_tables(double* kp, void* ph, const double* C, int nl, int n, double d, double g0, int f32) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m > n / 2) return;
+  double acc = 0.0;
+  for (int l = 1; l <= nl; ++l) {
+    const long long num = ((long long)(2 * l - 1) * m) % (2LL * n);  // (2l-1) m/n mod 2, exactly
+    acc += C[l - 1] * sinpi((double)num / (double)n);
+  }
+  kp[m] = 2.0 / d * acc / g0;
+  double sn, cs;
+  sincospi(-(double)m / (double)n, &sn, &cs);
+  if (f32) {
+    const float ch = (float)cs, sh = (float)sn;
+    static_cast<float4*>(ph)[m] = make_float4(ch, sh, (float)(cs - (double)ch), (float)(sn - (double)sh));
+  } else {
+    static_cast<double2*>(ph)[m] = make_double2(cs, sn);
+  }
+}
+
 __global__ void k_coefs(void* out, int f32, int e0, int e1, int e2, int nx, int ny, int nz,
                         double rx, double ry, double rz, double g0, double c, double dt,
-                        double eps0, double invN) {
+                        double eps0, double invN, const double* kpx, const double* kpy, const double* kpz) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t total = (int64_t)e0 * e1 * e2;
   if (idx >= total) return;
   const int iz = (int)(idx % e2);
   const int iy = (int)((idx / e2) % e1);
   const int ix = (int)(idx / ((int64_t)e1 * e2));
-  const double mx = (2 * ix == nx) ? 0.0 : ix;
-  const double my = (2 * iy == ny) ? 0.0 : iy;
-  const double mz = (nz > 1 && 2 * iz == nz) ? 0.0 : iz;
-  const double mm = sqrt((rx * mx) * (rx * mx) + (ry * my) * (ry * my) + (rz * mz) * (rz * mz));
+  double mm;
+  if (kpx) {  // staggered order p: |k_p| / g0 from the per-axis tables (Nyquist kept)
+    const double a = kpx[ix], b = kpy[iy], z = kpz ? kpz[iz] : 0.0;
+    mm = sqrt(a * a + b * b + z * z);
+  } else {
+    const double mx = (2 * ix == nx) ? 0.0 : ix;
+    const double my = (2 * iy == ny) ? 0.0 : iy;
+    const double mz = (nz > 1 && 2 * iz == nz) ? 0.0 : iz;
+    mm = sqrt((rx * mx) * (rx * mx) + (ry * my) * (ry * my) + (rz * mz) * (rz * mz));
+  }
   const double q = c * g0 * dt;  // x = q |mt|
   const double x = q * mm;
   double sx, cx;
@@ -183,12 +214,33 @@ cudaError_t launch_twiddles(void* out, int L, int ept, bool r2c, bool f32, cudaS
 
 cudaError_t launch_coefs(void* out, bool f32, int e0, int e1, int e2, int nx, int ny, int nz,
                          double rx, double ry, double rz, double g0, double c, double dt,
-                         double eps0, double invN, cudaStream_t st) {
+                         double eps0, double invN, cudaStream_t st, const double* const kp[3]) {
   const int64_t total = (int64_t)e0 * e1 * e2;
   const unsigned blocks = (unsigned)((total + 255) / 256);
   k_coefs<<<blocks, 256, 0, st>>>(out, f32 ? 1 : 0, e0, e1, e2, nx, ny, nz, rx, ry, rz, g0, c, dt,
-                                  eps0, invN);
+                                  eps0, invN, kp ? kp[0] : nullptr, kp ? kp[1] : nullptr, kp ? kp[2] : nullptr);
   return cudaGetLastError();
+}
+
+cudaError_t launch_kp_tables(double* kp, void* ph, const double* C, int nl, int n, double d, double g0, bool f32,
+                             cudaStream_t st) {
+  k_kp_tables<<<(n / 2 + 1 + 127) / 128, 128, 0, st>>>(kp, ph, C, nl, n, d, g0, f32 ? 1 : 0);
+  return cudaGetLastError();
+}
+
+// Staggered first-derivative weights of order p (f'(0) ~ (1/h) sum_l C_l
+// [f((l-1/2)h) - f(-(l-1/2)h)]): the ratio of consecutive weights,
+// C_l / C_(l-1) = -(2l-3)^2 (h-l+1) / ((2l-1)^2 (h+l-1)), h = p/2, fixes them up
+// to one factor, which the consistency condition sum_l (2l-1) C_l = 1 (exact
+// derivative of a linear function) sets.
+void staggered_weights(int p, double* C) {
+  const int h = p / 2;
+  C[0] = 1.0;
+  for (int l = 2; l <= h; ++l)
+    C[l - 1] = C[l - 2] * -((double)(2 * l - 3) * (2 * l - 3) * (h - l + 1)) / ((double)(2 * l - 1) * (2 * l - 1) * (h + l - 1));
+  double s = 0.0;
+  for (int l = 1; l <= h; ++l) s += (2 * l - 1) * C[l - 1];
+  for (int l = 1; l <= h; ++l) C[l - 1] /= s;
 }
 
 }  // namespace psatd

@@ -13,7 +13,14 @@ inline int row_ept(int L) { return L >= 16 ? 16 : 8; }
 inline int push_ept(int, bool tc = false) { return tc ? PushEPT<16, true>::value : PushEPT<16>::value; }
 // split-FP16 radix-16 DFT matrices of both directions, tensor-core operand layout
 cudaError_t launch_tc_dftmat(void* out, cudaStream_t st);
+// kp: per-axis order-p wavenumber tables (units of g0, n_i/2+1 entries) of a
+// staggered plan, or NULL for the collocated exact-k plan
 cudaError_t launch_coefs(void* out, bool f32, int e0, int e1, int e2, int nx, int ny, int nz,
                          double rx, double ry, double rz, double g0, double c, double dt,
-                         double eps0, double invN, cudaStream_t st);
+                         double eps0, double invN, cudaStream_t st, const double* const kp[3] = nullptr);
+// order-p wavenumbers (double, units of g0) and half-cell phases (twiddle type) of one axis
+cudaError_t launch_kp_tables(double* kp, void* ph, const double* C, int nl, int n, double d, double g0, bool f32,
+                             cudaStream_t st);
+// staggered Fornberg weights C_1..C_(p/2) of even order p (host, FP64)
+void staggered_weights(int p, double* C);
 }  // namespace psatd

@@ -33,13 +33,13 @@ def grid_n(shape):
 
 
 def psatd_gpu(shape, d, dt, E, B, J=None, r0=None, r1=None, *, layout, prec, src, nsteps=1, c=1.0,
-              eps0=1.0, plan=None, calls=1):
+              eps0=1.0, plan=None, calls=1, order=0):
     """Run ``calls`` x psatd_step(nsteps) on the GPU; returns numpy (E, B), absent components 0."""
     ensure_lib()
     pe, pb, pj = capi.PRESENT[layout]
     own = plan is None
     if own:
-        plan = capi.Plan(grid_n(shape), d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0)
+        plan = capi.Plan(grid_n(shape), d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0, order=order)
     Et = [torch_dev(E[i], prec) if pe[i] else None for i in range(3)]
     Bt = [torch_dev(B[i], prec) if pb[i] else None for i in range(3)]
     Jt = [torch_dev(J[i], prec) if (J is not None and pj[i] and src != "none") else None for i in range(3)]

@@ -170,3 +170,19 @@ def test_local_create_rejects_invalid_arguments(lib):
     assert lib.psatd_local_step(None, None, None, 1) == 1
     assert lib.psatd_local_destroy(None) == 0
     assert lib.psatd_local_plan(None) is None
+
+
+@pytest.mark.parametrize("order,expect", [(3, 1), (258, 1), (-2, 1), (1, 1)])
+def test_invalid_orders(lib, order, expect):
+    d = capi.make_desc((64, 32), (1.0, 1.0), 0.5, layout="te", src="J", order=order)
+    st, h = _create(lib, d)
+    assert st == expect and h.value is None
+    assert b"order" in lib.psatd_last_error(None)
+
+
+def test_order_is_psatd_only(lib):
+    d = capi.make_desc((64, 32), (1.0, 1.0), 0.5, layout="te", src="J", order=4)
+    f = capi.psatd_fields()
+    s = capi.psatd_sources()
+    assert lib.fdtd_step(ct.byref(d), 0, ct.byref(f), ct.byref(s), 1, None) == 1
+    assert lib.psatd_step_noalloc(ct.byref(d), ct.byref(f), ct.byref(s), 1, None) == 2
