@@ -68,14 +68,14 @@ def algorithmic_bytes(nx=NX, ny=NY, nz=1, n_in=N_IN, n_out=N_OUT, real=4):
     return out
 
 
-def sheet_profile(n, dt, dx):
-    """J_y(x) of the current sheet at t = (n + 1/2) dt (length NX, float64)."""
+def sheet_profile(n, dt, dx, nx=NX):
+    """J_y(x) of the current sheet at t = (n + 1/2) dt (length nx, float64)."""
     lam = LAM_CELLS * dx
     w0 = 2.0 * math.pi / lam
     t = (n + 0.5) * dt
-    Lx = NX * dx
+    Lx = nx * dx
     x0 = 0.5 * Lx + 0.9 * math.sin(w0 * t) / w0
-    x = np.arange(NX) * dx
+    x = np.arange(nx) * dx
     r = (x - x0 + 0.5 * Lx) % Lx - 0.5 * Lx
     return np.exp(-(r / (2.0 * dx)) ** 2)
 
@@ -269,7 +269,8 @@ def main():
                     help="te2048 arithmetic of the headline line: plain FP32, or tensor-core split-FP16 "
                          "radix-16 stages (the other one is timed too and reported under 'other_precision')")
     ap.add_argument("--no-side-precision", action="store_true", help="skip timing the other precision")
-    ap.add_argument("--workload", default="te2048", choices=["te2048", "3d256", "fdtd-yee", "fdtd-ckc", "batch512"],
+    ap.add_argument("--workload", default="te2048",
+                    choices=["te2048", "3d256", "fdtd-yee", "fdtd-ckc", "batch512", "local"],
                     help="te2048 (default) is the metric's configuration; the others are side measurements")
     args = ap.parse_args()
     world, rank, local = dist_setup()
@@ -472,7 +473,7 @@ def run_side_workload(args):
         dt = dx / math.sqrt(2.0)
         side_stream = torch.cuda.Stream()
         torch.cuda.synchronize()
-        b = capi.Batch(sizes, (dx, dx), dt, layout="te", prec="fp32", src="J", stream=side_stream)
+        b = capi.Batch(sizes, (dx, dx), dt, layout="te", prec=args.precision, src="J", stream=side_stream)
         tot = b.total
         Ex, Ey, Bz = (torch.zeros(tot, device=dev) for _ in range(3))
         Jx = torch.randn(tot, device=dev, generator=torch.Generator(device=dev).manual_seed(1613)) * 0.01
@@ -499,14 +500,49 @@ def run_side_workload(args):
         line.update({
             "value": tot * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
             "interior_cell_steps_per_s": interior * args.steps / (ms * 1e-3),
+            "dtype": "f32" if args.precision == "fp32" else "f16x2-split tensor + f32",
             "config": {"workload": "512 2D TE FP32 patches, interior U{64..512}^2, guards U{8..16}, periodic domain "
                                    "next_pow2(n+2g) per side, J-form, one CUDA graph of one step replayed",
+                       "precision": PREC_NOTE[args.precision],
                        "cells": tot, "interior_cells": interior, "size_classes": classes,
                        "l2": "inputs %.1f GB >> L2, flushed once before the run" % (tot * 5 * 4 / 1e9)},
             "step_gbs": alg / (ms / args.steps * 1e-3) / 1e9, "hbm_gbs_peak": hbm, "clocks": clk,
             "gpu_launches": 3 * classes * args.steps,
         })
         b.destroy()
+    elif args.workload == "local":
+        # the paper's decomposition (Sec. II.A.3): a 3840 x 1920 TE grid as 16 x 8 patches of 240^2
+        # interior cells with 8 guard cells (extended 256^2), guards refreshed from the neighbours every
+        # step, each patch advanced by its own FFTs; staggered PSATD of order 16 (Table 1, PSATD-p)
+        px, py, gd, order = 16, 8, 8, 16
+        nx, ny = px * 240, py * 240
+        dx = 1.0 / LAM_CELLS
+        dt = dx / math.sqrt(2.0)
+        L = capi.Local((nx, ny), (dx, dx), dt, px=px, py=py, guard=gd, layout="te", prec=args.precision, src="J",
+                       order=order, stream=stream)
+        Ex, Ey, Bz = (torch.zeros(ny, nx, device=dev) for _ in range(3))
+        Jx = torch.zeros(ny, nx, device=dev)
+        total = args.warmup + args.steps
+        prof = torch.from_numpy(np.stack([sheet_profile(k, dt, dx, nx) for k in range(total)])).float().to(dev)
+        Jy = [prof[k].expand(ny, nx).contiguous() for k in range(total)]
+        ms, clk = timed_steps(lambda i: L.step([Ex, Ey, None], [None, None, Bz], [Jx, Jy[i], None]), args.steps,
+                              args.warmup, flush, stream)
+        L.sync()
+        cells = nx * ny
+        ext = px * py * (240 + 2 * gd) ** 2
+        alg = sum(algorithmic_bytes(256, 256, 1, 5, 3).values()) * px * py
+        guard_bytes = 4 * (5 * ext + 5 * ext + 3 * cells + 3 * cells)  # gathers (read + write), scatter
+        line.update({
+            "value": cells * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+            "dtype": "f32" if args.precision == "fp32" else "f16x2-split tensor + f32",
+            "config": {"workload": "2D TE local-FFT decomposition: 3840x1920 grid, 16x8 patches of 240^2 + 8 guard "
+                                   "cells (extended 256^2), staggered PSATD order 16, current-sheet J",
+                       "precision": PREC_NOTE[args.precision], "cells": cells, "extended_cells": ext,
+                       "l2": "flushed before every timed step"},
+            "step_gbs": (alg + guard_bytes) / (ms / args.steps * 1e-3) / 1e9, "hbm_gbs_peak": hbm, "clocks": clk,
+            "gpu_launches": 6 * args.steps,
+        })
+        L.destroy()
     else:
         scheme = args.workload.split("-")[1]
         dx = 1.0 / LAM_CELLS
