@@ -270,7 +270,7 @@ def main():
                          "radix-16 stages (the other one is timed too and reported under 'other_precision')")
     ap.add_argument("--no-side-precision", action="store_true", help="skip timing the other precision")
     ap.add_argument("--workload", default="te2048",
-                    choices=["te2048", "3d256", "fdtd-yee", "fdtd-ckc", "batch512", "local"],
+                    choices=["te2048", "3d256", "fdtd-yee", "fdtd-ckc", "batch512", "local", "cost3d"],
                     help="te2048 (default) is the metric's configuration; the others are side measurements")
     args = ap.parse_args()
     world, rank, local = dist_setup()
@@ -510,6 +510,47 @@ def run_side_workload(args):
             "gpu_launches": 3 * classes * args.steps,
         })
         b.destroy()
+    elif args.workload == "cost3d":
+        # Table 2 (Sec. V) restated for the field solvers on this GPU: per cell-step cost of each
+        # scheme on one 3D 256^3 grid (FP32, J-form, L2 flushed before every step), the field-solver
+        # xi = t(PSATD-128) / t(Yee), and the paper's time factors with its resolution factor
+        # A = 2.3 (FDTD, lambda/322 vs lambda/140) and its PSTD step ratio 9 (c dt 0.110 dx).
+        n = 256
+        d = 1.0
+        cells = n ** 3
+        r0, r1, J, E0 = synth.gaussian_charges_torch((n, n, n), (d, d, d), 0.5, n_charges=64, seed=1610, device=dev)
+        J = [J[i].contiguous() for i in range(3)]
+        E = [E0[i].contiguous() for i in range(3)]
+        B = [torch.zeros(n, n, n, device=dev) for _ in range(3)]
+        res = {}
+        for name, kw, dtc in (("psatd_order128", dict(order=128), 0.99), ("psatd_exact_k", dict(order=0), 0.99),
+                              ("pstd", dict(order=0, scheme="pstd"), 0.110)):
+            plan = capi.Plan((n, n, n), (d, d, d), dtc * d, layout="3d6", prec=args.precision, src="J",
+                             stream=stream, **kw)
+            ms, _ = timed_steps(lambda i: plan.step(E, B, J), args.steps, args.warmup, flush, stream)
+            plan.sync()
+            plan.destroy()
+            res[name] = ms / args.steps
+        dty = d / math.sqrt(3.0) * 0.99
+        ms, clk = timed_steps(lambda i: capi.fdtd_step((n, n, n), (d, d, d), dty, E, B, J, scheme="yee", layout="3d6",
+                                                       prec="fp32", stream=stream), args.steps, args.warmup, flush,
+                              stream)
+        res["yee"] = ms / args.steps
+        xi = res["psatd_order128"] / res["yee"]
+        A = 2.3
+        line.update({
+            "value": cells / (res["psatd_order128"] * 1e-3), "ms_per_step": res["psatd_order128"],
+            "config": {"workload": "3D 256^3 FP32 J-form: PSATD order 128 (staggered), PSATD exact k, PSTD, Yee FDTD; "
+                                   "Table 2 time factors restated with this GPU's field-solver xi",
+                       "precision": PREC_NOTE[args.precision], "l2": "flushed before every timed step"},
+            "ns_per_cell_step": {k: v * 1e6 / cells for k, v in res.items()},
+            "xi_field_solver": xi,
+            "paper_xi_full_pic_mira": 1.8,
+            "time_factor_vs_psatd128": {"yee (A^4/xi, A = 2.3)": A ** 4 / xi,
+                                        "pstd (9 x step cost ratio)": 9.0 * res["pstd"] / res["psatd_order128"]},
+            "paper_time_factors": {"ckc": 16, "yee": 28, "pstd": 9},
+            "clocks": clk, "gpu_launches": None,
+        })
     elif args.workload == "local":
         # the paper's decomposition (Sec. II.A.3): a 3840 x 1920 TE grid as 16 x 8 patches of 240^2
         # interior cells with 8 guard cells (extended 256^2), guards refreshed from the neighbours every

@@ -100,6 +100,13 @@ typedef enum { PSATD_FDTD_YEE = 0, PSATD_FDTD_CKC = 1 } psatd_fdtd_scheme;
  * precision, layout, source form and sizes.  PSATD plans and batches only;
  * fdtd_step rejects it and psatd_step_noalloc ignores it. */
 #define PSATD_FLAG_AUTOTUNE 1
+/* PSATD_FLAG_PSTD: the plan's step is the pseudo-spectral time-domain scheme
+ * (Table 1 row PSTD) instead of PSATD: the same transforms, and per mode the
+ * leapfrog B -= (dt/2) i k x E; E += c^2 dt i k x B - dt J/eps0;
+ * B -= (dt/2) i k x E (co-temporal E, B in and out, like fdtd_step).  Stable for
+ * c dt |k| < 2 over the propagated modes (the caller's choice of dt); J-form or
+ * vacuum only (INVALID_ARG with the rho-form); any order (k or k_p). */
+#define PSATD_FLAG_PSTD 2
 
 /* Problem statement (the paper's arguments: grid sizes, cell sizes, dt, c, eps0). */
 typedef struct {

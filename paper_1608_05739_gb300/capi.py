@@ -83,6 +83,7 @@ EXPORTS = [
 ]
 
 FLAG_AUTOTUNE = 1
+FLAG_PSTD = 2
 
 
 def load(path: str = LIB_PATH):
@@ -107,7 +108,8 @@ def _check(status, plan=None):
         raise PsatdError(status, msg.decode() if msg else "")
 
 
-def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, autotune=False, order=0):
+def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, autotune=False, order=0,
+              scheme="psatd"):
     """psatd_desc for grid ``n`` = (nx, ny[, nz]) and cell sizes ``d``."""
     nd = len(n)
     desc = psatd_desc()
@@ -119,7 +121,9 @@ def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, a
     desc.dt, desc.c, desc.eps0 = float(dt), float(c), float(eps0)
     desc.prec = PREC[prec]
     desc.src = SRC[src]
-    desc.flags = FLAG_AUTOTUNE if autotune else 0
+    if scheme not in ("psatd", "pstd"):
+        raise ValueError("scheme must be 'psatd' or 'pstd'")
+    desc.flags = (FLAG_AUTOTUNE if autotune else 0) | (FLAG_PSTD if scheme == "pstd" else 0)
     desc.order = int(order)
     return desc
 
@@ -183,14 +187,14 @@ class Plan:
     """
 
     def __init__(self, n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, stream=None,
-                 autotune=False, order=0):
+                 autotune=False, order=0, scheme="psatd"):
         import torch
         lib = load()
         self.n, self.layout, self.prec, self.src = tuple(n), layout, prec, src
         self.shape = _grid_shape(n)
         self.dtype = _torch_dtype(prec)
         self.desc = make_desc(n, d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0, autotune=autotune,
-                              order=order)
+                              order=order, scheme=scheme)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -116,8 +116,10 @@ psatd_status validate_desc(psatd_plan p, const psatd_desc* d, bool psatd_limits)
   if (d->layout < 0 || d->layout > 3) return fail(p, PSATD_ERR_INVALID_ARG, "unknown layout %d", d->layout);
   if (d->ndim != layout_ndim(d->layout))
     return fail(p, PSATD_ERR_INVALID_ARG, "ndim %d does not match layout %d", d->ndim, d->layout);
-  if ((d->flags & ~(psatd_limits ? PSATD_FLAG_AUTOTUNE : 0)) != 0)
+  if ((d->flags & ~(psatd_limits ? (PSATD_FLAG_AUTOTUNE | PSATD_FLAG_PSTD) : 0)) != 0)
     return fail(p, PSATD_ERR_INVALID_ARG, "unknown flags");
+  if ((d->flags & PSATD_FLAG_PSTD) && d->src == PSATD_SRC_J_RHO)
+    return fail(p, PSATD_ERR_INVALID_ARG, "PSTD takes J only (src must be NONE or J)");
   if (d->order != 0) {
     if (!psatd_limits)
       return fail(p, PSATD_ERR_INVALID_ARG, "order applies to the PSATD step only (the FDTD schemes are order 2)");
@@ -366,6 +368,11 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     a.gmat = p->gmat;
     a.err = p->d_err;
     a.stag = p->order > 0 ? 1 : 0;
+    a.scheme = (p->d.flags & PSATD_FLAG_PSTD) ? 1 : 0;
+    a.p_h = (R)(0.5 * p->d.dt * p->g0);
+    a.p_e = (R)(p->d.c * p->d.c * p->d.dt * p->g0);
+    a.p_j = (R)(p->d.dt / p->d.eps0);
+    a.inv_n = (R)(1.0 / ((double)p->nx * (double)p->ny * (double)p->nz));
     for (int i = 0; i < 3; ++i) {
       a.kp[i] = p->kp_d[i];
       a.ph[i] = p->ph_d[i];
@@ -461,10 +468,11 @@ struct TuneCfg {
   int push_tb, push_ept;
 };
 struct TuneKey {
-  int prec, layout, form, npatch, order;
+  int prec, layout, form, npatch, order, flags;
   int64_t n[3];
   bool operator==(const TuneKey& o) const {
     return prec == o.prec && layout == o.layout && form == o.form && npatch == o.npatch && order == o.order &&
+           flags == o.flags &&
            n[0] == o.n[0] &&
            n[1] == o.n[1] && n[2] == o.n[2];
   }
@@ -473,7 +481,8 @@ std::mutex g_tune_mutex;
 std::vector<std::pair<TuneKey, TuneCfg>> g_tune_cache;
 
 TuneKey tune_key(psatd_plan p) {
-  return TuneKey{p->d.prec, p->layout, p->form, p->npatch, p->order, {p->nx, p->ny, p->nz}};
+  return TuneKey{p->d.prec, p->layout, p->form, p->npatch, p->order, p->d.flags & PSATD_FLAG_PSTD,
+                 {p->nx, p->ny, p->nz}};
 }
 void apply_cfg(psatd_plan p, const TuneCfg& c) {
   for (int i = 0; i < 4; ++i) p->cfg_log_tb[i] = c.log_tb[i];

@@ -58,6 +58,8 @@ struct PushArgs {
   R s_a6;            // 1 / (eps0 c^2 g0)
   const void* gmat;  // tensor-core pass: split DFT matrices (kTcTail image)
   int* err;          // tensor-core pass: device error word
+  int scheme;        // 0: PSATD (analytic in time); 1: PSTD (leapfrog, p_h / p_e / p_j / inv_n)
+  R p_h, p_e, p_j, inv_n;  // PSTD: dt g0 / 2, c^2 dt g0, dt / eps0, 1/N
   int stag;          // staggered order-p plan (PSATD-p): k_p and half-cell phases below
   const double* kp[3];  // per axis, k_p / g0 for |m| = 0..n/2
   const void* ph[3];    // per axis, exp(-i pi m/n) for m = 0..n/2 (twiddle type)
@@ -406,6 +408,35 @@ __device__ __forceinline__ void push_3d(C (&E)[3], C (&B)[3], const C (&J)[3], C
   }
 }
 
+// PSTD (Table 1): the leapfrog of the FDTD schemes with spectral derivatives, for
+// co-temporal E, B: B -= (dt/2) i k x E; E += c^2 dt i k x B - dt J/eps0;
+// B -= (dt/2) i k x E; then the 1/N of the inverse transform.  k = g0 m.
+template <typename R, class C>
+__device__ __forceinline__ void pstd_modes(C (&E)[3], C (&B)[3], const C (&J)[3], R mx, R my, R mz,
+                                           const PushArgs<R>& a) {
+  const R m[3] = {mx, my, mz};
+  auto curl = [&](const C (&F)[3], C (&out)[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int i1 = (i + 1) % 3, i2 = (i + 2) % 3;
+      out[i] = csub(rmul(m[i1], F[i2]), rmul(m[i2], F[i1]));
+    }
+  };
+  C t[3];
+  curl(E, t);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) B[i] = csub(B[i], iz(rmul(a.p_h, t[i])));
+  curl(B, t);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) E[i] = csub(cadd(E[i], iz(rmul(a.p_e, t[i]))), rmul(a.p_j, J[i]));
+  curl(E, t);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    B[i] = rmul(a.inv_n, csub(B[i], iz(rmul(a.p_h, t[i]))));
+    E[i] = rmul(a.inv_n, E[i]);
+  }
+}
+
 // Layout codes (psatd_layout): 0 3D6, 1 2D6, 2 TE, 3 TM.
 // Slot order: 3D6/2D6: E0 E1 E2 B0 B1 B2 [J0 J1 J2] [rho_n rho_np1]
 //             TE: E0 E1 B2 [J0 J1] [rho_n rho_np1];  TM: E2 B0 B1 [J2]
@@ -454,6 +485,36 @@ __device__ __forceinline__ void push_slots(typename Types<R>::C* st, int L, int 
     }
   };
   auto S = [&](int c) -> Ref { return Ref{&st[c * L + l], slot_stagger<LAYOUT>(c) & zmask, P}; };
+  if (a.scheme == 1) {  // PSTD: J-form or vacuum
+    C E[3] = {Z, Z, Z}, B[3] = {Z, Z, Z}, J[3] = {Z, Z, Z};
+    if constexpr (LAYOUT == 2) {
+      E[0] = S(0); E[1] = S(1); B[2] = S(2);
+      if (form) { J[0] = S(3); J[1] = S(4); }
+    } else if constexpr (LAYOUT == 3) {
+      E[2] = S(0); B[0] = S(1); B[1] = S(2);
+      if (form) J[2] = S(3);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        E[i] = S(i);
+        B[i] = S(3 + i);
+        if (form) J[i] = S(6 + i);
+      }
+    }
+    pstd_modes<R>(E, B, J, mx, my, mz, a);
+    if constexpr (LAYOUT == 2) {
+      S(0) = E[0]; S(1) = E[1]; S(2) = B[2];
+    } else if constexpr (LAYOUT == 3) {
+      S(0) = E[2]; S(1) = B[0]; S(2) = B[1];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        S(i) = E[i];
+        S(3 + i) = B[i];
+      }
+    }
+    return;
+  }
   if constexpr (LAYOUT == 2) {
     C E0 = S(0), E1 = S(1), B2 = S(2);
     const C J0 = form ? S(3) : Z, J1 = form ? S(4) : Z;
@@ -608,7 +669,8 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int l = t + T * (m0 + h);
-      q[h] = trow[(l <= L / 2) ? l : L - l];  // |m| along the line axis
+      if (a.scheme == 0) q[h] = trow[(l <= L / 2) ? l : L - l];  // |m| along the line axis
+      else q[h] = Coef<R>{};                                       // PSTD reads no coefficients
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {

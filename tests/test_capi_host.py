@@ -64,7 +64,7 @@ def _create(lib, desc):
     (lambda d: setattr(d, "prec", 2), 2),                  # split-BF16: not in this build
     (lambda d: setattr(d, "prec", 9), 1),
     (lambda d: setattr(d, "src", 7), 1),
-    (lambda d: setattr(d, "flags", 2), 1),                 # unknown flag bit
+    (lambda d: setattr(d, "flags", 4), 1),                 # unknown flag bit
     (lambda d: (setattr(d, "layout", 3), setattr(d, "src", 2)), 1),  # TM has no rho-form
     (lambda d: setattr(d, "layout", 9), 1),
 ])
@@ -186,3 +186,15 @@ def test_order_is_psatd_only(lib):
     s = capi.psatd_sources()
     assert lib.fdtd_step(ct.byref(d), 0, ct.byref(f), ct.byref(s), 1, None) == 1
     assert lib.psatd_step_noalloc(ct.byref(d), ct.byref(f), ct.byref(s), 1, None) == 2
+
+
+def test_pstd_flag_rules(lib):
+    d = capi.make_desc((64, 32), (1.0, 1.0), 0.5, layout="te", src="rho", scheme="pstd")
+    st, h = _create(lib, d)
+    assert st == 1 and b"PSTD" in lib.psatd_last_error(None)
+    d = capi.make_desc((64, 32), (1.0, 1.0), 0.5, layout="te", src="J", scheme="pstd")
+    f = capi.psatd_fields()
+    s = capi.psatd_sources()
+    assert lib.fdtd_step(ct.byref(d), 0, ct.byref(f), ct.byref(s), 1, None) == 1
+    with pytest.raises(ValueError):
+        capi.make_desc((64, 32), (1.0, 1.0), 0.5, scheme="leapfrog")
