@@ -240,6 +240,15 @@ int pick_log_tb(int L, int64_t nb, bool f32, bool tc = false) {
   while ((1 << lg) < tb) ++lg;
   return lg;
 }
+// lines per CTA of an inverse transposing pass: half the forward pass's (the
+// autotuner measured that faster at 2048^2 x, 256^3 x and y, and 512^2 x: the
+// gathered bin pairs of fewer lines per CTA), keeping the tensor-core minimum
+int pick_log_tb_inv(int L, int64_t nb, bool f32, bool tc = false) {
+  const int lg = pick_log_tb(L, nb, f32, tc);
+  const int T = L / row_ept(L);
+  if (lg == 0 || (tc && (T << (lg - 1)) < 128)) return lg;
+  return lg - 1;
+}
 
 // shared memory of a transposing pass: one L-element buffer per line, or the
 // [nk][tb + 1] transpose tile when the pass uses one (nk = 0: no tile)
@@ -396,7 +405,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
   if (p->ndim == 3) {
     // pass 4: inverse y lines: spec2 [c][kx][ky][z] -> spec1 [c][kx][z][y]
     PassGeom g;
-    g.log_tb = p->cfg_log_tb[2] >= 0 ? p->cfg_log_tb[2] : pick_log_tb((int)ny, nz, p->f32, TC);
+    g.log_tb = p->cfg_log_tb[2] >= 0 ? p->cfg_log_tb[2] : pick_log_tb_inv((int)ny, nz, p->f32, TC);
     g.grid = dim3((unsigned)(nz >> g.log_tb), (unsigned)nxh, (unsigned)p->n_out);
     g.smem = tail + tpass_smem((int)ny, g.log_tb, (size_t)ny, csz);
     for (int c = 0; c < p->n_out; ++c) {
@@ -410,7 +419,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
   // last pass: inverse x rows (C2R): spec1 -> out [z][y][x] (3D) / packed patches (2D)
   {
     PassGeom g;
-    g.log_tb = p->cfg_log_tb[3] >= 0 ? p->cfg_log_tb[3] : pick_log_tb(Lx, ny, p->f32, TC);
+    g.log_tb = p->cfg_log_tb[3] >= 0 ? p->cfg_log_tb[3] : pick_log_tb_inv(Lx, ny, p->f32, TC);
     g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)na0, (unsigned)p->n_out);
     g.smem = tail + tpass_smem(Lx, g.log_tb, 0, csz);
     for (int c = 0; c < p->n_out; ++c) {
@@ -888,7 +897,8 @@ psatd_status psatd_plan_get_launch(psatd_plan p, int32_t cfg[6]) {
   const bool tc = p->tc;
   const int dflt[4] = {pick_log_tb(Lx, p->ny, p->f32, tc),
                        p->ndim == 3 ? pick_log_tb((int)p->ny, p->nz, p->f32, tc) : -1,
-                       p->ndim == 3 ? pick_log_tb((int)p->ny, p->nz, p->f32, tc) : -1, pick_log_tb(Lx, p->ny, p->f32, tc)};
+                       p->ndim == 3 ? pick_log_tb_inv((int)p->ny, p->nz, p->f32, tc) : -1,
+                       pick_log_tb_inv(Lx, p->ny, p->f32, tc)};
   for (int k = 0; k < 4; ++k) cfg[k] = p->cfg_log_tb[k] >= 0 ? p->cfg_log_tb[k] : dflt[k];
   cfg[4] = p->cfg_push_tb > 0 ? p->cfg_push_tb : push_lines_per_cta(Ll, p->n_in, nlines, p->tc, p->f32, p->push_ept);
   cfg[5] = p->push_ept;

@@ -449,7 +449,7 @@ __device__ __forceinline__ int slot_stagger(int c) {
   else return c == 0 ? 1 : c == 1 ? 2 : c == 2 ? 4 : c == 3 ? 6 : c == 4 ? 5 : c == 5 ? 3 : c == 6 ? 1 : c == 7 ? 2 : c == 8 ? 4 : 0;
 }
 
-template <typename R, int LAYOUT>
+template <typename R, int LAYOUT, bool PSTD>
 __device__ __forceinline__ void push_slots(typename Types<R>::C* st, int L, int l, const CoefReg<R>& f,
                                            R mx, R my, R mz, const PushArgs<R>& a,
                                            const typename Types<R>::W* P) {
@@ -485,7 +485,7 @@ __device__ __forceinline__ void push_slots(typename Types<R>::C* st, int L, int 
     }
   };
   auto S = [&](int c) -> Ref { return Ref{&st[c * L + l], slot_stagger<LAYOUT>(c) & zmask, P}; };
-  if (a.scheme == 1) {  // PSTD: J-form or vacuum
+  if constexpr (PSTD) {  // J-form or vacuum
     C E[3] = {Z, Z, Z}, B[3] = {Z, Z, Z}, J[3] = {Z, Z, Z};
     if constexpr (LAYOUT == 2) {
       E[0] = S(0); E[1] = S(1); B[2] = S(2);
@@ -587,6 +587,64 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
+// The push of the EPT modes l = t + T m of one line, in the slots at positions
+// sw<kLastCX>(l): PSATD reads the coefficient table (two modes per iteration,
+// both loads issued together), PSTD none; staggered plans rotate every slot
+// value to its Yee position and back around the update.
+template <typename R, int L, int LAYOUT, int EPT, bool STAG, bool PSTD>
+__device__ __forceinline__ void push_line_modes(typename Types<R>::C* st, const PushArgs<R>& a,
+                                                const Coef<R>* trow, int t, int mxi, int myi, R kpx, R kpy,
+                                                typename Types<R>::W phx, typename Types<R>::W phy) {
+  typedef typename Types<R>::W Wt;
+  typedef FFTPlan<L, EPT> P;
+  constexpr int T = P::kT;
+  constexpr int CXL = P::kLastCX;
+#pragma unroll 1
+  for (int m0 = 0; m0 < EPT; m0 += 2) {
+    Coef<R> q[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int l = t + T * (m0 + h);
+      if constexpr (!PSTD) q[h] = trow[(l <= L / 2) ? l : L - l];  // |m| along the line axis
+      else q[h] = Coef<R>{};
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int l = t + T * (m0 + h);
+      CoefReg<R> f;
+      f.C_h = q[h].C_h; f.C_l = q[h].C_l; f.S_h = q[h].S_h; f.S_l = q[h].S_l;
+      f.A1 = q[h].A1; f.A4 = q[h].A4; f.B1 = q[h].B1; f.B2 = q[h].B2;
+      R mx, my, mz;
+      if constexpr (STAG) {
+        const int ml = l < L / 2 ? l : l - L;
+        R kl;
+        Wt pl;
+        stag_axis(a, a.ndim == 2 ? 1 : 2, ml, kl, pl);
+        Wt Ph[3];
+        Ph[0] = phx;
+        if (a.ndim == 2) {
+          mx = kpx; my = kl; mz = R(0);
+          Ph[1] = pl;
+          Ph[2] = phy;
+        } else {
+          mx = kpx; my = kpy; mz = kl;
+          Ph[1] = phy;
+          Ph[2] = pl;
+        }
+        push_slots<R, LAYOUT, PSTD>(st, L, sw<CXL>(l), f, mx, my, mz, a, Ph);
+      } else {
+        const int ml = (l == L / 2) ? 0 : (l < L / 2 ? l : l - L);
+        if (a.ndim == 2) {
+          mx = a.rx * R(mxi); my = a.ry * R(ml); mz = R(0);
+        } else {
+          mx = a.rx * R(mxi); my = a.ry * R(myi); mz = a.rz * R(ml);
+        }
+        push_slots<R, LAYOUT, PSTD>(st, L, sw<CXL>(l), f, mx, my, mz, a, nullptr);
+      }
+    }
+  }
+}
+
 // Fused last-axis pass: for TB lines (kx in 2D, (kx, ky) in 3D), forward FFT
 // of every input slot, per-mode push, inverse FFT of the n_out field slots,
 // written back in place.  Shared memory: n_in staged slots of L values per
@@ -662,50 +720,14 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
     for (int m = 0; m < EPT; ++m) sl[sw<CXL>(t + T * m)] = v[m];
   }
 
-  // push, two modes per iteration (both coefficient loads issued together)
-#pragma unroll 1
-  for (int m0 = 0; m0 < EPT; m0 += 2) {
-    Coef<R> q[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int l = t + T * (m0 + h);
-      if (a.scheme == 0) q[h] = trow[(l <= L / 2) ? l : L - l];  // |m| along the line axis
-      else q[h] = Coef<R>{};                                       // PSTD reads no coefficients
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int l = t + T * (m0 + h);
-      CoefReg<R> f;
-      f.C_h = q[h].C_h; f.C_l = q[h].C_l; f.S_h = q[h].S_h; f.S_l = q[h].S_l;
-      f.A1 = q[h].A1; f.A4 = q[h].A4; f.B1 = q[h].B1; f.B2 = q[h].B2;
-      R mx, my, mz;
-      if (a.stag) {
-        const int ml = l < L / 2 ? l : l - L;
-        R kl;
-        Wt pl;
-        stag_axis(a, a.ndim == 2 ? 1 : 2, ml, kl, pl);
-        Wt P[3];
-        P[0] = phx;
-        if (a.ndim == 2) {
-          mx = kpx; my = kl; mz = R(0);
-          P[1] = pl;
-          P[2] = phy;
-        } else {
-          mx = kpx; my = kpy; mz = kl;
-          P[1] = phy;
-          P[2] = pl;
-        }
-        push_slots<R, LAYOUT>(st, L, sw<CXL>(l), f, mx, my, mz, a, P);
-      } else {
-        const int ml = (l == L / 2) ? 0 : (l < L / 2 ? l : l - L);
-        if (a.ndim == 2) {
-          mx = a.rx * R(mxi); my = a.ry * R(ml); mz = R(0);
-        } else {
-          mx = a.rx * R(mxi); my = a.ry * R(myi); mz = a.rz * R(ml);
-        }
-        push_slots<R, LAYOUT>(st, L, sw<CXL>(l), f, mx, my, mz, a, nullptr);
-      }
-    }
+  // push every mode of the line (each thread its own positions); one loop per
+  // (staggered?, PSTD?) combination, chosen once per CTA
+  if (a.scheme == 0) {
+    if (a.stag) push_line_modes<R, L, LAYOUT, EPT, true, false>(st, a, trow, t, mxi, myi, kpx, kpy, phx, phy);
+    else push_line_modes<R, L, LAYOUT, EPT, false, false>(st, a, trow, t, mxi, myi, kpx, kpy, phx, phy);
+  } else {
+    if (a.stag) push_line_modes<R, L, LAYOUT, EPT, true, true>(st, a, trow, t, mxi, myi, kpx, kpy, phx, phy);
+    else push_line_modes<R, L, LAYOUT, EPT, false, true>(st, a, trow, t, mxi, myi, kpx, kpy, phx, phy);
   }
 
   for (int c = 0; c < a.n_out; ++c) {
