@@ -49,7 +49,10 @@ PREC_NOTE = {
     "fp32": "fp32 (compensated twiddles and C, S)",
     "mixed_fp16": "mixed: radix-16 stages as tcgen05 DFT-matrix MMAs, split-FP16 operands, FP32 accumulate; "
                   "rest fp32 as the plain path",
+    "mixed_bf16": "mixed: radix-16 stages as tcgen05 DFT-matrix MMAs, split-BF16 operands (3 pieces), FP32 "
+                  "accumulate; rest fp32 as the plain path",
 }
+DTYPE = {"fp32": "f32", "mixed_fp16": "f16x2-split tensor + f32", "mixed_bf16": "bf16x3-split tensor + f32"}
 
 
 def algorithmic_bytes(nx=NX, ny=NY, nz=1, n_in=N_IN, n_out=N_OUT, real=4):
@@ -265,9 +268,9 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=30.0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed_fp16"],
-                    help="te2048 arithmetic of the headline line: plain FP32, or tensor-core split-FP16 "
-                         "radix-16 stages (the other one is timed too and reported under 'other_precision')")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed_fp16", "mixed_bf16"],
+                    help="te2048 arithmetic of the headline line: plain FP32, or tensor-core split-FP16 / "
+                         "split-BF16 radix-16 stages (the others are timed too, under 'other_precision')")
     ap.add_argument("--no-side-precision", action="store_true", help="skip timing the other precision")
     ap.add_argument("--workload", default="te2048",
                     choices=["te2048", "3d256", "fdtd-yee", "fdtd-ckc", "batch512", "local", "cost3d"],
@@ -304,15 +307,17 @@ def main():
     Jy_all = [prof[n].expand(NY, NX).contiguous() for n in range(total)]  # resident before timing
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    other = "mixed_fp16" if args.precision == "fp32" else "fp32"
     side = None
     if not args.no_side_precision:
-        side_ms, side_kt, _, side_plan = time_te2048(capi, torch, other, args, dev, dt, dx, Jy_all, flush, stream,
-                                                     world, sample_clocks=False)
-        side_plan.destroy()
-        side = {"precision": PREC_NOTE[other], "value": NX * NY * args.steps / (side_ms * 1e-3),
-                "unit": "cell-steps/s", "ms_per_step": side_ms / args.steps,
-                "per_kernel_ms": {k: v[1] / v[0] for k, v in side_kt.items()}}
+        side = []
+        for other in (pr for pr in PREC_NOTE if pr != args.precision):
+            side_ms, side_kt, _, side_plan = time_te2048(capi, torch, other, args, dev, dt, dx, Jy_all, flush,
+                                                         stream, world, sample_clocks=False)
+            side_plan.destroy()
+            side.append({"precision": PREC_NOTE[other], "dtype": DTYPE[other],
+                         "value": NX * NY * args.steps / (side_ms * 1e-3), "unit": "cell-steps/s",
+                         "ms_per_step": side_ms / args.steps,
+                         "per_kernel_ms": {k: v[1] / v[0] for k, v in side_kt.items()}})
     ms, ktimes, clk, plan = time_te2048(capi, torch, args.precision, args, dev, dt, dx, Jy_all, flush, stream,
                                         world, sample_clocks=True)
 
@@ -372,7 +377,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f16x2-split tensor + f32",
+            "vs_baseline": None, "dtype": DTYPE[args.precision],
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": [NX, NY], "precision": PREC_NOTE[args.precision],
                        "l2": "flushed before every timed step (256 MiB write), step alone inside the events",
@@ -500,7 +505,7 @@ def run_side_workload(args):
         line.update({
             "value": tot * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
             "interior_cell_steps_per_s": interior * args.steps / (ms * 1e-3),
-            "dtype": "f32" if args.precision == "fp32" else "f16x2-split tensor + f32",
+            "dtype": DTYPE[args.precision],
             "config": {"workload": "512 2D TE FP32 patches, interior U{64..512}^2, guards U{8..16}, periodic domain "
                                    "next_pow2(n+2g) per side, J-form, one CUDA graph of one step replayed",
                        "precision": PREC_NOTE[args.precision],
@@ -575,7 +580,7 @@ def run_side_workload(args):
         guard_bytes = 4 * (5 * ext + 5 * ext + 3 * cells + 3 * cells)  # gathers (read + write), scatter
         line.update({
             "value": cells * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
-            "dtype": "f32" if args.precision == "fp32" else "f16x2-split tensor + f32",
+            "dtype": DTYPE[args.precision],
             "config": {"workload": "2D TE local-FFT decomposition: 3840x1920 grid, 16x8 patches of 240^2 + 8 guard "
                                    "cells (extended 256^2), staggered PSATD order 16, current-sheet J",
                        "precision": PREC_NOTE[args.precision], "cells": cells, "extended_cells": ext,

@@ -71,7 +71,8 @@ typedef enum {
 typedef enum {
   PSATD_FP64 = 0,        /* double storage and arithmetic                              */
   PSATD_FP32 = 1,        /* float storage; twiddles and C, S applied compensated (hi/lo) */
-  PSATD_MIXED_BF16 = 2,  /* reserved (tensor-core split-BF16 DFT passes)              */
+  PSATD_MIXED_BF16 = 2,  /* as PSATD_MIXED_FP16 with split-BF16 operands: a 8-bit
+                            fixed-point head and two BF16 remainders, six products */
   PSATD_MIXED_FP16 = 3   /* float storage; every radix-16 FFT stage is a 16 x 16 DFT-
                             matrix contraction on the tensor cores (tcgen05) with
                             split-FP16 operands (hi + lo, per-row power-of-two scale,
@@ -142,8 +143,8 @@ int32_t psatd_abi_version(void);
 
 /* Create a PSATD plan for `desc` on `cuda_stream`.
  * Supported (this build): every n[i] a power of two, 16 <= n[0] <= 4096,
- * 8 <= n[1], n[2] <= 4096; PSATD_FP64, PSATD_FP32 or PSATD_MIXED_FP16;
- * flags = 0.  PSATD_MIXED_FP16 also needs n[0] >= 32, n[1], n[2] >= 16 and
+ * 8 <= n[1], n[2] <= 4096; PSATD_FP64, PSATD_FP32, PSATD_MIXED_FP16 or _BF16;
+ * flags = 0.  The mixed precisions also need n[0] >= 32, n[1], n[2] >= 16 and
  * at least 128 threads per CTA in every pass (n[0]/32 * min(32, n[1]) >= 128
  * for the x pass; UNSUPPORTED otherwise).
  * Owns: its spectral scratch (about n_in * (n0/2+1) * n1 * n2 complex values,

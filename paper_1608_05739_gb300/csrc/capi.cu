@@ -55,7 +55,8 @@ struct psatd_plan_s {
   std::vector<EventPair> pool;
   int npatch = 1;             // 2D batches: patches of this size class
   int64_t* d_off = nullptr;   // their element offsets in the caller's packed arrays (device)
-  bool tc = false;            // split-FP16 tensor-core radix-16 stages (PSATD_MIXED_FP16)
+  bool tc = false;            // tensor-core radix-16 stages (PSATD_MIXED_FP16 / _BF16)
+  bool tc_bf16 = false;       // ... with split-BF16 operands (a third A piece)
   // launch configuration: lines per CTA of the passes fwd_x, fwd_y, inv_y, inv_x and of the
   // fused pass (-1: the built-in heuristic), and the fused pass's elements per thread
   // (8: radix-8 stages, 16: radix-16); set by psatd_plan_autotune
@@ -130,9 +131,7 @@ psatd_status validate_desc(psatd_plan p, const psatd_desc* d, bool psatd_limits)
   if (d->layout == PSATD_FIELDS_2D_TM && d->src == PSATD_SRC_J_RHO)
     return fail(p, PSATD_ERR_INVALID_ARG, "the TM layout has no rho-form (k.E = 0)");
   if (d->prec < 0 || d->prec > 3) return fail(p, PSATD_ERR_INVALID_ARG, "unknown precision %d", d->prec);
-  if (d->prec == PSATD_MIXED_BF16)
-    return fail(p, PSATD_ERR_UNSUPPORTED, "split-BF16 is not in this build (PSATD_MIXED_FP16 is)");
-  if (d->prec == PSATD_MIXED_FP16 && !psatd_limits)
+  if ((d->prec == PSATD_MIXED_FP16 || d->prec == PSATD_MIXED_BF16) && !psatd_limits)
     return fail(p, PSATD_ERR_UNSUPPORTED, "mixed precision applies to the PSATD step only");
   const int nd = d->ndim;
   for (int i = 0; i < nd; ++i)
@@ -274,6 +273,12 @@ int push_lines_per_cta(int L, int n_in, int64_t nlines, bool tc, bool f32, int e
   return tb;
 }
 
+// split-BF16 passes: shared memory of the third A piece of `threads` threads
+// (one 128-row piece per 128 threads), after the pass's exchange region
+size_t tc_a3_bytes(psatd_plan p, int threads) {
+  return p->tc_bf16 ? (size_t)(threads / 128) * TcGeom<16>::kAPiece : 0;
+}
+
 struct TimedLaunch {
   psatd_plan p;
   int slot;
@@ -296,7 +301,7 @@ struct TimedLaunch {
   }
 };
 
-template <typename R, bool TC>
+template <typename R, int TC>
 psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp]) {
   typedef typename Types<R>::C C;
   const size_t csz = sizeof(C);
@@ -319,7 +324,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     PassGeom g;
     g.log_tb = p->cfg_log_tb[0] >= 0 ? p->cfg_log_tb[0] : pick_log_tb(Lx, ny, p->f32, TC);
     g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)na0, (unsigned)p->n_in);
-    g.smem = tail + tpass_smem(Lx, g.log_tb, 0, csz);
+    g.smem = tail + tpass_smem(Lx, g.log_tb, 0, csz) + tc_a3_bytes(p, (Lx / row_ept(Lx)) << g.log_tb);
     for (int c = 0; c < p->n_in; ++c) {
       io.in[c] = in[c];
       io.out[c] = s1 + c * cs;
@@ -337,7 +342,8 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     PassGeom g;
     g.log_tb = p->cfg_log_tb[1] >= 0 ? p->cfg_log_tb[1] : pick_log_tb((int)ny, nz, p->f32, TC);
     g.grid = dim3((unsigned)(nz >> g.log_tb), (unsigned)nxh, (unsigned)p->n_in);
-    g.smem = tail + tpass_smem((int)ny, g.log_tb, (size_t)ny, csz);
+    g.smem = tail + tpass_smem((int)ny, g.log_tb, (size_t)ny, csz) +
+             tc_a3_bytes(p, ((int)ny / row_ept((int)ny)) << g.log_tb);
     for (int c = 0; c < p->n_in; ++c) {
       io.in[c] = s1 + c * cs;
       io.out[c] = s2 + c * cs;
@@ -391,10 +397,11 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
       const int tb = p->cfg_push_tb > 0 ? p->cfg_push_tb
                                         : push_lines_per_cta(Lline, p->n_in, nlines, TC, p->f32, p->push_ept);
       const size_t per_line = ((size_t)p->n_in + 1) * (size_t)Lline * csz;
+      const size_t a3 = tb > 1 ? tc_a3_bytes(p, tb * (Lline / p->push_ept)) : 0;  // one line: in its slot
       const dim3 grid((unsigned)((nlines + tb - 1) / tb));
       TimedLaunch tl(p, K_PUSH);
       if (p->push_ept == 16) {
-        e = launch_line_push<R, TC, 16>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl);
+        e = launch_line_push<R, TC, 16>(Lline, p->layout, grid, tb, tail + tb * per_line + a3, p->st, a, twl);
       } else {
         if constexpr (TC) e = cudaErrorInvalidValue;
         else e = launch_line_push<R, false, 8>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl);
@@ -407,7 +414,8 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     PassGeom g;
     g.log_tb = p->cfg_log_tb[2] >= 0 ? p->cfg_log_tb[2] : pick_log_tb_inv((int)ny, nz, p->f32, TC);
     g.grid = dim3((unsigned)(nz >> g.log_tb), (unsigned)nxh, (unsigned)p->n_out);
-    g.smem = tail + tpass_smem((int)ny, g.log_tb, (size_t)ny, csz);
+    g.smem = tail + tpass_smem((int)ny, g.log_tb, (size_t)ny, csz) +
+             tc_a3_bytes(p, ((int)ny / row_ept((int)ny)) << g.log_tb);
     for (int c = 0; c < p->n_out; ++c) {
       io.in[c] = s2 + c * cs;
       io.out[c] = s1 + c * cs;
@@ -421,7 +429,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     PassGeom g;
     g.log_tb = p->cfg_log_tb[3] >= 0 ? p->cfg_log_tb[3] : pick_log_tb_inv(Lx, ny, p->f32, TC);
     g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)na0, (unsigned)p->n_out);
-    g.smem = tail + tpass_smem(Lx, g.log_tb, 0, csz);
+    g.smem = tail + tpass_smem(Lx, g.log_tb, 0, csz) + tc_a3_bytes(p, (Lx / row_ept(Lx)) << g.log_tb);
     for (int c = 0; c < p->n_out; ++c) {
       io.in[c] = s1 + c * cs;
       io.out[c] = out[c];
@@ -435,8 +443,8 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
 }
 
 psatd_status step_once(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp]) {
-  if (p->tc) return run_step<float, true>(p, in, out);
-  return p->f32 ? run_step<float, false>(p, in, out) : run_step<double, false>(p, in, out);
+  if (p->tc) return p->tc_bf16 ? run_step<float, 2>(p, in, out) : run_step<float, 1>(p, in, out);
+  return p->f32 ? run_step<float, 0>(p, in, out) : run_step<double, 0>(p, in, out);
 }
 
 // Shape checks of the tensor-core variant: every transposing pass and the fused
@@ -456,7 +464,8 @@ psatd_status check_tc_shape(psatd_plan p, int maxsm) {
   }
   const int64_t nlines = p->ndim == 3 ? p->nxh * p->ny : p->nxh * p->npatch;
   const int tb = push_lines_per_cta(Ll, p->n_in, nlines, true, true, 16);
-  const size_t smem = (size_t)kTcTail + (size_t)tb * ((size_t)p->n_in + 1) * (size_t)Ll * 8;
+  const size_t smem = (size_t)kTcTail + (size_t)tb * ((size_t)p->n_in + 1) * (size_t)Ll * 8 +
+                      (tb > 1 ? tc_a3_bytes(p, tb * (Ll / 16)) : 0);
   if (maxsm > 0 && smem > (size_t)maxsm)
     return fail(nullptr, PSATD_ERR_UNSUPPORTED, "mixed precision: last-axis length %d needs %zu bytes of shared memory",
                 Ll, smem);
@@ -537,7 +546,8 @@ TuneSpace tune_space(psatd_plan p) {
     const int T = rowL[k] / row_ept(rowL[k]);
     for (int lg = 0; (1 << lg) <= 32 && (1 << lg) <= rowNb[k] && (T << lg) <= maxthr; ++lg) {
       if (p->tc && (T << lg) < 128) continue;
-      if (maxsm > 0 && tail + tpass_smem(rowL[k], lg, rowNk[k], csz) > (size_t)maxsm) continue;
+      if (maxsm > 0 && tail + tpass_smem(rowL[k], lg, rowNk[k], csz) + tc_a3_bytes(p, T << lg) > (size_t)maxsm)
+        continue;
       ts.rows[k].push_back(lg);
     }
   }
@@ -547,7 +557,7 @@ TuneSpace tune_space(psatd_plan p) {
     const size_t per_line = ((size_t)p->n_in + 1) * (size_t)ts.Ll * csz;
     for (int tb = 1; tb * T <= (T > 256 ? T : 256); tb *= 2) {
       if (p->tc && (tb * T) % 128 != 0) continue;
-      if (maxsm > 0 && tail + tb * per_line > (size_t)maxsm) continue;
+      if (maxsm > 0 && tail + tb * per_line + (tb > 1 ? tc_a3_bytes(p, tb * T) : 0) > (size_t)maxsm) continue;
       if (tb > 1 && tb / 2 >= nlines) break;
       ts.push.push_back({ept, tb});
     }
@@ -710,8 +720,9 @@ static psatd_status plan_create_n(const psatd_desc* desc, void* cuda_stream, int
   if (!p) return fail(nullptr, PSATD_ERR_OOM, "host allocation failed");
   p->d = *desc;
   p->st = static_cast<cudaStream_t>(cuda_stream);
-  p->f32 = desc->prec == PSATD_FP32 || desc->prec == PSATD_MIXED_FP16;
-  p->tc = desc->prec == PSATD_MIXED_FP16;
+  p->f32 = desc->prec != PSATD_FP64;
+  p->tc = desc->prec == PSATD_MIXED_FP16 || desc->prec == PSATD_MIXED_BF16;
+  p->tc_bf16 = desc->prec == PSATD_MIXED_BF16;
   p->push_ept = p->tc ? 16 : 8;
   p->order = desc->order;
   p->ndim = desc->ndim;
@@ -811,7 +822,7 @@ psatd_status psatd_coeffs_init(psatd_plan p) {
       if (e != cudaSuccess) return cuda_fail(p, e, "twiddle table launch");
     }
     if (p->tc) {
-      e = launch_tc_dftmat(p->gmat, p->st);
+      e = launch_tc_dftmat(p->gmat, p->tc_bf16, p->st);
       if (e != cudaSuccess) return cuda_fail(p, e, "tensor-core DFT matrix launch");
     }
     if (p->order > 0) {

@@ -246,7 +246,7 @@ struct RowEPT { static constexpr int value = L >= 16 ? 16 : 8; };
 // half the threads and, its shared memory being fixed per line, the SM half
 // the warps (measured slower).  The tensor-core variant (TC) takes 16, so that
 // its stages are radix-16 DFT-matrix contractions.
-template <int L, bool TC = false>
+template <int L, int TC = 0>
 struct PushEPT { static constexpr int value = TC ? 16 : 8; };
 
 template <int L, int EPT = 8>
@@ -319,7 +319,7 @@ __device__ __forceinline__ const typename Types<R>::W* stage_tw(const ExBuf<C>& 
 // so the threads of a warp read consecutive entries.
 
 // One forward stage.
-template <typename R, int L, int EPT, int S, bool TC>
+template <typename R, int L, int EPT, int S, int TC>
 __device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
                                           const typename Types<R>::W* __restrict__ tw, int t, TcCtx* tc) {
   typedef typename Types<R>::C C;
@@ -342,7 +342,7 @@ __device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[EPT], ExBuf<
 #pragma unroll
       for (int r = 1; r < RS; ++r) a[r] = twmul(a[r], __ldg(&tws[(r - 1) * NS]));
     }
-    if constexpr (TC && RS == 16) tc_dft<16, false>(a, *tc);
+    if constexpr (TC && RS == 16) tc_dft<16, false, TC == 2>(a, *tc);
     else butterfly<RS, false>(a);
     if constexpr (LAST) {
 #pragma unroll
@@ -361,7 +361,7 @@ __device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[EPT], ExBuf<
 }
 
 // Adjoint of fwd_stage<S>.
-template <typename R, int L, int EPT, int S, bool TC>
+template <typename R, int L, int EPT, int S, int TC>
 __device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
                                           const typename Types<R>::W* __restrict__ tw, int t, TcCtx* tc) {
   typedef typename Types<R>::C C;
@@ -390,7 +390,7 @@ __device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[EPT], ExBuf<
 #pragma unroll
       for (int r = 0; r < RS; ++r) a[r] = buf[sw<CX>(base + r * NS)];
     }
-    if constexpr (TC && RS == 16) tc_dft<16, true>(a, *tc);
+    if constexpr (TC && RS == 16) tc_dft<16, true, TC == 2>(a, *tc);
     else butterfly<RS, true>(a);
     if constexpr (NS > 1) {
       const typename Types<R>::W* tws = stage_tw<R>(ex) + P::tw_off(S) + k;
@@ -402,13 +402,13 @@ __device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[EPT], ExBuf<
   }
 }
 
-template <typename R, int L, int EPT, bool TC, int... S>
+template <typename R, int L, int EPT, int TC, int... S>
 __device__ __forceinline__ void fft_fwd_seq(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
                                             const typename Types<R>::W* tw, int t, TcCtx* tc,
                                             std::integer_sequence<int, S...>) {
   (fwd_stage<R, L, EPT, S, TC>(v, ex, tw, t, tc), ...);
 }
-template <typename R, int L, int EPT, bool TC, int... S>
+template <typename R, int L, int EPT, int TC, int... S>
 __device__ __forceinline__ void fft_inv_seq(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
                                             const typename Types<R>::W* tw, int t, TcCtx* tc,
                                             std::integer_sequence<int, S...>) {
@@ -418,15 +418,16 @@ __device__ __forceinline__ void fft_inv_seq(typename Types<R>::C (&v)[EPT], ExBu
 // Forward DFT of length L: v holds x[t + T m] on entry, X[t + T m] on exit
 // (T = L/EPT, m < EPT).  Every thread of the block must call it (block-wide
 // barriers inside); the exchanges alternate between the two buffers of `ex`.
-// TC: the radix-16 stages run on the tensor cores (tc_dft.cuh, context *tc).
-template <typename R, int L, int EPT, bool TC = false>
+// TC: the radix-16 stages run on the tensor cores (tc_dft.cuh, context *tc):
+// 1 split-FP16, 2 split-BF16.
+template <typename R, int L, int EPT, int TC = 0>
 __device__ __forceinline__ void block_fft_fwd(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
                                               const typename Types<R>::W* tw, int t, TcCtx* tc = nullptr) {
   static_assert(!TC || sizeof(R) == 4, "tensor-core stages take float data");
   fft_fwd_seq<R, L, EPT, TC>(v, ex, tw, t, tc, std::make_integer_sequence<int, FFTPlan<L, EPT>::kStages>{});
 }
 // Unnormalised inverse DFT (adjoint of block_fft_fwd).
-template <typename R, int L, int EPT, bool TC = false>
+template <typename R, int L, int EPT, int TC = 0>
 __device__ __forceinline__ void block_fft_inv(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
                                               const typename Types<R>::W* tw, int t, TcCtx* tc = nullptr) {
   static_assert(!TC || sizeof(R) == 4, "tensor-core stages take float data");

@@ -19,16 +19,16 @@ struct PassGeom {
 // a0_off: optional device table of per-patch element offsets into the caller's
 // arrays (input of launch_fwd_T, output of launch_inv_T); NULL: a0 * stride.
 // TC = true: the tensor-core (split-FP16) variants, float data only.
-template <typename R, bool TC = false>
+template <typename R, int TC = 0>
 cudaError_t launch_fwd_T(int L, bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io,
                          const void* tw, int64_t in_sa0, int64_t in_sb, int64_t out_sa0,
                          int64_t out_sk, const int64_t* a0_off = nullptr);
-template <typename R, bool TC = false>
+template <typename R, int TC = 0>
 cudaError_t launch_inv_T(int L, bool c2r, const PassGeom& g, cudaStream_t st, const LineIO& io,
                          const void* tw, int64_t in_sa0, int64_t in_sk, int64_t out_sa0,
                          int64_t out_sb, const int64_t* a0_off = nullptr);
 // EPT: 8 or 16 elements per thread (radix-8 / radix-16 stages); TC needs 16.
-template <typename R, bool TC, int EPT>
+template <typename R, int TC, int EPT>
 cudaError_t launch_line_push(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
                              const PushArgs<R>& a, const void* tw);
 

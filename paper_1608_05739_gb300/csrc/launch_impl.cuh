@@ -15,7 +15,7 @@ static cudaError_t set_smem(K kern, size_t smem) {
   return cudaSuccess;
 }
 
-template <typename R, bool TC, int L>
+template <typename R, int TC, int L>
 static cudaError_t fwd_T_L(bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io,
                            const void* tw, int64_t a, int64_t b, int64_t c, int64_t d, const int64_t* off) {
   typedef typename Types<R>::W W;
@@ -37,7 +37,7 @@ static cudaError_t fwd_T_L(bool r2c, const PassGeom& g, cudaStream_t st, const L
   return cudaGetLastError();
 }
 
-template <typename R, bool TC, int L>
+template <typename R, int TC, int L>
 static cudaError_t inv_T_L(bool c2r, const PassGeom& g, cudaStream_t st, const LineIO& io,
                            const void* tw, int64_t a, int64_t b, int64_t c, int64_t d, const int64_t* off) {
   typedef typename Types<R>::W W;
@@ -59,7 +59,7 @@ static cudaError_t inv_T_L(bool c2r, const PassGeom& g, cudaStream_t st, const L
   return cudaGetLastError();
 }
 
-template <typename R, bool TC, int EPT, int L>
+template <typename R, int TC, int EPT, int L>
 static cudaError_t push_L(int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
                           const PushArgs<R>& a, const void* tw) {
   typedef typename Types<R>::W W;
@@ -105,21 +105,21 @@ static cudaError_t push_L(int layout, dim3 grid, int tb, size_t smem, cudaStream
     default: return cudaErrorInvalidValue;                        \
   }
 
-template <typename R, bool TC>
+template <typename R, int TC>
 cudaError_t launch_fwd_T(int L, bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io,
                          const void* tw, int64_t in_sa0, int64_t in_sb, int64_t out_sa0,
                          int64_t out_sk, const int64_t* a0_off) {
   PSATD_L_SWITCH(fwd_T_L, r2c, g, st, io, tw, in_sa0, in_sb, out_sa0, out_sk, a0_off)
 }
 
-template <typename R, bool TC>
+template <typename R, int TC>
 cudaError_t launch_inv_T(int L, bool c2r, const PassGeom& g, cudaStream_t st, const LineIO& io,
                          const void* tw, int64_t in_sa0, int64_t in_sk, int64_t out_sa0,
                          int64_t out_sb, const int64_t* a0_off) {
   PSATD_L_SWITCH(inv_T_L, c2r, g, st, io, tw, in_sa0, in_sk, out_sa0, out_sb, a0_off)
 }
 
-template <typename R, bool TC, int EPT>
+template <typename R, int TC, int EPT>
 static cudaError_t push_L_e(int layout, dim3 grid, int tb, size_t smem, cudaStream_t st, const PushArgs<R>& a,
                             const void* tw, int L) {
 #define PUSH_E(LL) push_L<R, TC, EPT, LL>
@@ -140,7 +140,7 @@ static cudaError_t push_L_e(int layout, dim3 grid, int tb, size_t smem, cudaStre
 #undef PUSH_E
 }
 
-template <typename R, bool TC, int EPT>
+template <typename R, int TC, int EPT>
 cudaError_t launch_line_push(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
                              const PushArgs<R>& a, const void* tw) {
   return push_L_e<R, TC, EPT>(layout, grid, tb, smem, st, a, tw, L);

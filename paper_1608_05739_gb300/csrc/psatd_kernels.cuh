@@ -69,9 +69,10 @@ struct PushArgs {
 // Forward FFT along the contiguous axis of TB consecutive lines b, written out
 // with b contiguous: out[a1] + a0*out_sa0 + k*out_sk + b.  R2C: the input rows
 // are real (length 2L), the output has L+1 bins (half spectrum).
-// TC: radix-16 stages on the tensor cores; the dynamic shared memory then
-// starts with the kTcTail block and the A tiles alias the line buffers.
-template <typename R, int L, bool R2C, bool TC = false>
+// TC: radix-16 stages on the tensor cores (1 split-FP16, 2 split-BF16); the
+// dynamic shared memory then starts with the kTcTail block and the A tiles
+// alias the line buffers.
+template <typename R, int L, bool R2C, int TC = 0>
 __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
                                                int64_t in_sa0, int64_t in_sb, int64_t out_sa0,
                                                int64_t out_sk, int log_tb, const int64_t* __restrict__ in_off) {
@@ -89,7 +90,9 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO 
   __shared__ const void* twslot;
   if (t == 0 && g == 0) twslot = tw;
   TcCtx tc;
-  if constexpr (TC) tc_setup(tc, smem_raw, io.gmat, smem_u32(smem), io.err);
+  if constexpr (TC)  // split-BF16: the third A piece after the exchange region (line buffers or tile)
+    tc_setup(tc, smem_raw, io.gmat, smem_u32(smem), io.err, TC == 2,
+             smem_u32(smem + (R2C ? TB * L : L * (TB + 1))));
   ExBuf<C> ex{{smem + g * L, smem + g * L}, 0, &twslot, true};  // one exchange buffer per line
 
   C v[EPT];
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO 
 // in[a1] + a0*in_sa0 + k*in_sk + b, inverse FFT along k, write the lines
 // contiguously to out[a1] + a0*out_sa0 + b*out_sb.  C2R: L+1 Hermitian bins
 // in, real rows of length 2L out (unnormalised).
-template <typename R, int L, bool C2R, bool TC = false>
+template <typename R, int L, bool C2R, int TC = 0>
 __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_inv_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
                                                int64_t in_sa0, int64_t in_sk, int64_t out_sa0,
                                                int64_t out_sb, int log_tb, const int64_t* __restrict__ out_off) {
@@ -188,7 +191,9 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_inv_T(LineIO 
   __shared__ const void* twslot;
   if (t == 0 && g == 0) twslot = tw;
   TcCtx tc;
-  if constexpr (TC) tc_setup(tc, smem_raw, io.gmat, smem_u32(smem), io.err);
+  if constexpr (TC)
+    tc_setup(tc, smem_raw, io.gmat, smem_u32(smem), io.err, TC == 2,
+             smem_u32(smem + (C2R ? TB * L : L * (TB + 1))));
   C v[EPT];
   if constexpr (C2R) {
     // Z[k] = Fe + i Fo, Fe = X[k] + X*[L-k], Fo = (X[k] - X*[L-k]) conj(W_N^k), read straight
@@ -656,7 +661,7 @@ __device__ __forceinline__ void push_line_modes(typename Types<R>::C* st, const 
 // own positions.
 // EPT: elements per thread, 8 (radix-8 stages) or 16 (radix-16 stages; the
 // only choice of the tensor-core variant).
-template <typename R, int L, int LAYOUT, bool TC = false, int EPT = PushEPT<L, TC>::value>
+template <typename R, int L, int LAYOUT, int TC = 0, int EPT = PushEPT<L, TC>::value>
 __global__ void __launch_bounds__(FFTPlan<L, EPT>::kT > 256 ? FFTPlan<L, EPT>::kT : 256)
 k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   typedef typename Types<R>::C C;
@@ -675,7 +680,13 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   __shared__ const void* twslot;
   if (t == 0 && g == 0) twslot = tw;
   TcCtx tc;
-  if constexpr (TC) tc_setup(tc, smem_raw, a.gmat, smem_u32(base + (int)blockDim.y * a.n_in * L), a.err);
+  // split-BF16's third A piece: the current slot when the CTA holds one line (its
+  // own transforms leave it without live data at every stage boundary), else a
+  // region after the extra buffers
+  const bool a3_slot = blockDim.y == 1;
+  if constexpr (TC)
+    tc_setup(tc, smem_raw, a.gmat, smem_u32(base + (int)blockDim.y * a.n_in * L), a.err, TC == 2,
+             smem_u32(base + (int)blockDim.y * (a.n_in + 1) * L));
 
   int mxi, myi, rowi;
   line_modes(a, valid ? line : 0, mxi, myi, rowi);
@@ -715,6 +726,8 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
     for (int m = 0; m < EPT; ++m) v[m] = sl[t + T * m];
     __syncthreads();  // the slot becomes an exchange buffer
     ExBuf<C> ex{{sl, bufB}, 0, &twslot, false};
+    if constexpr (TC)
+      if (a3_slot) tc.a_tile3 = smem_u32(sl);
     block_fft_fwd<R, L, EPT, TC>(v, ex, tw, t, &tc);
 #pragma unroll
     for (int m = 0; m < EPT; ++m) sl[sw<CXL>(t + T * m)] = v[m];
@@ -735,6 +748,8 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
 #pragma unroll
     for (int m = 0; m < EPT; ++m) v[m] = sl[sw<CXL>(t + T * m)];
     ExBuf<C> ex{{sl, bufB}, 0, &twslot, false};
+    if constexpr (TC)
+      if (a3_slot) tc.a_tile3 = smem_u32(sl);
     block_fft_inv<R, L, EPT, TC>(v, ex, tw, t, &tc);
     if (valid) {
       C* dst = spec + c * a.cs + (int64_t)line * L;

@@ -182,7 +182,7 @@ __global__ void k_coefs(void* out, int f32, int e0, int e1, int e2, int nx, int 
 // G_h = G rounded to the 2^-8 grid (exact in FP16), G_l = FP16 of G - G_h,
 // G_ll = FP16 of G - G_h - G_l (all from the FP64 value); each piece stored as
 // 8-row x 16-byte core matrices (LBO 128 B, SBO 512 B).
-__global__ void k_tc_dftmat(unsigned short* out) {
+__global__ void k_tc_dftmat(unsigned short* out, int bf16) {
   typedef TcGeom<16> G;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= 2 * 32 * 32) return;
@@ -191,18 +191,30 @@ __global__ void k_tc_dftmat(unsigned short* out) {
   double sn, cs;
   sincospi((dir ? 2.0 : -2.0) * (double)((r * q) & 15) / 16.0, &sn, &cs);
   const double v = d == 0 ? (c == 0 ? cs : -sn) : (c == 0 ? sn : cs);
-  const double vh = rint(v * 256.0) / 256.0;
-  const __half h = __float2half_rn((float)vh);
-  const __half l = __float2half_rn((float)(v - vh));
-  const __half ll = __float2half_rn((float)(v - vh - (double)__half2float(l)));
   const int off = (n >> 3) * G::kSBO + (k >> 3) * 128 + (n & 7) * 16 + (k & 7) * 2;
-  out[(dir * G::kGDir + off) / 2] = __half_as_ushort(h);
-  out[(dir * G::kGDir + G::kGPiece + off) / 2] = __half_as_ushort(l);
-  out[(dir * G::kGDir + 2 * G::kGPiece + off) / 2] = __half_as_ushort(ll);
+  unsigned short u0, u1, u2;
+  if (bf16) {  // G_h on the 2^-7 grid, G_m and G_l the BF16 remainders
+    const double vh = rint(v * 128.0) / 128.0;
+    const __nv_bfloat16 m = __float2bfloat16_rn((float)(v - vh));
+    const __nv_bfloat16 l = __float2bfloat16_rn((float)(v - vh - (double)__bfloat162float(m)));
+    u0 = __bfloat16_as_ushort(__float2bfloat16_rn((float)vh));
+    u1 = __bfloat16_as_ushort(m);
+    u2 = __bfloat16_as_ushort(l);
+  } else {     // G_h on the 2^-8 grid, G_l and G_ll the FP16 remainders
+    const double vh = rint(v * 256.0) / 256.0;
+    const __half l = __float2half_rn((float)(v - vh));
+    const __half ll = __float2half_rn((float)(v - vh - (double)__half2float(l)));
+    u0 = __half_as_ushort(__float2half_rn((float)vh));
+    u1 = __half_as_ushort(l);
+    u2 = __half_as_ushort(ll);
+  }
+  out[(dir * G::kGDir + off) / 2] = u0;
+  out[(dir * G::kGDir + G::kGPiece + off) / 2] = u1;
+  out[(dir * G::kGDir + 2 * G::kGPiece + off) / 2] = u2;
 }
 
-cudaError_t launch_tc_dftmat(void* out, cudaStream_t st) {
-  k_tc_dftmat<<<8, 256, 0, st>>>(static_cast<unsigned short*>(out));
+cudaError_t launch_tc_dftmat(void* out, bool bf16, cudaStream_t st) {
+  k_tc_dftmat<<<8, 256, 0, st>>>(static_cast<unsigned short*>(out), bf16 ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -11,8 +11,8 @@ cudaError_t launch_twiddles(void* out, int L, int ept, bool r2c, bool f32, cudaS
 // elements per thread of the transposing passes (RowEPT in fft_core.cuh) and of the fused pass
 inline int row_ept(int L) { return L >= 16 ? 16 : 8; }
 inline int push_ept(int, bool tc = false) { return tc ? PushEPT<16, true>::value : PushEPT<16>::value; }
-// split-FP16 radix-16 DFT matrices of both directions, tensor-core operand layout
-cudaError_t launch_tc_dftmat(void* out, cudaStream_t st);
+// split-FP16 (or split-BF16) radix-16 DFT matrices of both directions, tensor-core operand layout
+cudaError_t launch_tc_dftmat(void* out, bool bf16, cudaStream_t st);
 // kp: per-axis order-p wavenumber tables (units of g0, n_i/2+1 entries) of a
 // staggered plan, or NULL for the collocated exact-k plan
 cudaError_t launch_coefs(void* out, bool f32, int e0, int e1, int e2, int nx, int ny, int nz,

@@ -21,12 +21,21 @@
 // nearest) and the row is scaled back by 1/s.  What is dropped (A_l G_ll and
 // the remainders of the splits) is below 2^-24 of the row maximum.
 //
+// Split-BF16 (bf16 = 1; BF16 keeps 8 bits): the head A_h rounds the scaled row
+// to multiples of 128 (8 bits), A_m and A_l are the BF16 roundings of the two
+// remainders (a third A piece, in its own region a_tile3); G_h is on the 2^-7
+// grid, G_m and G_l the BF16 remainders.  The head products are integers below
+// 2^15 (32-term sums exact in FP32); the corrections A_h G_m, A_m G_h, A_h G_l,
+// A_l G_h, A_m G_m go to the second accumulator; what is dropped is below 2^-24
+// of the row maximum.
+//
 // Shared-memory operand layout (K-major, no swizzle): 8-row x 16-byte core
 // matrices, the K-adjacent ones 128 B apart (LBO), the 8-row groups
 // R/4 * 128 B apart (SBO).  One 16-bit K step of an MMA covers two core
 // matrices along K, so the second K step of R = 16 starts 256 B further on.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
 
@@ -36,12 +45,14 @@ namespace psatd {
 constexpr int kErrMmaWait = 1;  // an MMA-completion wait ran out of iterations
 
 struct TcCtx {
-  uint32_t mbar;    // shared address of the MMA-completion mbarrier
-  uint32_t tmem;    // TMEM address of the CTA's accumulators (lane 0, first column)
-  uint32_t a_tile;  // shared address of this CTA's A tiles (group g at + g * tile bytes)
-  uint32_t bmat;    // shared address of the split DFT matrices, forward then adjoint
-  uint32_t phase;   // parity of the next mbarrier phase (identical in every thread)
-  int* err;         // device error word (may be null)
+  uint32_t mbar;     // shared address of the MMA-completion mbarrier
+  uint32_t tmem;     // TMEM address of the CTA's accumulators (lane 0, first column)
+  uint32_t a_tile;   // shared address of this CTA's A tiles (group g at + g * tile bytes)
+  uint32_t a_tile3;  // split-BF16: third A piece (group g at + g * piece bytes)
+  uint32_t bmat;     // shared address of the split DFT matrices, forward then adjoint
+  uint32_t phase;    // parity of the next mbarrier phase (identical in every thread)
+  int* err;          // device error word (may be null)
+  int bf16;          // 0 split-FP16, 1 split-BF16
 };
 
 // Bytes of one split piece (hi or lo) of the A tile of 128 rows / of G.
@@ -54,8 +65,10 @@ template <int RS> struct TcGeom {
   static constexpr int kKSteps = RS / 8;            // MMAs (K = 16) per product
   static constexpr int kCols = 2 * RS;              // columns of one accumulator (N)
   // instruction descriptor: F32 accumulate, F16 A and B, both K-major,
-  // N = 2R (bits 17-22: N >> 3), M = 128 (bits 24-28: M >> 4)
+  // N = 2R (bits 17-22: N >> 3), M = 128 (bits 24-28: M >> 4); BF16 A and B
+  // set the format fields (bits 7-9, 10-12) to 1
   static constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(2 * RS / 8) << 17) | (8u << 24);
+  static constexpr uint32_t kIdescBF16 = kIdesc | (1u << 7) | (1u << 10);
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -152,6 +165,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t h2u(__half2 h) { return *reinterpret_cast<uint32_t*>(&h); }
+__device__ __forceinline__ uint32_t b2u(__nv_bfloat162 h) { return *reinterpret_cast<uint32_t*>(&h); }
 
 // Columns of TMEM per CTA for `nthreads` threads: per group of 128 rows a
 // 32-column head accumulator and a 32-column correction accumulator (a power
@@ -165,7 +179,8 @@ __host__ __device__ constexpr int tc_tmem_cols(int nthreads) {
 // thread's butterfly, on the tensor cores.  Every thread of the CTA calls it
 // (block barriers inside); blockDim.x * blockDim.y is a multiple of 128.  The
 // A tiles alias exchange space that holds no live data at a stage boundary.
-template <int RS, bool ADJ>
+// BF16: split-BF16 operands (else split-FP16).
+template <int RS, bool ADJ, bool BF16>
 __device__ __forceinline__ void tc_dft(float2 (&a)[RS], TcCtx& tc) {
   typedef TcGeom<RS> G;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -180,21 +195,41 @@ __device__ __forceinline__ void tc_dft(float2 (&a)[RS], TcCtx& tc) {
   int k = be ? 141 - be : 0;
   k = k > 126 ? 126 : k;
   const float s = __int_as_float((127 + k) << 23), is = __int_as_float((127 - k) << 23);
-  constexpr float kRound16 = 201326592.0f;  // 1.5 * 2^27: (t + c) - c rounds t to a multiple of 16
+  constexpr float kRound16 = 201326592.0f;    // 1.5 * 2^27: (t + c) - c rounds t to a multiple of 16
+  constexpr float kRound128 = 1610612736.0f;  // 1.5 * 2^30: to a multiple of 128
 
   __syncthreads();  // every exchange read of the previous stage is done
   {
     const uint32_t base = tc.a_tile + grp * G::kATile + (row >> 3) * G::kSBO + (row & 7) * 16;
+    const uint32_t base3 = tc.a_tile3 + grp * G::kAPiece + (row >> 3) * G::kSBO + (row & 7) * 16;
 #pragma unroll
     for (int kc = 0; kc < RS / 4; ++kc) {
-      uint32_t hi[4], lo[4];
+      uint32_t hi[4], lo[4], l3[4];
+      if constexpr (BF16) {
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float tx = a[4 * kc + e].x * s, ty = a[4 * kc + e].y * s;
-        const float hx = __fsub_rn(__fadd_rn(tx, kRound16), kRound16);
-        const float hy = __fsub_rn(__fadd_rn(ty, kRound16), kRound16);
-        hi[e] = h2u(__floats2half2_rn(hx, hy));
-        lo[e] = h2u(__floats2half2_rn(__fsub_rn(tx, hx), __fsub_rn(ty, hy)));
+        for (int e = 0; e < 4; ++e) {
+          const float tx = a[4 * kc + e].x * s, ty = a[4 * kc + e].y * s;
+          const float hx = __fsub_rn(__fadd_rn(tx, kRound128), kRound128);
+          const float hy = __fsub_rn(__fadd_rn(ty, kRound128), kRound128);
+          const float rx = __fsub_rn(tx, hx), ry = __fsub_rn(ty, hy);
+          const __nv_bfloat162 m = __floats2bfloat162_rn(rx, ry);
+          const float2 mf = __bfloat1622float2(m);
+          hi[e] = b2u(__floats2bfloat162_rn(hx, hy));
+          lo[e] = b2u(m);
+          l3[e] = b2u(__floats2bfloat162_rn(__fsub_rn(rx, mf.x), __fsub_rn(ry, mf.y)));
+        }
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(base3 + kc * 128), "r"(l3[0]),
+                     "r"(l3[1]), "r"(l3[2]), "r"(l3[3])
+                     : "memory");
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float tx = a[4 * kc + e].x * s, ty = a[4 * kc + e].y * s;
+          const float hx = __fsub_rn(__fadd_rn(tx, kRound16), kRound16);
+          const float hy = __fsub_rn(__fadd_rn(ty, kRound16), kRound16);
+          hi[e] = h2u(__floats2half2_rn(hx, hy));
+          lo[e] = h2u(__floats2half2_rn(__fsub_rn(tx, hx), __fsub_rn(ty, hy)));
+        }
       }
       asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(base + kc * 128), "r"(hi[0]), "r"(hi[1]),
                    "r"(hi[2]), "r"(hi[3])
@@ -209,19 +244,32 @@ __device__ __forceinline__ void tc_dft(float2 (&a)[RS], TcCtx& tc) {
   if (tid == 0) {
     tc_fence_after();
     const uint32_t g0 = tc.bmat + (ADJ ? G::kGDir : 0);
+    constexpr uint32_t idesc = BF16 ? G::kIdescBF16 : G::kIdesc;
+    // products: p = 0 head -> columns 0..31; the others -> 32..63 (second accumulator)
+    //   FP16: A_h G_l, A_l G_h, A_h G_ll, A_l G_l        (A pieces h, l; G pieces h, l, ll)
+    //   BF16: A_h G_m, A_m G_h, A_h G_l, A_l G_h, A_m G_m (A pieces h, m, l; G pieces h, m, l)
+    constexpr int np = BF16 ? 6 : 5;
 #pragma unroll 1
     for (int gi = 0; gi < ngrp; ++gi) {
       const uint32_t a0 = tc.a_tile + gi * G::kATile;
+      const uint32_t a3 = tc.a_tile3 + gi * G::kAPiece;
       const uint32_t d = tc.tmem + gi * 64;
-      // p = 0: head A_h G_h -> columns 0..31; p = 1..4: A_h G_l, A_l G_h, A_h G_ll, A_l G_l -> 32..63
 #pragma unroll
-      for (int p = 0; p < 5; ++p) {
-        const uint32_t ap = a0 + ((p == 2 || p == 4) ? G::kAPiece : 0);
-        const uint32_t gp = g0 + (p == 1 || p == 4 ? 1 : p == 3 ? 2 : 0) * G::kGPiece;
+      for (int p = 0; p < np; ++p) {
+        int ai, gj;
+        if constexpr (BF16) {
+          ai = p == 2 || p == 5 ? 1 : p == 4 ? 2 : 0;
+          gj = p == 1 || p == 5 ? 1 : p == 3 ? 2 : 0;
+        } else {
+          ai = (p == 2 || p == 4) ? 1 : 0;
+          gj = p == 1 || p == 4 ? 1 : p == 3 ? 2 : 0;
+        }
+        const uint32_t ap = ai == 2 ? a3 : a0 + ai * G::kAPiece;
+        const uint32_t gp = g0 + gj * G::kGPiece;
 #pragma unroll
         for (int ks = 0; ks < G::kKSteps; ++ks)
           tc_mma(d + (p ? 32 : 0), tc_desc(ap + ks * 256, 128, G::kSBO), tc_desc(gp + ks * 256, 128, G::kSBO),
-                 G::kIdesc, (p > 1 || ks > 0) ? 1u : 0u);
+                 idesc, (p > 1 || ks > 0) ? 1u : 0u);
       }
     }
     tc_commit(tc.mbar);
@@ -248,6 +296,7 @@ __device__ __forceinline__ void tc_dft(float2 (&a)[RS], TcCtx& tc) {
   tc_fence_before();
 }
 
+
 // Shared-memory tail of a tensor-core pass kernel (at the start of its dynamic
 // shared memory): the split radix-16 DFT matrices of both directions, the
 // mbarrier and the TMEM address word.
@@ -257,7 +306,7 @@ constexpr int kTcTail = 2 * TcGeom<16>::kGDir + 1024;
 // by the plan, 16-byte aligned) into the tail, allocate the CTA's TMEM
 // columns (warp 0), initialise the mbarrier.  Contains a block barrier.
 __device__ __forceinline__ void tc_setup(TcCtx& tc, unsigned char* tail, const void* gmat, uint32_t a_tile,
-                                         int* err) {
+                                         int* err, int bf16 = 0, uint32_t a_tile3 = 0) {
   const int nthr = blockDim.x * blockDim.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   constexpr int kG = 2 * TcGeom<16>::kGDir;
@@ -276,6 +325,8 @@ __device__ __forceinline__ void tc_setup(TcCtx& tc, unsigned char* tail, const v
   tc.mbar = smem_u32(mb);
   tc.tmem = *reinterpret_cast<volatile uint32_t*>(slot);
   tc.a_tile = a_tile;
+  tc.a_tile3 = a_tile3;
+  tc.bf16 = bf16;
   tc.bmat = smem_u32(tail);
   tc.phase = 0u;
   tc.err = err;

@@ -61,7 +61,7 @@ def _create(lib, desc):
     (lambda d: setattr(d, "c", -1.0), 1),
     (lambda d: setattr(d, "eps0", float("nan")), 1),
     (lambda d: d.d.__setitem__(1, 0.0), 1),
-    (lambda d: setattr(d, "prec", 2), 2),                  # split-BF16: not in this build
+    (lambda d: setattr(d, "prec", 2), 2),                  # split-BF16: 64 threads, no 128-row group
     (lambda d: setattr(d, "prec", 9), 1),
     (lambda d: setattr(d, "src", 7), 1),
     (lambda d: setattr(d, "flags", 4), 1),                 # unknown flag bit

@@ -1,6 +1,7 @@
-"""GPU parity of the mixed-precision PSATD step (PSATD_MIXED_FP16): every
-radix-16 FFT stage is a 16 x 16 DFT-matrix contraction on the tensor cores
-(tcgen05, split-FP16 operands, FP32 accumulation in TMEM), the rest as FP32.
+"""GPU parity of the mixed-precision PSATD steps (PSATD_MIXED_FP16 and
+PSATD_MIXED_BF16): every radix-16 FFT stage is a 16 x 16 DFT-matrix contraction
+on the tensor cores (tcgen05, split-FP16 or split-BF16 operands with an exact
+head, FP32 accumulation in TMEM), the rest as FP32.
 
 Tolerances (relative L2 over all E and c*B components, vs the FP64 oracle on
 the same float32-rounded inputs):
@@ -24,10 +25,10 @@ pytestmark = pytest.mark.gpu
 
 TOL_STEP = 4e-6
 TOL_RUN = 2e-5
-P = "mixed_fp16"
+MIXED = ["mixed_fp16", "mixed_bf16"]
 
 
-def _inputs(shape, layout, src, seed):
+def _inputs(shape, layout, src, seed, P):
     E = mask_layout(synth.random_fields(shape, 3, seed), layout, "E")
     B = mask_layout(synth.random_fields(shape, 3, seed + 1), layout, "B")
     J = mask_layout(synth.random_fields(shape, 3, seed + 2), layout, "J") if src != "none" else None
@@ -49,32 +50,35 @@ CASES_2D = [
 ]
 
 
+@pytest.mark.parametrize("P", MIXED)
 @pytest.mark.parametrize("shape,layout,src", CASES_2D)
-def test_mixed_2d_one_step_matches_oracle(shape, layout, src):
+def test_mixed_2d_one_step_matches_oracle(shape, layout, src, P):
     d, dt = (1.0, 0.7), 0.45
-    E, B, J, r0, r1 = _inputs(shape, layout, src, 4321)
+    E, B, J, r0, r1 = _inputs(shape, layout, src, 4321, P)
     Eg, Bg = psatd_gpu(shape, d, dt, E, B, J, r0, r1, layout=layout, prec=P, src=src)
     Eo, Bo = _oracle(E, B, J, r0, r1, d, dt, src)
     Eo, Bo = mask_layout(Eo, layout, "E"), mask_layout(Bo, layout, "B")
     assert rel_l2_fields(Eg, Bg, Eo, Bo) < TOL_STEP
 
 
+@pytest.mark.parametrize("P", MIXED)
 @pytest.mark.parametrize("shape,src", [((32, 64, 128), "J"), ((32, 64, 128), "rho"), ((32, 64, 256), "none")])
-def test_mixed_3d_one_step_matches_oracle(shape, src):
+def test_mixed_3d_one_step_matches_oracle(shape, src, P):
     d, dt = (1.0, 0.8, 1.2), 0.6
-    E, B, J, r0, r1 = _inputs(shape, "3d6", src, 77)
+    E, B, J, r0, r1 = _inputs(shape, "3d6", src, 77, P)
     Eg, Bg = psatd_gpu(shape, d, dt, E, B, J, r0, r1, layout="3d6", prec=P, src=src)
     Eo, Bo = _oracle(E, B, J, r0, r1, d, dt, src)
     assert rel_l2_fields(Eg, Bg, Eo, Bo) < TOL_STEP
 
 
+@pytest.mark.parametrize("P", MIXED)
 @pytest.mark.parametrize("scale", [1e-30, 1e30])
-def test_mixed_rows_with_zeros_and_extreme_magnitudes(scale):
+def test_mixed_rows_with_zeros_and_extreme_magnitudes(scale, P):
     """Inputs scaled by 1e-30 or 1e30 (the per-row power-of-two scale follows each
     row, so FP16's range does not limit the data) with some rows and one source
     component entirely zero (the row scale falls back to 1): same bound."""
     shape, d, dt = (256, 256), (1.0, 1.0), 0.5
-    E, B, J, _, _ = _inputs(shape, "te", "J", 5)
+    E, B, J, _, _ = _inputs(shape, "te", "J", 5, P)
     B[2][::3, :] = 0.0
     J[1][:, :] = 0.0
     E, B, J = (rounded(a * scale, P) for a in (E, B, J))
@@ -87,7 +91,8 @@ def _sheet_J(shape, d, n, dt, lam):
     return synth.current_sheet(shape, d, (n + 0.5) * dt, lam=lam, a=0.9, w=2.0 * d[0])
 
 
-def test_mixed_config2_full_size_one_step():
+@pytest.mark.parametrize("P", MIXED)
+def test_mixed_config2_full_size_one_step(P):
     """2048^2 TE, dx = lambda/64, c dt = dx/sqrt(2), current-sheet J (the bench's workload)."""
     shape = (2048, 2048)
     d = (1.0 / 64, 1.0 / 64)
@@ -101,7 +106,8 @@ def test_mixed_config2_full_size_one_step():
     assert rel_l2_fields(Eg, Bg, mask_layout(Eo, "te", "E"), mask_layout(Bo, "te", "B")) < TOL_STEP
 
 
-def test_mixed_sheet_long_run_within_2e5():
+@pytest.mark.parametrize("P", MIXED)
+def test_mixed_sheet_long_run_within_2e5(P):
     """Current-sheet drive from zero fields on 512^2 (dx = lambda/64, c dt = dx/sqrt(2)),
     time-varying J one call per step: relative L2 vs the FP64 oracle below 2e-5 at
     100 steps (the batched workload's run length) and at 2000 steps (the FP32 test's)."""
@@ -127,23 +133,25 @@ def test_mixed_sheet_long_run_within_2e5():
             Eg[0], Eg[1], Bg[2] = (t.double().cpu().numpy() for t in (Et[0], Et[1], Bz))
             errs[n + 1] = rel_l2_fields(Eg, Bg, E, B)
     plan.destroy()
-    print("mixed long-run rel L2:", errs)
+    print(P, "long-run rel L2:", errs)
     assert errs[100] < TOL_RUN and errs[2000] < TOL_RUN, errs
 
 
-def test_mixed_config3_full_size_one_step():
+@pytest.mark.parametrize("P", MIXED)
+def test_mixed_config3_full_size_one_step(P):
     """3D 256^3 rho-form, all five passes with tensor-core radix-16 stages."""
     shape = (256, 256, 256)
     d, dt = (1.0, 1.0, 1.0), 0.5
-    E, B, J, r0, r1 = _inputs(shape, "3d6", "rho", 2024)
+    E, B, J, r0, r1 = _inputs(shape, "3d6", "rho", 2024, P)
     Eg, Bg = psatd_gpu(shape, d, dt, E, B, J, r0, r1, layout="3d6", prec=P, src="rho")
     Eo, Bo = _oracle(E, B, J, r0, r1, d, dt, "rho")
     assert rel_l2_fields(Eg, Bg, Eo, Bo) < TOL_STEP
 
 
-def test_mixed_nsteps_equals_repeated_calls_bitwise():
+@pytest.mark.parametrize("P", MIXED)
+def test_mixed_nsteps_equals_repeated_calls_bitwise(P):
     shape, d, dt = (128, 256), (1.0, 1.0), 0.4
-    E, B, J, _, _ = _inputs(shape, "te", "J", 11)
+    E, B, J, _, _ = _inputs(shape, "te", "J", 11, P)
     E1, B1 = psatd_gpu(shape, d, dt, E, B, J, layout="te", prec=P, src="J", nsteps=5)
     E2, B2 = psatd_gpu(shape, d, dt, E, B, J, layout="te", prec=P, src="J", calls=5)
     assert np.array_equal(E1, E2) and np.array_equal(B1, B2)
@@ -151,7 +159,8 @@ def test_mixed_nsteps_equals_repeated_calls_bitwise():
     assert rel_l2_fields(E1, B1, mask_layout(Eo, "te", "E"), mask_layout(Bo, "te", "B")) < TOL_RUN
 
 
-def test_mixed_batch_matches_oracle_per_patch():
+@pytest.mark.parametrize("P", MIXED)
+def test_mixed_batch_matches_oracle_per_patch(P):
     """A batch of uneven patches with tensor-core stages: each patch vs the oracle alone."""
     import torch
     ensure_lib()
@@ -159,7 +168,7 @@ def test_mixed_batch_matches_oracle_per_patch():
     d, dt = (1.0, 1.0), 0.5
     per = []
     for i, (nx, ny) in enumerate(sizes):
-        E, B, J, _, _ = _inputs((ny, nx), "te", "J", 300 + 10 * i)
+        E, B, J, _, _ = _inputs((ny, nx), "te", "J", 300 + 10 * i, P)
         per.append((E, B, J))
     pe, pb, pj = capi.PRESENT["te"]
 
