@@ -463,15 +463,21 @@ def run_side_workload(args):
         plan.destroy()
     elif args.workload == "batch512":
         # 512 local-FFT patches (Sec. II.A.3): interior n ~ U{64..512} per side, guard g ~ U{8..16},
-        # each patch a periodic domain of side next_pow2(n + 2g) (this build's transforms are
-        # power-of-two); TE J-form FP32, smooth random J; the whole run is one psatd_batch_step
-        # call (a CUDA graph of one step replayed `steps` times)
+        # each patch a periodic domain whose side is the smallest transform length >= n + 2g: a power
+        # of two, or (FP32) 3 * 2^k from 96 up; TE J-form, smooth random J; the whole run is one
+        # psatd_batch_step call (a CUDA graph of one step replayed `steps` times)
+        mixed_ok = args.precision == "fp32"
+
+        def fft_side(v):
+            c = [1 << k for k in range(4, 13)] + ([3 << k for k in range(5, 11)] if mixed_ok else [])
+            return min(x for x in c if x >= v)
+
         g = synth.rng(1612)
         sizes, interior = [], 0
         for _ in range(512):
             n = g.integers(64, 513, size=2)
             gg = g.integers(8, 17, size=2)
-            side = [1 << int(math.ceil(math.log2(int(a) + 2 * int(b)))) for a, b in zip(n, gg)]
+            side = [fft_side(int(a) + 2 * int(b)) for a, b in zip(n, gg)]
             sizes.append((side[0], side[1]))
             interior += int(n[0]) * int(n[1])
         dx = 1.0 / LAM_CELLS
@@ -506,8 +512,9 @@ def run_side_workload(args):
             "value": tot * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
             "interior_cell_steps_per_s": interior * args.steps / (ms * 1e-3),
             "dtype": DTYPE[args.precision],
-            "config": {"workload": "512 2D TE FP32 patches, interior U{64..512}^2, guards U{8..16}, periodic domain "
-                                   "next_pow2(n+2g) per side, J-form, one CUDA graph of one step replayed",
+            "config": {"workload": "512 2D TE patches, interior U{64..512}^2, guards U{8..16}, periodic domain "
+                                   "of the smallest transform length >= n+2g per side (%s), J-form, one CUDA "
+                                   "graph of one step replayed" % ("2^k or 3*2^k" if mixed_ok else "2^k"),
                        "precision": PREC_NOTE[args.precision],
                        "cells": tot, "interior_cells": interior, "size_classes": classes,
                        "l2": "inputs %.1f GB >> L2, flushed once before the run" % (tot * 5 * 4 / 1e9)},

@@ -143,8 +143,14 @@ int32_t psatd_abi_version(void);
 
 /* Create a PSATD plan for `desc` on `cuda_stream`.
  * Supported (this build): every n[i] a power of two, 16 <= n[0] <= 4096,
- * 8 <= n[1], n[2] <= 4096; PSATD_FP64, PSATD_FP32, PSATD_MIXED_FP16 or _BF16;
- * flags = 0.  The mixed precisions also need n[0] >= 32, n[1], n[2] >= 16 and
+ * 8 <= n[1], n[2] <= 4096; with PSATD_FP32 also the mixed-radix lengths
+ * n[0] = 6 * 2^k in [96, 3072] (x rows of n[0]/2 = 3 * 2^(k-1) points) and
+ * n[1], n[2] = 3 * 2^k in [48, 3072], on any axis and combined freely with
+ * powers of two (radix-3 first stage); PSATD_FP64, PSATD_FP32,
+ * PSATD_MIXED_FP16 or _BF16; flags from PSATD_FLAG_*.  A last axis of n
+ * points needs (n_in + 1) * n * 8 (FP32) or 16 (FP64) bytes of shared memory
+ * per CTA (UNSUPPORTED beyond the device's opt-in limit).
+ * The mixed precisions also need n[0] >= 32, n[1], n[2] >= 16 and
  * at least 128 threads per CTA in every pass (n[0]/32 * min(32, n[1]) >= 128
  * for the x pass; UNSUPPORTED otherwise).
  * Owns: its spectral scratch (about n_in * (n0/2+1) * n1 * n2 complex values,
@@ -169,8 +175,9 @@ psatd_status psatd_coeffs_init(psatd_plan plan);
  * allocates and frees, keeps the fastest, and caches it for the process:
  *   lines per CTA of each transposing pass (x forward/inverse, y in 3D), and
  *   the fused pass's radix schedule (radix-8 or radix-16 stages, i.e. 8 or 16
- *   elements per thread; radix 16 only for PSATD_MIXED_FP16) with its lines
- *   per CTA.
+ *   elements per thread; radix 16 only for the mixed precisions; 24 and a
+ *   radix-3 first stage, the only schedule, for 3 * 2^k lengths) with its
+ *   lines per CTA.
  * Results do not depend on the choice (same arithmetic, same order per line).
  * `report` (may be NULL) receives a one-line summary of the times, the chosen
  * ones marked '*', truncated to report_len - 1 bytes.  Synchronous.
@@ -182,7 +189,8 @@ psatd_status psatd_plan_autotune(psatd_plan plan, int32_t reps, char* report, si
  *   cfg[0..3] log2(lines per CTA) of the x forward, y forward (3D), y inverse
  *             (3D) and x inverse passes (-1 / unused: 2D y passes);
  *   cfg[4]    lines per CTA of the fused pass;
- *   cfg[5]    its elements per thread: 8 (radix-8 stages) or 16 (radix-16).
+ *   cfg[5]    its elements per thread: 8 (radix-8 stages), 16 (radix-16) or,
+ *             for a last axis of 3 * 2^k points, 24 (radix 3, 2/4, 8).
  * psatd_plan_get_launch reports the shapes the next step will use.
  * psatd_plan_set_launch sets them (-1 entries: the built-in choice) after
  * checking each against the shapes the autotuner would consider

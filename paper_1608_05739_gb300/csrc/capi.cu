@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/psatd.h"
@@ -89,6 +90,8 @@ psatd_status cuda_fail(psatd_plan p, cudaError_t e, const char* what) {
 }
 
 bool pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+// 3 * 2^k with k >= 4: the mixed-radix lengths of the FP32 passes (radix-3 first stage)
+bool three_pow2(int64_t v) { return v >= 48 && v % 3 == 0 && pow2(v / 3); }
 bool pos_finite(double v) { return std::isfinite(v) && v > 0; }
 
 int layout_ndim(int layout) { return layout == PSATD_FIELDS_3D6 ? 3 : 2; }
@@ -142,11 +145,18 @@ psatd_status validate_desc(psatd_plan p, const psatd_desc* d, bool psatd_limits)
   for (int i = 0; i < nd; ++i)
     if (d->n[i] < 2) return fail(p, PSATD_ERR_INVALID_ARG, "n[%d] = %lld too small", i, (long long)d->n[i]);
   if (psatd_limits) {
-    if (!pow2(d->n[0]) || d->n[0] < 16 || d->n[0] > 4096)
-      return fail(p, PSATD_ERR_UNSUPPORTED, "n[0] must be a power of two in [16, 4096]");
-    for (int i = 1; i < nd; ++i)
-      if (!pow2(d->n[i]) || d->n[i] < 8 || d->n[i] > 4096)
-        return fail(p, PSATD_ERR_UNSUPPORTED, "n[%d] must be a power of two in [8, 4096]", i);
+    // x is transformed as a complex line of nx/2 points, y and z as lines of n points:
+    // powers of two, or 3 * 2^k (FP32 only) from 48 to 3072 points per line
+    const bool mixed_ok = d->prec == PSATD_FP32;
+    for (int i = 0; i < nd; ++i) {
+      const int64_t L = i == 0 ? d->n[0] / 2 : d->n[i];
+      const bool ok = (i > 0 || d->n[0] % 2 == 0) &&
+                      ((pow2(L) && L >= 8 && d->n[i] <= 4096) || (mixed_ok && three_pow2(L) && d->n[i] <= 3072));
+      if (!ok) {
+        const char* alt = !mixed_ok ? "" : i == 0 ? " or 6 * 2^k in [96, 3072]" : " or 3 * 2^k in [48, 3072]";
+        return fail(p, PSATD_ERR_UNSUPPORTED, "n[%d] must be a power of two in [%d, 4096]%s", i, i == 0 ? 16 : 8, alt);
+      }
+    }
   } else {
     for (int i = 0; i < nd; ++i)
       if (d->n[i] > (1LL << 20)) return fail(p, PSATD_ERR_UNSUPPORTED, "n[%d] too large", i);
@@ -224,17 +234,19 @@ psatd_status alloc(psatd_plan p, void** ptr, size_t bytes, const char* what) {
   return PSATD_OK;
 }
 
-// lines per CTA for a transposing pass of length L with `nb` lines available
-// (at most 16 lines: the row-dependent XOR of the transposed store spreads 16
-// lines over the banks, 32 would read one bank twice; the tensor-core variant
-// goes to 32 where it needs that for 128 threads)
+// threads per CTA a transposing pass may launch (the kernels' launch bounds)
+int row_maxthr(int L, bool f32) { return row_ept(L) == 24 || !f32 ? 256 : 512; }
+// lines per CTA for a transposing pass of length L over `nb` lines (a divisor
+// of nb; at most 16 lines: the row-dependent XOR of the transposed store
+// spreads 16 lines over the banks, 32 would read one bank twice; the
+// tensor-core variant goes to 32 where it needs that for 128 threads)
 int pick_log_tb(int L, int64_t nb, bool f32, bool tc = false) {
   const int T = L / row_ept(L);
-  const int maxthr = f32 ? 512 : 256;
+  const int maxthr = row_maxthr(L, f32);
   int tb = 1;
-  while (tb * 2 * T <= maxthr && tb * 2 <= 16 && tb * 2 <= nb) tb *= 2;
+  while (tb * 2 * T <= maxthr && tb * 2 <= 16 && nb % (tb * 2) == 0) tb *= 2;
   if (tc)
-    while (tb * T < 128 && tb * 2 * T <= maxthr && tb * 2 <= 32 && tb * 2 <= nb) tb *= 2;
+    while (tb * T < 128 && tb * 2 * T <= maxthr && tb * 2 <= 32 && nb % (tb * 2) == 0) tb *= 2;
   int lg = 0;
   while ((1 << lg) < tb) ++lg;
   return lg;
@@ -301,6 +313,25 @@ struct TimedLaunch {
   }
 };
 
+// Pass launchers by line length: powers of two, or the mixed lengths 3 * 2^k
+// (float, no tensor-core stages; the size checks admit nothing else).
+template <typename R, int TC>
+cudaError_t fwd_T_any(int L, bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io, const void* tw,
+                      int64_t in_sa0, int64_t in_sb, int64_t out_sa0, int64_t out_sk, const int64_t* a0_off = nullptr) {
+  if (pow2(L)) return launch_fwd_T<R, TC>(L, r2c, g, st, io, tw, in_sa0, in_sb, out_sa0, out_sk, a0_off);
+  if constexpr (std::is_same<R, float>::value && TC == 0)
+    return launch_fwd_T3<R>(L, r2c, g, st, io, tw, in_sa0, in_sb, out_sa0, out_sk, a0_off);
+  return cudaErrorInvalidValue;
+}
+template <typename R, int TC>
+cudaError_t inv_T_any(int L, bool c2r, const PassGeom& g, cudaStream_t st, const LineIO& io, const void* tw,
+                      int64_t in_sa0, int64_t in_sk, int64_t out_sa0, int64_t out_sb, const int64_t* a0_off = nullptr) {
+  if (pow2(L)) return launch_inv_T<R, TC>(L, c2r, g, st, io, tw, in_sa0, in_sk, out_sa0, out_sb, a0_off);
+  if constexpr (std::is_same<R, float>::value && TC == 0)
+    return launch_inv_T3<R>(L, c2r, g, st, io, tw, in_sa0, in_sk, out_sa0, out_sb, a0_off);
+  return cudaErrorInvalidValue;
+}
+
 template <typename R, int TC>
 psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp]) {
   typedef typename Types<R>::C C;
@@ -330,7 +361,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
       io.out[c] = s1 + c * cs;
     }
     TimedLaunch tl(p, K_FWD_X);
-    e = launch_fwd_T<R, TC>(Lx, true, g, p->st, io, p->tw[0], d3 ? ny * nx : 0, nx, d3 ? ny : nxh * ny, nz * ny,
+    e = fwd_T_any<R, TC>(Lx, true, g, p->st, io, p->tw[0], d3 ? ny * nx : 0, nx, d3 ? ny : nxh * ny, nz * ny,
                         d3 ? nullptr : p->d_off);
     if (e != cudaSuccess) return cuda_fail(p, e, "fwd_x_r2c launch");
   }
@@ -349,7 +380,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
       io.out[c] = s2 + c * cs;
     }
     TimedLaunch tl(p, K_FWD_Y);
-    e = launch_fwd_T<R, TC>((int)ny, false, g, p->st, io, p->tw[1], nz * ny, ny, ny * nz, nz);
+    e = fwd_T_any<R, TC>((int)ny, false, g, p->st, io, p->tw[1], nz * ny, ny, ny * nz, nz);
     if (e != cudaSuccess) return cuda_fail(p, e, "fwd_y_c2c launch");
     sp = s2;
     Lline = (int)nz;
@@ -400,7 +431,12 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
       const size_t a3 = tb > 1 ? tc_a3_bytes(p, tb * (Lline / p->push_ept)) : 0;  // one line: in its slot
       const dim3 grid((unsigned)((nlines + tb - 1) / tb));
       TimedLaunch tl(p, K_PUSH);
-      if (p->push_ept == 16) {
+      if (p->push_ept == 24) {
+        if constexpr (std::is_same<R, float>::value && TC == 0)
+          e = launch_line_push3<R>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl);
+        else
+          e = cudaErrorInvalidValue;
+      } else if (p->push_ept == 16) {
         e = launch_line_push<R, TC, 16>(Lline, p->layout, grid, tb, tail + tb * per_line + a3, p->st, a, twl);
       } else {
         if constexpr (TC) e = cudaErrorInvalidValue;
@@ -421,7 +457,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
       io.out[c] = s1 + c * cs;
     }
     TimedLaunch tl(p, K_INV_Y);
-    e = launch_inv_T<R, TC>((int)ny, false, g, p->st, io, p->tw[1], ny * nz, nz, nz * ny, ny);
+    e = inv_T_any<R, TC>((int)ny, false, g, p->st, io, p->tw[1], ny * nz, nz, nz * ny, ny);
     if (e != cudaSuccess) return cuda_fail(p, e, "inv_y_c2c launch");
   }
   // last pass: inverse x rows (C2R): spec1 -> out [z][y][x] (3D) / packed patches (2D)
@@ -435,7 +471,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
       io.out[c] = out[c];
     }
     TimedLaunch tl(p, K_INV_X);
-    e = launch_inv_T<R, TC>(Lx, true, g, p->st, io, p->tw[0], d3 ? ny : nxh * ny, nz * ny, d3 ? ny * nx : 0, nx,
+    e = inv_T_any<R, TC>(Lx, true, g, p->st, io, p->tw[0], d3 ? ny : nxh * ny, nz * ny, d3 ? ny * nx : 0, nx,
                         d3 ? nullptr : p->d_off);
     if (e != cudaSuccess) return cuda_fail(p, e, "inv_x_c2r launch");
   }
@@ -532,7 +568,6 @@ TuneSpace tune_space(psatd_plan p) {
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
   const size_t csz = p->f32 ? 8 : 16;
   const size_t tail = p->tc ? (size_t)kTcTail : 0;
-  const int maxthr = p->f32 ? 512 : 256;
   const int Lx = (int)(p->nx / 2);
   ts.Ll = (int)(p->ndim == 3 ? p->nz : p->ny);
   const int64_t nlines = p->ndim == 3 ? p->nxh * p->ny : p->nxh * p->npatch;
@@ -544,15 +579,16 @@ TuneSpace tune_space(psatd_plan p) {
     ts.rowL[k] = rowL[k];
     if (!rowOn[k]) continue;
     const int T = rowL[k] / row_ept(rowL[k]);
-    for (int lg = 0; (1 << lg) <= 32 && (1 << lg) <= rowNb[k] && (T << lg) <= maxthr; ++lg) {
+    const int maxthr = row_maxthr(rowL[k], p->f32);
+    for (int lg = 0; (1 << lg) <= 32 && rowNb[k] % (1 << lg) == 0 && (T << lg) <= maxthr; ++lg) {
       if (p->tc && (T << lg) < 128) continue;
       if (maxsm > 0 && tail + tpass_smem(rowL[k], lg, rowNk[k], csz) + tc_a3_bytes(p, T << lg) > (size_t)maxsm)
         continue;
       ts.rows[k].push_back(lg);
     }
   }
-  for (int ept : {8, 16}) {
-    if ((p->tc && ept != 16) || ts.Ll < ept) continue;
+  for (int ept : {8, 16, 24}) {
+    if ((p->tc && ept != 16) || ts.Ll < ept || (ept == 24) == pow2(ts.Ll)) continue;
     const int T = ts.Ll / ept;
     const size_t per_line = ((size_t)p->n_in + 1) * (size_t)ts.Ll * csz;
     for (int tb = 1; tb * T <= (T > 256 ? T : 256); tb *= 2) {
@@ -723,7 +759,7 @@ static psatd_status plan_create_n(const psatd_desc* desc, void* cuda_stream, int
   p->f32 = desc->prec != PSATD_FP64;
   p->tc = desc->prec == PSATD_MIXED_FP16 || desc->prec == PSATD_MIXED_BF16;
   p->tc_bf16 = desc->prec == PSATD_MIXED_BF16;
-  p->push_ept = p->tc ? 16 : 8;
+  p->push_ept = push_ept((int)(desc->ndim == 3 ? desc->n[2] : desc->n[1]), p->tc);
   p->order = desc->order;
   p->ndim = desc->ndim;
   p->layout = desc->layout;
@@ -880,7 +916,7 @@ psatd_status psatd_plan_set_launch(psatd_plan p, const int32_t cfg[6]) {
   if (!p || !cfg) return fail(p, PSATD_ERR_INVALID_ARG, "plan or cfg is NULL");
   if (!p->coeffs_ready) return fail(p, PSATD_ERR_INVALID_ARG, "psatd_coeffs_init was not called");
   TuneSpace ts = tune_space(p);
-  TuneCfg c{{-1, -1, -1, -1}, -1, p->tc ? 16 : 8};
+  TuneCfg c{{-1, -1, -1, -1}, -1, push_ept((int)(p->ndim == 3 ? p->nz : p->ny), p->tc)};
   for (int k = 0; k < 4; ++k) {
     if (cfg[k] < 0) continue;
     if (cfg[k] > 30 || std::find(ts.rows[k].begin(), ts.rows[k].end(), cfg[k]) == ts.rows[k].end())
@@ -888,7 +924,8 @@ psatd_status psatd_plan_set_launch(psatd_plan p, const int32_t cfg[6]) {
     c.log_tb[k] = cfg[k];
   }
   if (cfg[5] >= 0) {
-    if (cfg[5] != 8 && cfg[5] != 16) return fail(p, PSATD_ERR_INVALID_ARG, "cfg[5] must be 8, 16 or -1");
+    if (cfg[5] != 8 && cfg[5] != 16 && cfg[5] != 24)
+      return fail(p, PSATD_ERR_INVALID_ARG, "cfg[5] must be 8, 16, 24 or -1");
     c.push_ept = cfg[5];
   }
   bool ok = false;
@@ -1079,6 +1116,7 @@ extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_f
   p.nz = p.ndim == 3 ? desc->n[2] : 1;
   p.nxh = p.nx / 2 + 1;
   p.cs = p.nxh * p.ny * p.nz;
+  p.push_ept = push_ept((int)(p.ndim == 3 ? p.nz : p.ny));
   const size_t csz = p.f32 ? 8 : 16;
   const int64_t ns[3] = {p.nx, p.ny, p.nz};
   p.tab_e[0] = p.nx / 2 + 1;
@@ -1156,7 +1194,7 @@ extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_f
   for (int i = 0; i < p.ndim; ++i) {
     const int L = i == 0 ? (int)(ns[0] / 2) : (int)ns[i];
     const bool push_axis = (i == p.ndim - 1) && i > 0;
-    e = launch_twiddles(p.tw[i], L, push_axis ? push_ept(L) : row_ept(L), i == 0, p.f32, p.st);
+    e = launch_twiddles(p.tw[i], L, push_axis ? p.push_ept : row_ept(L), i == 0, p.f32, p.st);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "twiddle table launch");
   }
   const double N = (double)p.nx * (double)p.ny * (double)p.nz;

@@ -220,9 +220,33 @@ __device__ __forceinline__ void dft16_adj(C* a) {
   for (int i = 0; i < 16; ++i) a[i] = x[i];
 }
 
+// v * sqrt(3)/2; in float as hi + lo
+constexpr double kHalfSqrt3 = 0.86602540378443864676;
+__device__ __forceinline__ float r3_mul(float v) {
+  constexpr float h = (float)kHalfSqrt3, l = (float)(kHalfSqrt3 - (double)(float)kHalfSqrt3);
+  return fmaf(v, h, v * l);
+}
+__device__ __forceinline__ double r3_mul(double v) { return v * kHalfSqrt3; }
+
+// Radix-3 DFT in place (forward: exp(-2 pi i/3) = -1/2 - i sqrt3/2; adjoint:
+// the conjugate constant): X0 = a0 + (a1 + a2), X1,2 = a0 - (a1 + a2)/2 -+ i
+// sqrt3/2 (a1 - a2) (forward), +- (adjoint).
+template <bool ADJ, class C>
+__device__ __forceinline__ void dft3(C& a0, C& a1, C& a2) {
+  const C t = cadd(a1, a2), d = csub(a1, a2);
+  const C m = mkc(a0.x - 0.5f * t.x, a0.y - 0.5f * t.y);
+  const C sd = mkc(r3_mul(d.x), r3_mul(d.y));
+  const C s = ADJ ? cmul_pi(sd) : cmul_mi(sd);
+  a0 = cadd(a0, t);
+  a1 = cadd(m, s);
+  a2 = csub(m, s);
+}
+
 template <int RS, bool ADJ, class C>
 __device__ __forceinline__ void butterfly(C* a) {
-  if constexpr (RS == 2) {
+  if constexpr (RS == 3) {
+    dft3<ADJ>(a[0], a[1], a[2]);
+  } else if constexpr (RS == 2) {
     C s = cadd(a[0], a[1]), d = csub(a[0], a[1]);
     a[0] = s;
     a[1] = d;
@@ -240,26 +264,37 @@ __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v
 
 // Elements per thread of the transposing row/line passes (16 from L = 16 on)
 // and of the fused last-axis pass (8).
+__host__ __device__ constexpr bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Lengths 3 * 2^k (k >= 4) are mixed-radix: 24 elements per thread in every pass.
 template <int L>
-struct RowEPT { static constexpr int value = L >= 16 ? 16 : 8; };
+struct RowEPT { static constexpr int value = !is_pow2(L) ? 24 : L >= 16 ? 16 : 8; };
 // The fused pass keeps 8 elements per thread: with 16 a 2048-point line has
 // half the threads and, its shared memory being fixed per line, the SM half
 // the warps (measured slower).  The tensor-core variant (TC) takes 16, so that
 // its stages are radix-16 DFT-matrix contractions.
 template <int L, int TC = 0>
-struct PushEPT { static constexpr int value = TC ? 16 : 8; };
+struct PushEPT { static constexpr int value = !is_pow2(L) ? 24 : TC ? 16 : 8; };
 
+// Power-of-two L: a radix-2/4/8 first stage when log2 L is not a multiple of
+// log2 EPT, then radix-EPT stages.  Mixed L = 3 * 2^k (EPT = 24): a radix-3
+// first stage, a radix-2 or radix-4 stage when k is not a multiple of 3, then
+// radix-8 stages; every radix divides 24.
 template <int L, int EPT = 8>
 struct FFTPlan {
   static constexpr int kEPT = EPT;
-  static constexpr int kLog = ilog2(L);
-  static constexpr int kB = ilog2(EPT);
+  static constexpr bool kMixed = !is_pow2(L);
+  static constexpr int kLog = kMixed ? ilog2(L / 3) : ilog2(L);  // log2 of the power-of-two part
+  static constexpr int kB = kMixed ? 3 : ilog2(EPT);
   static constexpr int kRem = kLog % kB;
-  static constexpr int kR0 = kRem ? (1 << kRem) : EPT;
-  static constexpr int kStages = kRem ? kLog / kB + 1 : kLog / kB;
+  static constexpr int kR0 = kMixed ? 3 : kRem ? (1 << kRem) : EPT;
+  static constexpr int kStages = kMixed ? 1 + (kRem ? 1 : 0) + kLog / 3 : kRem ? kLog / kB + 1 : kLog / kB;
   static constexpr int kT = L / EPT;
   static constexpr int kBuf = L;  // exchange buffer (XOR-swizzled, no padding)
-  __host__ __device__ static constexpr int radix(int s) { return s == 0 ? kR0 : EPT; }
+  __host__ __device__ static constexpr int radix(int s) {
+    if (kMixed) return s == 0 ? 3 : (s == 1 && kRem) ? (1 << kRem) : 8;
+    return s == 0 ? kR0 : EPT;
+  }
   __host__ __device__ static constexpr int span(int s) {  // Ns of stage s
     int ns = 1;
     for (int i = 0; i < s; ++i) ns *= radix(i);
@@ -275,11 +310,14 @@ struct FFTPlan {
   static constexpr int kTwEntries = L - kR0;
   // XOR multiplier of the exchange written by stage s (bank-conflict free for
   // the Stockham write pattern of that stage and the contiguous reads after it)
-  __host__ __device__ static constexpr int swz(int s) { return EPT == 16 ? 1 : (span(s) == 1 ? 1 : 10); }
+  __host__ __device__ static constexpr int swz(int s) {
+    return (kMixed || EPT == 16) ? 1 : (span(s) == 1 ? 1 : 10);
+  }
   // swizzle of the last exchange: forward output / inverse input positions
   // sw<kLastCX>(t + T m) are each touched by their own thread only
   static constexpr int kLastCX = (kStages >= 2) ? swz(kStages - 2) : 0;
-  static_assert(L >= EPT && (L & (L - 1)) == 0, "L must be a power of two >= EPT");
+  static_assert(kMixed ? (L == 3 * (1 << kLog) && EPT == 24 && kLog >= 4) : (L >= EPT && EPT != 24),
+                "L must be a power of two >= EPT, or 3 * 2^k (k >= 4) with EPT = 24");
 };
 
 // element i of an exchange buffer, rows of 16 elements (128 B) XOR-swizzled
@@ -333,7 +371,7 @@ __device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[EPT], ExBuf<
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int j = t + q * T;
-    const int k = j & (NS - 1);
+    const int k = is_pow2(NS) ? (j & (NS - 1)) : (int)((unsigned)j % (unsigned)NS);
     C a[RS];
 #pragma unroll
     for (int r = 0; r < RS; ++r) a[r] = v[q + r * Q];
@@ -380,7 +418,7 @@ __device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[EPT], ExBuf<
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int j = t + q * T;
-    const int k = j & (NS - 1);
+    const int k = is_pow2(NS) ? (j & (NS - 1)) : (int)((unsigned)j % (unsigned)NS);
     C a[RS];
     if constexpr (FIRST) {
 #pragma unroll

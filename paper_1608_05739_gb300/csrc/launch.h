@@ -32,6 +32,19 @@ template <typename R, int TC, int EPT>
 cudaError_t launch_line_push(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
                              const PushArgs<R>& a, const void* tw);
 
+// the same passes for the mixed lengths L = 3 * 2^k (48..3072; R2C / C2R up to 1536), float only
+template <typename R>
+cudaError_t launch_fwd_T3(int L, bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io, const void* tw,
+                          int64_t in_sa0, int64_t in_sb, int64_t out_sa0, int64_t out_sk,
+                          const int64_t* a0_off = nullptr);
+template <typename R>
+cudaError_t launch_inv_T3(int L, bool c2r, const PassGeom& g, cudaStream_t st, const LineIO& io, const void* tw,
+                          int64_t in_sa0, int64_t in_sk, int64_t out_sa0, int64_t out_sb,
+                          const int64_t* a0_off = nullptr);
+template <typename R>
+cudaError_t launch_line_push3(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
+                              const PushArgs<R>& a, const void* tw);
+
 template <typename R>
 cudaError_t launch_fdtd(int ndim, int scheme, int64_t nx, int64_t ny, int64_t nz, const double* d,
                         double dt, double c, double eps0, void* const E[3], void* const B[3],

@@ -105,6 +105,44 @@ static cudaError_t push_L(int layout, dim3 grid, int tb, size_t smem, cudaStream
     default: return cudaErrorInvalidValue;                        \
   }
 
+// Mixed lengths 3 * 2^k (FP32, no tensor-core stages).
+#define PSATD_L3_SWITCH(FN, ...)                         \
+  switch (L) {                                           \
+    case 48: return FN<R, 0, 48>(__VA_ARGS__);           \
+    case 96: return FN<R, 0, 96>(__VA_ARGS__);           \
+    case 192: return FN<R, 0, 192>(__VA_ARGS__);         \
+    case 384: return FN<R, 0, 384>(__VA_ARGS__);         \
+    case 768: return FN<R, 0, 768>(__VA_ARGS__);         \
+    case 1536: return FN<R, 0, 1536>(__VA_ARGS__);       \
+    case 3072: return FN<R, 0, 3072>(__VA_ARGS__);       \
+    default: return cudaErrorInvalidValue;               \
+  }
+
+template <typename R>
+cudaError_t launch_fwd_T3(int L, bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io, const void* tw,
+                          int64_t in_sa0, int64_t in_sb, int64_t out_sa0, int64_t out_sk, const int64_t* a0_off) {
+  PSATD_L3_SWITCH(fwd_T_L, r2c, g, st, io, tw, in_sa0, in_sb, out_sa0, out_sk, a0_off)
+}
+template <typename R>
+cudaError_t launch_inv_T3(int L, bool c2r, const PassGeom& g, cudaStream_t st, const LineIO& io, const void* tw,
+                          int64_t in_sa0, int64_t in_sk, int64_t out_sa0, int64_t out_sb, const int64_t* a0_off) {
+  PSATD_L3_SWITCH(inv_T_L, c2r, g, st, io, tw, in_sa0, in_sk, out_sa0, out_sb, a0_off)
+}
+template <typename R>
+cudaError_t launch_line_push3(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
+                              const PushArgs<R>& a, const void* tw) {
+  switch (L) {
+    case 48: return push_L<R, 0, 24, 48>(layout, grid, tb, smem, st, a, tw);
+    case 96: return push_L<R, 0, 24, 96>(layout, grid, tb, smem, st, a, tw);
+    case 192: return push_L<R, 0, 24, 192>(layout, grid, tb, smem, st, a, tw);
+    case 384: return push_L<R, 0, 24, 384>(layout, grid, tb, smem, st, a, tw);
+    case 768: return push_L<R, 0, 24, 768>(layout, grid, tb, smem, st, a, tw);
+    case 1536: return push_L<R, 0, 24, 1536>(layout, grid, tb, smem, st, a, tw);
+    case 3072: return push_L<R, 0, 24, 3072>(layout, grid, tb, smem, st, a, tw);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename R, int TC>
 cudaError_t launch_fwd_T(int L, bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io,
                          const void* tw, int64_t in_sa0, int64_t in_sb, int64_t out_sa0,

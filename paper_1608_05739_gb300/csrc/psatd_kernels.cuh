@@ -65,6 +65,11 @@ struct PushArgs {
   const void* ph[3];    // per axis, exp(-i pi m/n) for m = 0..n/2 (twiddle type)
 };
 
+// Threads per CTA a transposing pass of length L may use (the register budget
+// of 24 elements per thread halves it for the mixed lengths).
+template <typename R, int L>
+struct RowThreads { static constexpr int value = RowEPT<L>::value == 24 ? 256 : sizeof(R) == 4 ? 512 : 256; };
+
 // ---------------------------------------------------------------- pass 1 / 2
 // Forward FFT along the contiguous axis of TB consecutive lines b, written out
 // with b contiguous: out[a1] + a0*out_sa0 + k*out_sk + b.  R2C: the input rows
@@ -73,7 +78,7 @@ struct PushArgs {
 // dynamic shared memory then starts with the kTcTail block and the A tiles
 // alias the line buffers.
 template <typename R, int L, bool R2C, int TC = 0>
-__global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
+__global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_fwd_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
                                                int64_t in_sa0, int64_t in_sb, int64_t out_sa0,
                                                int64_t out_sk, int log_tb, const int64_t* __restrict__ in_off) {
   typedef typename Types<R>::C C;
@@ -138,7 +143,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO 
       for (int j = 0; j < 4; ++j) {
         const int k = k0 + (j0 + j) * T;
         const C zk = zr[k ^ xgg];
-        const C zm = cconj(zr[((L - k) & (L - 1)) ^ xgg]);
+        const C zm = cconj(zr[(is_pow2(L) ? ((L - k) & (L - 1)) : (k == 0 ? 0 : L - k)) ^ xgg]);
         const C fe = mkc(R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y + zm.y));
         const C fo = mkc(R(0.5) * (zk.y - zm.y), R(-0.5) * (zk.x - zm.x));
         o[(j0 + j) * ostep] = cadd(fe, twmul(fo, w[j]));
@@ -174,7 +179,7 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_fwd_T(LineIO 
 // contiguously to out[a1] + a0*out_sa0 + b*out_sb.  C2R: L+1 Hermitian bins
 // in, real rows of length 2L out (unnormalised).
 template <typename R, int L, bool C2R, int TC = 0>
-__global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256, 2) k_inv_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
+__global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_inv_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
                                                int64_t in_sa0, int64_t in_sk, int64_t out_sa0,
                                                int64_t out_sb, int log_tb, const int64_t* __restrict__ out_off) {
   typedef typename Types<R>::C C;

@@ -3,8 +3,8 @@
 // the field state every step).
 //
 // Twiddles of a length-L transform with EPT elements per thread, in the order
-// the FFT stages read them (fft_core.cuh): for each stage s >= 1 (radix EPT,
-// span Ns), entry (r-1) Ns + k holds W_L^(r k L/(EPT Ns)); an R2C/C2R axis
+// the FFT stages read them (fft_core.cuh): for each stage s >= 1 (radix R_s,
+// span Ns), entry (r-1) Ns + k holds W_L^(r k L/(R_s Ns)); an R2C/C2R axis
 // (N = 2L real points) appends W_N^k, k < L, for the even/odd split.
 //
 // Coefficient octant: one entry per (|mx|, |my|, |mz|), |m_i| <= n_i/2, with
@@ -26,30 +26,48 @@
 
 namespace psatd {
 
-__global__ void k_twiddles(void* out, int L, int ept, int r2c, int f32) {
-  int lg = 0, b = 0;
-  while ((1 << lg) < L) ++lg;
-  while ((1 << b) < ept) ++b;
-  const int rem = lg % b;
-  const int r0 = rem ? (1 << rem) : ept;
-  const int nstage = L - r0;
+// Stage radices of a length-L transform with ept elements per thread, in stage
+// order (the rules of FFTPlan in fft_core.cuh).
+struct Radices {
+  int n;
+  int r[16];
+};
+static Radices plan_radices(int L, int ept) {
+  Radices R{};
+  auto lg = [](int v) { int k = 0; while ((1 << k) < v) ++k; return k; };
+  if (L & (L - 1)) {  // 3 * 2^k
+    const int k = lg(L / 3), rem = k % 3;
+    R.r[R.n++] = 3;
+    if (rem) R.r[R.n++] = 1 << rem;
+    for (int i = 0; i < k / 3; ++i) R.r[R.n++] = 8;
+  } else {
+    const int k = lg(L), b = lg(ept), rem = k % b;
+    R.r[R.n++] = rem ? (1 << rem) : ept;
+    for (int i = 0; i < k / b - (rem ? 0 : 1); ++i) R.r[R.n++] = ept;
+  }
+  return R;
+}
+
+__global__ void k_twiddles(void* out, int L, Radices rad, int r2c, int f32) {
+  const int nstage = L - rad.r[0];
   const int total = nstage + (r2c ? L : 0);
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= total) return;
   double num, den;  // W = exp(-2 pi i num/den)
   if (e < nstage) {
-    int off = 0, ns = r0;
+    int off = 0, ns = rad.r[0];
     num = 0.0;
     den = (double)L;
-    while (true) {
-      const int size = (ept - 1) * ns;
+    for (int st = 1; st < rad.n; ++st) {
+      const int R = rad.r[st];
+      const int size = (R - 1) * ns;
       if (e < off + size) {
         const int r = (e - off) / ns + 1, k = (e - off) % ns;
-        num = (double)((long long)r * k * (L / (ept * ns)));
+        num = (double)((long long)r * k * (L / (R * ns)));
         break;
       }
       off += size;
-      ns *= ept;
+      ns *= R;
     }
   } else {
     num = (double)(e - nstage);
@@ -220,7 +238,7 @@ cudaError_t launch_tc_dftmat(void* out, bool bf16, cudaStream_t st) {
 
 cudaError_t launch_twiddles(void* out, int L, int ept, bool r2c, bool f32, cudaStream_t st) {
   const int total = 2 * L;
-  k_twiddles<<<(total + 255) / 256, 256, 0, st>>>(out, L, ept, r2c ? 1 : 0, f32 ? 1 : 0);
+  k_twiddles<<<(total + 255) / 256, 256, 0, st>>>(out, L, plan_radices(L, ept), r2c ? 1 : 0, f32 ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -132,6 +132,20 @@ def test_mixed_fp16_shape_limits(lib, n, why):
     assert why in lib.psatd_last_error(None)
 
 
+@pytest.mark.parametrize("n,prec", [
+    ((96, 64), "fp64"), ((64, 48), "mixed_fp16"), ((96, 96), "mixed_bf16"),   # 3 * 2^k lengths: FP32 only
+    ((6144, 64), "fp32"),                    # x rows of 3072 points: the R2C pass stops at 1536
+    ((64, 6144), "fp32"), ((64, 24), "fp32"), ((72, 64), "fp32"), ((64, 80), "fp32"),
+])
+def test_mixed_radix_length_limits(lib, n, prec):
+    """Lines of 3 * 2^k points (48 to 3072; x rows are nx/2 points) are FP32-only;
+    other lengths and other precisions are refused before any allocation."""
+    d = capi.make_desc(n, (1.0, 1.0), 0.5, layout="te", prec=prec, src="J")
+    st, h = _create(lib, d)
+    assert st == 2 and h.value is None
+    assert b"power of two" in lib.psatd_last_error(None)
+
+
 def test_mixed_fp16_only_for_the_psatd_step(lib):
     d = capi.make_desc((64, 64), (1.0, 1.0), 0.5, layout="te", prec="mixed_fp16", src="J")
     f = capi.psatd_fields()

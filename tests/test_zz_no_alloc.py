@@ -31,7 +31,8 @@ def _np(ts):
     return np.stack([t.double().cpu().numpy() if t is not None else np.zeros(1) for t in ts if t is not None])
 
 
-@pytest.mark.parametrize("prec,layout,shape", [("fp32", "te", (256, 256)), ("fp64", "2d6", (64, 128))])
+@pytest.mark.parametrize("prec,layout,shape", [("fp32", "te", (256, 256)), ("fp64", "2d6", (64, 128)),
+                                               ("fp32", "te", (192, 96))])
 def test_noalloc_matches_plan_step_on_two_calls(prec, layout, shape):
     import torch
     ensure_lib()
