@@ -175,9 +175,9 @@ psatd_status psatd_coeffs_init(psatd_plan plan);
  * allocates and frees, keeps the fastest, and caches it for the process:
  *   lines per CTA of each transposing pass (x forward/inverse, y in 3D), and
  *   the fused pass's radix schedule (radix-8 or radix-16 stages, i.e. 8 or 16
- *   elements per thread; radix 16 only for the mixed precisions; 24 and a
- *   radix-3 first stage, the only schedule, for 3 * 2^k lengths) with its
- *   lines per CTA.
+ *   elements per thread; radix 16 only for the mixed precisions; for 3 * 2^k
+ *   lengths only 12 elements per thread: a radix-12 first stage, then radix
+ *   2 and 4) with its lines per CTA.
  * Results do not depend on the choice (same arithmetic, same order per line).
  * `report` (may be NULL) receives a one-line summary of the times, the chosen
  * ones marked '*', truncated to report_len - 1 bytes.  Synchronous.
@@ -190,7 +190,7 @@ psatd_status psatd_plan_autotune(psatd_plan plan, int32_t reps, char* report, si
  *             (3D) and x inverse passes (-1 / unused: 2D y passes);
  *   cfg[4]    lines per CTA of the fused pass;
  *   cfg[5]    its elements per thread: 8 (radix-8 stages), 16 (radix-16) or,
- *             for a last axis of 3 * 2^k points, 24 (radix 3, 2/4, 8).
+ *             for a last axis of 3 * 2^k points, 12 (radix 12, then 2/4).
  * psatd_plan_get_launch reports the shapes the next step will use.
  * psatd_plan_set_launch sets them (-1 entries: the built-in choice) after
  * checking each against the shapes the autotuner would consider

@@ -431,7 +431,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
       const size_t a3 = tb > 1 ? tc_a3_bytes(p, tb * (Lline / p->push_ept)) : 0;  // one line: in its slot
       const dim3 grid((unsigned)((nlines + tb - 1) / tb));
       TimedLaunch tl(p, K_PUSH);
-      if (p->push_ept == 24) {
+      if (p->push_ept == 12) {
         if constexpr (std::is_same<R, float>::value && TC == 0)
           e = launch_line_push3<R>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl);
         else
@@ -587,8 +587,8 @@ TuneSpace tune_space(psatd_plan p) {
       ts.rows[k].push_back(lg);
     }
   }
-  for (int ept : {8, 16, 24}) {
-    if ((p->tc && ept != 16) || ts.Ll < ept || (ept == 24) == pow2(ts.Ll)) continue;
+  for (int ept : {8, 16, 12}) {
+    if ((p->tc && ept != 16) || ts.Ll < ept || (ept == 12) == pow2(ts.Ll)) continue;
     const int T = ts.Ll / ept;
     const size_t per_line = ((size_t)p->n_in + 1) * (size_t)ts.Ll * csz;
     for (int tb = 1; tb * T <= (T > 256 ? T : 256); tb *= 2) {
@@ -924,8 +924,8 @@ psatd_status psatd_plan_set_launch(psatd_plan p, const int32_t cfg[6]) {
     c.log_tb[k] = cfg[k];
   }
   if (cfg[5] >= 0) {
-    if (cfg[5] != 8 && cfg[5] != 16 && cfg[5] != 24)
-      return fail(p, PSATD_ERR_INVALID_ARG, "cfg[5] must be 8, 16, 24 or -1");
+    if (cfg[5] != 8 && cfg[5] != 16 && cfg[5] != 12)
+      return fail(p, PSATD_ERR_INVALID_ARG, "cfg[5] must be 8, 16, 12 or -1");
     c.push_ept = cfg[5];
   }
   bool ok = false;
@@ -1223,6 +1223,13 @@ struct psatd_batch_s {
   int npatch = 0;
   bool f32 = true;
   std::vector<psatd_plan> cls;  // one plan per patch size class
+  // The classes are independent (each plan has its own scratch): every step
+  // forks from st into branch streams, each running its share of the classes
+  // (balanced by cells), and joins back, so that the kernels of small classes
+  // run beside those of other classes instead of one after another.
+  std::vector<cudaStream_t> br;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
   int64_t total_cells = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -1236,6 +1243,12 @@ void batch_release(psatd_batch b) {
   if (b->graph) cudaGraphDestroy(b->graph);
   b->gexec = nullptr;
   b->graph = nullptr;
+  for (cudaStream_t s : b->br) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  b->br.clear();
+  b->join.clear();
+  b->fork = nullptr;
   for (psatd_plan p : b->cls) {
     release(p);
     delete p;
@@ -1244,12 +1257,26 @@ void batch_release(psatd_batch b) {
 }
 
 psatd_status batch_launch_all(psatd_batch b, const void* in[kMaxComp], void* out[kMaxComp]) {
+  const bool forked = !b->br.empty();
+  cudaError_t e = cudaSuccess;
+  if (forked) {
+    e = cudaEventRecord(b->fork, b->st);
+    for (size_t k = 0; k < b->br.size() && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->br[k], b->fork, 0);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch fork");
+  }
   for (psatd_plan p : b->cls) {
     psatd_status s = step_once(p, in, out);
     if (s != PSATD_OK) {
       g_err = p->err;
       return s;
     }
+  }
+  if (forked) {
+    for (size_t k = 0; k < b->br.size() && e == cudaSuccess; ++k) {
+      e = cudaEventRecord(b->join[k], b->br[k]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->st, b->join[k], 0);
+    }
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch join");
   }
   return PSATD_OK;
 }
@@ -1319,6 +1346,36 @@ extern "C" psatd_status psatd_batch_create(const psatd_desc* base, int32_t npatc
       return s;
     }
     b->cls.push_back(p);
+  }
+  // branch streams: up to 4, classes assigned largest first to the least loaded branch
+  const int nbr = (int)std::min<size_t>(4, b->cls.size());
+  if (nbr > 1) {
+    cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int k = 0; k < nbr && e == cudaSuccess; ++k) {
+      cudaStream_t st = nullptr;
+      cudaEvent_t ev = nullptr;
+      e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      if (e == cudaSuccess) b->br.push_back(st);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) b->join.push_back(ev);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);  // the classes' tables are built on st
+    if (e != cudaSuccess) {
+      psatd_status r = cuda_fail(nullptr, e, "batch branch streams");
+      batch_release(b);
+      delete b;
+      return r;
+    }
+    std::vector<int> order(b->cls.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    auto cells = [&](int i) { return b->cls[i]->nx * b->cls[i]->ny * b->cls[i]->npatch; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cells(a) > cells(c); });
+    std::vector<int64_t> load(nbr, 0);
+    for (int i : order) {
+      const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      load[k] += cells(i);
+      b->cls[i]->st = b->br[k];
+    }
   }
   *out = b;
   return PSATD_OK;

@@ -242,10 +242,59 @@ __device__ __forceinline__ void dft3(C& a0, C& a1, C& a2) {
   a2 = csub(m, s);
 }
 
+// Radix-12 DFT in place, natural order in and out, as the prime-factor
+// (Good-Thomas) split 12 = 3 x 4: with n = (4 n1 + 3 n2) mod 12 and
+// k = (4 k1 + 9 k2) mod 12, W12^(n k) = W3^(n1 k1) W4^(n2 k2), so radix-3 DFTs
+// over n1 and radix-4 DFTs over n2 need no twiddles between them.  The adjoint
+// runs the same steps in reverse order with the conjugate DFTs.
+template <bool ADJ, class C>
+__device__ __forceinline__ void dft12(C* a) {
+  C y[12];
+  if constexpr (!ADJ) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      C c0 = a[(3 * n2) % 12], c1 = a[(4 + 3 * n2) % 12], c2 = a[(8 + 3 * n2) % 12];
+      dft3<false>(c0, c1, c2);
+      y[3 * n2] = c0;
+      y[3 * n2 + 1] = c1;
+      y[3 * n2 + 2] = c2;
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+      C d0 = y[k1], d1 = y[3 + k1], d2 = y[6 + k1], d3 = y[9 + k1];
+      dft4<false>(d0, d1, d2, d3);
+      a[(4 * k1) % 12] = d0;
+      a[(4 * k1 + 9) % 12] = d1;
+      a[(4 * k1 + 18) % 12] = d2;
+      a[(4 * k1 + 27) % 12] = d3;
+    }
+  } else {
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+      C d0 = a[(4 * k1) % 12], d1 = a[(4 * k1 + 9) % 12], d2 = a[(4 * k1 + 18) % 12], d3 = a[(4 * k1 + 27) % 12];
+      dft4<true>(d0, d1, d2, d3);
+      y[k1] = d0;
+      y[3 + k1] = d1;
+      y[6 + k1] = d2;
+      y[9 + k1] = d3;
+    }
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      C c0 = y[3 * n2], c1 = y[3 * n2 + 1], c2 = y[3 * n2 + 2];
+      dft3<true>(c0, c1, c2);
+      a[(3 * n2) % 12] = c0;
+      a[(4 + 3 * n2) % 12] = c1;
+      a[(8 + 3 * n2) % 12] = c2;
+    }
+  }
+}
+
 template <int RS, bool ADJ, class C>
 __device__ __forceinline__ void butterfly(C* a) {
   if constexpr (RS == 3) {
     dft3<ADJ>(a[0], a[1], a[2]);
+  } else if constexpr (RS == 12) {
+    dft12<ADJ>(a);
   } else if constexpr (RS == 2) {
     C s = cadd(a[0], a[1]), d = csub(a[0], a[1]);
     a[0] = s;
@@ -266,7 +315,9 @@ __host__ __device__ constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v
 // and of the fused last-axis pass (8).
 __host__ __device__ constexpr bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
-// Lengths 3 * 2^k (k >= 4) are mixed-radix: 24 elements per thread in every pass.
+// Lengths 3 * 2^k (k >= 4) are mixed-radix: 24 elements per thread in the
+// transposing passes, 12 in the fused pass (whose shared memory per line is
+// fixed, so that fewer elements per thread keep more threads on an SM).
 template <int L>
 struct RowEPT { static constexpr int value = !is_pow2(L) ? 24 : L >= 16 ? 16 : 8; };
 // The fused pass keeps 8 elements per thread: with 16 a 2048-point line has
@@ -274,25 +325,28 @@ struct RowEPT { static constexpr int value = !is_pow2(L) ? 24 : L >= 16 ? 16 : 8
 // the warps (measured slower).  The tensor-core variant (TC) takes 16, so that
 // its stages are radix-16 DFT-matrix contractions.
 template <int L, int TC = 0>
-struct PushEPT { static constexpr int value = !is_pow2(L) ? 24 : TC ? 16 : 8; };
+struct PushEPT { static constexpr int value = !is_pow2(L) ? 12 : TC ? 16 : 8; };
 
 // Power-of-two L: a radix-2/4/8 first stage when log2 L is not a multiple of
-// log2 EPT, then radix-EPT stages.  Mixed L = 3 * 2^k (EPT = 24): a radix-3
+// log2 EPT, then radix-EPT stages.  Mixed L = 3 * 2^k: with EPT = 24 a radix-3
 // first stage, a radix-2 or radix-4 stage when k is not a multiple of 3, then
-// radix-8 stages; every radix divides 24.
+// radix-8 stages; with EPT = 12 a radix-12 first stage (prime-factor 3 x 4),
+// a radix-2 stage when k is odd, then radix-4 stages.  Every radix divides EPT.
 template <int L, int EPT = 8>
 struct FFTPlan {
   static constexpr int kEPT = EPT;
   static constexpr bool kMixed = !is_pow2(L);
   static constexpr int kLog = kMixed ? ilog2(L / 3) : ilog2(L);  // log2 of the power-of-two part
-  static constexpr int kB = kMixed ? 3 : ilog2(EPT);
-  static constexpr int kRem = kLog % kB;
-  static constexpr int kR0 = kMixed ? 3 : kRem ? (1 << kRem) : EPT;
-  static constexpr int kStages = kMixed ? 1 + (kRem ? 1 : 0) + kLog / 3 : kRem ? kLog / kB + 1 : kLog / kB;
+  static constexpr int kHeadLog = (kMixed && EPT == 12) ? 2 : 0;  // power of two taken by the first stage
+  static constexpr int kB = kMixed ? (EPT == 12 ? 2 : 3) : ilog2(EPT);
+  static constexpr int kRem = (kLog - kHeadLog) % kB;
+  static constexpr int kR0 = kMixed ? 3 << kHeadLog : kRem ? (1 << kRem) : EPT;
+  static constexpr int kStages = kMixed ? 1 + (kRem ? 1 : 0) + (kLog - kHeadLog) / kB
+                                        : kRem ? kLog / kB + 1 : kLog / kB;
   static constexpr int kT = L / EPT;
   static constexpr int kBuf = L;  // exchange buffer (XOR-swizzled, no padding)
   __host__ __device__ static constexpr int radix(int s) {
-    if (kMixed) return s == 0 ? 3 : (s == 1 && kRem) ? (1 << kRem) : 8;
+    if (kMixed) return s == 0 ? kR0 : (s == 1 && kRem) ? (1 << kRem) : (1 << kB);
     return s == 0 ? kR0 : EPT;
   }
   __host__ __device__ static constexpr int span(int s) {  // Ns of stage s
@@ -316,8 +370,9 @@ struct FFTPlan {
   // swizzle of the last exchange: forward output / inverse input positions
   // sw<kLastCX>(t + T m) are each touched by their own thread only
   static constexpr int kLastCX = (kStages >= 2) ? swz(kStages - 2) : 0;
-  static_assert(kMixed ? (L == 3 * (1 << kLog) && EPT == 24 && kLog >= 4) : (L >= EPT && EPT != 24),
-                "L must be a power of two >= EPT, or 3 * 2^k (k >= 4) with EPT = 24");
+  static_assert(kMixed ? (L == 3 * (1 << kLog) && (EPT == 24 || EPT == 12) && kLog >= 4)
+                       : (L >= EPT && EPT != 24 && EPT != 12),
+                "L must be a power of two >= EPT, or 3 * 2^k (k >= 4) with EPT = 12 or 24");
 };
 
 // element i of an exchange buffer, rows of 16 elements (128 B) XOR-swizzled

@@ -132,13 +132,13 @@ template <typename R>
 cudaError_t launch_line_push3(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
                               const PushArgs<R>& a, const void* tw) {
   switch (L) {
-    case 48: return push_L<R, 0, 24, 48>(layout, grid, tb, smem, st, a, tw);
-    case 96: return push_L<R, 0, 24, 96>(layout, grid, tb, smem, st, a, tw);
-    case 192: return push_L<R, 0, 24, 192>(layout, grid, tb, smem, st, a, tw);
-    case 384: return push_L<R, 0, 24, 384>(layout, grid, tb, smem, st, a, tw);
-    case 768: return push_L<R, 0, 24, 768>(layout, grid, tb, smem, st, a, tw);
-    case 1536: return push_L<R, 0, 24, 1536>(layout, grid, tb, smem, st, a, tw);
-    case 3072: return push_L<R, 0, 24, 3072>(layout, grid, tb, smem, st, a, tw);
+    case 48: return push_L<R, 0, 12, 48>(layout, grid, tb, smem, st, a, tw);
+    case 96: return push_L<R, 0, 12, 96>(layout, grid, tb, smem, st, a, tw);
+    case 192: return push_L<R, 0, 12, 192>(layout, grid, tb, smem, st, a, tw);
+    case 384: return push_L<R, 0, 12, 384>(layout, grid, tb, smem, st, a, tw);
+    case 768: return push_L<R, 0, 12, 768>(layout, grid, tb, smem, st, a, tw);
+    case 1536: return push_L<R, 0, 12, 1536>(layout, grid, tb, smem, st, a, tw);
+    case 3072: return push_L<R, 0, 12, 3072>(layout, grid, tb, smem, st, a, tw);
     default: return cudaErrorInvalidValue;
   }
 }

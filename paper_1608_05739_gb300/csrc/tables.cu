@@ -35,11 +35,12 @@ struct Radices {
 static Radices plan_radices(int L, int ept) {
   Radices R{};
   auto lg = [](int v) { int k = 0; while ((1 << k) < v) ++k; return k; };
-  if (L & (L - 1)) {  // 3 * 2^k
-    const int k = lg(L / 3), rem = k % 3;
-    R.r[R.n++] = 3;
+  if (L & (L - 1)) {  // 3 * 2^k: radix 3, (2|4), 8, ... (ept 24) or radix 12, (2), 4, ... (ept 12)
+    const int head = ept == 12 ? 2 : 0, b = ept == 12 ? 2 : 3;
+    const int k = lg(L / 3) - head, rem = k % b;
+    R.r[R.n++] = 3 << head;
     if (rem) R.r[R.n++] = 1 << rem;
-    for (int i = 0; i < k / 3; ++i) R.r[R.n++] = 8;
+    for (int i = 0; i < k / b; ++i) R.r[R.n++] = 1 << b;
   } else {
     const int k = lg(L), b = lg(ept), rem = k % b;
     R.r[R.n++] = rem ? (1 << rem) : ept;

@@ -10,7 +10,7 @@ namespace psatd {
 cudaError_t launch_twiddles(void* out, int L, int ept, bool r2c, bool f32, cudaStream_t st);
 // elements per thread of the transposing passes (RowEPT in fft_core.cuh) and of the fused pass
 inline int row_ept(int L) { return !is_pow2(L) ? 24 : L >= 16 ? 16 : 8; }
-inline int push_ept(int L, bool tc = false) { return !is_pow2(L) ? 24 : tc ? 16 : 8; }
+inline int push_ept(int L, bool tc = false) { return !is_pow2(L) ? 12 : tc ? 16 : 8; }
 // split-FP16 (or split-BF16) radix-16 DFT matrices of both directions, tensor-core operand layout
 cudaError_t launch_tc_dftmat(void* out, bool bf16, cudaStream_t st);
 // kp: per-axis order-p wavenumber tables (units of g0, n_i/2+1 entries) of a

@@ -148,7 +148,7 @@ def test_batch_of_mixed_and_power_of_two_patches():
 
 def test_every_launch_shape_of_a_mixed_plan():
     """Lines per CTA change no arithmetic: all accepted shapes give the same bits;
-    the fused pass takes 24 elements per thread only (radix-8/16 schedules do
+    the fused pass takes 12 elements per thread only (radix-8/16 schedules do
     not divide 3 * 2^k)."""
     shape, d, dt = (384, 768), (1.0, 0.8), 0.5
     E, B, J, _, _ = _inputs(shape, "te", 1200)
@@ -156,8 +156,8 @@ def test_every_launch_shape_of_a_mixed_plan():
     Eo, Bo = mask_layout(Eo, "te", "E"), mask_layout(Bo, "te", "B")
     ensure_lib()
     plan = capi.Plan((768, 384), d, dt, layout="te", prec="fp32", src="J")
-    assert plan.get_launch()[5] == 24
-    for ept in (8, 16):
+    assert plan.get_launch()[5] == 12
+    for ept in (8, 16, 24):
         with pytest.raises(capi.PsatdError):
             plan.set_launch([-1, -1, -1, -1, -1, ept])
     shapes = []
@@ -172,10 +172,10 @@ def test_every_launch_shape_of_a_mixed_plan():
             shapes.append(cfg)
     for tb in (1, 2, 4, 8, 16, 32):
         try:
-            plan.set_launch([-1, -1, -1, -1, tb, 24])
+            plan.set_launch([-1, -1, -1, -1, tb, 12])
         except capi.PsatdError:
             continue
-        shapes.append([-1, -1, -1, -1, tb, 24])
+        shapes.append([-1, -1, -1, -1, tb, 12])
     assert len(shapes) >= 6
     ref = None
     for cfg in shapes:
@@ -187,7 +187,7 @@ def test_every_launch_shape_of_a_mixed_plan():
         else:
             assert np.array_equal(Eg, ref[0]) and np.array_equal(Bg, ref[1]), cfg
     rep = plan.autotune(2)
-    assert "push" in rep and plan.get_launch()[5] == 24
+    assert "push" in rep and plan.get_launch()[5] == 12
     Eg, Bg = psatd_gpu(shape, d, dt, E, B, J, layout="te", prec="fp32", src="J", plan=plan)
     assert np.array_equal(Eg, ref[0]) and np.array_equal(Bg, ref[1])
     plan.destroy()
