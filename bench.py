@@ -259,6 +259,67 @@ def time_te2048(capi, torch, prec, args, dev, dt, dx, Jy_all, flush, stream, wor
     return ms, ktimes, clk, plan
 
 
+def cufft_comparator(torch, args, dev, dt, dx, Jy_all, flush, stream, plan):
+    """The same 2048^2 TE J-form step written with library calls, for context
+    (not the product path): torch.fft (cuFFT) rfft2 of the five inputs, the
+    per-mode update of the collocated exact-k scheme as torch elementwise ops on
+    FP32 coefficient arrays (computed in FP64, Nyquist k := 0, c = eps0 = 1),
+    irfft2 of the three fields.  Timed like the step (L2 flushed, CUDA events),
+    and compared once with the library's step from the same random state."""
+    c, eps0 = 1.0, 1.0
+    kx = 2.0 * math.pi * torch.fft.rfftfreq(NX, d=dx, dtype=torch.float64, device=dev)
+    ky = 2.0 * math.pi * torch.fft.fftfreq(NY, d=dx, dtype=torch.float64, device=dev)
+    kx[NX // 2] = 0.0
+    ky[NY // 2] = 0.0
+    KX = kx[None, :].expand(NY, -1)
+    KY = ky[:, None].expand(-1, NX // 2 + 1)
+    k = torch.sqrt(KX * KX + KY * KY)
+    zero = k == 0
+    ks = torch.where(zero, torch.ones_like(k), k)
+    C = torch.cos(c * k * dt)
+    S = torch.sin(c * k * dt)
+    sck = torch.where(zero, torch.full_like(k, dt), S / (c * ks))
+    f32 = lambda t: t.float().contiguous()
+    co = {"C": f32(C), "a1": f32(1.0 - C), "cS": f32(c * S), "sck": f32(sck), "sJ": f32(sck / eps0),
+          "aJL": f32(torch.where(zero, torch.zeros_like(k), (sck - dt) / eps0)),
+          "bJ": f32(torch.where(zero, torch.zeros_like(k), (1.0 - C) / (eps0 * c * c * ks * ks))),
+          "kapx": f32(KX / ks), "kapy": f32(KY / ks), "kx": f32(KX), "ky": f32(KY)}
+
+    def step(Ex, Ey, Bz, Jx, Jy):
+        ex, ey, bz, jx, jy = torch.fft.rfft2(torch.stack([Ex, Ey, Bz, Jx, Jy]))
+        kE = co["kapx"] * ex + co["kapy"] * ey
+        kJ = co["kapx"] * jx + co["kapy"] * jy
+        ex1 = co["C"] * ex + co["a1"] * co["kapx"] * kE + 1j * co["cS"] * co["kapy"] * bz - co["sJ"] * jx \
+            + co["aJL"] * co["kapx"] * kJ
+        ey1 = co["C"] * ey + co["a1"] * co["kapy"] * kE - 1j * co["cS"] * co["kapx"] * bz - co["sJ"] * jy \
+            + co["aJL"] * co["kapy"] * kJ
+        bz1 = co["C"] * bz - 1j * co["sck"] * (co["kx"] * ey - co["ky"] * ex) \
+            + 1j * co["bJ"] * (co["kx"] * jy - co["ky"] * jx)
+        out = torch.fft.irfft2(torch.stack([ex1, ey1, bz1]), s=(NY, NX))
+        Ex.copy_(out[0])
+        Ey.copy_(out[1])
+        Bz.copy_(out[2])
+
+    # agreement with the library's step from one random state
+    g = torch.Generator(device=dev).manual_seed(1615)
+    st = [torch.randn(NY, NX, device=dev, generator=g) for _ in range(5)]
+    a = [t.clone() for t in st]
+    step(a[0], a[1], a[2], a[3], a[4])
+    b = [t.clone() for t in st]
+    plan.step([b[0], b[1], None], [None, None, b[2]], [b[3], b[4], None])
+    torch.cuda.synchronize()
+    num = sum(float(torch.sum((a[i].double() - b[i].double()) ** 2)) for i in range(3))
+    den = sum(float(torch.sum(b[i].double() ** 2)) for i in range(3))
+    Ex, Ey, Bz, Jx = (torch.zeros(NY, NX, device=dev) for _ in range(4))
+    steps = min(args.steps, 50)
+    ms, _ = timed_steps(lambda i: step(Ex, Ey, Bz, Jx, Jy_all[i % len(Jy_all)]), steps, max(args.warmup, 3),
+                        flush, stream)
+    return {"what": "torch.fft (cuFFT) rfft2 / irfft2 + torch elementwise push, FP32, same workload; "
+                    "context only, not the product path",
+            "ms_per_step": ms / steps, "value": NX * NY * steps / (ms * 1e-3), "unit": "cell-steps/s",
+            "rel_l2_vs_library_step": math.sqrt(num / den)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -272,6 +333,7 @@ def main():
                     help="te2048 arithmetic of the headline line: plain FP32, or tensor-core split-FP16 / "
                          "split-BF16 radix-16 stages (the others are timed too, under 'other_precision')")
     ap.add_argument("--no-side-precision", action="store_true", help="skip timing the other precision")
+    ap.add_argument("--no-comparator", action="store_true", help="skip timing the cuFFT comparator")
     ap.add_argument("--workload", default="te2048",
                     choices=["te2048", "3d256", "fdtd-yee", "fdtd-ckc", "batch512", "local", "cost3d"],
                     help="te2048 (default) is the metric's configuration; the others are side measurements")
@@ -345,6 +407,10 @@ def main():
     e2e_ms = e0.elapsed_time(e1)
     e2e_value = NX * NY * e2e_steps / (e2e_ms * 1e-3)
 
+    comparator = None
+    if rank == 0 and not args.no_comparator:
+        comparator = cufft_comparator(torch, args, dev, dt, dx, Jy_all, flush, stream, plan)
+
     cells = NX * NY
     value, t_max = replica_throughput(ms, cells, args.steps, world, dev)
 
@@ -388,6 +454,14 @@ def main():
             "roofline": roof,
             "clocks": clk,
         }
+        # whole-step byte efficiency: compulsory (each input read once, each output written
+        # once: 5 x 4 + 3 x 4 B per cell) and the three-pass model (sum of the passes' bytes)
+        step_s = t_max / args.steps * 1e-3
+        for name, bpc in (("compulsory", 32.0), ("pass_model", sum(alg.values()) / cells)):
+            gbs = bpc * cells / step_s / 1e9
+            line["step_bytes_" + name] = {"bytes_per_cell": bpc, "gbs": gbs, "frac": gbs / hbm}
+        if comparator is not None:
+            line["cufft_comparator"] = comparator
         if side is not None:
             line["other_precision"] = side
         if world == 1 and not args.no_cpu_baseline:
