@@ -335,7 +335,7 @@ def main():
     ap.add_argument("--no-side-precision", action="store_true", help="skip timing the other precision")
     ap.add_argument("--no-comparator", action="store_true", help="skip timing the cuFFT comparator")
     ap.add_argument("--workload", default="te2048",
-                    choices=["te2048", "3d256", "fdtd-yee", "fdtd-ckc", "batch512", "local", "cost3d"],
+                    choices=["te2048", "3d256", "3d512", "fdtd-yee", "fdtd-ckc", "batch512", "local", "cost3d"],
                     help="te2048 (default) is the metric's configuration; the others are side measurements")
     args = ap.parse_args()
     world, rank, local = dist_setup()
@@ -535,25 +535,50 @@ def run_side_workload(args):
             "hbm_gbs_peak": hbm, "clocks": clk, "gpu_launches": sum(v[0] for v in kt.values()),
         })
         plan.destroy()
+    elif args.workload == "3d512":
+        # the large 3D workload: 512 x 512 x 1024 cells, rho-form, divergence-free k^-2 fields plus
+        # 1e5 moving Gaussian charges (sigma = 3 dx), c dt = 0.5 dx; FP32 and split-FP16 tensor-core
+        # stages on the same inputs (each from the same initial state), L2 flushed before every step
+        shape = (1024, 512, 512)
+        d = (1.0, 1.0, 1.0)
+        dt = 0.5
+        E0, B0, J, r0, r1 = synth.large_3d_inputs_torch(shape, d, dt, seed=1614, device=dev)
+        J = [J[i] for i in range(3)]
+        cells = 512 * 512 * 1024
+        alg = algorithmic_bytes(512, 512, 1024, 11, 6)
+        res = {}
+        clk = None
+        for prec in ("fp32", "mixed_fp16"):
+            E = [E0[i].clone() for i in range(3)]
+            B = [B0[i].clone() for i in range(3)]
+            plan = capi.Plan((512, 512, 1024), d, dt, layout="3d6", prec=prec, src="rho", stream=stream)
+            plan.set_timing(True)
+            ms, c_ = timed_steps(lambda i: plan.step(E, B, J, r0, r1), args.steps, args.warmup, flush, stream)
+            kt = plan.kernel_times()
+            plan.sync()
+            plan.destroy()
+            clk = clk or c_
+            per = {k: v[1] / v[0] for k, v in kt.items()}
+            res[prec] = {"ms_per_step": ms / args.steps, "value": cells * args.steps / (ms * 1e-3),
+                         "per_kernel_ms": per, "gpu_launches": sum(v[0] for v in kt.values()),
+                         "per_kernel_gbs": {k: alg[k] / (per[k] * 1e-3) / 1e9 for k in per}}
+            del E, B
+        line.update({
+            "value": res["fp32"]["value"], "ms_per_step": res["fp32"]["ms_per_step"],
+            "config": {"workload": "3D PSATD 512x512x1024, rho-form, divergence-free fields with |F(k)|^2 ~ k^-2 "
+                                   "plus 1e5 moving Gaussian charges (sigma = 3 dx, |v| < 0.5c), c dt = 0.5 dx",
+                       "l2": "flushed before every timed step", "state_gb": 11 * cells * 4 / 1e9},
+            "fp32": res["fp32"], "mixed_fp16": res["mixed_fp16"],
+            "step_algorithmic_bytes_per_cell": sum(alg.values()) / cells,
+            "hbm_gbs_peak": hbm, "clocks": clk, "gpu_launches": res["fp32"]["gpu_launches"],
+        })
     elif args.workload == "batch512":
         # 512 local-FFT patches (Sec. II.A.3): interior n ~ U{64..512} per side, guard g ~ U{8..16},
         # each patch a periodic domain whose side is the smallest transform length >= n + 2g: a power
         # of two, or (FP32) 3 * 2^k from 96 up; TE J-form, smooth random J; the whole run is one
         # psatd_batch_step call (a CUDA graph of one step replayed `steps` times)
         mixed_ok = args.precision == "fp32"
-
-        def fft_side(v):
-            c = [1 << k for k in range(4, 13)] + ([3 << k for k in range(5, 11)] if mixed_ok else [])
-            return min(x for x in c if x >= v)
-
-        g = synth.rng(1612)
-        sizes, interior = [], 0
-        for _ in range(512):
-            n = g.integers(64, 513, size=2)
-            gg = g.integers(8, 17, size=2)
-            side = [fft_side(int(a) + 2 * int(b)) for a, b in zip(n, gg)]
-            sizes.append((side[0], side[1]))
-            interior += int(n[0]) * int(n[1])
+        sizes, interior = synth.batch_patch_sizes(512, 1612, mixed_ok=mixed_ok)
         dx = 1.0 / LAM_CELLS
         dt = dx / math.sqrt(2.0)
         side_stream = torch.cuda.Stream()

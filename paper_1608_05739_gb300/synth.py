@@ -16,6 +16,10 @@ a plasma; these prescribed fields and sources stand in for them):
 * ``gaussian_charges`` -- moving Gaussian macro-charges whose rho^n, rho^(n+1)
                        and J^(n+1/2) satisfy discrete continuity exactly.
 * ``random_fields`` -- white-noise component arrays for parity tests.
+* ``batch_patch_sizes`` -- the batched workload's 512 patch domains (interior
+                       plus guards, rounded up to a transform length).
+* ``large_3d_inputs_torch`` -- the large 3D workload (512 x 512 x 1024): k^-2
+                       divergence-free fields plus 1e5 Gaussian charges.
 """
 from __future__ import annotations
 
@@ -25,7 +29,7 @@ import numpy as np
 
 __all__ = [
     "rng", "plane_waves", "plane_wave_fields", "current_sheet", "random_fields",
-    "gaussian_charges", "coulomb_field",
+    "gaussian_charges", "coulomb_field", "batch_patch_sizes", "large_3d_inputs_torch",
 ]
 
 
@@ -110,8 +114,9 @@ def random_fields(shape, ncomp, seed, scale=1.0):
     return scale * rng(seed).standard_normal((ncomp,) + tuple(shape))
 
 
-def _kaxes(shape, d):
-    """Signed discrete wavenumbers per axis (Nyquist entry 0), rfft half along x."""
+def _kaxes(shape, d, keep_nyquist=False):
+    """Signed discrete wavenumbers per axis (Nyquist entry 0 unless ``keep_nyquist``),
+    rfft half along x."""
     ks = []
     for ax, n in enumerate(shape):
         h = d[len(shape) - 1 - ax]
@@ -120,7 +125,7 @@ def _kaxes(shape, d):
         else:
             m = np.fft.fftfreq(n) * n
         k = 2.0 * math.pi * m / (n * h)
-        if n % 2 == 0:
+        if n % 2 == 0 and not keep_nyquist:
             k[np.abs(m) == n // 2] = 0.0
         sh = [1] * len(shape)
         sh[ax] = k.size
@@ -248,3 +253,107 @@ def gaussian_charges_torch(shape, d, dt, *, n_charges=64, sigma=None, vmax=0.5, 
         Eh = torch.where(k2 > 0, -1j * ks[a] * rho0 / k2s, torch.zeros_like(rho0))
         E[a] = torch.fft.irfftn(Eh, s=shape, dim=dims)
     return r0.float(), r1.float(), J.float(), E.float()
+
+
+def batch_patch_sizes(npatch=512, seed=1612, mixed_ok=True):
+    """Patch domains of the batched local-FFT workload (Sec. II.A.3): per patch an
+    interior n ~ U{64..512} and a guard width g ~ U{8..16}, drawn independently per
+    axis (x first), each side the smallest transform length >= n + 2g -- a power of
+    two, or with ``mixed_ok`` also 3 * 2^k from 96 up.  Returns ([(nx, ny), ...],
+    interior cells)."""
+    cand = [1 << k for k in range(4, 13)] + ([3 << k for k in range(5, 11)] if mixed_ok else [])
+
+    def side(v):
+        return min(x for x in cand if x >= v)
+
+    g = rng(seed)
+    sizes, interior = [], 0
+    for _ in range(npatch):
+        n = g.integers(64, 513, size=2)
+        gg = g.integers(8, 17, size=2)
+        sizes.append((side(int(n[0]) + 2 * int(gg[0])), side(int(n[1]) + 2 * int(gg[1]))))
+        interior += int(n[0]) * int(n[1])
+    return sizes, interior
+
+
+def large_3d_inputs_torch(shape, d, dt, *, n_charges=100000, sigma=None, vmax=0.5, c=1.0, eps0=1.0,
+                          seed=1614, device="cuda"):
+    """Inputs of the large 3D workload (``shape`` = (nz, ny, nx), e.g. 1024 x 512 x 512),
+    built with torch on ``device`` in FP64 and returned as float32 tensors
+    (E, B, J each ``(3, *shape)``, rho_n, rho_np1).
+
+    * Sources: ``n_charges`` Gaussian macro-charges (sigma = 3 dx, q = +1/-1
+      alternating, velocities uniform in the ball |v| < vmax c) centred on grid
+      nodes, so that the sum over charges is the transform of a node deposit:
+      rho^n(k) = G(k) FFT(sum_j q_j (N/V) delta_j), J(k) likewise with q_j v_j,
+      G = exp(-sigma^2 |k|^2 / 2) on the true wavenumbers (Nyquist pi/d, where G
+      is below 1e-19 at sigma = 3 dx); rho^(n+1) = rho^n - i dt k.J imposes
+      discrete continuity exactly.
+    * Fields: E = the Coulomb field of rho^n plus a divergence-free random field,
+      B a divergence-free random field, the random parts with per-mode power
+      |F(k)|^2 ~ |k|^-2 (complex Gaussian modes from the transform of real white
+      noise, divided by |k|, projected transverse, scaled to unit rms).
+    Wavenumbers: the discrete ones with the Nyquist entries 0."""
+    import torch
+
+    nz, ny, nx = shape
+    g = rng(seed)
+    ix = [torch.from_numpy(g.integers(0, n, n_charges)).to(device) for n in (nx, ny, nz)]
+    dirs = g.standard_normal((n_charges, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    speed = vmax * c * g.uniform(0.0, 1.0, n_charges) ** (1.0 / 3.0)
+    vel = torch.from_numpy(dirs * speed[:, None]).to(device)
+    q = torch.from_numpy(np.where(np.arange(n_charges) % 2 == 0, 1.0, -1.0)).to(device)
+    sigma = 3.0 * d[0] if sigma is None else sigma
+    kx, ky, kz = (torch.from_numpy(np.ascontiguousarray(k)).to(device) for k in _kaxes(shape, d))
+    k2 = kx * kx + ky * ky + kz * kz
+    N = float(nx * ny * nz)
+    V = N * d[0] * d[1] * d[2]
+    G = torch.exp(-0.5 * sigma * sigma * sum(
+        k * k for k in (torch.from_numpy(np.ascontiguousarray(v)).to(device)
+                        for v in _kaxes(shape, d, keep_nyquist=True))))
+    flat = (ix[2] * ny + ix[1]) * nx + ix[0]
+    dims = (0, 1, 2)
+
+    def deposited(w):
+        a = torch.zeros(nz * ny * nx, dtype=torch.float64, device=device)
+        a.index_add_(0, flat, w * (N / V))
+        return torch.fft.rfftn(a.view(shape), dim=dims) * G
+
+    R0 = deposited(q)
+    kJ = torch.zeros_like(R0)
+    J = torch.empty((3,) + tuple(shape), dtype=torch.float32, device=device)
+    for a, ka in enumerate((kx, ky, kz)):
+        Jh = deposited(q * vel[:, a])
+        kJ += ka * Jh
+        J[a] = torch.fft.irfftn(Jh, s=shape, dim=dims).float()
+        del Jh
+    r0 = torch.fft.irfftn(R0, s=shape, dim=dims).float()
+    r1 = torch.fft.irfftn(R0 - 1j * dt * kJ, s=shape, dim=dims).float()
+    del kJ
+    nzk = k2 > 0
+    k2s = torch.where(nzk, k2, torch.ones_like(k2))
+    gen = torch.Generator(device=device).manual_seed(seed + 1)
+
+    def transverse_random():
+        W = [torch.fft.rfftn(torch.randn(shape, dtype=torch.float64, device=device, generator=gen), dim=dims)
+             for _ in range(3)]
+        kw = (kx * W[0] + ky * W[1] + kz * W[2]) / k2s
+        out = []
+        for a, ka in enumerate((kx, ky, kz)):
+            F = torch.where(nzk, (W[a] - ka * kw) / torch.sqrt(k2s), torch.zeros_like(W[a]))
+            out.append(torch.fft.irfftn(F, s=shape, dim=dims))
+        rms = math.sqrt(sum(float(torch.mean(f * f)) for f in out) / 3.0)
+        return [f / rms for f in out]
+
+    E = torch.empty((3,) + tuple(shape), dtype=torch.float32, device=device)
+    ET = transverse_random()
+    for a, ka in enumerate((kx, ky, kz)):
+        EL = torch.where(nzk, -1j * ka * R0 / (eps0 * k2s), torch.zeros_like(R0))
+        E[a] = (ET[a] + torch.fft.irfftn(EL, s=shape, dim=dims)).float()
+    del ET
+    B = torch.empty_like(E)
+    BT = transverse_random()
+    for a in range(3):
+        B[a] = BT[a].float()
+    return E, B, J, r0, r1

@@ -1,0 +1,130 @@
+"""Parity at the full sizes of the batched and the large 3D workloads, in the
+launch configuration the bench times, on outputs the FP64 oracle can compute
+one by one.
+
+* 512 batched TE patches (the bench's size list: interior U{64..512} + guards
+  U{8..16}, 46 size classes in FP32 with 3 * 2^k sides, 16 power-of-two classes
+  for the mixed precisions), two steps as one graph replay on a side stream: a
+  seeded sample of patches (always including the smallest and the largest
+  class) each against the oracle on that patch alone.
+* 3D 512 x 512 x 1024 rho-form (k^-2 fields, 1e5 Gaussian charges), one step,
+  FP32 and split-FP16: a PSATD step acts mode by mode, so every output mode is
+  the oracle's per-mode update (``push_modes``) of the same input mode.  Input
+  and output modes are taken at sampled wavenumbers (the origin, Nyquist planes,
+  the smallest |k| and seeded random modes) by brute-force FP64 DFT sums on the
+  GPU.  Each mode's error (the six components together) is taken relative to
+  the larger of that mode's size and the rms mode size (the fields' L2 norm, by
+  Parseval): with a k^-2 spectrum the lowest modes are ~300 times the rms, so
+  FP32 rounding alone puts their absolute error far above the rms-level modes'.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_helpers import ensure_lib, mask_layout, rel_l2_fields, rounded
+from oracle import psatd as orc
+from paper_1608_05739_gb300 import capi, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 4e-6), ("mixed_fp16", 8e-6)])
+def test_batch512_full_size_sampled_patches(prec, tol):
+    import torch
+    ensure_lib()
+    sizes, _ = synth.batch_patch_sizes(mixed_ok=prec == "fp32")
+    dx = 1.0 / 64
+    d, dt = (dx, dx), dx / math.sqrt(2.0)
+    total = sum(a * b for a, b in sizes)
+    g = torch.Generator(device="cuda").manual_seed(1616)
+    Ex, Ey, Bz, Jx, Jy = (torch.randn(total, device="cuda", generator=g) for _ in range(5))
+    host0 = [t.double().cpu().numpy() for t in (Ex, Ey, Bz, Jx, Jy)]
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    b = capi.Batch(sizes, d, dt, layout="te", prec=prec, src="J", stream=stream)
+    with torch.cuda.stream(stream):
+        b.step([Ex, Ey, None], [None, None, Bz], [Jx, Jy, None], nsteps=2)
+    torch.cuda.synchronize()
+    b.destroy()
+    out = [t.double().cpu().numpy() for t in (Ex, Ey, Bz)]
+    offs = np.concatenate([[0], np.cumsum([a * c for a, c in sizes])])
+    area = [a * c for a, c in sizes]
+    pick = {int(np.argmin(area)), int(np.argmax(area))}
+    pick |= set(int(i) for i in synth.rng(1617).choice(len(sizes), 8, replace=False))
+    for i in sorted(pick):
+        nx, ny = sizes[i]
+        cut = lambda a: a[offs[i]:offs[i + 1]].reshape(ny, nx)
+        z = np.zeros((ny, nx))
+        E = np.stack([cut(host0[0]), cut(host0[1]), z])
+        B = np.stack([z, z, cut(host0[2])])
+        J = np.stack([cut(host0[3]), cut(host0[4]), z])
+        Eo, Bo = orc.psatd_step(E, B, J, d=d, dt=dt, form="J", nsteps=2)
+        Eg = np.stack([cut(out[0]), cut(out[1]), z])
+        Bg = np.stack([z, z, cut(out[2])])
+        err = rel_l2_fields(Eg, Bg, mask_layout(Eo, "te", "E"), mask_layout(Bo, "te", "B"))
+        assert err < tol, (i, nx, ny, err)
+
+
+def _modes(shape, M, seed):
+    """Sampled (mz, my, mx) rfftn indices: the origin, Nyquist planes, the smallest
+    |k| on each axis, and seeded random modes."""
+    nz, ny, nx = shape
+    fixed = [(0, 0, 0), (0, 0, 1), (0, 1, 0), (1, 0, 0), (0, 0, nx // 2), (0, ny // 2, 3), (nz // 2, 5, 7),
+             (nz // 2, ny // 2, nx // 2), (nz - 1, ny - 1, 1), (nz // 3, 2 * ny // 3, nx // 4)]
+    g = synth.rng(seed)
+    rnd = [(int(g.integers(nz)), int(g.integers(ny)), int(g.integers(nx // 2 + 1))) for _ in range(M - len(fixed))]
+    return fixed + rnd
+
+
+def _dft_at(f, modes):
+    """Brute-force FP64 DFT sum_x f(x) exp(-2 pi i m.x/n) of a real CUDA array f
+    [nz, ny, nx] at the given (mz, my, mx) modes (separable phase factors)."""
+    import torch
+    nz, ny, nx = f.shape
+    dev = f.device
+    m = torch.tensor(modes, dtype=torch.float64, device=dev)  # [M, 3]
+
+    def phase(n, col):
+        x = torch.arange(n, dtype=torch.float64, device=dev)
+        return torch.exp(-2j * math.pi * torch.outer(x, m[:, col]) / n)  # [n, M]
+
+    px, py, pz = phase(nx, 2), phase(ny, 1), phase(nz, 0)
+    f64 = f.double().reshape(nz * ny, nx)
+    t = torch.complex(f64 @ px.real, f64 @ px.imag).reshape(nz, ny, -1)  # [nz, ny, M]
+    t = torch.einsum("zym,ym->zm", t, py)
+    return torch.einsum("zm,zm->m", t, pz).cpu().numpy()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 1e-5), ("mixed_fp16", 4e-5)])
+def test_large_3d_sampled_modes(prec, tol):
+    import torch
+    ensure_lib()
+    shape = (1024, 512, 512)
+    d, dt = (1.0, 1.0, 1.0), 0.5
+    E, B, J, r0, r1 = synth.large_3d_inputs_torch(shape, d, dt, seed=1614)
+    modes = _modes(shape, 40, 1618)
+    spec = lambda comps: [_dft_at(c, modes) for c in comps]
+    Ein, Bin, Jin = spec(E), spec(B), spec(J)
+    R0, R1 = _dft_at(r0, modes), _dft_at(r1, modes)
+    plan = capi.Plan((512, 512, 1024), d, dt, layout="3d6", prec=prec, src="rho")
+    Et, Bt, Jt = [E[i] for i in range(3)], [B[i] for i in range(3)], [J[i] for i in range(3)]
+    plan.step(Et, Bt, Jt, r0, r1)
+    plan.sync()
+    plan.destroy()
+    Eout, Bout = spec(Et), spec(Bt)
+    kx = orc.wavenumbers(512, d[0], half=True)
+    ky = orc.wavenumbers(512, d[1])
+    kz = orc.wavenumbers(1024, d[2])
+    k = (np.array([kx[mx] for _, _, mx in modes]), np.array([ky[my] for _, my, _ in modes]),
+         np.array([kz[mz] for mz, _, _ in modes]))
+    Eo, Bo = orc.push_modes(k, Ein, Bin, Jin, R0, R1, dt=dt, form="rho")
+    rms = math.sqrt(sum(float(torch.sum(t.double() ** 2)) for t in Et + Bt))
+    got = np.stack([np.asarray(a) for a in Eout + Bout])
+    ref = np.stack([np.asarray(b) for b in Eo + Bo])
+    dif = np.sqrt(np.sum(np.abs(got - ref) ** 2, axis=0))
+    size = np.sqrt(np.sum(np.abs(ref) ** 2, axis=0))
+    err = dif / np.maximum(size, rms)
+    print("%s: sampled modes, max error / max(|mode|, rms) = %.2e (mode %s), max |mode|/rms = %.0f"
+          % (prec, err.max(), modes[int(np.argmax(err))], size.max() / rms))
+    assert err.max() < tol
