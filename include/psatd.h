@@ -28,9 +28,15 @@
  * The Nyquist index of every even axis is treated as k_i = 0.
  *
  * Conventions common to every entry point
- *   - Arrays are caller-owned DEVICE memory, one array per field component,
- *     x contiguous: 2D [ny][nx], 3D [nz][ny][nx]; element type double for
- *     PSATD_FP64 and float for PSATD_FP32; base addresses 16-byte aligned.
+ *   - Arrays are caller-owned, one array per field component, x contiguous:
+ *     2D [ny][nx], 3D [nz][ny][nx]; element type double for PSATD_FP64 and
+ *     float for PSATD_FP32; base addresses 16-byte aligned.  Each array is
+ *     memory of the plan's device (or managed memory), or pinned host memory
+ *     (cudaHostAlloc / cudaHostRegister): the first and last passes then read
+ *     and write the host arrays directly over the host-GPU link, with no
+ *     separate copies.  Pageable host memory and other devices' memory are
+ *     refused with PSATD_ERR_INVALID_ARG (cudaPointerGetAttributes, before
+ *     any launch).
  *   - Staggering: PSATD is collocated (all components on the nodes); the FDTD
  *     arrays use the Yee positions Ex(i+1/2,j,k) Ey(i,j+1/2,k) Ez(i,j,k+1/2)
  *     Bx(i,j+1/2,k+1/2) By(i+1/2,j,k+1/2) Bz(i+1/2,j+1/2,k), J with E.

@@ -129,11 +129,13 @@ def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, a
 
 
 def _ptr(t, shape, dtype, what):
-    """Device pointer of tensor ``t`` after checking device, dtype, shape, layout."""
+    """Pointer of tensor ``t`` after checking device, dtype, shape, layout: a CUDA
+    tensor, or a pinned host tensor (the passes then read and write host memory
+    directly over the host link)."""
     if t is None:
         return None
-    if not getattr(t, "is_cuda", False):
-        raise ValueError("%s must be a CUDA tensor" % what)
+    if not getattr(t, "is_cuda", False) and not (hasattr(t, "is_pinned") and t.is_pinned()):
+        raise ValueError("%s must be a CUDA tensor or a pinned host tensor" % what)
     if t.dtype != dtype:
         raise ValueError("%s must be %s (got %s)" % (what, dtype, t.dtype))
     if tuple(t.shape) != tuple(shape):

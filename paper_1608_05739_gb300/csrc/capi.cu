@@ -166,6 +166,23 @@ psatd_status validate_desc(psatd_plan p, const psatd_desc* d, bool psatd_limits)
 
 bool aligned16(const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15u) == 0; }
 
+// A pointer the kernels may dereference on `device`: memory of that device,
+// managed memory, or host memory allocated or registered through CUDA (pinned:
+// under unified addressing the kernels use the host address itself, and the
+// passes then read and write it over the host link).  Pageable host memory,
+// and other devices' memory, are refused before any launch.
+bool dev_accessible(const void* q, int device) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeDevice) return at.device == device;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  if (at.type == cudaMemoryTypeHost) return at.devicePointer == q;
+  return false;
+}
+
 // Collect the input slots of a step in kernel slot order; checks presence,
 // absence and alignment of every pointer.
 psatd_status gather_slots(psatd_plan p, const psatd_fields* f, const psatd_sources* s,
@@ -181,6 +198,10 @@ psatd_status gather_slots(psatd_plan p, const psatd_fields* f, const psatd_sourc
       return fail(p, PSATD_ERR_INVALID_ARG, "B%c must be %s for this layout", names[i], pb[i] ? "non-NULL" : "NULL");
     if (f->E[i] && !aligned16(f->E[i])) return fail(p, PSATD_ERR_INVALID_ARG, "E%c not 16-byte aligned", names[i]);
     if (f->B[i] && !aligned16(f->B[i])) return fail(p, PSATD_ERR_INVALID_ARG, "B%c not 16-byte aligned", names[i]);
+    if (f->E[i] && !dev_accessible(f->E[i], p->device))
+      return fail(p, PSATD_ERR_INVALID_ARG, "E%c is not accessible from the plan's device", names[i]);
+    if (f->B[i] && !dev_accessible(f->B[i], p->device))
+      return fail(p, PSATD_ERR_INVALID_ARG, "B%c is not accessible from the plan's device", names[i]);
   }
   if (p->form != PSATD_SRC_NONE) {
     if (!s) return fail(p, PSATD_ERR_INVALID_ARG, "sources is NULL but the plan's source form needs them");
@@ -188,11 +209,15 @@ psatd_status gather_slots(psatd_plan p, const psatd_fields* f, const psatd_sourc
       if (pj[i] != (s->J[i] != nullptr))
         return fail(p, PSATD_ERR_INVALID_ARG, "J%c must be %s for this layout", names[i], pj[i] ? "non-NULL" : "NULL");
       if (s->J[i] && !aligned16(s->J[i])) return fail(p, PSATD_ERR_INVALID_ARG, "J%c not 16-byte aligned", names[i]);
+      if (s->J[i] && !dev_accessible(s->J[i], p->device))
+        return fail(p, PSATD_ERR_INVALID_ARG, "J%c is not accessible from the plan's device", names[i]);
     }
     if (p->form == PSATD_SRC_J_RHO) {
       if (!s->rho_n || !s->rho_np1) return fail(p, PSATD_ERR_INVALID_ARG, "rho-form needs rho_n and rho_np1");
       if (!aligned16(s->rho_n) || !aligned16(s->rho_np1))
         return fail(p, PSATD_ERR_INVALID_ARG, "rho arrays not 16-byte aligned");
+      if (!dev_accessible(s->rho_n, p->device) || !dev_accessible(s->rho_np1, p->device))
+        return fail(p, PSATD_ERR_INVALID_ARG, "rho arrays are not accessible from the plan's device");
     }
   }
   int k = 0;
@@ -1047,6 +1072,11 @@ psatd_status fdtd_step(const psatd_desc* desc, int32_t scheme, const psatd_field
     if ((fields->E[i] && !aligned16(fields->E[i])) || (fields->B[i] && !aligned16(fields->B[i])))
       return fail(nullptr, PSATD_ERR_INVALID_ARG, "field arrays must be 16-byte aligned");
   }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int i = 0; i < 3; ++i)
+    if ((fields->E[i] && !dev_accessible(fields->E[i], dev)) || (fields->B[i] && !dev_accessible(fields->B[i], dev)))
+      return fail(nullptr, PSATD_ERR_INVALID_ARG, "field arrays must be accessible from the current device");
   if (desc->src == PSATD_SRC_J) {
     if (!sources) return fail(nullptr, PSATD_ERR_INVALID_ARG, "sources is NULL");
     for (int i = 0; i < 3; ++i) {
@@ -1054,6 +1084,8 @@ psatd_status fdtd_step(const psatd_desc* desc, int32_t scheme, const psatd_field
         return fail(nullptr, PSATD_ERR_INVALID_ARG, "J component %d presence does not match the layout", i);
       if (sources->J[i] && !aligned16(sources->J[i]))
         return fail(nullptr, PSATD_ERR_INVALID_ARG, "J arrays must be 16-byte aligned");
+      if (sources->J[i] && !dev_accessible(sources->J[i], dev))
+        return fail(nullptr, PSATD_ERR_INVALID_ARG, "J arrays must be accessible from the current device");
       J[i] = sources->J[i];
     }
   }
@@ -1106,6 +1138,7 @@ extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_f
   psatd_plan_s p;
   p.d = *desc;
   p.st = static_cast<cudaStream_t>(cuda_stream);
+  cudaGetDevice(&p.device);
   p.f32 = desc->prec == PSATD_FP32;
   p.ndim = desc->ndim;
   p.layout = desc->layout;
