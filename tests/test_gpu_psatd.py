@@ -15,7 +15,7 @@ import pytest
 from analytic import plane_waves_at
 from gpu_helpers import mask_layout, psatd_gpu, rel_l2_fields, rounded
 from oracle import psatd as orc
-from paper_1608_05739_gb300 import synth
+from paper_1608_05739_gb300 import capi, synth
 
 pytestmark = pytest.mark.gpu
 
@@ -218,3 +218,17 @@ def test_config3_full_size_one_step_fp32():
     Eg, Bg = psatd_gpu(shape, d, dt, E, B, J, r0, r1, layout="3d6", prec="fp32", src="rho")
     Eo, Bo = _oracle(E, B, J, r0, r1, d, dt, "rho")
     assert rel_l2_fields(Eg, Bg, Eo, Bo) < TOL["fp32"]
+
+
+def test_longest_lines_fp32_and_the_fp64_shared_memory_limit():
+    """4096-point fused-pass lines: FP32 TE J-form stages (5 + 1) x 4096 x 8 B = 192 KB
+    per line and matches the oracle; FP64 would need 384 KB and is refused at plan
+    creation (UNSUPPORTED, nothing allocated)."""
+    shape, d, dt = (4096, 32), (1.0, 1.0), 0.5
+    E, B, J, r0, r1 = _inputs(shape, "te", "J", 4096, d, dt, "fp32")
+    Eg, Bg = psatd_gpu(shape, d, dt, E, B, J, layout="te", prec="fp32", src="J", nsteps=2)
+    Eo, Bo = _oracle(E, B, J, None, None, d, dt, "J", nsteps=2)
+    assert rel_l2_fields(Eg, Bg, mask_layout(Eo, "te", "E"), mask_layout(Bo, "te", "B")) < 2 * TOL["fp32"]
+    with pytest.raises(capi.PsatdError) as ei:
+        capi.Plan((32, 4096), d, dt, layout="te", prec="fp64", src="J")
+    assert ei.value.status == 2 and "shared memory" in str(ei.value)
