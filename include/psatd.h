@@ -71,7 +71,7 @@ typedef enum {
   PSATD_ERR_OOM = 3,          /* device allocation failed                             */
   PSATD_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed                 */
   PSATD_ERR_TIMEOUT = 5,      /* a bounded device-side wait expired                   */
-  PSATD_ERR_NONFINITE = 6     /* reserved: non-finite values detected                 */
+  PSATD_ERR_NONFINITE = 6     /* PSATD_FLAG_CHECKED: NaN or Inf in a step's output   */
 } psatd_status;
 
 typedef enum {
@@ -114,6 +114,12 @@ typedef enum { PSATD_FDTD_YEE = 0, PSATD_FDTD_CKC = 1 } psatd_fdtd_scheme;
  * c dt |k| < 2 over the propagated modes (the caller's choice of dt); J-form or
  * vacuum only (INVALID_ARG with the rho-form); any order (k or k_p). */
 #define PSATD_FLAG_PSTD 2
+/* PSATD_FLAG_CHECKED: after every step the output field arrays are scanned for
+ * NaN and Inf (one more read of the outputs, on the plan's stream); a hit sets
+ * the plan's device error word and the next psatd_plan_sync returns
+ * PSATD_ERR_NONFINITE (and clears it).  PSATD plans, batches and local
+ * decompositions; psatd_step_noalloc and fdtd_step refuse it. */
+#define PSATD_FLAG_CHECKED 4
 
 /* Problem statement (the paper's arguments: grid sizes, cell sizes, dt, c, eps0). */
 typedef struct {
@@ -217,7 +223,8 @@ psatd_status psatd_step(psatd_plan plan, const psatd_fields* fields,
 /* Synchronise the plan's stream and report any asynchronous CUDA error, or
  * PSATD_ERR_TIMEOUT when a tensor-core pass (PSATD_MIXED_FP16) gave up a
  * bounded wait for its MMAs since the last sync (the step's output is then
- * not valid; the flag is cleared).                                          */
+ * not valid), or PSATD_ERR_NONFINITE when a checked plan (PSATD_FLAG_CHECKED)
+ * saw NaN or Inf in a step's output since the last sync; the word is cleared. */
 psatd_status psatd_plan_sync(psatd_plan plan);
 
 /* Release the plan and everything it owns (synchronises its stream first).
@@ -275,6 +282,11 @@ psatd_status psatd_batch_step(psatd_batch batch, const psatd_fields* fields,
 
 /* Total cells of the batch (sum over patches). */
 int64_t psatd_batch_cells(psatd_batch batch);
+
+/* Synchronise the batch's stream and report, as psatd_plan_sync does for each
+ * size class, an asynchronous CUDA error, PSATD_ERR_TIMEOUT (tensor-core waits)
+ * or PSATD_ERR_NONFINITE (PSATD_FLAG_CHECKED) since the last sync. */
+psatd_status psatd_batch_sync(psatd_batch batch);
 
 /* Release the batch (synchronises its stream).  NULL is accepted. */
 psatd_status psatd_batch_destroy(psatd_batch batch);

@@ -71,6 +71,7 @@ EXPORTS = [
                                       ct.POINTER(ct.c_void_p)]),
     ("psatd_batch_step", ct.c_int, [ct.c_void_p, ct.POINTER(psatd_fields), ct.POINTER(psatd_sources), ct.c_int32]),
     ("psatd_batch_cells", ct.c_int64, [ct.c_void_p]),
+    ("psatd_batch_sync", ct.c_int, [ct.c_void_p]),
     ("psatd_batch_destroy", ct.c_int, [ct.c_void_p]),
     ("psatd_plan_autotune", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_char_p, ct.c_size_t]),
     ("psatd_plan_set_launch", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32)]),
@@ -84,6 +85,7 @@ EXPORTS = [
 
 FLAG_AUTOTUNE = 1
 FLAG_PSTD = 2
+FLAG_CHECKED = 4
 
 
 def load(path: str = LIB_PATH):
@@ -109,7 +111,7 @@ def _check(status, plan=None):
 
 
 def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, autotune=False, order=0,
-              scheme="psatd"):
+              scheme="psatd", checked=False):
     """psatd_desc for grid ``n`` = (nx, ny[, nz]) and cell sizes ``d``."""
     nd = len(n)
     desc = psatd_desc()
@@ -123,7 +125,8 @@ def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, a
     desc.src = SRC[src]
     if scheme not in ("psatd", "pstd"):
         raise ValueError("scheme must be 'psatd' or 'pstd'")
-    desc.flags = (FLAG_AUTOTUNE if autotune else 0) | (FLAG_PSTD if scheme == "pstd" else 0)
+    desc.flags = ((FLAG_AUTOTUNE if autotune else 0) | (FLAG_PSTD if scheme == "pstd" else 0)
+                  | (FLAG_CHECKED if checked else 0))
     desc.order = int(order)
     return desc
 
@@ -189,14 +192,14 @@ class Plan:
     """
 
     def __init__(self, n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, stream=None,
-                 autotune=False, order=0, scheme="psatd"):
+                 autotune=False, order=0, scheme="psatd", checked=False):
         import torch
         lib = load()
         self.n, self.layout, self.prec, self.src = tuple(n), layout, prec, src
         self.shape = _grid_shape(n)
         self.dtype = _torch_dtype(prec)
         self.desc = make_desc(n, d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0, autotune=autotune,
-                              order=order, scheme=scheme)
+                              order=order, scheme=scheme, checked=checked)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -266,7 +269,7 @@ class Batch:
     """
 
     def __init__(self, sizes, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, stream=None,
-                 autotune=False, order=0):
+                 autotune=False, order=0, checked=False):
         import torch
         lib = load()
         self.sizes = [(int(a), int(b)) for a, b in sizes]
@@ -279,7 +282,7 @@ class Batch:
             self.offsets.append(acc)
             acc += a * b
         desc = make_desc(self.sizes[0], d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0,
-                         autotune=autotune, order=order)
+                         autotune=autotune, order=order, checked=checked)
         arr = (ct.c_int64 * (2 * len(self.sizes)))(*[v for ab in self.sizes for v in ab])
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -298,6 +301,10 @@ class Batch:
 
     def cells(self):
         return int(load().psatd_batch_cells(self.handle))
+
+    def sync(self):
+        """psatd_batch_sync: wait for the batch and raise on a recorded device error."""
+        _check(load().psatd_batch_sync(self.handle))
 
     def destroy(self):
         if getattr(self, "handle", None) is not None:

@@ -120,7 +120,7 @@ psatd_status validate_desc(psatd_plan p, const psatd_desc* d, bool psatd_limits)
   if (d->layout < 0 || d->layout > 3) return fail(p, PSATD_ERR_INVALID_ARG, "unknown layout %d", d->layout);
   if (d->ndim != layout_ndim(d->layout))
     return fail(p, PSATD_ERR_INVALID_ARG, "ndim %d does not match layout %d", d->ndim, d->layout);
-  if ((d->flags & ~(psatd_limits ? (PSATD_FLAG_AUTOTUNE | PSATD_FLAG_PSTD) : 0)) != 0)
+  if ((d->flags & ~(psatd_limits ? (PSATD_FLAG_AUTOTUNE | PSATD_FLAG_PSTD | PSATD_FLAG_CHECKED) : 0)) != 0)
     return fail(p, PSATD_ERR_INVALID_ARG, "unknown flags");
   if ((d->flags & PSATD_FLAG_PSTD) && d->src == PSATD_SRC_J_RHO)
     return fail(p, PSATD_ERR_INVALID_ARG, "PSTD takes J only (src must be NONE or J)");
@@ -504,8 +504,15 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
 }
 
 psatd_status step_once(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp]) {
-  if (p->tc) return p->tc_bf16 ? run_step<float, 2>(p, in, out) : run_step<float, 1>(p, in, out);
-  return p->f32 ? run_step<float, 0>(p, in, out) : run_step<double, 0>(p, in, out);
+  psatd_status s;
+  if (p->tc) s = p->tc_bf16 ? run_step<float, 2>(p, in, out) : run_step<float, 1>(p, in, out);
+  else s = p->f32 ? run_step<float, 0>(p, in, out) : run_step<double, 0>(p, in, out);
+  if (s == PSATD_OK && (p->d.flags & PSATD_FLAG_CHECKED)) {
+    cudaError_t e = launch_nonfinite(p->f32, out, p->n_out, p->d_off, p->npatch, p->nx * p->ny * p->nz, p->d_err,
+                                     p->st);
+    if (e != cudaSuccess) return cuda_fail(p, e, "non-finite scan launch");
+  }
+  return s;
 }
 
 // Shape checks of the tensor-core variant: every transposing pass and the fused
@@ -850,8 +857,9 @@ static psatd_status plan_create_n(const psatd_desc* desc, void* cuda_stream, int
   }
   if (a == PSATD_OK && p->order > 0)
     a = alloc(p, reinterpret_cast<void**>(&p->cw_d), (size_t)(p->order / 2) * sizeof(double), "stencil weights");
-  if (a == PSATD_OK && p->tc) a = alloc(p, reinterpret_cast<void**>(&p->d_err), sizeof(int), "error word");
-  if (a == PSATD_OK && p->tc) {
+  const bool need_err = p->tc || (desc->flags & PSATD_FLAG_CHECKED);
+  if (a == PSATD_OK && need_err) a = alloc(p, reinterpret_cast<void**>(&p->d_err), sizeof(int), "error word");
+  if (a == PSATD_OK && need_err) {
     cudaError_t e = cudaMemset(p->d_err, 0, sizeof(int));
     if (e != cudaSuccess) a = cuda_fail(p, e, "error word clear");
   }
@@ -1005,7 +1013,9 @@ psatd_status psatd_plan_sync(psatd_plan p) {
     if (e != cudaSuccess) return cuda_fail(p, e, "error word read");
     if (w != 0) {
       cudaMemset(p->d_err, 0, sizeof(int));
-      return fail(p, PSATD_ERR_TIMEOUT, "a tensor-core pass gave up waiting for its MMAs (error word %d)", w);
+      if (w & kErrMmaWait)
+        return fail(p, PSATD_ERR_TIMEOUT, "a tensor-core pass gave up waiting for its MMAs (error word %d)", w);
+      return fail(p, PSATD_ERR_NONFINITE, "NaN or Inf in a step's output since the last sync (error word %d)", w);
     }
   }
   return PSATD_OK;
@@ -1133,6 +1143,8 @@ extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_f
     return fail(nullptr, PSATD_ERR_UNSUPPORTED, "psatd_step_noalloc runs PSATD_FP32 and PSATD_FP64 only");
   if (desc->order != 0)
     return fail(nullptr, PSATD_ERR_UNSUPPORTED, "psatd_step_noalloc runs the collocated exact-k step (order 0) only");
+  if (desc->flags & PSATD_FLAG_CHECKED)
+    return fail(nullptr, PSATD_ERR_UNSUPPORTED, "psatd_step_noalloc has no error word for PSATD_FLAG_CHECKED");
 
   // a plan-shaped descriptor on the stack whose buffers are carved from the array
   psatd_plan_s p;
@@ -1466,6 +1478,20 @@ extern "C" psatd_status psatd_batch_step(psatd_batch b, const psatd_fields* fiel
 }
 
 extern "C" int64_t psatd_batch_cells(psatd_batch b) { return b ? b->total_cells : 0; }
+
+extern "C" psatd_status psatd_batch_sync(psatd_batch b) {
+  if (!b) return fail(nullptr, PSATD_ERR_INVALID_ARG, "batch is NULL");
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "stream synchronise");
+  for (psatd_plan p : b->cls) {
+    psatd_status s = psatd_plan_sync(p);
+    if (s != PSATD_OK) {
+      g_err = p->err;
+      return s;
+    }
+  }
+  return PSATD_OK;
+}
 
 extern "C" psatd_status psatd_batch_destroy(psatd_batch b) {
   if (!b) return PSATD_OK;

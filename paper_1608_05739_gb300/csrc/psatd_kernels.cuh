@@ -65,6 +65,25 @@ struct PushArgs {
   const void* ph[3];    // per axis, exp(-i pi m/n) for m = 0..n/2 (twiddle type)
 };
 
+// Error-word bit of the non-finite scan (PSATD_FLAG_CHECKED); the tensor-core
+// passes use kErrMmaWait (tc_dft.cuh).
+constexpr int kErrNonfinite = 1 << 8;
+
+// Scan `n` elements of each of gridDim.y arrays (at p[y] + off[patch], patches
+// along gridDim.z; off == NULL: one array from p[y]) for NaN / Inf and set
+// kErrNonfinite in *err on a hit (grid-stride over x).
+struct NfPtrs {
+  const void* p[6];
+};
+template <typename R>
+__global__ void k_nonfinite(NfPtrs ptrs, const int64_t* __restrict__ off, int64_t n, int* err) {
+  const R* a = static_cast<const R*>(ptrs.p[blockIdx.y]) + (off ? off[blockIdx.z] : 0);
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(a[i]);
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(err, kErrNonfinite);
+}
+
 // Threads per CTA a transposing pass of length L may use (the register budget
 // of 24 elements per thread halves it for the mixed lengths).
 template <typename R, int L>

@@ -274,4 +274,15 @@ void staggered_weights(int p, double* C) {
   for (int l = 1; l <= h; ++l) C[l - 1] /= s;
 }
 
+cudaError_t launch_nonfinite(bool f32, void* const* out, int n_out, const int64_t* off, int npatch,
+                             int64_t count, int* err, cudaStream_t st) {
+  NfPtrs ptrs{};
+  for (int c = 0; c < n_out && c < 6; ++c) ptrs.p[c] = out[c];
+  const int64_t want = (count + 255) / 256;
+  const dim3 grid((unsigned)(want < 1216 ? (want < 1 ? 1 : want) : 1216), (unsigned)n_out, (unsigned)npatch);
+  if (f32) k_nonfinite<float><<<grid, 256, 0, st>>>(ptrs, off, count, err);
+  else k_nonfinite<double><<<grid, 256, 0, st>>>(ptrs, off, count, err);
+  return cudaGetLastError();
+}
+
 }  // namespace psatd

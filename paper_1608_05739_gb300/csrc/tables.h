@@ -23,4 +23,10 @@ cudaError_t launch_kp_tables(double* kp, void* ph, const double* C, int nl, int 
                              cudaStream_t st);
 // staggered Fornberg weights C_1..C_(p/2) of even order p (host, FP64)
 void staggered_weights(int p, double* C);
+// NaN / Inf scan of the n_out output arrays (PSATD_FLAG_CHECKED): `count`
+// elements per patch, patches at off[0 .. npatch) (off NULL: one array each);
+// sets the non-finite bit in *err.
+cudaError_t launch_nonfinite(bool f32, void* const* out, int n_out, const int64_t* off, int npatch,
+                             int64_t count, int* err, cudaStream_t st);
+
 }  // namespace psatd

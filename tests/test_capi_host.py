@@ -64,7 +64,7 @@ def _create(lib, desc):
     (lambda d: setattr(d, "prec", 2), 2),                  # split-BF16: 64 threads, no 128-row group
     (lambda d: setattr(d, "prec", 9), 1),
     (lambda d: setattr(d, "src", 7), 1),
-    (lambda d: setattr(d, "flags", 4), 1),                 # unknown flag bit
+    (lambda d: setattr(d, "flags", 8), 1),                 # unknown flag bit
     (lambda d: (setattr(d, "layout", 3), setattr(d, "src", 2)), 1),  # TM has no rho-form
     (lambda d: setattr(d, "layout", 9), 1),
 ])
@@ -212,3 +212,15 @@ def test_pstd_flag_rules(lib):
     assert lib.fdtd_step(ct.byref(d), 0, ct.byref(f), ct.byref(s), 1, None) == 1
     with pytest.raises(ValueError):
         capi.make_desc((64, 32), (1.0, 1.0), 0.5, scheme="leapfrog")
+
+
+def test_checked_flag_limits(lib):
+    """PSATD_FLAG_CHECKED is a plan flag: fdtd_step refuses any flag, the
+    allocation-free step has no error word for it; batch sync needs a batch."""
+    d = capi.make_desc((64, 64), (1.0, 1.0), 0.5, layout="te", prec="fp32", src="J", checked=True)
+    f = capi.psatd_fields()
+    s = capi.psatd_sources()
+    assert lib.fdtd_step(ct.byref(d), 0, ct.byref(f), ct.byref(s), 1, None) == 1
+    assert lib.psatd_step_noalloc(ct.byref(d), ct.byref(f), ct.byref(s), 1, None) == 2
+    assert b"CHECKED" in lib.psatd_last_error(None)
+    assert lib.psatd_batch_sync(None) == 1
