@@ -51,6 +51,10 @@
  *     the ABI.  Message of the last failure: psatd_last_error(plan) (or
  *     psatd_last_error(NULL) for failures without a plan, thread-local).
  *   - A plan may be used by one host thread / one stream at a time.
+ *   - Results are deterministic: no data-path atomics or reductions whose order
+ *     varies, so a plan gives the same bits for the same inputs on every run,
+ *     and changing lines per CTA (psatd_plan_set_launch cfg[0..4]) does not
+ *     change them either; the radix schedule (cfg[5]) and the precision do.
  */
 #ifndef PSATD_H
 #define PSATD_H
