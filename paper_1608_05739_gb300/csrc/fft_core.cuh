@@ -495,6 +495,85 @@ __device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[EPT], ExBuf<
   }
 }
 
+// Forward transform with the twiddles of stage s + 1 loaded before stage s's
+// exchange barrier (the barrier and the exchange hide their latency; plain
+// fwd_stage issues them right before the multiply that needs them).  Holds one
+// stage's twiddles in registers (kPF per thread), for kernels with registers to
+// spare (the fused pass at 8 elements per thread).
+template <int L, int EPT>
+struct PFCount {
+  typedef FFTPlan<L, EPT> P;
+  static constexpr int at(int s) { return s >= 1 && s < P::kStages ? (EPT / P::radix(s)) * (P::radix(s) - 1) : 0; }
+  static constexpr int max_from(int s) { return s >= P::kStages ? 1 : (at(s) > max_from(s + 1) ? at(s) : max_from(s + 1)); }
+  static constexpr int value = max_from(1);
+};
+
+template <typename R, int L, int EPT, int S>
+__device__ __forceinline__ void load_stage_tw(typename Types<R>::W (&pf)[PFCount<L, EPT>::value],
+                                              const typename Types<R>::W* __restrict__ base, int t) {
+  typedef FFTPlan<L, EPT> P;
+  if constexpr (S >= 1 && S < P::kStages) {
+    constexpr int RS = P::radix(S), NS = P::span(S), Q = EPT / RS, T = P::kT;
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int q = 0; q < Q; ++q) {
+        const int j = t + q * T;
+        const int k = is_pow2(NS) ? (j & (NS - 1)) : (int)((unsigned)j % (unsigned)NS);
+        const typename Types<R>::W* tws = base + P::tw_off(S) + k;
+#pragma unroll
+        for (int r = 1; r < RS; ++r) pf[q * (RS - 1) + r - 1] = __ldg(&tws[(r - 1) * NS]);
+      }
+    }
+  }
+}
+
+template <typename R, int L, int EPT, int S>
+__device__ __forceinline__ void fwd_stage_pf(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
+                                             typename Types<R>::W (&pf)[PFCount<L, EPT>::value], int t) {
+  typedef typename Types<R>::C C;
+  typedef FFTPlan<L, EPT> P;
+  constexpr int RS = P::radix(S), NS = P::span(S), Q = EPT / RS, T = P::kT;
+  constexpr bool LAST = (S == P::kStages - 1);
+  constexpr int CX = P::swz(S);
+  C* buf = nullptr;
+  if constexpr (!LAST) buf = ex.next();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int j = t + q * T;
+    const int k = is_pow2(NS) ? (j & (NS - 1)) : (int)((unsigned)j % (unsigned)NS);
+    C a[RS];
+#pragma unroll
+    for (int r = 0; r < RS; ++r) a[r] = v[q + r * Q];
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < RS; ++r) a[r] = twmul(a[r], pf[q * (RS - 1) + r - 1]);
+    }
+    butterfly<RS, false>(a);
+    if constexpr (LAST) {
+#pragma unroll
+      for (int r = 0; r < RS; ++r) v[q + r * Q] = a[r];
+    } else {
+      const int base = (j - k) * RS + k;
+#pragma unroll
+      for (int r = 0; r < RS; ++r) buf[sw<CX>(base + r * NS)] = a[r];
+    }
+  }
+  if constexpr (!LAST) {
+    load_stage_tw<R, L, EPT, S + 1>(pf, stage_tw<R>(ex), t);
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < EPT; ++m) v[m] = buf[sw<CX>(t + T * m)];
+  }
+}
+
+template <typename R, int L, int EPT, int... S>
+__device__ __forceinline__ void fft_fwd_pf_seq(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
+                                               int t, std::integer_sequence<int, S...>) {
+  typename Types<R>::W pf[PFCount<L, EPT>::value];
+  load_stage_tw<R, L, EPT, 1>(pf, stage_tw<R>(ex), t);
+  (fwd_stage_pf<R, L, EPT, S>(v, ex, pf, t), ...);
+}
+
 template <typename R, int L, int EPT, int TC, int... S>
 __device__ __forceinline__ void fft_fwd_seq(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
                                             const typename Types<R>::W* tw, int t, TcCtx* tc,
@@ -519,6 +598,69 @@ __device__ __forceinline__ void block_fft_fwd(typename Types<R>::C (&v)[EPT], Ex
   static_assert(!TC || sizeof(R) == 4, "tensor-core stages take float data");
   fft_fwd_seq<R, L, EPT, TC>(v, ex, tw, t, tc, std::make_integer_sequence<int, FFTPlan<L, EPT>::kStages>{});
 }
+// Adjoint of fwd_stage_pf's stage S: the stage's twiddles are loaded before its
+// exchange barrier (they are applied after the butterfly).
+template <typename R, int L, int EPT, int S>
+__device__ __forceinline__ void inv_stage_pf(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
+                                             typename Types<R>::W (&pf)[PFCount<L, EPT>::value], int t) {
+  typedef typename Types<R>::C C;
+  typedef FFTPlan<L, EPT> P;
+  constexpr int RS = P::radix(S), NS = P::span(S), Q = EPT / RS, T = P::kT;
+  constexpr bool FIRST = (S == P::kStages - 1);
+  constexpr int CX = P::swz(S);
+  C* buf = nullptr;
+  if constexpr (!FIRST) {
+    buf = ex.next();
+#pragma unroll
+    for (int m = 0; m < EPT; ++m) buf[sw<CX>(t + T * m)] = v[m];
+  }
+  load_stage_tw<R, L, EPT, S>(pf, stage_tw<R>(ex), t);
+  if constexpr (!FIRST) __syncthreads();
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int j = t + q * T;
+    const int k = is_pow2(NS) ? (j & (NS - 1)) : (int)((unsigned)j % (unsigned)NS);
+    C a[RS];
+    if constexpr (FIRST) {
+#pragma unroll
+      for (int r = 0; r < RS; ++r) a[r] = v[q + r * Q];
+    } else {
+      const int base = (j - k) * RS + k;
+#pragma unroll
+      for (int r = 0; r < RS; ++r) a[r] = buf[sw<CX>(base + r * NS)];
+    }
+    butterfly<RS, true>(a);
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < RS; ++r) a[r] = twmul_conj(a[r], pf[q * (RS - 1) + r - 1]);
+    }
+#pragma unroll
+    for (int r = 0; r < RS; ++r) v[q + r * Q] = a[r];
+  }
+}
+
+template <typename R, int L, int EPT, int... S>
+__device__ __forceinline__ void fft_inv_pf_seq(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
+                                               int t, std::integer_sequence<int, S...>) {
+  typename Types<R>::W pf[PFCount<L, EPT>::value];
+  (inv_stage_pf<R, L, EPT, FFTPlan<L, EPT>::kStages - 1 - S>(v, ex, pf, t), ...);
+}
+
+// block_fft_inv with each stage's twiddles loaded before its exchange barrier.
+template <typename R, int L, int EPT>
+__device__ __forceinline__ void block_fft_inv_pf(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
+                                                 int t) {
+  fft_inv_pf_seq<R, L, EPT>(v, ex, t, std::make_integer_sequence<int, FFTPlan<L, EPT>::kStages>{});
+}
+
+// block_fft_fwd with next-stage twiddle prefetch (no tensor-core stages); the
+// twiddle table is read through ex.twslot, which must be visible before the call.
+template <typename R, int L, int EPT>
+__device__ __forceinline__ void block_fft_fwd_pf(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
+                                                 int t) {
+  fft_fwd_pf_seq<R, L, EPT>(v, ex, t, std::make_integer_sequence<int, FFTPlan<L, EPT>::kStages>{});
+}
+
 // Unnormalised inverse DFT (adjoint of block_fft_fwd).
 template <typename R, int L, int EPT, int TC = 0>
 __device__ __forceinline__ void block_fft_inv(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,

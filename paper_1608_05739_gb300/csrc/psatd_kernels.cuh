@@ -752,7 +752,10 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
     ExBuf<C> ex{{sl, bufB}, 0, &twslot, false};
     if constexpr (TC)
       if (a3_slot) tc.a_tile3 = smem_u32(sl);
-    block_fft_fwd<R, L, EPT, TC>(v, ex, tw, t, &tc);
+    if constexpr (TC == 0 && EPT == 8)
+      block_fft_fwd_pf<R, L, EPT>(v, ex, t);
+    else
+      block_fft_fwd<R, L, EPT, TC>(v, ex, tw, t, &tc);
 #pragma unroll
     for (int m = 0; m < EPT; ++m) sl[sw<CXL>(t + T * m)] = v[m];
   }
@@ -774,7 +777,10 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
     ExBuf<C> ex{{sl, bufB}, 0, &twslot, false};
     if constexpr (TC)
       if (a3_slot) tc.a_tile3 = smem_u32(sl);
-    block_fft_inv<R, L, EPT, TC>(v, ex, tw, t, &tc);
+    if constexpr (TC == 0 && EPT == 8)
+      block_fft_inv_pf<R, L, EPT>(v, ex, t);
+    else
+      block_fft_inv<R, L, EPT, TC>(v, ex, tw, t, &tc);
     if (valid) {
       C* dst = spec + c * a.cs + (int64_t)line * L;
 #pragma unroll
