@@ -752,7 +752,7 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
     ExBuf<C> ex{{sl, bufB}, 0, &twslot, false};
     if constexpr (TC)
       if (a3_slot) tc.a_tile3 = smem_u32(sl);
-    if constexpr (TC == 0 && EPT == 8)
+    if constexpr (TC == 0 && (EPT == 8 || EPT == 12))
       block_fft_fwd_pf<R, L, EPT>(v, ex, t);
     else
       block_fft_fwd<R, L, EPT, TC>(v, ex, tw, t, &tc);
@@ -777,7 +777,7 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
     ExBuf<C> ex{{sl, bufB}, 0, &twslot, false};
     if constexpr (TC)
       if (a3_slot) tc.a_tile3 = smem_u32(sl);
-    if constexpr (TC == 0 && EPT == 8)
+    if constexpr (TC == 0 && (EPT == 8 || EPT == 12))
       block_fft_inv_pf<R, L, EPT>(v, ex, t);
     else
       block_fft_inv<R, L, EPT, TC>(v, ex, tw, t, &tc);
