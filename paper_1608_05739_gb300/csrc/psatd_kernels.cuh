@@ -628,14 +628,19 @@ __device__ __forceinline__ void push_line_modes(typename Types<R>::C* st, const 
   typedef FFTPlan<L, EPT> P;
   constexpr int T = P::kT;
   constexpr int CXL = P::kLastCX;
+  // coefficient pairs software-pipelined: the next pair's loads are issued
+  // before the current pair's update
+  auto coef = [&](int l) -> Coef<R> {
+    if constexpr (!PSTD) return trow[(l <= L / 2) ? l : L - l];  // |m| along the line axis
+    else return Coef<R>{};
+  };
+  Coef<R> qn[2] = {coef(t), coef(t + T)};
 #pragma unroll 1
   for (int m0 = 0; m0 < EPT; m0 += 2) {
-    Coef<R> q[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int l = t + T * (m0 + h);
-      if constexpr (!PSTD) q[h] = trow[(l <= L / 2) ? l : L - l];  // |m| along the line axis
-      else q[h] = Coef<R>{};
+    const Coef<R> q[2] = {qn[0], qn[1]};
+    if (m0 + 2 < EPT) {
+      qn[0] = coef(t + T * (m0 + 2));
+      qn[1] = coef(t + T * (m0 + 3));
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
