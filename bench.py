@@ -334,6 +334,8 @@ def main():
                          "split-BF16 radix-16 stages (the others are timed too, under 'other_precision')")
     ap.add_argument("--no-side-precision", action="store_true", help="skip timing the other precision")
     ap.add_argument("--no-comparator", action="store_true", help="skip timing the cuFFT comparator")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the end-to-end legs (profiling runs: only the timed steps' kernels)")
     ap.add_argument("--workload", default="te2048",
                     choices=["te2048", "3d256", "3d512", "fdtd-yee", "fdtd-ckc", "batch512", "local", "cost3d"],
                     help="te2048 (default) is the metric's configuration; the others are side measurements")
@@ -414,8 +416,10 @@ def main():
         return NX * NY * e2e_steps / (e0.elapsed_time(e1) * 1e-3)
 
     plan.set_timing(False)
-    e2e_value = e2e_run(False)
-    e2e_staged = e2e_run(True)
+    e2e_value = e2e_staged = None
+    if not args.no_e2e:
+        e2e_value = e2e_run(False)
+        e2e_staged = e2e_run(True)
 
     comparator = None
     if rank == 0 and not args.no_comparator:
