@@ -263,7 +263,7 @@ class Plan:
 class Batch:
     """A batch of independent 2D periodic patches (psatd_batch_create) on a CUDA stream.
 
-    ``sizes`` = [(nx, ny), ...] (powers of two).  Fields and sources are passed
+    ``sizes`` = [(nx, ny), ...] (sizes as for Plan).  Fields and sources are passed
     per component as one contiguous CUDA tensor of ``total`` elements holding
     the patches back to back, patch i being its (ny_i, nx_i) row-major block.
     """

@@ -1,12 +1,13 @@
 // fft_core.cuh -- register/shared-memory Stockham FFT building blocks for sm_103a.
 //
-// A length-L transform (L a power of two, 8 <= L <= 4096) is computed by T = L/8
-// threads; thread t holds the eight elements x[t + T*m], m = 0..7, in registers
-// before and after the transform (natural order in both domains).  Stages:
-// one radix-2 or radix-4 stage first (when log2 L is not a multiple of 3),
-// then radix-8 stages.  Between stages the data go through shared memory in
-// rows of 16 elements whose columns are XOR-swizzled per exchange (free of
-// bank conflicts for each stage's write pattern); two buffers alternate.
+// A length-L transform is computed by T = L/EPT threads; thread t holds the EPT
+// elements x[t + T*m], m < EPT, in registers before and after the transform
+// (natural order in both domains).  Lengths: powers of two 8..4096 with 8 or
+// 16 elements per thread (a radix-2/4/8 first stage, then radix-EPT stages), or
+// 3 * 2^k, 48..3072, with 24 (radix 3, then 2/4, then 8) or 12 (prime-factor
+// radix 12, then 2, then 4) -- FFTPlan below.  Between stages the data go
+// through shared memory in rows of 16 elements whose columns are XOR-swizzled
+// per exchange (free of bank conflicts for each stage's write pattern).
 //
 // Forward = Stockham decimation in time: stage (radix R, span Ns) multiplies
 // input r of butterfly j by w^(r*k), w = exp(-2 pi i/(Ns R)), k = j mod Ns,

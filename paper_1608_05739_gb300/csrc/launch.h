@@ -1,7 +1,7 @@
-// launch.h -- host-side launchers of the PSATD pass kernels, one set per
-// precision (kernels_f32.cu, kernels_f64.cu).  L is the transform length along
-// the pass axis (power of two, 8..4096); every launcher returns the launch's
-// cudaError_t.
+// launch.h -- host-side launchers of the PSATD pass kernels, instantiated per
+// precision and variant in the rows_* / push_* translation units.  L is the
+// transform length along the pass axis (a power of two 8..4096, or 3 * 2^k for
+// the *3 launchers); every launcher returns the launch's cudaError_t.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

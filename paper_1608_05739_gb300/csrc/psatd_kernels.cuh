@@ -1,5 +1,5 @@
 // psatd_kernels.cuh -- the PSATD step's pass kernels (templates; instantiated
-// per precision in kernels_f32.cu / kernels_f64.cu).
+// per precision and variant by the rows_* / push_* translation units).
 //
 // Data flow of one step (2D: passes 1, 3, 5; 3D: passes 1-5):
 //   1  k_fwd_T<R2C>  x-rows of every input array -> R2C -> half spectrum,
@@ -10,7 +10,9 @@
 //                    of the E and B components, in place
 //   4  k_inv_T<C2C>  (3D) inverse y-lines, read z-contiguous
 //   5  k_inv_T<C2R>  inverse x-rows (C2R) into the caller's E and B arrays
-// A CTA handles TB lines (blockDim.y) of T = L/8 threads each (blockDim.x).
+// A CTA handles TB lines (blockDim.y) of T = L/EPT threads each (blockDim.x).
+// Sources without a plan-time role (the optional NaN / Inf scan of the outputs)
+// follow the passes: k_nonfinite.
 #pragma once
 
 #include "fft_core.cuh"
