@@ -128,3 +128,37 @@ def test_large_3d_sampled_modes(prec, tol):
     print("%s: sampled modes, max error / max(|mode|, rms) = %.2e (mode %s), max |mode|/rms = %.0f"
           % (prec, err.max(), modes[int(np.argmax(err))], size.max() / rms))
     assert err.max() < tol
+
+
+def test_config2_full_size_2000_steps_within_1e5():
+    """The bench workload itself (2048^2 TE FP32, dx = lambda/64, c dt = dx/sqrt(2),
+    current sheet J_y(x, t), one psatd_step call per step) run for 2000 steps: every
+    row of the GPU field against the FP64 oracle within the stated FP32 bound 1e-5
+    (relative L2).  The drive is uniform in y and the fields start at zero, so only
+    ky = 0 modes are ever excited and the exact solution is the same on every row:
+    the oracle runs the identical per-mode update on a 2048 x 8 grid."""
+    import torch
+    from analytic import rel_l2
+    ensure_lib()
+    nx, ny = 2048, 2048
+    dx = 1.0 / 64
+    d, dt = (dx, dx), dx / math.sqrt(2.0)
+    steps = 2000
+    plan = capi.Plan((nx, ny), d, dt, layout="te", prec="fp32", src="J")
+    Ex, Ey, Bz, Jx = (torch.zeros(ny, nx, device="cuda") for _ in range(4))
+    small = (8, nx)
+    E = np.zeros((3,) + small)
+    B = np.zeros((3,) + small)
+    for n in range(steps):
+        J = synth.current_sheet(small, d, (n + 0.5) * dt, lam=1.0, a=0.9, w=2.0 * dx)
+        J = J.astype(np.float32).astype(np.float64)
+        Jy = torch.from_numpy(J[1][0]).float().to("cuda").expand(ny, nx).contiguous()
+        plan.step([Ex, Ey, None], [None, None, Bz], [Jx, Jy, None])
+        E, B = orc.psatd_step(E, B, J, d=d, dt=dt, form="J")
+    plan.sync()
+    plan.destroy()
+    got = np.concatenate([t.double().cpu().numpy().ravel() for t in (Ex, Ey, Bz)])
+    want = np.concatenate([np.broadcast_to(a[0], (ny, nx)).ravel() for a in (E[0], E[1], B[2])])
+    err = rel_l2(got, want)
+    print("2048^2 TE FP32, 2000 steps: rel. L2 vs the oracle %.2e" % err)
+    assert err < 1e-5, err
