@@ -265,7 +265,7 @@ int row_maxthr(int L, bool f32) { return row_ept(L) == 24 || !f32 ? 256 : 512; }
 // of nb; at most 16 lines: the row-dependent XOR of the transposed store
 // spreads 16 lines over the banks, 32 would read one bank twice; the
 // tensor-core variant goes to 32 where it needs that for 128 threads)
-int pick_log_tb(int L, int64_t nb, bool f32, bool tc = false) {
+int pick_log_tb_raw(int L, int64_t nb, bool f32, bool tc) {
   const int T = L / row_ept(L);
   const int maxthr = row_maxthr(L, f32);
   int tb = 1;
@@ -276,11 +276,21 @@ int pick_log_tb(int L, int64_t nb, bool f32, bool tc = false) {
   while ((1 << lg) < tb) ++lg;
   return lg;
 }
-// lines per CTA of an inverse transposing pass: half the forward pass's (the
-// autotuner measured that faster at 2048^2 x, 256^3 x and y, and 512^2 x: the
-// gathered bin pairs of fewer lines per CTA), keeping the tensor-core minimum
+// lines per CTA of a forward transposing pass: as above, but at most 8 where a
+// line's threads are whole warps (T a multiple of 32): the lines then
+// synchronise only their own warps between stages (named barriers 1..8), which
+// measured faster than 16 lines on one CTA-wide barrier (1024^2 x: 23.0 -> 21.0 us)
+int pick_log_tb(int L, int64_t nb, bool f32, bool tc = false) {
+  const int lg = pick_log_tb_raw(L, nb, f32, tc);
+  const int T = L / row_ept(L);
+  return (!tc && T % 32 == 0 && lg > 3) ? 3 : lg;
+}
+// lines per CTA of an inverse transposing pass: half the forward rule's value
+// before the cap above (the autotuner measured that faster at 2048^2 x, 1024^2 x,
+// 256^3 x and y: the gathered bin pairs of fewer lines per CTA), keeping the
+// tensor-core minimum
 int pick_log_tb_inv(int L, int64_t nb, bool f32, bool tc = false) {
-  const int lg = pick_log_tb(L, nb, f32, tc);
+  const int lg = pick_log_tb_raw(L, nb, f32, tc);
   const int T = L / row_ept(L);
   if (lg == 0 || (tc && (T << (lg - 1)) < 128)) return lg;
   return lg - 1;

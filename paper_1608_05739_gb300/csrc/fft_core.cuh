@@ -388,16 +388,26 @@ __device__ __forceinline__ int sw(int i) { return i ^ (((i >> 4) * CX) & 15); }
 // transform in a kernel into registers).
 // With b[0] == b[1] (one buffer, `single`), next() adds the barrier that lets
 // the previous exchange's reads finish before the buffer is overwritten.
+// The exchange barrier: the whole CTA (bar_n == 0), or, when each line's
+// transform is private to its own warps, the named barrier bar_id over the
+// line's bar_n threads (a multiple of 32), so that lines do not wait for one
+// another between stages.
 template <class C>
 struct ExBuf {
   C* b[2];
   int cur;
   const void* const* twslot;
   bool single;
+  int bar_id = 0;
+  int bar_n = 0;
+  __device__ __forceinline__ void sync() const {
+    if (bar_n) asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(bar_n) : "memory");
+    else __syncthreads();
+  }
   __device__ __forceinline__ C* next() {
     C* p = b[cur];
     cur ^= 1;
-    if (single) __syncthreads();
+    if (single) sync();
     return p;
   }
 };
@@ -448,7 +458,7 @@ __device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[EPT], ExBuf<
     }
   }
   if constexpr (!LAST) {
-    __syncthreads();
+    ex.sync();
 #pragma unroll
     for (int m = 0; m < EPT; ++m) v[m] = buf[sw<CX>(t + T * m)];
   }
@@ -468,7 +478,7 @@ __device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[EPT], ExBuf<
     buf = ex.next();
 #pragma unroll
     for (int m = 0; m < EPT; ++m) buf[sw<CX>(t + T * m)] = v[m];
-    __syncthreads();
+    ex.sync();
   }
   asm volatile("" : "+r"(t)::"memory");  // stage boundary (see fwd_stage)
 #pragma unroll
@@ -561,7 +571,7 @@ __device__ __forceinline__ void fwd_stage_pf(typename Types<R>::C (&v)[EPT], ExB
   }
   if constexpr (!LAST) {
     load_stage_tw<R, L, EPT, S + 1>(pf, stage_tw<R>(ex), t);
-    __syncthreads();
+    ex.sync();
 #pragma unroll
     for (int m = 0; m < EPT; ++m) v[m] = buf[sw<CX>(t + T * m)];
   }
@@ -616,7 +626,7 @@ __device__ __forceinline__ void inv_stage_pf(typename Types<R>::C (&v)[EPT], ExB
     for (int m = 0; m < EPT; ++m) buf[sw<CX>(t + T * m)] = v[m];
   }
   load_stage_tw<R, L, EPT, S>(pf, stage_tw<R>(ex), t);
-  if constexpr (!FIRST) __syncthreads();
+  if constexpr (!FIRST) ex.sync();
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int j = t + q * T;

@@ -120,6 +120,11 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_fwd_T(LineIO io,
     tc_setup(tc, smem_raw, io.gmat, smem_u32(smem), io.err, TC == 2,
              smem_u32(smem + (R2C ? TB * L : L * (TB + 1))));
   ExBuf<C> ex{{smem + g * L, smem + g * L}, 0, &twslot, true};  // one exchange buffer per line
+  if constexpr (!TC && T % 32 == 0)
+    if (TB <= 8) {  // each line's warps synchronise among themselves between stages
+      ex.bar_id = 1 + g;
+      ex.bar_n = T;
+    }
 
   C v[EPT];
   {
@@ -132,7 +137,8 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_fwd_T(LineIO io,
 #pragma unroll
     for (int m = 0; m < EPT; ++m) v[m] = row[t + T * m];
   }
-  if constexpr (P::kStages == 1) __syncthreads();  // twslot visible (else the first exchange's barrier)
+  // twslot visible to every line (else the first exchange barrier publishes it, when it spans the CTA)
+  if (P::kStages == 1 || ex.bar_n) __syncthreads();
   block_fft_fwd<R, L, EPT, TC>(v, ex, tw, t, &tc);
 
   if constexpr (R2C) {
@@ -294,6 +300,11 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_inv_T(LineIO io,
     __syncthreads();
   }
   ExBuf<C> ex{{smem + g * L, smem + g * L}, 0, &twslot, true};  // one exchange buffer per line
+  if constexpr (!TC && T % 32 == 0)
+    if (TB <= 8) {  // line-private stages: the line's own warps synchronise
+      ex.bar_id = 1 + g;
+      ex.bar_n = T;
+    }
   block_fft_inv<R, L, EPT, TC>(v, ex, tw, t, &tc);
   C* row;
   const int64_t o0 = out_off ? out_off[a0] : a0 * out_sa0;  // per-patch offsets of a batch
