@@ -276,14 +276,16 @@ int pick_log_tb_raw(int L, int64_t nb, bool f32, bool tc) {
   while ((1 << lg) < tb) ++lg;
   return lg;
 }
-// lines per CTA of a forward transposing pass: as above, but at most 8 where a
-// line's threads are whole warps (T a multiple of 32): the lines then
-// synchronise only their own warps between stages (named barriers 1..8), which
-// measured faster than 16 lines on one CTA-wide barrier (1024^2 x: 23.0 -> 21.0 us)
-int pick_log_tb(int L, int64_t nb, bool f32, bool tc = false) {
+// lines per CTA of a forward transposing pass: as above; for the x rows (R2C,
+// `rows`) at most 8 where a line's threads are whole warps (T a multiple of 32):
+// the lines then synchronise only their own warps between stages (named barriers
+// 1..8), measured faster than 16 lines on one CTA-wide barrier (1024^2 x: 23.0 ->
+// 21.0 us).  The C2C y pass keeps 16 (its tile store writes 128-byte runs of z;
+// 8 lines measured slower at 512 x 512 x 1024: 5.01 -> 5.42 ms).
+int pick_log_tb(int L, int64_t nb, bool f32, bool tc = false, bool rows = false) {
   const int lg = pick_log_tb_raw(L, nb, f32, tc);
   const int T = L / row_ept(L);
-  return (!tc && T % 32 == 0 && lg > 3) ? 3 : lg;
+  return (rows && !tc && T % 32 == 0 && lg > 3) ? 3 : lg;
 }
 // lines per CTA of an inverse transposing pass: half the forward rule's value
 // before the cap above (the autotuner measured that faster at 2048^2 x, 1024^2 x,
@@ -388,7 +390,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
   // pass 1: x rows (R2C), b = y -> spec1 [c][kx][z][y] (3D) / [c][patch][kx][y] (2D)
   {
     PassGeom g;
-    g.log_tb = p->cfg_log_tb[0] >= 0 ? p->cfg_log_tb[0] : pick_log_tb(Lx, ny, p->f32, TC);
+    g.log_tb = p->cfg_log_tb[0] >= 0 ? p->cfg_log_tb[0] : pick_log_tb(Lx, ny, p->f32, TC, true);
     g.grid = dim3((unsigned)(ny >> g.log_tb), (unsigned)na0, (unsigned)p->n_in);
     g.smem = tail + tpass_smem(Lx, g.log_tb, 0, csz) + tc_a3_bytes(p, (Lx / row_ept(Lx)) << g.log_tb);
     for (int c = 0; c < p->n_in; ++c) {
@@ -986,7 +988,7 @@ psatd_status psatd_plan_get_launch(psatd_plan p, int32_t cfg[6]) {
   const int64_t nlines = p->ndim == 3 ? p->nxh * p->ny : p->nxh * p->npatch;
   const int Ll = (int)(p->ndim == 3 ? p->nz : p->ny);
   const bool tc = p->tc;
-  const int dflt[4] = {pick_log_tb(Lx, p->ny, p->f32, tc),
+  const int dflt[4] = {pick_log_tb(Lx, p->ny, p->f32, tc, true),
                        p->ndim == 3 ? pick_log_tb((int)p->ny, p->nz, p->f32, tc) : -1,
                        p->ndim == 3 ? pick_log_tb_inv((int)p->ny, p->nz, p->f32, tc) : -1,
                        pick_log_tb_inv(Lx, p->ny, p->f32, tc)};
