@@ -19,6 +19,11 @@ Particle-In-Cell codes") says the solvers compute:
 * ``dispersion`` -- the vacuum refractive index of each solver (Table 1), the
                     Snell-Descartes refraction toy model (Sec. IV.A, Eq. Snell)
                     and the closed forms of Appendix A.
+* ``local``      -- the local-FFT decomposition (Sec. II.A.3): patches with
+                    guard cells refreshed from their neighbours, each advanced as
+                    a periodic domain of its own.
+``psatd`` also holds the staggered order-p variant (Table 1 row PSATD-p) and the
+PSTD scheme (Table 1 row PSTD).
 
 It shares no code with the CUDA path.  All floating point is FP64 (numpy).
 """
