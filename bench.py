@@ -337,7 +337,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the end-to-end legs (profiling runs: only the timed steps' kernels)")
     ap.add_argument("--workload", default="te2048",
-                    choices=["te2048", "3d256", "3d512", "fdtd-yee", "fdtd-ckc", "batch512", "local", "cost3d"],
+                    choices=["te2048", "3d256", "3d512", "fdtd-yee", "fdtd-ckc", "batch512", "local", "cost3d",
+                             "small128"],
                     help="te2048 (default) is the metric's configuration; the others are side measurements")
     args = ap.parse_args()
     world, rank, local = dist_setup()
@@ -680,6 +681,47 @@ def run_side_workload(args):
                                         "pstd (9 x step cost ratio)": 9.0 * res["pstd"] / res["psatd_order128"]},
             "paper_time_factors": {"ckc": 16, "yee": 28, "pstd": 9},
             "clocks": clk, "gpu_launches": None,
+        })
+    elif args.workload == "small128":
+        # the small FP64 case: 2D 128^2, six components, vacuum, 8 on-grid plane waves, c dt = 0.5 dx,
+        # PSATD and Yee; the whole state (3 MB) stays in L2, so these are L2-resident times, not an
+        # HBM measurement (no flush between steps; the run is a sequence of steps, as in use)
+        n = 128
+        waves = synth.plane_waves((n, n), 8, seed=1608)
+        E0, B0 = synth.plane_wave_fields(waves, (n, n), (1.0, 1.0))
+        res = {}
+        clk = None
+        for scheme in ("psatd", "yee"):
+            E = [torch.from_numpy(E0[i]).to(dev, torch.float64) for i in range(3)]
+            B = [torch.from_numpy(B0[i]).to(dev, torch.float64) for i in range(3)]
+            if scheme == "psatd":
+                plan = capi.Plan((n, n), (1.0, 1.0), 0.5, layout="2d6", prec="fp64", src="none", stream=stream)
+                step = lambda i: plan.step(E, B)
+            else:
+                step = lambda i: capi.fdtd_step((n, n), (1.0, 1.0), 0.5, E, B, scheme="yee", layout="2d6",
+                                                prec="fp64", stream=stream)
+            for i in range(args.warmup):
+                step(i)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            clocks = ClockSampler(0)
+            clocks.start()
+            time.sleep(0.3)
+            e0.record(stream)
+            for i in range(args.steps):
+                step(i)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            clk = clocks.stop()
+            res[scheme] = e0.elapsed_time(e1) / args.steps
+            if scheme == "psatd":
+                plan.destroy()
+        line.update({
+            "value": n * n / (res["psatd"] * 1e-3), "ms_per_step": res["psatd"], "dtype": "f64",
+            "config": {"workload": "2D 128^2 FP64 six-component vacuum, 8 on-grid plane waves, c dt = 0.5 dx",
+                       "l2": "L2-resident (3 MB of state): a latency/launch-bound time, not an HBM figure"},
+            "ms_per_step_yee": res["yee"], "clocks": clk, "gpu_launches": 3 * args.steps,
         })
     elif args.workload == "local":
         # the paper's decomposition (Sec. II.A.3): a 3840 x 1920 TE grid as 16 x 8 patches of 240^2
