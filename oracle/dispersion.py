@@ -27,6 +27,11 @@ is also the propagation angle arctan(k_z/k_x) of Fig. 2.
 Appendix A: eta (here c dt/dx; the appendix's "dx/(c dt)" is read as a typo,
 the only reading consistent with its equations), beta' = -4 beta, the
 angle-tuned coefficients and the Nyquist stability bound.
+
+Parity unpinned: the PSTD cut-off harmonic at theta_i = 80 deg (Sec. IV.B).
+The paper's PIC runs show it near harmonic 17; this model, at order 128 and a
+time step the paper does not fix, only brackets it (the test checks a range,
+not a value).
 """
 from __future__ import annotations
 
