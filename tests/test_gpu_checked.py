@@ -62,3 +62,20 @@ def test_checked_batch_reports_the_bad_patch_class():
         b.sync()
     assert ei.value.status == NONFINITE
     b.destroy()
+
+
+def test_allocation_failure_is_reported_and_leaves_no_plan():
+    """A plan whose spectral scratch cannot fit in HBM (4096^3 cells, about 1.6 TB)
+    fails at plan creation with PSATD_ERR_OOM (a host-side failure: cudaMalloc
+    returns an error, nothing is launched), and a normal plan works afterwards."""
+    ensure_lib()
+    with pytest.raises(capi.PsatdError) as ei:
+        capi.Plan((4096, 4096, 4096), (1.0, 1.0, 1.0), 0.5, layout="3d6", prec="fp32", src="none")
+    assert ei.value.status == 3 and "cudaMalloc" in str(ei.value)
+    free0 = torch.cuda.mem_get_info()[0]
+    a = _te((64, 128), 9)
+    p = capi.Plan((128, 64), (1.0, 1.0), 0.5, layout="te", prec="fp32", src="J")
+    p.step([a[0], a[1], None], [None, None, a[2]], [a[3], a[4], None])
+    p.sync()
+    p.destroy()
+    assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)   # nothing of the failed plan is held
