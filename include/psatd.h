@@ -263,13 +263,16 @@ psatd_status fdtd_step(const psatd_desc* desc, int32_t scheme, const psatd_field
  * (Sec. II.A.3).  A batch holds npatch independent periodic 2D patches sharing
  * the base descriptor's layout (2D6, TE or TM), precision, source form, cell
  * sizes, dt, c and eps0; patch i has n[2i] x n[2i+1] cells (sizes as for
- * psatd_plan_create: powers of two, or 3 * 2^k lengths in FP32).  Fields and sources of all patches are packed
- * per component: one array per component holding patch 0, patch 1, ... back
- * to back (patch i at element offset sum_{j<i} n[2j] n[2j+1]).
- * Patches of equal size form a class advanced with one launch per pass; a
- * call with nsteps > 1 on a non-default stream records one step of all
- * classes into a CUDA graph (re-recorded when the field/source pointers
- * change) and replays it nsteps times.  Guard cells are part of each patch
+ * psatd_plan_create: powers of two, or 3 * 2^k lengths in FP32).  Fields and
+ * sources of all patches are packed per component: one array per component
+ * holding patch 0, patch 1, ... back to back (patch i at element offset
+ * sum_{j<i} n[2j] n[2j+1]).
+ * Patches of equal size form a class advanced with one launch per pass; each
+ * step forks from the batch's stream into up to four internal streams that
+ * run the classes side by side, and joins back.  A call with nsteps > 1 on a
+ * non-default stream records one step of all classes into a CUDA graph
+ * (re-recorded when the field/source pointers change) and replays it nsteps
+ * times.  Guard cells are part of each patch
  * (the caller fills them; no exchange between patches is done here).      */
 typedef struct psatd_batch_s* psatd_batch;
 
