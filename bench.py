@@ -193,8 +193,10 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(seconds):
-    """Time the oracle as it stands on a bounded sample of the workload."""
+def cpu_baseline(seconds, with_state=False):
+    """Time the oracle as it stands on a bounded sample of the workload (the first
+    steps of the run from zero fields); with_state: also return the oracle's fields
+    after those steps and their count, for the accuracy check of the same steps."""
     from oracle import psatd as orc
     dx = 1.0 / LAM_CELLS
     dt = dx / math.sqrt(2.0)
@@ -211,9 +213,10 @@ def cpu_baseline(seconds):
         el = time.perf_counter() - t0
         if el > seconds or steps >= 50:
             break
-    return {"value": NX * NY * steps / el, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
-            "sample": "%d FP64 oracle steps of the 2048^2 TE workload (numpy pocketfft, one thread), %.1f s"
-                      % (steps, el)}
+    out = {"value": NX * NY * steps / el, "unit": "cell-steps/s", "cores": 1, "kind": "oracle",
+           "sample": "%d FP64 oracle steps of the 2048^2 TE workload (numpy pocketfft, one thread), %.1f s"
+                     % (steps, el)}
+    return (out, E, B, steps) if with_state else out
 
 
 def time_te2048(capi, torch, prec, args, dev, dt, dx, Jy_all, flush, stream, world, sample_clocks):
@@ -485,7 +488,22 @@ def main():
         if side is not None:
             line["other_precision"] = side
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+            cb, Eo, Bo, nst = cpu_baseline(args.cpu_seconds, with_state=True)
+            line["cpu_baseline"] = cb
+            # the same first steps on the GPU path at the headline precision, against the oracle
+            p2 = capi.Plan((NX, NY), (dx, dx), dt, layout="te", prec=args.precision, src="J", stream=stream)
+            G = [torch.zeros(NY, NX, device=dev) for _ in range(4)]
+            for n in range(nst):
+                Jn = torch.from_numpy(sheet_profile(n, dt, dx)).float().to(dev).expand(NY, NX).contiguous()
+                p2.step([G[0], G[1], None], [None, None, G[2]], [G[3], Jn, None])
+            p2.sync()
+            p2.destroy()
+            got = np.concatenate([G[i].double().cpu().numpy().ravel() for i in range(3)])
+            want = np.concatenate([Eo[0].ravel(), Eo[1].ravel(), Bo[2].ravel()])
+            line["rel_l2_vs_oracle"] = {
+                "value": float(np.linalg.norm(got - want) / np.linalg.norm(want)), "steps": nst,
+                "what": "E, B after the oracle sample's steps (same J, zero initial fields), GPU at the line's "
+                        "precision vs the FP64 oracle; relative L2 over Ex, Ey, Bz"}
         print(json.dumps(line), flush=True)
     plan.destroy()
     if world > 1:
