@@ -124,6 +124,14 @@ typedef enum { PSATD_FDTD_YEE = 0, PSATD_FDTD_CKC = 1 } psatd_fdtd_scheme;
  * PSATD_ERR_NONFINITE (and clears it).  PSATD plans, batches and local
  * decompositions; psatd_step_noalloc and fdtd_step refuse it. */
 #define PSATD_FLAG_CHECKED 4
+/* PSATD_FLAG_TEST_STALL_MMA: a test hook of the failure path, for
+ * PSATD_MIXED_FP16 / _BF16 plans only (INVALID_ARG otherwise).  The
+ * tensor-core passes issue no MMA, so the first completion wait of every CTA
+ * runs out after a short poll limit; the CTA then stops using the tensor
+ * cores, frees its TMEM and finishes, and psatd_plan_sync returns
+ * PSATD_ERR_TIMEOUT.  The step's output is not valid.  Never set it in
+ * production use. */
+#define PSATD_FLAG_TEST_STALL_MMA 8
 
 /* Problem statement (the paper's arguments: grid sizes, cell sizes, dt, c, eps0). */
 typedef struct {
@@ -225,9 +233,10 @@ psatd_status psatd_step(psatd_plan plan, const psatd_fields* fields,
                         const psatd_sources* sources, int32_t nsteps);
 
 /* Synchronise the plan's stream and report any asynchronous CUDA error, or
- * PSATD_ERR_TIMEOUT when a tensor-core pass (PSATD_MIXED_FP16) gave up a
- * bounded wait for its MMAs since the last sync (the step's output is then
- * not valid), or PSATD_ERR_NONFINITE when a checked plan (PSATD_FLAG_CHECKED)
+ * PSATD_ERR_TIMEOUT when a tensor-core pass (PSATD_MIXED_FP16 / _BF16) gave up
+ * a bounded wait for its MMAs since the last sync (the CTA then skipped its
+ * remaining tensor-core stages and freed its TMEM; the step's output is not
+ * valid), or PSATD_ERR_NONFINITE when a checked plan (PSATD_FLAG_CHECKED)
  * saw NaN or Inf in a step's output since the last sync; the word is cleared. */
 psatd_status psatd_plan_sync(psatd_plan plan);
 
@@ -336,13 +345,20 @@ psatd_status psatd_local_destroy(psatd_local local);
  * memory, or a host that must not allocate after start-up).  The paper has no
  * counterpart: this is a deployment variant of psatd_plan_create +
  * psatd_coeffs_init + psatd_step + psatd_plan_destroy in one call.
- *   Scratch: one fixed 16 MiB device array inside the library, held by every
- *   GPU that loads the library until the process exits.  Grids whose spectra
- *   and tables need more (for FP32 2D TE J-form, anything above about 512^2)
- *   are rejected with PSATD_ERR_UNSUPPORTED and a message naming the size.
- *   The caller still passes (and owns) every field and source array.
+ *   Scratch: one fixed 16 MiB (16,777,216-byte) device array inside the
+ *   library, held by every GPU that loads the library until the process exits.
+ *   A call needs, each part rounded up to 256 bytes: the spectra
+ *   n_in * (n0/2+1) * n1 * n2 complex values (twice that in 3D; 8 B each in
+ *   FP32, 16 B in FP64), twiddles of 16 B per point of every axis, and the
+ *   coefficient table (n0/2+1)(n1/2+1)(n2/2+1 in 3D) entries of 32 B (FP32) or
+ *   64 B (FP64).  Larger grids are rejected with PSATD_ERR_UNSUPPORTED and a
+ *   message naming the size: for FP32 2D TE J-form (n_in = 5) 768^2 fits and
+ *   1024^2 does not.  The caller still passes (and owns) every field and source
+ *   array.
  *   Set-up: the first call on a device looks up the array's device address
- *   (with that device current); make that first call before any stream capture.
+ *   (with that device current), and looks it up again when the device's context
+ *   has changed since (after a device reset); make the first call, and the first
+ *   call after a reset, before any stream capture.
  *   Each call rebuilds the twiddle and coefficient tables in the array (the
  *   array keeps the previous call's contents; the spectra are overwritten
  *   before they are read, so nothing needs clearing).

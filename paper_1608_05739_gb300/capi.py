@@ -86,6 +86,7 @@ EXPORTS = [
 FLAG_AUTOTUNE = 1
 FLAG_PSTD = 2
 FLAG_CHECKED = 4
+FLAG_TEST_STALL_MMA = 8  # test hook of the failure path (mixed precisions): see include/psatd.h
 
 
 def load(path: str = LIB_PATH):
@@ -111,7 +112,7 @@ def _check(status, plan=None):
 
 
 def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, autotune=False, order=0,
-              scheme="psatd", checked=False):
+              scheme="psatd", checked=False, test_stall_mma=False):
     """psatd_desc for grid ``n`` = (nx, ny[, nz]) and cell sizes ``d``."""
     nd = len(n)
     desc = psatd_desc()
@@ -126,7 +127,7 @@ def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, a
     if scheme not in ("psatd", "pstd"):
         raise ValueError("scheme must be 'psatd' or 'pstd'")
     desc.flags = ((FLAG_AUTOTUNE if autotune else 0) | (FLAG_PSTD if scheme == "pstd" else 0)
-                  | (FLAG_CHECKED if checked else 0))
+                  | (FLAG_CHECKED if checked else 0) | (FLAG_TEST_STALL_MMA if test_stall_mma else 0))
     desc.order = int(order)
     return desc
 
@@ -192,14 +193,14 @@ class Plan:
     """
 
     def __init__(self, n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, stream=None,
-                 autotune=False, order=0, scheme="psatd", checked=False):
+                 autotune=False, order=0, scheme="psatd", checked=False, test_stall_mma=False):
         import torch
         lib = load()
         self.n, self.layout, self.prec, self.src = tuple(n), layout, prec, src
         self.shape = _grid_shape(n)
         self.dtype = _torch_dtype(prec)
         self.desc = make_desc(n, d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0, autotune=autotune,
-                              order=order, scheme=scheme, checked=checked)
+                              order=order, scheme=scheme, checked=checked, test_stall_mma=test_stall_mma)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -381,7 +382,7 @@ def fdtd_step(n, d, dt, E, B, J=None, *, scheme="yee", layout="te", prec="fp32",
 
 
 def step_noalloc(n, d, dt, E, B, J=None, rho_n=None, rho_np1=None, *, layout="te", prec="fp32", src="J",
-                 c=1.0, eps0=1.0, nsteps=1, stream=None):
+                 c=1.0, eps0=1.0, nsteps=1, stream=None, scheme="psatd"):
     """psatd_step_noalloc: one-call PSATD step that allocates no device memory.
 
     For callers that cannot allocate on the GPU: the library's scratch is a
@@ -396,7 +397,7 @@ def step_noalloc(n, d, dt, E, B, J=None, rho_n=None, rho_np1=None, *, layout="te
     fn.restype = ct.c_int
     fn.argtypes = [ct.POINTER(psatd_desc), ct.POINTER(psatd_fields), ct.POINTER(psatd_sources), ct.c_int32,
                    ct.c_void_p]
-    desc = make_desc(n, d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0)
+    desc = make_desc(n, d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0, scheme=scheme)
     shape = _grid_shape(n)
     dtype = _torch_dtype(prec)
     f = _fields_struct(layout, shape, dtype, E, B)

@@ -120,8 +120,11 @@ psatd_status validate_desc(psatd_plan p, const psatd_desc* d, bool psatd_limits)
   if (d->layout < 0 || d->layout > 3) return fail(p, PSATD_ERR_INVALID_ARG, "unknown layout %d", d->layout);
   if (d->ndim != layout_ndim(d->layout))
     return fail(p, PSATD_ERR_INVALID_ARG, "ndim %d does not match layout %d", d->ndim, d->layout);
-  if ((d->flags & ~(psatd_limits ? (PSATD_FLAG_AUTOTUNE | PSATD_FLAG_PSTD | PSATD_FLAG_CHECKED) : 0)) != 0)
+  if ((d->flags & ~(psatd_limits ? (PSATD_FLAG_AUTOTUNE | PSATD_FLAG_PSTD | PSATD_FLAG_CHECKED |
+                                     PSATD_FLAG_TEST_STALL_MMA) : 0)) != 0)
     return fail(p, PSATD_ERR_INVALID_ARG, "unknown flags");
+  if ((d->flags & PSATD_FLAG_TEST_STALL_MMA) && d->prec != PSATD_MIXED_FP16 && d->prec != PSATD_MIXED_BF16)
+    return fail(p, PSATD_ERR_INVALID_ARG, "PSATD_FLAG_TEST_STALL_MMA applies to the mixed precisions only");
   if ((d->flags & PSATD_FLAG_PSTD) && d->src == PSATD_SRC_J_RHO)
     return fail(p, PSATD_ERR_INVALID_ARG, "PSTD takes J only (src must be NONE or J)");
   if (d->order != 0) {
@@ -382,6 +385,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
   std::memset(&io, 0, sizeof io);
   io.gmat = p->gmat;
   io.err = p->d_err;
+  io.tc_ctl = (p->d.flags & PSATD_FLAG_TEST_STALL_MMA) ? kTcStallMma : 0;
   const size_t tail = TC ? (size_t)kTcTail : 0;  // tensor-core passes: matrices + mbarrier first
 
   // a0: z in 3D (strided), the patch in a 2D batch (offset table; spectra [c][patch][kx][y])
@@ -450,6 +454,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     a.s_a6 = (R)(1.0 / (p->d.eps0 * c * c * p->g0));
     a.gmat = p->gmat;
     a.err = p->d_err;
+    a.tc_ctl = io.tc_ctl;
     a.stag = p->order > 0 ? 1 : 0;
     a.scheme = (p->d.flags & PSATD_FLAG_PSTD) ? 1 : 0;
     a.p_h = (R)(0.5 * p->d.dt * p->g0);
@@ -1139,10 +1144,43 @@ constexpr size_t kNoAllocBytes = size_t(16) << 20;  // 16 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kNoAllocMaxDevices = 64;
+// per device: the array's device address and the id of the context it was looked up in
 void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kNoAllocMaxDevices] = {};
 std::mutex g_noalloc_mutex;
 
 size_t round256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Unique id of the calling thread's current CUDA context (driver entry points
+// reached through the runtime, so the library needs no link against libcuda).
+// A device reset destroys the context that the array was mapped in and the next
+// runtime call creates a new one with a new id, so a cached address is looked up
+// again.  Returns false when the id is not available (the caller then looks the
+// address up on every call).
+bool current_ctx_id(unsigned long long* id) {
+  typedef int (*GetCurrentFn)(void**);
+  typedef int (*GetIdFn)(void*, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {  // called with g_noalloc_mutex held
+    resolved = true;
+    cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<GetCurrentFn>(f1);
+      get_id = reinterpret_cast<GetIdFn>(f2);
+    }
+    cudaGetLastError();
+  }
+  if (!get_current || !get_id) return false;
+  void* ctx = nullptr;
+  if (get_current(&ctx) != 0 || !ctx) return false;
+  return get_id(ctx, id) == 0;
+}
 
 }  // namespace
 
@@ -1203,15 +1241,26 @@ extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_f
     if (maxsm > 0 && smem > (size_t)maxsm)
       return fail(nullptr, PSATD_ERR_UNSUPPORTED, "last-axis length %d needs %zu bytes of shared memory", L, smem);
   }
+  const void* in[kMaxComp] = {};
+  void* out[kMaxComp] = {};
+  s = gather_slots(&p, fields, sources, in, out);  // also brings up the device's context
+  if (s != PSATD_OK) {
+    g_err = p.err;
+    return s;
+  }
   unsigned char* base = nullptr;
   {
-    // one-time set-up per device (with that device current): the device address of the array
+    // set-up once per device and context (with that device current): the device address
+    // of the array; a host-side reference to g_noalloc_scratch is not that address
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    unsigned long long ctx = 0;
+    const bool have_ctx = current_ctx_id(&ctx);
+    if (!g_noalloc_ptr[dev] || !have_ctx || g_noalloc_ctx[dev] != ctx) {
       void* ptr = nullptr;
       e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
       if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetSymbolAddress of the no-alloc scratch");
       g_noalloc_ptr[dev] = ptr;
+      g_noalloc_ctx[dev] = have_ctx ? ctx : 0;
     }
     base = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
   }
@@ -1228,13 +1277,6 @@ extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_f
   }
   p.tab = base + off;
 
-  const void* in[kMaxComp] = {};
-  void* out[kMaxComp] = {};
-  s = gather_slots(&p, fields, sources, in, out);
-  if (s != PSATD_OK) {
-    g_err = p.err;
-    return s;
-  }
   // wavenumber scale as in psatd_plan_create
   p.g0 = 2.0 * M_PI / ((double)p.nx * desc->d[0]);
   for (int i = 0; i < 3; ++i) {

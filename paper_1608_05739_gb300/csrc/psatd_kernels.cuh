@@ -27,6 +27,7 @@ struct LineIO {
   void* out[kMaxComp];
   const void* gmat;  // tensor-core passes: split DFT matrices (kTcTail image)
   int* err;          // tensor-core passes: device error word
+  int tc_ctl;        // tensor-core passes: control word (kTcStallMma test hook)
 };
 
 // k-space coefficient table entry (one per |m|-octant point), see tables.cu.
@@ -60,6 +61,7 @@ struct PushArgs {
   R s_a6;            // 1 / (eps0 c^2 g0)
   const void* gmat;  // tensor-core pass: split DFT matrices (kTcTail image)
   int* err;          // tensor-core pass: device error word
+  int tc_ctl;        // tensor-core pass: control word (kTcStallMma test hook)
   int scheme;        // 0: PSATD (analytic in time); 1: PSTD (leapfrog, p_h / p_e / p_j / inv_n)
   R p_h, p_e, p_j, inv_n;  // PSTD: dt g0 / 2, c^2 dt g0, dt / eps0, 1/N
   int stag;          // staggered order-p plan (PSATD-p): k_p and half-cell phases below
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_fwd_T(LineIO io,
   TcCtx tc;
   if constexpr (TC)  // split-BF16: the third A piece after the exchange region (line buffers or tile)
     tc_setup(tc, smem_raw, io.gmat, smem_u32(smem), io.err, TC == 2,
-             smem_u32(smem + (R2C ? TB * L : L * (TB + 1))));
+             smem_u32(smem + (R2C ? TB * L : L * (TB + 1))), io.tc_ctl);
   ExBuf<C> ex{{smem + g * L, smem + g * L}, 0, &twslot, true};  // one exchange buffer per line
   if constexpr (!TC && T % 32 == 0)
     if (TB <= 8) {  // each line's warps synchronise among themselves between stages
@@ -225,7 +227,7 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_inv_T(LineIO io,
   TcCtx tc;
   if constexpr (TC)
     tc_setup(tc, smem_raw, io.gmat, smem_u32(smem), io.err, TC == 2,
-             smem_u32(smem + (C2R ? TB * L : L * (TB + 1))));
+             smem_u32(smem + (C2R ? TB * L : L * (TB + 1))), io.tc_ctl);
   C v[EPT];
   if constexpr (C2R) {
     // Z[k] = Fe + i Fo, Fe = X[k] + X*[L-k], Fo = (X[k] - X*[L-k]) conj(W_N^k), read straight
@@ -728,7 +730,7 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   const bool a3_slot = blockDim.y == 1;
   if constexpr (TC)
     tc_setup(tc, smem_raw, a.gmat, smem_u32(base + (int)blockDim.y * a.n_in * L), a.err, TC == 2,
-             smem_u32(base + (int)blockDim.y * (a.n_in + 1) * L));
+             smem_u32(base + (int)blockDim.y * (a.n_in + 1) * L), a.tc_ctl);
 
   int mxi, myi, rowi;
   line_modes(a, valid ? line : 0, mxi, myi, rowi);

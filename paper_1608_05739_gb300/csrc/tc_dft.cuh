@@ -44,6 +44,11 @@ namespace psatd {
 // Status bits written to the plan's device error word.
 constexpr int kErrMmaWait = 1;  // an MMA-completion wait ran out of iterations
 
+// Bits of the passes' tensor-core control word (LineIO::tc_ctl, PushArgs::tc_ctl).
+// kTcStallMma is a test hook for the failure path: the issuing thread commits
+// no MMA, so every completion wait runs out (after kTestWaitIters polls).
+constexpr int kTcStallMma = 1;
+
 struct TcCtx {
   uint32_t mbar;     // shared address of the MMA-completion mbarrier
   uint32_t tmem;     // TMEM address of the CTA's accumulators (lane 0, first column)
@@ -51,8 +56,11 @@ struct TcCtx {
   uint32_t a_tile3;  // split-BF16: third A piece (group g at + g * piece bytes)
   uint32_t bmat;     // shared address of the split DFT matrices, forward then adjoint
   uint32_t phase;    // parity of the next mbarrier phase (identical in every thread)
+  volatile int* abort;  // CTA-shared word: nonzero once any thread's completion wait ran out
   int* err;          // device error word (may be null)
   int bf16;          // 0 split-FP16, 1 split-BF16
+  int wait_iters;    // poll limit of each completion wait
+  int stall;         // kTcStallMma: issue nothing (test hook)
 };
 
 // Bytes of one split piece (hi or lo) of the A tile of 128 rows / of G.
@@ -112,13 +120,15 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Wait for the phase with parity `phase` to complete, at most kWaitIters
-// polls (each may suspend the thread briefly); on expiry the error word gets
-// kErrMmaWait and the wait returns so the kernel can finish and free TMEM.
+// Wait for the phase with parity `phase` to complete, at most `iters` polls
+// (each may suspend the thread briefly).  Returns false when the limit is
+// reached; the caller then records the failure (tc_dft) so that the CTA stops
+// using the tensor cores, finishes and frees its TMEM.
 constexpr int kWaitIters = 1 << 21;
-__device__ __forceinline__ void mbar_wait(uint32_t mbar, uint32_t phase, int* err) {
+constexpr int kTestWaitIters = 256;
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, int iters) {
   uint32_t done = 0;
-  for (int i = 0; i < kWaitIters; ++i) {
+  for (int i = 0; i < iters; ++i) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -126,9 +136,9 @@ __device__ __forceinline__ void mbar_wait(uint32_t mbar, uint32_t phase, int* er
         : "=r"(done)
         : "r"(mbar), "r"(phase)
         : "memory");
-    if (done) return;
+    if (done) return true;
   }
-  if (err) atomicOr(err, kErrMmaWait);
+  return false;
 }
 
 // TMEM allocation of `ncols` columns (a power of two >= 32) by one whole warp;
@@ -180,6 +190,12 @@ __host__ __device__ constexpr int tc_tmem_cols(int nthreads) {
 // (block barriers inside); blockDim.x * blockDim.y is a multiple of 128.  The
 // A tiles alias exchange space that holds no live data at a stage boundary.
 // BF16: split-BF16 operands (else split-FP16).
+// Failure path: a thread whose completion wait runs out sets the CTA's abort
+// word and the error word and leaves a[] as it is (its TMEM row may still be
+// written by the MMAs).  The abort word is read after the stage's first
+// barrier, so every thread sees the same value: once it is set, no thread
+// splits, issues, waits or reads TMEM again, and tc_teardown makes one last
+// bounded wait for the outstanding commit before it frees the TMEM columns.
 template <int RS, bool ADJ, bool BF16>
 __device__ __forceinline__ void tc_dft(float2 (&a)[RS], TcCtx& tc) {
   typedef TcGeom<RS> G;
@@ -199,7 +215,8 @@ __device__ __forceinline__ void tc_dft(float2 (&a)[RS], TcCtx& tc) {
   constexpr float kRound128 = 1610612736.0f;  // 1.5 * 2^30: to a multiple of 128
 
   __syncthreads();  // every exchange read of the previous stage is done
-  {
+  const bool aborted = *tc.abort != 0;
+  if (!aborted) {
     const uint32_t base = tc.a_tile + grp * G::kATile + (row >> 3) * G::kSBO + (row & 7) * 16;
     const uint32_t base3 = tc.a_tile3 + grp * G::kAPiece + (row >> 3) * G::kSBO + (row & 7) * 16;
 #pragma unroll
@@ -241,7 +258,8 @@ __device__ __forceinline__ void tc_dft(float2 (&a)[RS], TcCtx& tc) {
   }
   fence_async_smem();
   __syncthreads();
-  if (tid == 0) {
+  if (aborted) return;
+  if (tid == 0 && !tc.stall) {
     tc_fence_after();
     const uint32_t g0 = tc.bmat + (ADJ ? G::kGDir : 0);
     constexpr uint32_t idesc = BF16 ? G::kIdescBF16 : G::kIdesc;
@@ -274,8 +292,14 @@ __device__ __forceinline__ void tc_dft(float2 (&a)[RS], TcCtx& tc) {
     }
     tc_commit(tc.mbar);
   }
-  mbar_wait(tc.mbar, tc.phase, tc.err);
+  // warp-uniform outcome: the TMEM loads below are .sync.aligned
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(tc.mbar, tc.phase, tc.wait_iters));
   tc.phase ^= 1u;
+  if (!ok) {
+    *tc.abort = 1;
+    if (tc.err) atomicOr(tc.err, kErrMmaWait);
+    return;
+  }
   tc_fence_after();
   const uint32_t taddr = tc.tmem + ((uint32_t)((tid >> 5) & 3) << 21) + grp * 64;  // lane base 32 (warp % 4)
   // 16 columns (8 complex outputs) at a time: head, then correction added
@@ -299,14 +323,15 @@ __device__ __forceinline__ void tc_dft(float2 (&a)[RS], TcCtx& tc) {
 
 // Shared-memory tail of a tensor-core pass kernel (at the start of its dynamic
 // shared memory): the split radix-16 DFT matrices of both directions, the
-// mbarrier and the TMEM address word.
+// mbarrier, the TMEM address word and the abort word.
 constexpr int kTcTail = 2 * TcGeom<16>::kGDir + 1024;
 
 // Set up a tensor-core pass: copy the split DFT matrices (kTcTail image made
 // by the plan, 16-byte aligned) into the tail, allocate the CTA's TMEM
-// columns (warp 0), initialise the mbarrier.  Contains a block barrier.
+// columns (warp 0), initialise the mbarrier and clear the abort word.
+// ctl: the pass's control word (kTcStallMma).  Contains a block barrier.
 __device__ __forceinline__ void tc_setup(TcCtx& tc, unsigned char* tail, const void* gmat, uint32_t a_tile,
-                                         int* err, int bf16 = 0, uint32_t a_tile3 = 0) {
+                                         int* err, int bf16, uint32_t a_tile3, int ctl) {
   const int nthr = blockDim.x * blockDim.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   constexpr int kG = 2 * TcGeom<16>::kGDir;
@@ -314,6 +339,8 @@ __device__ __forceinline__ void tc_setup(TcCtx& tc, unsigned char* tail, const v
     reinterpret_cast<uint4*>(tail)[i] = __ldg(static_cast<const uint4*>(gmat) + i);
   uint64_t* mb = reinterpret_cast<uint64_t*>(tail + kG);
   uint32_t* slot = reinterpret_cast<uint32_t*>(tail + kG + 8);
+  int* abort_word = reinterpret_cast<int*>(tail + kG + 12);
+  if (tid == 0) *abort_word = 0;
   if (tid < 32) {
     tmem_alloc(smem_u32(slot), (uint32_t)tc_tmem_cols(nthr));
     tc_fence_before();
@@ -329,16 +356,23 @@ __device__ __forceinline__ void tc_setup(TcCtx& tc, unsigned char* tail, const v
   tc.bf16 = bf16;
   tc.bmat = smem_u32(tail);
   tc.phase = 0u;
+  tc.abort = abort_word;
   tc.err = err;
+  tc.stall = ctl & kTcStallMma;
+  tc.wait_iters = tc.stall ? kTestWaitIters : kWaitIters;
 }
 
 // Release the TMEM columns once every thread is done with them (block barrier).
+// After an expired wait (abort word set) the last commit may still be
+// outstanding: warp 0 first waits for it once more (bounded), then frees.
 __device__ __forceinline__ void tc_teardown(const TcCtx& tc) {
   const int nthr = blockDim.x * blockDim.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   tc_fence_before();
   __syncthreads();
   if (tid < 32) {
+    if (*tc.abort) mbar_wait(tc.mbar, tc.phase ^ 1u, tc.wait_iters);
+    __syncwarp();
     tc_fence_after();
     tmem_free(tc.tmem, (uint32_t)tc_tmem_cols(nthr));
   }

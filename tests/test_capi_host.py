@@ -64,7 +64,8 @@ def _create(lib, desc):
     (lambda d: setattr(d, "prec", 2), 2),                  # split-BF16: 64 threads, no 128-row group
     (lambda d: setattr(d, "prec", 9), 1),
     (lambda d: setattr(d, "src", 7), 1),
-    (lambda d: setattr(d, "flags", 8), 1),                 # unknown flag bit
+    (lambda d: setattr(d, "flags", 16), 1),                # unknown flag bit
+    (lambda d: setattr(d, "flags", 8), 1),                 # the MMA-stall test hook on an FP32 plan
     (lambda d: (setattr(d, "layout", 3), setattr(d, "src", 2)), 1),  # TM has no rho-form
     (lambda d: setattr(d, "layout", 9), 1),
 ])

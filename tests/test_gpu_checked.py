@@ -2,7 +2,13 @@
 a hit is reported by the next sync as PSATD_ERR_NONFINITE (host-made failure:
 a NaN placed in an input; nothing faults on the GPU).  A checked plan computes
 the same bits as an unchecked one, the word is cleared by the sync that reports
-it, and the plan stays usable."""
+it, and the plan stays usable.
+
+The bounded MMA-completion wait of the tensor-core passes: with the test hook
+PSATD_FLAG_TEST_STALL_MMA nothing is committed to the mbarrier, so every CTA's
+first wait runs out (a short poll limit), the CTA stops using the tensor cores
+and frees its TMEM, and the sync reports PSATD_ERR_TIMEOUT; a normal plan run
+afterwards (whose CTAs allocate TMEM again on the same SMs) is correct."""
 import numpy as np
 import pytest
 import torch
@@ -79,3 +85,38 @@ def test_allocation_failure_is_reported_and_leaves_no_plan():
     p.sync()
     p.destroy()
     assert torch.cuda.mem_get_info()[0] >= free0 - (64 << 20)   # nothing of the failed plan is held
+
+
+TIMEOUT = 5
+
+
+@pytest.mark.parametrize("prec", ["mixed_fp16", "mixed_bf16"])
+def test_expired_mma_wait_reports_timeout_and_frees_tmem(prec):
+    from gpu_helpers import mask_layout, rel_l2_fields, rounded
+    from oracle import psatd as orc
+    ensure_lib()
+    n, shape = (256, 256), (256, 256)
+    a = _te(shape, 3)
+    stalled = capi.Plan(n, (1.0, 1.0), 0.5, layout="te", prec=prec, src="J", test_stall_mma=True)
+    stalled.step([a[0], a[1], None], [None, None, a[2]], [a[3], a[4], None])
+    with pytest.raises(capi.PsatdError) as ei:
+        stalled.sync()
+    assert ei.value.status == TIMEOUT
+    stalled.sync()                      # reported once, then cleared
+    stalled.destroy()
+    # the same kind of plan without the hook, on fresh inputs, against the oracle
+    b = _te(shape, 4)
+    host = [t.double().cpu().numpy() for t in b]
+    good = capi.Plan(n, (1.0, 1.0), 0.5, layout="te", prec=prec, src="J")
+    good.step([b[0], b[1], None], [None, None, b[2]], [b[3], b[4], None], nsteps=2)
+    good.sync()
+    good.destroy()
+    z = np.zeros(shape)
+    E = np.stack([host[0], host[1], z])
+    B = np.stack([z, z, host[2]])
+    J = np.stack([host[3], host[4], z])
+    Eo, Bo = orc.psatd_step(E, B, J, d=(1.0, 1.0), dt=0.5, form="J", nsteps=2)
+    Eg = np.stack([b[0].double().cpu().numpy(), b[1].double().cpu().numpy(), z])
+    Bg = np.stack([z, z, b[2].double().cpu().numpy()])
+    err = rel_l2_fields(Eg, Bg, mask_layout(Eo, "te", "E"), mask_layout(Bo, "te", "B"))
+    assert err < 4e-6, err

@@ -31,31 +31,41 @@ def _np(ts):
     return np.stack([t.double().cpu().numpy() if t is not None else np.zeros(1) for t in ts if t is not None])
 
 
-@pytest.mark.parametrize("prec,layout,shape", [("fp32", "te", (256, 256)), ("fp64", "2d6", (64, 128)),
-                                               ("fp32", "te", (192, 96))])
-def test_noalloc_matches_plan_step_on_two_calls(prec, layout, shape):
+# (precision, layout, grid [nz,] ny, nx, steps per call, scheme): 2D TE and 2D6, a mixed-radix
+# grid, a 3D grid (whose second spectrum is carved from the array after the first), calls
+# of three steps, and the PSTD scheme
+CASES = [("fp32", "te", (256, 256), 1, "psatd"), ("fp64", "2d6", (64, 128), 1, "psatd"),
+         ("fp32", "te", (192, 96), 1, "psatd"), ("fp64", "3d6", (32, 32, 32), 1, "psatd"),
+         ("fp32", "3d6", (16, 32, 64), 3, "psatd"), ("fp32", "te", (128, 256), 3, "psatd"),
+         ("fp64", "te", (64, 64), 2, "pstd"),
+         ("fp32", "te", (768, 768), 1, "psatd")]   # the largest square FP32 TE grid the array holds
+
+
+@pytest.mark.parametrize("prec,layout,shape,nsteps,scheme", CASES)
+def test_noalloc_matches_plan_step_on_two_calls(prec, layout, shape, nsteps, scheme):
     import torch
     ensure_lib()
     n = tuple(reversed(shape))
-    d = (1.0 / 64, 1.0 / 64)
-    dt = d[0] / math.sqrt(2.0)
+    d = tuple([1.0 / 64] * len(shape))
+    dt = d[0] / math.sqrt(len(shape)) * (0.5 if scheme == "pstd" else 1.0)
     Ea, Ba, Ja = _state(shape, layout, 41, prec)
     Eb = [t.clone() if t is not None else None for t in Ea]
     Bb = [t.clone() if t is not None else None for t in Ba]
-    plan = capi.Plan(n, d, dt, layout=layout, prec=prec, src="J")
+    plan = capi.Plan(n, d, dt, layout=layout, prec=prec, src="J", scheme=scheme)
     for call in range(2):
-        plan.step(Ea, Ba, Ja)
-        capi.step_noalloc(n, d, dt, Eb, Bb, Ja, layout=layout, prec=prec, src="J")
+        plan.step(Ea, Ba, Ja, nsteps=nsteps)
+        capi.step_noalloc(n, d, dt, Eb, Bb, Ja, layout=layout, prec=prec, src="J", nsteps=nsteps, scheme=scheme)
         torch.cuda.synchronize()
         err = rel_l2_fields(_np(Eb), _np(Bb), _np(Ea), _np(Ba))
         assert err < TOL[prec], (call, err)
     plan.destroy()
 
 
-def test_noalloc_rejects_grids_beyond_its_array():
+@pytest.mark.parametrize("n", [1024, 2048])
+def test_noalloc_rejects_grids_beyond_its_array(n):
     ensure_lib()
-    z = torch_dev(np.zeros((2048, 2048)), "fp32")
+    z = torch_dev(np.zeros((n, n)), "fp32")
     with pytest.raises(capi.PsatdError) as ei:
-        capi.step_noalloc((2048, 2048), (1.0, 1.0), 0.5, [z, z, None], [None, None, z], [z, z, None],
+        capi.step_noalloc((n, n), (1.0, 1.0), 0.5, [z, z, None], [None, None, z], [z, z, None],
                           layout="te", prec="fp32", src="J")
     assert ei.value.status == 2 and "scratch" in str(ei.value)
