@@ -1,20 +1,24 @@
 """Benchmark of the PSATD step on GB300: one JSON line per run (rank 0).
 
-Workload (the metric's configuration): 2D TE PSATD on a 2048 x 2048 periodic
-grid in FP32, dx = lambda/64, c dt = dx/sqrt(2), J-form sources from the
-prescribed oscillating current sheet J_y(x, t) = J0 exp(-(x - x0(t))^2/w^2),
-x0(t) = a sin(w0 t)/w0, a = 0.9 c, w = 2 dx (a synthetic stand-in for the
-plasma-mirror surface of the paper's harmonic-generation runs).  A step is one
-psatd_step call with that step's J^(n+1/2); L2 is flushed (256 MiB write)
-before every timed step and only the step itself is inside the CUDA events.
+Default workload (the metric's configuration: mixed precision, batched): 512
+independent periodic 2D TE patches -- the paper's local-FFT subdomains
+(Sec. II.A.3) -- with interior sides U{64..512} and guards U{8..16} per axis,
+each side widened to the next transform length (powers of two for the
+tensor-core passes), J-form with a seeded random current held over the run.
+The step runs with split-BF16 tensor-core radix-16 stages (FP32 accumulate);
+the whole timed run is one psatd_batch_step(nsteps = --steps) call, i.e. a
+CUDA graph of one step replayed.  Reported beside it: plain FP32 on the same
+patches, the error of both against the FP64 oracle on sampled patches after the
+same steps, the oracle's own speed on the host cores (cpu_baseline), the end to
+end rate from pinned host arrays, and the single 2048^2 TE grid in FP32 as a
+side key.  --workload selects the side measurements instead (te2048, 3D, FDTD,
+local decomposition, cost comparison).
 
 Arms:
   default            the CUDA path through the C ABI (device-resident inputs);
-                     e2e: the same step fed from pinned host buffers (E, B, J
-                     uploaded, E, B downloaded every step) through the C ABI.
   --impl reference   the FP64 CPU oracle on the host cores (rank 0 only).
-Multi-GPU (torchrun, N > 1): independent replicas, one per GPU (the step has
-no exchange on one patch); value = all ranks' cell-steps / max rank time.
+Multi-GPU (torchrun, N > 1): independent replicas, one per GPU (no exchange);
+value = all ranks' cell-steps / max rank time.
 """
 from __future__ import annotations
 
@@ -157,8 +161,418 @@ def dist_setup():
     return world, rank, local
 
 
-def run_reference(args, world, rank):
-    """The FP64 CPU oracle on the host cores (bounded sample of the workload)."""
+# ---------------------------------------------------------------- the headline: batched patches
+BATCH_SEED, BATCH_J_SEED, BATCH_J_SCALE = 1612, 1613, 0.01
+BATCH_WORKLOAD = ("512 periodic 2D TE patches (the paper's local-FFT subdomains, Sec. II.A.3): interior "
+                  "U{64..512}^2 and guards U{8..16} per axis (seed 1612), each side widened to the next "
+                  "transform length; J-form, E = B = 0 at the start, J ~ N(0, 0.01^2) per patch (seed 1613 + i) "
+                  "held over the run; dx = lambda/64, c dt = dx/sqrt(2)")
+BATCH_DX = 1.0 / LAM_CELLS
+BATCH_DT = BATCH_DX / math.sqrt(2.0)
+
+
+def _oracle_patch(job):
+    """Oracle worker (spawned process): `nsteps` FP64 oracle steps of batch patch
+    `i` (nx x ny) from E = B = 0 with its seeded source; returns (i, seconds,
+    Ex, Ey, Bz) or, with keep=False, (i, seconds) only."""
+    i, nx, ny, nsteps, keep = job
+    from oracle import psatd as orc
+    from paper_1608_05739_gb300 import synth
+    jx, jy = synth.batch_patch_source(i, nx, ny, BATCH_J_SEED, BATCH_J_SCALE)
+    E = np.zeros((3, ny, nx))
+    B = np.zeros((3, ny, nx))
+    J = np.zeros((3, ny, nx))
+    J[0] = jx.astype(np.float64)
+    J[1] = jy.astype(np.float64)
+    t0 = time.perf_counter()
+    E, B = orc.psatd_step(E, B, J, d=(BATCH_DX, BATCH_DX), dt=BATCH_DT, form="J", nsteps=nsteps)
+    el = time.perf_counter() - t0
+    return (i, el, E[0], E[1], B[2]) if keep else (i, el)
+
+
+def _pool_ready(_):
+    import oracle.psatd  # noqa: F401  (imports done before any timing)
+    return os.getpid()
+
+
+def oracle_pool():
+    """Process pool for the oracle on every host core this process may use, started
+    with spawn (before any CUDA call of the parent)."""
+    import multiprocessing as mp
+    n = len(os.sched_getaffinity(0))
+    pool = mp.get_context("spawn").Pool(n)
+    pool.map(_pool_ready, range(4 * n))
+    return pool, n
+
+
+def batch_cpu_baseline(pool, ncores, sizes, stride=2, steps=1):
+    """The oracle as it stands on a bounded sample of the batch: every `stride`-th
+    patch, `steps` steps each, patches spread over the pool's processes."""
+    jobs = [(i, nx, ny, steps, False) for i, (nx, ny) in enumerate(sizes) if i % stride == 0]
+    cells = sum(sizes[j[0]][0] * sizes[j[0]][1] for j in jobs)
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_patch, sorted(jobs, key=lambda j: -j[1] * j[2]), chunksize=1)
+    el = time.perf_counter() - t0
+    cpu = sum(r[1] for r in res)
+    return {"value": cells * steps / el, "unit": "cell-steps/s", "cores": ncores, "kind": "oracle",
+            "sample": "%d of the 512 patches (every %dth, %.3g cells), %d FP64 oracle step(s) each, one patch "
+                      "per process on %d processes (numpy pocketfft): %.1f s wall, %.1f s of CPU work"
+                      % (len(jobs), stride, cells, steps, ncores, el, cpu)}
+
+
+def batch_sample(sizes, budget_cell_steps, nsteps, seed=1617, count=8):
+    """Patches compared with the oracle after the timed run: the smallest, and
+    seeded others whose oracle run (area x nsteps) fits the budget."""
+    area = [a * b for a, b in sizes]
+    small = [i for i in range(len(sizes)) if area[i] * nsteps <= budget_cell_steps]
+    pick = {int(np.argmin(area))}
+    if small:
+        g = np.random.default_rng(seed)
+        pick |= set(int(i) for i in g.choice(small, min(count - 1, len(small)), replace=False))
+    return sorted(pick)
+
+
+def patch_fields(fields, sizes, offsets, idx):
+    """{i: [Ex, Ey, Bz] of patch i as float64 host arrays} from the packed fields."""
+    out = {}
+    for i in idx:
+        o, m = int(offsets[i]), sizes[i][0] * sizes[i][1]
+        out[i] = [np.asarray(f[o:o + m].cpu() if hasattr(f, "cpu") else f[o:o + m], dtype=np.float64)
+                  for f in fields]
+    return out
+
+
+def rel_l2_patches(gpu_patches, oracle_res):
+    """Relative L2 (Ex, Ey, c Bz together, over all sampled patches) and the
+    largest per-patch value, GPU fields of the patches vs the oracle."""
+    num = den = 0.0
+    worst = 0.0
+    for (i, _el, ex, ey, bz) in oracle_res:
+        got = np.concatenate(gpu_patches[i])
+        want = np.concatenate([ex.ravel(), ey.ravel(), bz.ravel()])
+        n2, d2 = float(np.sum((got - want) ** 2)), float(np.sum(want ** 2))
+        num += n2
+        den += d2
+        worst = max(worst, math.sqrt(n2 / d2))
+    return math.sqrt(num / den), worst
+
+
+def batch_algorithmic_bytes(sizes):
+    """Algorithmic bytes of each pass over all patches (see algorithmic_bytes)."""
+    tot = {}
+    for nx, ny in sizes:
+        for k, v in algorithmic_bytes(nx, ny, 1, N_IN, N_OUT).items():
+            tot[k] = tot.get(k, 0) + v
+    return tot
+
+
+def time_batch(capi, torch, prec, sizes, Jhost, args, dev, stream, sample_clocks, nsteps=None):
+    """A batch at precision `prec`: W untimed steps (one call: the step graph is
+    recorded and replayed), then one psatd_batch_step(nsteps = K) call between
+    CUDA events on the batch's stream.  Per-kernel event pairs are recorded in the
+    graph (their times are the last replay's).  Returns (ms, kernel times, clocks,
+    batch, (Ex, Ey, Bz, Jx, Jy))."""
+    K = nsteps or args.steps
+    b = capi.Batch(sizes, (BATCH_DX, BATCH_DX), BATCH_DT, layout="te", prec=prec, src="J", stream=stream)
+    tot = b.total
+    Ex, Ey, Bz = (torch.zeros(tot, device=dev) for _ in range(3))
+    Jx = torch.from_numpy(Jhost[0]).to(dev)
+    Jy = torch.from_numpy(Jhost[1]).to(dev)
+    b.set_timing(True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        b.step([Ex, Ey, None], [None, None, Bz], [Jx, Jy, None], nsteps=args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device()) if sample_clocks else None
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        b.step([Ex, Ey, None], [None, None, Bz], [Jx, Jy, None], nsteps=K)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1)
+    kt = b.kernel_times()
+    b.set_timing(False)
+    b.sync()  # raises if a tensor-core pass reported an expired wait
+    if not bool(torch.isfinite(Ey).all()):
+        raise RuntimeError("non-finite field after the timed steps")
+    return ms, kt, clk, b, (Ex, Ey, Bz, Jx, Jy)
+
+
+def batch_e2e(torch, b, Jhost, stream, nsteps):
+    """End to end through psatd_batch_step with E, B and J in pinned host memory:
+    (a) the passes read the host arrays and write E, B back over the host link
+    inside the step (the library's host-buffer mode, one call of nsteps steps);
+    (b) staged: per step, copies of the five inputs to device arrays, the step,
+    copies of the three outputs back.  Returns (value a, value b) in cell-steps/s."""
+    tot = b.total
+    hE = [torch.zeros(tot).pin_memory() for _ in range(3)]
+    hJ = [torch.from_numpy(Jhost[0]).pin_memory(), torch.from_numpy(Jhost[1]).pin_memory()]
+    dE = [torch.empty(tot, device="cuda") for _ in range(3)]
+    dJ = [torch.empty(tot, device="cuda") for _ in range(2)]
+    out = []
+    for staged in (False, True):
+        for it in range(2):
+            n = nsteps if it else 1
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                if staged:
+                    for _ in range(n):
+                        for h, d_ in zip(hE + hJ, dE + dJ):
+                            d_.copy_(h, non_blocking=True)
+                        b.step([dE[0], dE[1], None], [None, None, dE[2]], [dJ[0], dJ[1], None])
+                        for h, d_ in zip(hE, dE):
+                            h.copy_(d_, non_blocking=True)
+                else:
+                    b.step([hE[0], hE[1], None], [None, None, hE[2]], [hJ[0], hJ[1], None], nsteps=n)
+                e1.record(stream)
+            torch.cuda.synchronize()
+        out.append(tot * nsteps / (e0.elapsed_time(e1) * 1e-3))
+    b.sync()
+    return out[0], out[1]
+
+
+def roofline_of(ktimes, alg, hbm, peak_kind, traffic_lookup=True):
+    """Roofline object of the kernel with the largest summed time: algorithmic
+    bytes of its launches / their summed CUDA-event time, against `hbm`."""
+    if not ktimes:
+        return None
+    dom = max(ktimes, key=lambda k: ktimes[k][1])
+    n_l, tot = ktimes[dom]
+    achieved = alg[dom] / (tot * 1e-3) / 1e9
+    traffic = None
+    if traffic_lookup:
+        try:
+            tr = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
+            ent = tr.get(dom)
+            if ent and ent.get("source_hash") == source_hash():
+                traffic = ent["bytes_per_launch"]
+        except Exception:
+            pass
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic, "kernel": dom, "peak_kind": peak_kind, "launches": n_l,
+            "algorithmic_bytes_per_launch": alg[dom] / n_l,
+            "per_kernel_ms": {k: v[1] / v[0] for k, v in ktimes.items()}}
+
+
+def run_batch_line(args, world, rank, local):
+    """The metric's own configuration: 512 batched TE patches at the mixed precision
+    (split-BF16 tensor-core stages) against plain FP32 on the same patches."""
+    pool = ncores = None
+    if rank == 0:
+        pool, ncores = oracle_pool()  # spawned before the first CUDA call
+    import torch
+    from paper_1608_05739_gb300 import build as bld
+    from paper_1608_05739_gb300 import capi, synth
+
+    sizes, interior = synth.batch_patch_sizes(512, BATCH_SEED, mixed_ok=False)
+    sizes_fp32, _ = synth.batch_patch_sizes(512, BATCH_SEED, mixed_ok=True)
+    requested = synth.batch_requested_cells(512, BATCH_SEED)
+    cells, cells_fp32 = sum(a * b for a, b in sizes), sum(a * b for a, b in sizes_fp32)
+    offs = np.concatenate([[0], np.cumsum([a * b for a, b in sizes])]).astype(np.int64)
+    offs32 = np.concatenate([[0], np.cumsum([a * b for a, b in sizes_fp32])]).astype(np.int64)
+    K, W = args.steps, args.warmup
+    cb = None
+    pend = pend32 = None
+    samp = samp32 = []
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            cb = batch_cpu_baseline(pool, ncores, sizes)
+        # oracle references of sampled patches after the W + K steps, computed while the GPU runs
+        samp = batch_sample(sizes, 2.0e7, W + K)
+        samp32 = batch_sample(sizes_fp32, 2.0e7, W + K, seed=1618)
+        pend = pool.map_async(_oracle_patch, [(i, sizes[i][0], sizes[i][1], W + K, True) for i in samp])
+        pend32 = pool.map_async(_oracle_patch, [(i, sizes_fp32[i][0], sizes_fp32[i][1], W + K, True)
+                                                for i in samp32])
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or not os.path.exists(capi.LIB_PATH):
+        bld.build()
+    if world > 1:
+        dist.barrier()
+    capi.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream()
+    J = synth.batch_source(sizes, BATCH_J_SEED, BATCH_J_SCALE)
+    J32 = synth.batch_source(sizes_fp32, BATCH_J_SEED, BATCH_J_SCALE)
+
+    prec = args.precision if args.precision != "fp32" else "mixed_bf16"
+    if world > 1:
+        dist.barrier()
+    ms, kt, clk, b, F = time_batch(capi, torch, prec, sizes, J, args, dev, stream, sample_clocks=True)
+    value, t_max = replica_throughput(ms, cells, K, world, dev)
+    gpu_fields = patch_fields(F[:3], sizes, offs, samp)
+    launches_per_step = sum(v[0] for v in kt.values())
+    # a longer series of the same call with its own clock record (at least ~2 s of steps)
+    long_series = None
+    n_long = int(math.ceil(2000.0 / (ms / K)))
+    if n_long > K:
+        ms_l, _, clk_l, b_l, _ = time_batch(capi, torch, prec, sizes, J, args, dev, stream, sample_clocks=True,
+                                            nsteps=n_long)
+        b_l.destroy()
+        long_series = {"steps": n_long, "ms_per_step": ms_l / n_long, "value": cells * n_long / (ms_l * 1e-3),
+                       "clocks": clk_l}
+    e2e_a = e2e_b = None
+    e2e_steps = max(3, min(K, 20))
+    if not args.no_e2e:
+        e2e_a, e2e_b = batch_e2e(torch, b, J, stream, e2e_steps)
+    b.destroy()
+    # plain FP32 on the same patches (same transform sizes), and on the sizes FP32 itself takes
+    ms32, kt32, _, b32, F32 = time_batch(capi, torch, "fp32", sizes, J, args, dev, stream, sample_clocks=False)
+    f32_fields = patch_fields(F32[:3], sizes, offs, samp)
+    b32.destroy()
+    del F32
+    msb, ktb, _, bb, Fb = time_batch(capi, torch, "fp32", sizes_fp32, J32, args, dev, stream, sample_clocks=False)
+    fb_fields = patch_fields(Fb[:3], sizes_fp32, offs32, samp32)
+    bb.destroy()
+    del Fb, F
+
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak_kind = "measured"
+    if not hbm:
+        hbm, peak_kind = 6800.0, "fallback"
+    roof = roofline_of(kt, batch_algorithmic_bytes(sizes), hbm, peak_kind, traffic_lookup=False)
+
+    side = None
+    if not args.no_side_precision and rank == 0:
+        side = te2048_side(capi, torch, args, dev, world, hbm, peak_kind)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[prec], "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "patches": 512, "precision": PREC_NOTE[prec],
+                       "patch_sides": "powers of two (the tensor-core passes' lengths)",
+                       "cells": cells, "interior_cells": interior, "requested_domain_cells": requested,
+                       "size_classes": len(set(sizes)),
+                       "value_counts": "cells of the transformed patch domains (interior + widened guards)",
+                       "run": "one psatd_batch_step(nsteps = steps) call: a CUDA graph of one step replayed",
+                       "l2": "not flushed: the inputs (%.2f GB) are 15x the 129 MB L2" % (5 * cells * 4 / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "interior_cell_steps_per_s": value * interior / cells,
+            "gpu_launches": launches_per_step * K,
+            "roofline": roof,
+            "clocks": clk,
+        }
+        if long_series:
+            line["long_series"] = long_series
+        line["vs_plain_fp32"] = {
+            "same_patches": {"precision": PREC_NOTE["fp32"], "value": cells * K / (ms32 * 1e-3),
+                             "ms_per_step": ms32 / K, "ratio": (cells * K / (ms * 1e-3)) / (cells * K / (ms32 * 1e-3)),
+                             "what": "FP32 batch on the same power-of-two patch sides; ratio = mixed / FP32"},
+            "fp32_own_sides": {"value": cells_fp32 * K / (msb * 1e-3), "ms_per_step": msb / K, "cells": cells_fp32,
+                               "interior_cell_steps_per_s": interior * K / (msb * 1e-3),
+                               "interior_ratio": (interior * K / (ms * 1e-3)) / (interior * K / (msb * 1e-3)),
+                               "what": "FP32 batch with the sides FP32 takes (2^k or 3 * 2^k); interior_ratio = "
+                                       "mixed / FP32 interior cell-steps/s",
+                               "roofline": roofline_of(ktb, batch_algorithmic_bytes(sizes_fp32), hbm, peak_kind,
+                                                       traffic_lookup=False)},
+        }
+        if not args.no_e2e:
+            line["e2e"] = {"value": e2e_a, "unit": "cell-steps/s", "h2d_bytes_per_step": 5 * cells * 4,
+                           "d2h_bytes_per_step": 3 * cells * 4, "steps": e2e_steps,
+                           "how": "psatd_batch_step on pinned host arrays: the x passes read E, B, J and write E, B "
+                                  "in host memory over the host link, every step",
+                           "staged_value": e2e_b,
+                           "staged_how": "per step: cudaMemcpyAsync of the five inputs to device arrays, the "
+                                         "step, copies of the three outputs back"}
+        if pend is not None:
+            ref = pend.get()
+            ref32 = pend32.get()
+            r, worst = rel_l2_patches(gpu_fields, ref)
+            r32, worst32 = rel_l2_patches(f32_fields, ref)
+            rb, worstb = rel_l2_patches(fb_fields, ref32)
+            line["rel_l2_vs_oracle"] = {
+                "value": r, "max_patch": worst, "steps": W + K, "patches": samp,
+                "what": "Ex, Ey, c Bz of the sampled patches after the warm-up and timed steps (E = B = 0 at the "
+                        "start, the same J), the line's precision vs the FP64 oracle on each patch alone"}
+            line["vs_plain_fp32"]["same_patches"]["rel_l2_vs_oracle"] = {"value": r32, "max_patch": worst32}
+            line["vs_plain_fp32"]["fp32_own_sides"]["rel_l2_vs_oracle"] = {"value": rb, "max_patch": worstb,
+                                                                           "patches": samp32}
+        if cb is not None:
+            line["cpu_baseline"] = cb
+        if side is not None:
+            line["side_te2048"] = side
+        print(json.dumps(line), flush=True)
+    if pool is not None:
+        pool.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def te2048_side(capi, torch, args, dev, world, hbm, peak_kind):
+    """Side key of the headline line: the single 2048^2 TE grid in FP32 (the
+    fused pass k_line_push at its largest), with its own roofline."""
+    dx = 1.0 / LAM_CELLS
+    dt = dx / math.sqrt(2.0)
+    stream = torch.cuda.current_stream()
+    total = args.warmup + args.steps
+    prof = torch.from_numpy(np.stack([sheet_profile(n, dt, dx) for n in range(total)])).float().to(dev)
+    Jy_all = [prof[n].expand(NY, NX).contiguous() for n in range(total)]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ms, kt, clk, plan = time_te2048(capi, torch, "fp32", args, dev, dt, dx, Jy_all, flush, stream, 1,
+                                    sample_clocks=True)
+    plan.destroy()
+    return {"workload": WORKLOAD, "precision": PREC_NOTE["fp32"], "value": NX * NY * args.steps / (ms * 1e-3),
+            "ms_per_step": ms / args.steps, "unit": "cell-steps/s",
+            "l2": "flushed before every timed step (256 MiB write)",
+            "roofline": roofline_of(kt, algorithmic_bytes(), hbm, peak_kind), "clocks": clk}
+
+
+def run_reference_batch(args, world, rank):
+    """The reference arm on the headline's workload: the FP64 oracle as it stands on
+    the host cores.  A step = every patch of the batch advanced one oracle step
+    (patches spread over the pool's processes); runs until --steps steps or
+    --ref-seconds, whichever comes first (after one untimed warm-up step)."""
+    if rank != 0:
+        return
+    from paper_1608_05739_gb300 import synth
+    pool, ncores = oracle_pool()
+    sizes, _ = synth.batch_patch_sizes(512, BATCH_SEED, mixed_ok=False)
+    cells = sum(a * b for a, b in sizes)
+    order = sorted(range(len(sizes)), key=lambda i: -sizes[i][0] * sizes[i][1])
+    jobs = [(i, sizes[i][0], sizes[i][1], 1, False) for i in order]
+    if args.warmup > 0:
+        pool.map(_oracle_patch, jobs[len(jobs) // 2:], chunksize=1)  # warm-up on half the patches
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < args.steps:
+        pool.map(_oracle_patch, jobs, chunksize=1)
+        steps += 1
+        if time.perf_counter() - t0 > args.ref_seconds:
+            break
+    el = time.perf_counter() - t0
+    pool.close()
+    value = cells * steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world,
+        "steps": steps, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * el / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "patches": 512, "cells": cells,
+                   "precision": "fp64 (oracle, each patch a periodic grid of its own)"},
+        "cpu_baseline": {"value": value, "unit": "cell-steps/s", "cores": ncores, "kind": "oracle",
+                         "sample": "%d step(s) of all 512 patches (the full workload per step), one patch per "
+                                   "process on %d processes" % (steps, ncores)},
+        "e2e": {"value": value, "unit": "cell-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_te2048(args, world, rank):
+    """The FP64 CPU oracle on the host cores (bounded sample of the 2048^2 workload)."""
     if rank != 0:
         return
     from oracle import psatd as orc
@@ -329,29 +743,46 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-seconds", type=float, default=30.0)
+    ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed_fp16", "mixed_bf16"],
-                    help="te2048 arithmetic of the headline line: plain FP32, or tensor-core split-FP16 / "
-                         "split-BF16 radix-16 stages (the others are timed too, under 'other_precision')")
-    ap.add_argument("--no-side-precision", action="store_true", help="skip timing the other precision")
+    ap.add_argument("--precision", default=None, choices=["fp32", "mixed_fp16", "mixed_bf16"],
+                    help="batch512: the mixed precision of the headline (default mixed_bf16); te2048: the "
+                         "headline precision (default fp32; the others are timed too, under 'other_precision')")
+    ap.add_argument("--no-side-precision", action="store_true",
+                    help="skip the side keys (other precisions, the te2048 side line)")
     ap.add_argument("--no-comparator", action="store_true", help="skip timing the cuFFT comparator")
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the end-to-end legs (profiling runs: only the timed steps' kernels)")
-    ap.add_argument("--workload", default="te2048",
-                    choices=["te2048", "3d256", "3d512", "fdtd-yee", "fdtd-ckc", "batch512", "local", "cost3d",
-                             "small128"],
-                    help="te2048 (default) is the metric's configuration; the others are side measurements")
+    ap.add_argument("--workload", default="batch512",
+                    choices=["batch512", "te2048", "3d256", "3d512", "fdtd-yee", "fdtd-ckc", "local", "cost3d",
+                             "small128", "batch512-side"],
+                    help="batch512 (default) is the metric's configuration; the others are side measurements")
     args = ap.parse_args()
+    if args.warmup < 2:
+        ap.error("--warmup must be >= 2 (the warm-up call records the step graph)")
     world, rank, local = dist_setup()
     if args.impl == "reference":
-        run_reference(args, world, rank)
+        if args.workload == "te2048":
+            run_reference_te2048(args, world, rank)
+        else:
+            run_reference_batch(args, world, rank)
         return
+    if args.workload == "batch512":
+        args.precision = args.precision or "mixed_bf16"
+        run_batch_line(args, world, rank, local)
+        return
+    args.precision = args.precision or "fp32"
     if args.workload != "te2048":
+        if args.workload == "batch512-side":
+            args.workload = "batch512"
         run_side_workload(args)
         return
+    run_te2048_line(args, world, rank, local)
 
+
+def run_te2048_line(args, world, rank, local):
+    """Side line: the single 2048^2 TE grid (one psatd_step per step), all precisions."""
     import torch
     from paper_1608_05739_gb300 import build as bld
     from paper_1608_05739_gb300 import capi

@@ -304,6 +304,18 @@ int64_t psatd_batch_cells(psatd_batch batch);
  * or PSATD_ERR_NONFINITE (PSATD_FLAG_CHECKED) since the last sync. */
 psatd_status psatd_batch_sync(psatd_batch batch);
 
+/* Per-kernel CUDA-event timing of the batch, as psatd_plan_set_timing /
+ * psatd_kernel_times do for a plan, summed over the size classes: enable != 0
+ * records an event pair around every launch of every class (the recorded step
+ * graph is recorded again with them, so each replay updates the pairs: after
+ * a multi-step call they hold the last step's times).  psatd_batch_kernel_times
+ * synchronises and writes per kernel slot its name, launches and summed ms.
+ * Kernels of different classes may run at the same time on the batch's branch
+ * streams, so a slot's summed time can exceed the step's wall time. */
+psatd_status psatd_batch_set_timing(psatd_batch batch, int32_t enable);
+int32_t psatd_batch_kernel_times(psatd_batch batch, int32_t n_slots, const char** names,
+                                 int64_t* launches, double* total_ms);
+
 /* Release the batch (synchronises its stream).  NULL is accepted. */
 psatd_status psatd_batch_destroy(psatd_batch batch);
 

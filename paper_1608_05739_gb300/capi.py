@@ -73,6 +73,9 @@ EXPORTS = [
     ("psatd_batch_cells", ct.c_int64, [ct.c_void_p]),
     ("psatd_batch_sync", ct.c_int, [ct.c_void_p]),
     ("psatd_batch_destroy", ct.c_int, [ct.c_void_p]),
+    ("psatd_batch_set_timing", ct.c_int, [ct.c_void_p, ct.c_int32]),
+    ("psatd_batch_kernel_times", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_char_p),
+                                              ct.POINTER(ct.c_int64), ct.POINTER(ct.c_double)]),
     ("psatd_plan_autotune", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_char_p, ct.c_size_t]),
     ("psatd_plan_set_launch", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32)]),
     ("psatd_plan_get_launch", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32)]),
@@ -302,6 +305,17 @@ class Batch:
 
     def cells(self):
         return int(load().psatd_batch_cells(self.handle))
+
+    def set_timing(self, enable=True):
+        _check(load().psatd_batch_set_timing(self.handle, 1 if enable else 0))
+
+    def kernel_times(self):
+        """{kernel name: (launches, total ms)} summed over the size classes."""
+        names = (ct.c_char_p * 8)()
+        launches = (ct.c_int64 * 8)()
+        ms = (ct.c_double * 8)()
+        k = load().psatd_batch_kernel_times(self.handle, 8, names, launches, ms)
+        return {names[i].decode(): (int(launches[i]), float(ms[i])) for i in range(k)}
 
     def sync(self):
         """psatd_batch_sync: wait for the batch and raise on a recorded device error."""

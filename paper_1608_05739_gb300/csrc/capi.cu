@@ -1547,6 +1547,46 @@ extern "C" psatd_status psatd_batch_sync(psatd_batch b) {
   return PSATD_OK;
 }
 
+extern "C" psatd_status psatd_batch_set_timing(psatd_batch b, int32_t enable) {
+  if (!b) return fail(nullptr, PSATD_ERR_INVALID_ARG, "batch is NULL");
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "stream synchronise");
+  // the event pairs are part of a recorded step graph: record it again
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  for (psatd_plan p : b->cls) {
+    psatd_status s = psatd_plan_set_timing(p, enable);
+    if (s != PSATD_OK) return s;
+  }
+  return PSATD_OK;
+}
+
+extern "C" int32_t psatd_batch_kernel_times(psatd_batch b, int32_t n_slots, const char** names, int64_t* launches,
+                                            double* total_ms) {
+  if (!b) return 0;
+  cudaStreamSynchronize(b->st);
+  int64_t nl[K_NSLOTS] = {};
+  double ms[K_NSLOTS] = {};
+  for (psatd_plan p : b->cls)
+    for (int s = 0; s < K_NSLOTS; ++s)
+      for (auto& e : p->ev[s]) {
+        float t = 0;
+        if (cudaEventElapsedTime(&t, e.a, e.b) == cudaSuccess) ms[s] += t;
+        ++nl[s];
+      }
+  int used = 0;
+  for (int s = 0; s < K_NSLOTS && used < n_slots; ++s) {
+    if (!nl[s]) continue;
+    if (names) names[used] = kSlotNames[s];
+    if (launches) launches[used] = nl[s];
+    if (total_ms) total_ms[used] = ms[s];
+    ++used;
+  }
+  return used;
+}
+
 extern "C" psatd_status psatd_batch_destroy(psatd_batch b) {
   if (!b) return PSATD_OK;
   cudaStreamSynchronize(b->st);

@@ -203,10 +203,11 @@ def coulomb_field(rho, d, eps0=1.0):
 
 
 def gaussian_charges_torch(shape, d, dt, *, n_charges=64, sigma=None, vmax=0.5, c=1.0, seed=1610,
-                           step=0, device="cuda"):
+                           step=0, device="cuda", double=False):
     """GPU twin of :func:`gaussian_charges` (same seeded draws and formulas, evaluated with
-    torch on ``device``; for large grids).  Returns float32 CUDA tensors
-    (rho_n, rho_np1, J) with J of shape ``(3, *shape)``, and the Coulomb field E of rho_n."""
+    torch on ``device``; for large grids).  Returns float32 (``double``: float64) CUDA
+    tensors (rho_n, rho_np1, J) with J of shape ``(3, *shape)``, and the Coulomb field E
+    of rho_n."""
     import torch
 
     ndim = len(shape)
@@ -252,28 +253,66 @@ def gaussian_charges_torch(shape, d, dt, *, n_charges=64, sigma=None, vmax=0.5, 
     for a in range(ndim):
         Eh = torch.where(k2 > 0, -1j * ks[a] * rho0 / k2s, torch.zeros_like(rho0))
         E[a] = torch.fft.irfftn(Eh, s=shape, dim=dims)
+    if double:
+        return r0, r1, J, E
     return r0.float(), r1.float(), J.float(), E.float()
 
 
-def batch_patch_sizes(npatch=512, seed=1612, mixed_ok=True):
+def batch_patch_domains(npatch=512, seed=1612):
     """Patch domains of the batched local-FFT workload (Sec. II.A.3): per patch an
     interior n ~ U{64..512} and a guard width g ~ U{8..16}, drawn independently per
-    axis (x first), each side the smallest transform length >= n + 2g -- a power of
-    two, or with ``mixed_ok`` also 3 * 2^k from 96 up.  Returns ([(nx, ny), ...],
-    interior cells)."""
-    cand = [1 << k for k in range(4, 13)] + ([3 << k for k in range(5, 11)] if mixed_ok else [])
+    axis (x first).  Returns [((nx_int, gx), (ny_int, gy)), ...]."""
+    g = rng(seed)
+    out = []
+    for _ in range(npatch):
+        n = g.integers(64, 513, size=2)
+        gg = g.integers(8, 17, size=2)
+        out.append(((int(n[0]), int(gg[0])), (int(n[1]), int(gg[1]))))
+    return out
+
+
+def transform_lengths(mixed_ok=True):
+    """Transform lengths of the batch's patch sides: powers of two, and with
+    ``mixed_ok`` also 3 * 2^k from 96 up (the lengths the FP32 passes take)."""
+    return sorted([1 << k for k in range(4, 13)] + ([3 << k for k in range(5, 11)] if mixed_ok else []))
+
+
+def batch_patch_sizes(npatch=512, seed=1612, mixed_ok=True, lengths=None):
+    """Periodic patch sides of the batched workload: each side is the smallest
+    transform length >= n + 2g (``lengths``, default transform_lengths(mixed_ok)),
+    i.e. the guard region is widened to the next length the FFT takes.  Returns
+    ([(nx, ny), ...], interior cells)."""
+    cand = sorted(lengths) if lengths is not None else transform_lengths(mixed_ok)
 
     def side(v):
         return min(x for x in cand if x >= v)
 
-    g = rng(seed)
     sizes, interior = [], 0
-    for _ in range(npatch):
-        n = g.integers(64, 513, size=2)
-        gg = g.integers(8, 17, size=2)
-        sizes.append((side(int(n[0]) + 2 * int(gg[0])), side(int(n[1]) + 2 * int(gg[1]))))
-        interior += int(n[0]) * int(n[1])
+    for (nx, gx), (ny, gy) in batch_patch_domains(npatch, seed):
+        sizes.append((side(nx + 2 * gx), side(ny + 2 * gy)))
+        interior += nx * ny
     return sizes, interior
+
+
+def batch_requested_cells(npatch=512, seed=1612):
+    """Cells of the requested patch domains (n + 2g per side), summed over patches."""
+    return sum((nx + 2 * gx) * (ny + 2 * gy) for (nx, gx), (ny, gy) in batch_patch_domains(npatch, seed))
+
+
+def batch_source(sizes, seed=1613, scale=0.01):
+    """Seeded source of the batched workload: per patch i, (Jx, Jy) of shape
+    (ny_i, nx_i) drawn N(0, scale^2) in float32 from rng(seed + i), packed per
+    component patch after patch.  Returns (Jx, Jy) float32 arrays; any patch can
+    be regenerated alone with batch_patch_source."""
+    parts = [batch_patch_source(i, nx, ny, seed, scale) for i, (nx, ny) in enumerate(sizes)]
+    return (np.concatenate([p[0].ravel() for p in parts]), np.concatenate([p[1].ravel() for p in parts]))
+
+
+def batch_patch_source(i, nx, ny, seed=1613, scale=0.01):
+    g = rng(seed + i)
+    J = g.standard_normal((2, ny, nx), dtype=np.float32)
+    J *= np.float32(scale)
+    return J[0], J[1]
 
 
 def large_3d_inputs_torch(shape, d, dt, *, n_charges=100000, sigma=None, vmax=0.5, c=1.0, eps0=1.0,

@@ -1,5 +1,7 @@
 """Helpers for the GPU parity tests: run the CUDA path through the C ABI on
 numpy inputs and compare with the FP64 oracle on the same (rounded) inputs."""
+import math
+
 import numpy as np
 
 from paper_1608_05739_gb300 import build as bld
@@ -91,7 +93,42 @@ def mask_layout(F, layout, which):
     return F
 
 
+# Largest element error allowed, in units of (tolerance x rms of the reference):
+# an error spread like noise over N elements peaks at a few times its rms
+# (about sqrt(2 ln N) < 6 for N < 1e8), while an error confined to one line of a
+# 2048^2 grid peaks at sqrt(2048) = 45 times its rms and fails.
+PEAK_K = 30.0
+
+
+class ParityErr(float):
+    """Relative L2 error of a parity comparison that also carries its peak: the
+    largest |a - b| over the rms of the reference b.  `err < tol` (tol a plain
+    number) holds when both rel-L2 < tol and peak <= PEAK_K * tol; between two
+    errors, and for every other operator, it is the plain rel-L2 float."""
+
+    def __new__(cls, rel, peak):
+        obj = float.__new__(cls, rel)
+        obj.peak = peak
+        return obj
+
+    def __lt__(self, other):
+        if isinstance(other, ParityErr) or not isinstance(other, (int, float)):
+            return float(self) < other
+        return float(self) < other and self.peak <= PEAK_K * other
+
+    def __le__(self, other):
+        if isinstance(other, ParityErr) or not isinstance(other, (int, float)):
+            return float(self) <= other
+        return float(self) <= other and self.peak <= PEAK_K * other
+
+    def __repr__(self):
+        return "%r (peak %.3g x rms)" % (float(self), self.peak)
+
+
 def rel_l2_fields(E1, B1, E2, B2, c=1.0):
+    """Relative L2 over all E and c B components, with the per-element peak (ParityErr)."""
     a = np.concatenate([np.ravel(E1), c * np.ravel(B1)])
     b = np.concatenate([np.ravel(E2), c * np.ravel(B2)])
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    nb = float(np.linalg.norm(b))
+    rms = nb / math.sqrt(b.size)
+    return ParityErr(float(np.linalg.norm(a - b)) / nb, float(np.max(np.abs(a - b))) / rms)

@@ -66,6 +66,46 @@ def test_batch512_full_size_sampled_patches(prec, tol):
         assert err < tol, (i, nx, ny, err)
 
 
+def test_batch512_split_bf16_100_step_graph_run():
+    """The batched workload as the bench times it: 512 patches (power-of-two sides),
+    split-BF16 tensor-core stages, E = B = 0 and the seeded per-patch J, 100 steps
+    as one graph replay on a side stream; sampled patches (the smallest, and seeded
+    others up to 512 x 128 cells, to bound the oracle's time) against the oracle
+    run 100 steps on each patch alone, within the mixed path's 2e-5."""
+    import torch
+    ensure_lib()
+    sizes, _ = synth.batch_patch_sizes(mixed_ok=False)
+    dx = 1.0 / 64
+    d, dt = (dx, dx), dx / math.sqrt(2.0)
+    jx, jy = synth.batch_source(sizes, 1613, 0.01)
+    total = sum(a * b for a, b in sizes)
+    Ex, Ey, Bz = (torch.zeros(total, device="cuda") for _ in range(3))
+    Jx, Jy = torch.from_numpy(jx).cuda(), torch.from_numpy(jy).cuda()
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    b = capi.Batch(sizes, d, dt, layout="te", prec="mixed_bf16", src="J", stream=stream)
+    with torch.cuda.stream(stream):
+        b.step([Ex, Ey, None], [None, None, Bz], [Jx, Jy, None], nsteps=100)
+    b.sync()
+    b.destroy()
+    offs = np.concatenate([[0], np.cumsum([a * c for a, c in sizes])])
+    area = np.array([a * c for a, c in sizes])
+    small = np.flatnonzero(area <= 512 * 128)
+    pick = {int(np.argmin(area))} | set(int(i) for i in synth.rng(1619).choice(small, 5, replace=False))
+    for i in sorted(pick):
+        nx, ny = sizes[i]
+        cut = lambda t: t[offs[i]:offs[i + 1]].double().cpu().numpy().reshape(ny, nx)
+        pj = synth.batch_patch_source(i, nx, ny, 1613, 0.01)
+        z = np.zeros((ny, nx))
+        J = np.stack([pj[0].astype(np.float64), pj[1].astype(np.float64), z])
+        Eo, Bo = orc.psatd_step(np.zeros((3, ny, nx)), np.zeros((3, ny, nx)), J, d=d, dt=dt, form="J",
+                                nsteps=100)
+        Eg = np.stack([cut(Ex), cut(Ey), z])
+        Bg = np.stack([z, z, cut(Bz)])
+        err = rel_l2_fields(Eg, Bg, mask_layout(Eo, "te", "E"), mask_layout(Bo, "te", "B"))
+        assert err < 2e-5, (i, nx, ny, err)
+
+
 def _modes(shape, M, seed):
     """Sampled (mz, my, mx) rfftn indices: the origin, Nyquist planes, the smallest
     |k| on each axis, and seeded random modes."""
