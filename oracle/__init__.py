@@ -22,6 +22,9 @@ Particle-In-Cell codes") says the solvers compute:
 * ``local``      -- the local-FFT decomposition (Sec. II.A.3): patches with
                     guard cells refreshed from their neighbours, each advanced as
                     a periodic domain of its own.
+* ``farfield``   -- the Fraunhofer far-field transform of a field snapshot
+                    (Sec. II.B), the diagnostic of the angularly resolved
+                    harmonic spectrum.
 ``psatd`` also holds the staggered order-p variant (Table 1 row PSATD-p) and the
 PSTD scheme (Table 1 row PSTD).
 
