@@ -381,6 +381,31 @@ psatd_status psatd_local_destroy(psatd_local local);
 psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_fields* fields,
                                 const psatd_sources* sources, int32_t nsteps, void* cuda_stream);
 
+/* Fraunhofer far-field transform of a 2D field snapshot: the diagnostic of the
+ * angularly resolved harmonic spectrum (Sec. II.B applies the Fraunhofer
+ * diffraction integral to the reflected field of the simulation).  For every
+ * wavevector k_j = (k[2j], k[2j+1]):
+ *   U_j = sum_{x0 <= i < x1, y0 <= j' < y1} w_i v_j' F[j'][i]
+ *         exp(-i (k[2j] i dx + k[2j+1] j' dy)) dx dy,
+ * the far-field amplitude radiated towards direction k_j/|k_j| at wavenumber
+ * |k_j| (harmonic n of a fundamental k0: the ring |k| = n k0).  w, v: Hann
+ * apodisation sin^2(pi (i - x0 + 1/2)/(x1 - x0)) along x (apodise >= 1) and
+ * along y (apodise == 2), else 1.
+ * grid: ndim 2, n[0] = nx, n[1] = ny (the field's row length and rows), d[0],
+ * d[1]; prec PSATD_FP32 (float field) or PSATD_FP64 (double); the other
+ * members are ignored.  field: [ny][nx], x contiguous; window = {x0, x1, y0,
+ * y1} (cells, half-open, inside the grid; rows of at most 8192 cells); k: nk
+ * (kx, ky) pairs of doubles; out: nk (re, im) pairs of doubles, written.  The
+ * field, k and out are device memory or pinned host memory of the current
+ * device, caller-owned.  One launch on `cuda_stream`, no allocation, no
+ * synchronisation; the sums are taken in a fixed order (deterministic), rows in
+ * the field's precision, the phases and the sum over rows in FP64.
+ * Errors: INVALID_ARG (NULL, empty or out-of-grid window, nk < 1, bad apodise,
+ * inaccessible or misaligned pointer), UNSUPPORTED (3D, longer rows), CUDA.  */
+psatd_status psatd_farfield(const psatd_desc* grid, const void* field, const int64_t window[4],
+                            int32_t apodise, int32_t nk, const double* k, double* out,
+                            void* cuda_stream);
+
 /* Message of the last failure on `plan`, or of this thread's last failure
  * without a plan when plan == NULL.  Never NULL. */
 const char* psatd_last_error(psatd_plan plan);

@@ -84,6 +84,8 @@ EXPORTS = [
     ("psatd_local_step", ct.c_int, [ct.c_void_p, ct.POINTER(psatd_fields), ct.POINTER(psatd_sources), ct.c_int32]),
     ("psatd_local_plan", ct.c_void_p, [ct.c_void_p]),
     ("psatd_local_destroy", ct.c_int, [ct.c_void_p]),
+    ("psatd_farfield", ct.c_int, [ct.POINTER(psatd_desc), ct.c_void_p, ct.POINTER(ct.c_int64), ct.c_int32, ct.c_int32,
+                                  ct.c_void_p, ct.c_void_p, ct.c_void_p]),
 ]
 
 FLAG_AUTOTUNE = 1
@@ -420,3 +422,32 @@ def step_noalloc(n, d, dt, E, B, J=None, rho_n=None, rho_np1=None, *, layout="te
         stream = torch.cuda.current_stream()
     _check(fn(ct.byref(desc), ct.byref(f), ct.byref(s) if s is not None else None, int(nsteps),
               ct.c_void_p(stream.cuda_stream)))
+
+
+APODISE = {"none": 0, "x": 1, "xy": 2}
+
+
+def farfield(n, d, field, k, *, x_range=None, y_range=None, window="none", stream=None):
+    """psatd_farfield: the Fraunhofer far-field transform of the 2D snapshot ``field``
+    ([ny, nx] CUDA tensor, float32 or float64) at the wavevectors ``k`` ((nk, 2)
+    float64 CUDA tensor of (kx, ky)); returns a complex128 CUDA tensor (nk,).
+    x_range / y_range: (start, stop) cells of the window (default the whole
+    axis); window: Hann apodisation "none", "x" or "xy"."""
+    import torch
+    lib = load()
+    prec = "fp32" if field.dtype == torch.float32 else "fp64"
+    desc = make_desc(n, d, 1.0, layout="te", prec=prec, src="none")
+    shape = _grid_shape(n)
+    ptr = _ptr(field, shape, field.dtype, "field")
+    if k.dtype != torch.float64 or k.dim() != 2 or k.shape[1] != 2 or not k.is_contiguous():
+        raise ValueError("k must be a contiguous float64 tensor of shape (nk, 2)")
+    nx, ny = int(n[0]), int(n[1])
+    x0, x1 = x_range if x_range is not None else (0, nx)
+    y0, y1 = y_range if y_range is not None else (0, ny)
+    win = (ct.c_int64 * 4)(int(x0), int(x1), int(y0), int(y1))
+    out = torch.empty((k.shape[0], 2), dtype=torch.float64, device=k.device)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib.psatd_farfield(ct.byref(desc), ptr, win, APODISE[window], int(k.shape[0]), k.data_ptr(),
+                              out.data_ptr(), ct.c_void_p(stream.cuda_stream)))
+    return torch.view_as_complex(out)

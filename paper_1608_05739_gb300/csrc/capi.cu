@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "../../include/psatd.h"
+#include "farfield.h"
 #include "launch.h"
 #include "local.h"
 #include "tables.h"
@@ -331,10 +332,21 @@ size_t tc_a3_bytes(psatd_plan p, int threads) {
   return p->tc_bf16 ? (size_t)(threads / 128) * TcGeom<16>::kAPiece : 0;
 }
 
+// Event pair around one launch on the plan's stream.  While the stream is being
+// captured into a graph (multi-step batch calls) the events are captured as
+// external event-record nodes, so that every replay records them again (a plain
+// record during capture only expresses a dependency and is never timed).
 struct TimedLaunch {
   psatd_plan p;
   int slot;
   EventPair ep{};
+  static void record(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+      cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else
+      cudaEventRecord(e, st);
+  }
   TimedLaunch(psatd_plan pl, int s) : p(pl), slot(s) {
     if (!p->timing) return;
     if (!p->pool.empty()) {
@@ -344,11 +356,11 @@ struct TimedLaunch {
       cudaEventCreate(&ep.a);
       cudaEventCreate(&ep.b);
     }
-    cudaEventRecord(ep.a, p->st);
+    record(ep.a, p->st);
   }
   ~TimedLaunch() {
     if (!p->timing) return;
-    cudaEventRecord(ep.b, p->st);
+    record(ep.b, p->st);
     p->ev[slot].push_back(ep);
   }
 };
@@ -469,8 +481,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     {
       const int tb = p->cfg_push_tb > 0 ? p->cfg_push_tb
                                         : push_lines_per_cta(Lline, p->n_in, nlines, TC, p->f32, p->push_ept);
-      const size_t per_line = ((size_t)p->n_in + 1) * (size_t)Lline * csz;
-      const size_t a3 = tb > 1 ? tc_a3_bytes(p, tb * (Lline / p->push_ept)) : 0;  // one line: in its slot
+      const size_t per_line = ((size_t)p->n_in + 1) * (size_t)Lline * csz;  // split-BF16's third piece: in a slot
       const dim3 grid((unsigned)((nlines + tb - 1) / tb));
       TimedLaunch tl(p, K_PUSH);
       if (p->push_ept == 12) {
@@ -479,7 +490,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
         else
           e = cudaErrorInvalidValue;
       } else if (p->push_ept == 16) {
-        e = launch_line_push<R, TC, 16>(Lline, p->layout, grid, tb, tail + tb * per_line + a3, p->st, a, twl);
+        e = launch_line_push<R, TC, 16>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl);
       } else {
         if constexpr (TC) e = cudaErrorInvalidValue;
         else e = launch_line_push<R, false, 8>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl);
@@ -549,8 +560,7 @@ psatd_status check_tc_shape(psatd_plan p, int maxsm) {
   }
   const int64_t nlines = p->ndim == 3 ? p->nxh * p->ny : p->nxh * p->npatch;
   const int tb = push_lines_per_cta(Ll, p->n_in, nlines, true, true, 16);
-  const size_t smem = (size_t)kTcTail + (size_t)tb * ((size_t)p->n_in + 1) * (size_t)Ll * 8 +
-                      (tb > 1 ? tc_a3_bytes(p, tb * (Ll / 16)) : 0);
+  const size_t smem = (size_t)kTcTail + (size_t)tb * ((size_t)p->n_in + 1) * (size_t)Ll * 8;
   if (maxsm > 0 && smem > (size_t)maxsm)
     return fail(nullptr, PSATD_ERR_UNSUPPORTED, "mixed precision: last-axis length %d needs %zu bytes of shared memory",
                 Ll, smem);
@@ -642,7 +652,7 @@ TuneSpace tune_space(psatd_plan p) {
     const size_t per_line = ((size_t)p->n_in + 1) * (size_t)ts.Ll * csz;
     for (int tb = 1; tb * T <= (T > 256 ? T : 256); tb *= 2) {
       if (p->tc && (tb * T) % 128 != 0) continue;
-      if (maxsm > 0 && tail + tb * per_line + (tb > 1 ? tc_a3_bytes(p, tb * T) : 0) > (size_t)maxsm) continue;
+      if (maxsm > 0 && tail + tb * per_line > (size_t)maxsm) continue;
       if (tb > 1 && tb / 2 >= nlines) break;
       ts.push.push_back({ept, tb});
     }
@@ -1069,6 +1079,7 @@ int32_t psatd_kernel_times(psatd_plan p, int32_t n_slots, const char** names, in
     for (auto& e : p->ev[s]) {
       float t = 0;
       if (cudaEventElapsedTime(&t, e.a, e.b) == cudaSuccess) ms += t;
+      else cudaGetLastError();
     }
     if (names) names[used] = kSlotNames[s];
     if (launches) launches[used] = (int64_t)p->ev[s].size();
@@ -1125,6 +1136,51 @@ psatd_status fdtd_step(const psatd_desc* desc, int32_t scheme, const psatd_field
                       : launch_fdtd<double>(desc->ndim, scheme, desc->n[0], desc->n[1], nz, desc->d, desc->dt, desc->c,
                                             desc->eps0, fields->E, fields->B, J, nsteps, st);
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "fdtd launch");
+  return PSATD_OK;
+}
+
+psatd_status psatd_farfield(const psatd_desc* grid, const void* field, const int64_t window[4], int32_t apodise,
+                            int32_t nk, const double* k, double* out, void* cuda_stream) {
+  if (!grid || !field || !window || !k || !out)
+    return fail(nullptr, PSATD_ERR_INVALID_ARG, "grid, field, window, k and out must be non-NULL");
+  if (grid->ndim != 2) return fail(nullptr, PSATD_ERR_UNSUPPORTED, "the far-field transform takes 2D fields");
+  if (grid->prec != PSATD_FP32 && grid->prec != PSATD_FP64)
+    return fail(nullptr, PSATD_ERR_INVALID_ARG, "the field must be PSATD_FP32 or PSATD_FP64");
+  const int64_t nx = grid->n[0], ny = grid->n[1];
+  if (nx < 1 || ny < 1 || !pos_finite(grid->d[0]) || !pos_finite(grid->d[1]))
+    return fail(nullptr, PSATD_ERR_INVALID_ARG, "grid sizes must be >= 1 and cell sizes finite and > 0");
+  const int64_t x0 = window[0], x1 = window[1], y0 = window[2], y1 = window[3];
+  if (x0 < 0 || x1 > nx || x0 >= x1 || y0 < 0 || y1 > ny || y0 >= y1)
+    return fail(nullptr, PSATD_ERR_INVALID_ARG, "window [%lld, %lld) x [%lld, %lld) is empty or outside the grid",
+                (long long)x0, (long long)x1, (long long)y0, (long long)y1);
+  if (x1 - x0 > kFarfieldMaxRow)
+    return fail(nullptr, PSATD_ERR_UNSUPPORTED, "window rows longer than %lld cells", (long long)kFarfieldMaxRow);
+  if (apodise < 0 || apodise > 2) return fail(nullptr, PSATD_ERR_INVALID_ARG, "apodise must be 0, 1 or 2");
+  if (nk < 1) return fail(nullptr, PSATD_ERR_INVALID_ARG, "nk must be >= 1");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (!dev_accessible(field, dev) || !dev_accessible(k, dev) || !dev_accessible(out, dev))
+    return fail(nullptr, PSATD_ERR_INVALID_ARG, "field, k and out must be accessible from the current device");
+  const size_t esz = grid->prec == PSATD_FP32 ? 4 : 8;
+  if ((reinterpret_cast<uintptr_t>(field) % esz) || (reinterpret_cast<uintptr_t>(k) % 8) ||
+      (reinterpret_cast<uintptr_t>(out) % 8))
+    return fail(nullptr, PSATD_ERR_INVALID_ARG, "field, k or out misaligned for its element type");
+  FarfieldArgs a;
+  a.F = field;
+  a.nx = nx;
+  a.x0 = x0;
+  a.x1 = x1;
+  a.y0 = y0;
+  a.y1 = y1;
+  a.dx = grid->d[0];
+  a.dy = grid->d[1];
+  a.win_x = apodise >= 1;
+  a.win_y = apodise == 2;
+  a.k = k;
+  a.out = out;
+  a.nk = nk;
+  cudaError_t e = launch_farfield(grid->prec == PSATD_FP32, a, static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "far-field launch");
   return PSATD_OK;
 }
 
@@ -1574,6 +1630,7 @@ extern "C" int32_t psatd_batch_kernel_times(psatd_batch b, int32_t n_slots, cons
       for (auto& e : p->ev[s]) {
         float t = 0;
         if (cudaEventElapsedTime(&t, e.a, e.b) == cudaSuccess) ms[s] += t;
+        else cudaGetLastError();
         ++nl[s];
       }
   int used = 0;

@@ -494,7 +494,7 @@ __device__ __forceinline__ int slot_stagger(int c) {
 }
 
 template <typename R, int LAYOUT, bool PSTD>
-__device__ __forceinline__ void push_slots(typename Types<R>::C* st, int L, int l, const CoefReg<R>& f,
+__device__ __forceinline__ void push_slots(typename Types<R>::C* st, int ss, int l, const CoefReg<R>& f,
                                            R mx, R my, R mz, const PushArgs<R>& a,
                                            const typename Types<R>::W* P) {
   typedef typename Types<R>::C C;
@@ -528,7 +528,7 @@ __device__ __forceinline__ void push_slots(typename Types<R>::C* st, int L, int 
       return *this;
     }
   };
-  auto S = [&](int c) -> Ref { return Ref{&st[c * L + l], slot_stagger<LAYOUT>(c) & zmask, P}; };
+  auto S = [&](int c) -> Ref { return Ref{&st[c * ss + l], slot_stagger<LAYOUT>(c) & zmask, P}; };
   if constexpr (PSTD) {  // J-form or vacuum
     C E[3] = {Z, Z, Z}, B[3] = {Z, Z, Z}, J[3] = {Z, Z, Z};
     if constexpr (LAYOUT == 2) {
@@ -636,7 +636,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // both loads issued together), PSTD none; staggered plans rotate every slot
 // value to its Yee position and back around the update.
 template <typename R, int L, int LAYOUT, int EPT, bool STAG, bool PSTD>
-__device__ __forceinline__ void push_line_modes(typename Types<R>::C* st, const PushArgs<R>& a,
+__device__ __forceinline__ void push_line_modes(typename Types<R>::C* st, int ss, const PushArgs<R>& a,
                                                 const Coef<R>* trow, int t, int mxi, int myi, R kpx, R kpy,
                                                 typename Types<R>::W phx, typename Types<R>::W phy) {
   typedef typename Types<R>::W Wt;
@@ -680,7 +680,7 @@ __device__ __forceinline__ void push_line_modes(typename Types<R>::C* st, const 
           Ph[1] = phy;
           Ph[2] = pl;
         }
-        push_slots<R, LAYOUT, PSTD>(st, L, sw<CXL>(l), f, mx, my, mz, a, Ph);
+        push_slots<R, LAYOUT, PSTD>(st, ss, sw<CXL>(l), f, mx, my, mz, a, Ph);
       } else {
         const int ml = (l == L / 2) ? 0 : (l < L / 2 ? l : l - L);
         if (a.ndim == 2) {
@@ -688,7 +688,7 @@ __device__ __forceinline__ void push_line_modes(typename Types<R>::C* st, const 
         } else {
           mx = a.rx * R(mxi); my = a.ry * R(myi); mz = a.rz * R(ml);
         }
-        push_slots<R, LAYOUT, PSTD>(st, L, sw<CXL>(l), f, mx, my, mz, a, nullptr);
+        push_slots<R, LAYOUT, PSTD>(st, ss, sw<CXL>(l), f, mx, my, mz, a, nullptr);
       }
     }
   }
@@ -696,13 +696,16 @@ __device__ __forceinline__ void push_line_modes(typename Types<R>::C* st, const 
 
 // Fused last-axis pass: for TB lines (kx in 2D, (kx, ky) in 3D), forward FFT
 // of every input slot, per-mode push, inverse FFT of the n_out field slots,
-// written back in place.  Shared memory: n_in staged slots of L values per
-// line, then one extra exchange buffer per line (contiguous, so that in the
-// tensor-core variant TC they hold the A tiles of the CTA's 128-row groups);
-// a slot doubles as the other exchange buffer of its own transforms.  After
-// its forward FFT a slot holds the spectrum at positions sw<kLastCX>(t + T m),
-// so the push and the inverse FFT's first exchange only touch each thread's
-// own positions.
+// written back in place.  Shared memory, component-major: slot c of the TB
+// lines (TB x L values, line g at offset g L), c < n_in, then one extra
+// exchange buffer per line (contiguous, so that in the tensor-core variant TC
+// they hold the A tiles of the CTA's 128-row groups); a slot doubles as the
+// other exchange buffer of its own transforms, and in split-BF16 the TB lines'
+// slot c of the component being transformed holds the third A piece (no line
+// keeps live data there at a tensor-core stage boundary), so the pass needs no
+// further region.  After its forward FFT a slot holds the spectrum at positions
+// sw<kLastCX>(t + T m), so the push and the inverse FFT's first exchange only
+// touch each thread's own positions.
 // EPT: elements per thread, 8 (radix-8 stages) or 16 (radix-16 stages; the
 // only choice of the tensor-core variant).
 template <typename R, int L, int LAYOUT, int TC = 0, int EPT = PushEPT<L, TC>::value>
@@ -718,19 +721,15 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   const int line = blockIdx.x * blockDim.y + g;
   const bool valid = line < a.nlines;
   C* base = reinterpret_cast<C*>(smem_raw + (TC ? kTcTail : 0));
-  C* st = base + g * (a.n_in * L);
-  C* bufB = base + (int)blockDim.y * a.n_in * L + g * L;
+  const int ss = (int)blockDim.y * L;  // slot stride (component-major)
+  C* st = base + g * L;                // this line's slot 0; slot c at st + c * ss
+  C* bufB = base + a.n_in * ss + g * L;
   C* spec = static_cast<C*>(a.spec);
   __shared__ const void* twslot;
   if (t == 0 && g == 0) twslot = tw;
   TcCtx tc;
-  // split-BF16's third A piece: the current slot when the CTA holds one line (its
-  // own transforms leave it without live data at every stage boundary), else a
-  // region after the extra buffers
-  const bool a3_slot = blockDim.y == 1;
-  if constexpr (TC)
-    tc_setup(tc, smem_raw, a.gmat, smem_u32(base + (int)blockDim.y * a.n_in * L), a.err, TC == 2,
-             smem_u32(base + (int)blockDim.y * (a.n_in + 1) * L), a.tc_ctl);
+  if constexpr (TC)  // split-BF16's third A piece: set per component below
+    tc_setup(tc, smem_raw, a.gmat, smem_u32(base + a.n_in * ss), a.err, TC == 2, smem_u32(base), a.tc_ctl);
 
   int mxi, myi, rowi;
   line_modes(a, valid ? line : 0, mxi, myi, rowi);
@@ -754,7 +753,7 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
     constexpr int CH = (L * (int)sizeof(C)) / 16;  // chunks per slot
     for (int c = 0; c < a.n_in; ++c) {
       const char* src = reinterpret_cast<const char*>(spec + c * a.cs + (int64_t)line * L);
-      char* dst = reinterpret_cast<char*>(st + c * L);
+      char* dst = reinterpret_cast<char*>(st + c * ss);
       for (int i = t; i < CH; i += T) {
         if (valid) cp_async16(dst + 16 * i, src + 16 * i);
         else reinterpret_cast<float4*>(dst)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -765,13 +764,12 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   }
   C v[EPT];
   for (int c = 0; c < a.n_in; ++c) {
-    C* sl = st + c * L;
+    C* sl = st + c * ss;
 #pragma unroll
     for (int m = 0; m < EPT; ++m) v[m] = sl[t + T * m];
     __syncthreads();  // the slot becomes an exchange buffer
     ExBuf<C> ex{{sl, bufB}, 0, &twslot, false};
-    if constexpr (TC)
-      if (a3_slot) tc.a_tile3 = smem_u32(sl);
+    if constexpr (TC) tc.a_tile3 = smem_u32(base + c * ss);
     if constexpr (TC == 0 && (EPT == 8 || EPT == 12))
       block_fft_fwd_pf<R, L, EPT>(v, ex, t);
     else
@@ -783,20 +781,19 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   // push every mode of the line (each thread its own positions); one loop per
   // (staggered?, PSTD?) combination, chosen once per CTA
   if (a.scheme == 0) {
-    if (a.stag) push_line_modes<R, L, LAYOUT, EPT, true, false>(st, a, trow, t, mxi, myi, kpx, kpy, phx, phy);
-    else push_line_modes<R, L, LAYOUT, EPT, false, false>(st, a, trow, t, mxi, myi, kpx, kpy, phx, phy);
+    if (a.stag) push_line_modes<R, L, LAYOUT, EPT, true, false>(st, ss, a, trow, t, mxi, myi, kpx, kpy, phx, phy);
+    else push_line_modes<R, L, LAYOUT, EPT, false, false>(st, ss, a, trow, t, mxi, myi, kpx, kpy, phx, phy);
   } else {
-    if (a.stag) push_line_modes<R, L, LAYOUT, EPT, true, true>(st, a, trow, t, mxi, myi, kpx, kpy, phx, phy);
-    else push_line_modes<R, L, LAYOUT, EPT, false, true>(st, a, trow, t, mxi, myi, kpx, kpy, phx, phy);
+    if (a.stag) push_line_modes<R, L, LAYOUT, EPT, true, true>(st, ss, a, trow, t, mxi, myi, kpx, kpy, phx, phy);
+    else push_line_modes<R, L, LAYOUT, EPT, false, true>(st, ss, a, trow, t, mxi, myi, kpx, kpy, phx, phy);
   }
 
   for (int c = 0; c < a.n_out; ++c) {
-    C* sl = st + c * L;
+    C* sl = st + c * ss;
 #pragma unroll
     for (int m = 0; m < EPT; ++m) v[m] = sl[sw<CXL>(t + T * m)];
     ExBuf<C> ex{{sl, bufB}, 0, &twslot, false};
-    if constexpr (TC)
-      if (a3_slot) tc.a_tile3 = smem_u32(sl);
+    if constexpr (TC) tc.a_tile3 = smem_u32(base + c * ss);
     if constexpr (TC == 0 && (EPT == 8 || EPT == 12))
       block_fft_inv_pf<R, L, EPT>(v, ex, t);
     else

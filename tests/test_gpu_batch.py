@@ -82,3 +82,37 @@ def test_batch_graph_replay_equals_single_calls():
             assert np.array_equal(a, b)
     Eo, Bo = orc.psatd_step(per[4][0], per[4][1], per[4][2], d=d, dt=dt, form="J", nsteps=6)
     assert rel_l2_fields(_patch(E1, 4), _patch(B1, 4), mask_layout(Eo, "te", "E"), mask_layout(Bo, "te", "B")) < 1e-5
+
+
+@pytest.mark.parametrize("prec", ["fp32", "mixed_bf16"])
+def test_batch_kernel_times_of_a_graph_replay(prec):
+    """Batch timing with a multi-step call: the event pairs are recorded inside the
+    step graph, each replay times the launches again, and the results stay those of
+    an untimed run (bitwise)."""
+    import torch
+    ensure_lib()
+    sizes = [(256, 128), (128, 128), (256, 128), (512, 256)]
+    tot = sum(a * b for a, b in sizes)
+    g = torch.Generator(device="cuda").manual_seed(9)
+    init = [torch.randn(tot, device="cuda", generator=g) for _ in range(5)]
+    out = []
+    for timed in (False, True):
+        F = [t.clone() for t in init]
+        stream = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        b = capi.Batch(sizes, (1.0, 1.0), 0.5, layout="te", prec=prec, src="J", stream=stream)
+        if timed:
+            b.set_timing(True)
+        with torch.cuda.stream(stream):
+            b.step([F[0], F[1], None], [None, None, F[2]], [F[3], F[4], None], nsteps=4)
+        b.sync()
+        if timed:
+            kt = b.kernel_times()
+            assert set(kt) == {"fwd_x_r2c", "line_fft_push", "inv_x_c2r"}, kt
+            assert all(v[0] == 3 and v[1] > 0 for v in kt.values()), kt   # three size classes, one step's launches
+            b.set_timing(False)
+        b.sync()
+        b.destroy()
+        out.append(F[:3])
+    for x, y in zip(*out):
+        assert torch.equal(x, y)
