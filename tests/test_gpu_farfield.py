@@ -67,7 +67,11 @@ WIN = (X0 + 64, X0 + 576)        # snapshot window along x (all y)
 DT = 0.5
 HARM = (1, 2, 3, 4, 5, 6, 8)
 RAMP = 320.0
-STEPS = 2400                     # the window is in the steady state, before the periodic images
+# Along x a harmonic's energy moves at the group velocity c cos(theta_i) = 0.58 c (its parallel
+# wavenumber is fixed), so the turn-on tail leaves the window's far edge at t = RAMP + 576 / 0.58
+# = 1306; the snapshot is taken at t = 1700, long before the sheet's wave going the other way
+# comes round the periodic x axis (3520 cells at 0.58 c).
+STEPS = 3400
 
 
 def _snapshot(solver):
