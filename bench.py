@@ -340,14 +340,16 @@ def batch_e2e(torch, b, Jhost, stream, nsteps):
     return out[0], out[1]
 
 
-def roofline_of(ktimes, alg, hbm, peak_kind, traffic_lookup=True):
-    """Roofline object of the kernel with the largest summed time: algorithmic
-    bytes of its launches / their summed CUDA-event time, against `hbm`."""
+def roofline_of(ktimes, bytes_of, hbm, peak_kind, traffic_lookup=True, note=None):
+    """Roofline object of the kernel with the largest summed time: the algorithmic
+    bytes of its timed launches (bytes_of(kernel, launches)) over their summed
+    CUDA-event time, against `hbm`."""
     if not ktimes:
         return None
     dom = max(ktimes, key=lambda k: ktimes[k][1])
     n_l, tot = ktimes[dom]
-    achieved = alg[dom] / (tot * 1e-3) / 1e9
+    nbytes = bytes_of(dom, n_l)
+    achieved = nbytes / (tot * 1e-3) / 1e9
     traffic = None
     if traffic_lookup:
         try:
@@ -357,10 +359,24 @@ def roofline_of(ktimes, alg, hbm, peak_kind, traffic_lookup=True):
                 traffic = ent["bytes_per_launch"]
         except Exception:
             pass
-    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": traffic, "kernel": dom, "peak_kind": peak_kind, "launches": n_l,
-            "algorithmic_bytes_per_launch": alg[dom] / n_l,
-            "per_kernel_ms": {k: v[1] / v[0] for k, v in ktimes.items()}}
+    out = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+           "traffic": traffic, "kernel": dom, "peak_kind": peak_kind, "launches": n_l,
+           "algorithmic_bytes_per_launch": nbytes / n_l,
+           "per_kernel_ms": {k: v[1] / v[0] for k, v in ktimes.items()}}
+    if note:
+        out["note"] = note
+    return out
+
+
+def step_bytes(pass_bytes_per_step, cells, ms_per_step, hbm):
+    """Whole-step byte rates: the pass model (every pass's algorithmic bytes) and
+    the compulsory bytes (5 inputs read once, 3 outputs written once, 4 B each)."""
+    s = ms_per_step * 1e-3
+    out = {}
+    for name, nb in (("pass_model", pass_bytes_per_step), ("compulsory", 32.0 * cells)):
+        gbs = nb / s / 1e9
+        out[name] = {"bytes_per_cell": nb / cells, "gbs": gbs, "frac": gbs / hbm}
+    return out
 
 
 def run_batch_line(args, world, rank, local):
@@ -443,7 +459,11 @@ def run_batch_line(args, world, rank, local):
     peak_kind = "measured"
     if not hbm:
         hbm, peak_kind = 6800.0, "fallback"
-    roof = roofline_of(kt, batch_algorithmic_bytes(sizes), hbm, peak_kind, traffic_lookup=False)
+    alg_b = batch_algorithmic_bytes(sizes)
+    alg_fb = batch_algorithmic_bytes(sizes_fp32)
+    concurrent = ("the size classes' kernels run side by side on the batch's branch streams, so each launch's "
+                  "duration includes time shared with other classes' kernels")
+    roof = roofline_of(kt, lambda k, n: alg_b[k], hbm, peak_kind, traffic_lookup=False, note=concurrent)
 
     side = None
     if not args.no_side_precision and rank == 0:
@@ -465,6 +485,7 @@ def run_batch_line(args, world, rank, local):
             "interior_cell_steps_per_s": value * interior / cells,
             "gpu_launches": launches_per_step * K,
             "roofline": roof,
+            "step_bytes": step_bytes(sum(alg_b.values()), cells, t_max / K, hbm),
             "clocks": clk,
         }
         if long_series:
@@ -472,14 +493,18 @@ def run_batch_line(args, world, rank, local):
         line["vs_plain_fp32"] = {
             "same_patches": {"precision": PREC_NOTE["fp32"], "value": cells * K / (ms32 * 1e-3),
                              "ms_per_step": ms32 / K, "ratio": (cells * K / (ms * 1e-3)) / (cells * K / (ms32 * 1e-3)),
-                             "what": "FP32 batch on the same power-of-two patch sides; ratio = mixed / FP32"},
+                             "what": "FP32 batch on the same power-of-two patch sides; ratio = mixed / FP32",
+                             "roofline": roofline_of(kt32, lambda k, n: alg_b[k], hbm, peak_kind,
+                                                     traffic_lookup=False, note=concurrent),
+                             "step_bytes": step_bytes(sum(alg_b.values()), cells, ms32 / K, hbm)},
             "fp32_own_sides": {"value": cells_fp32 * K / (msb * 1e-3), "ms_per_step": msb / K, "cells": cells_fp32,
                                "interior_cell_steps_per_s": interior * K / (msb * 1e-3),
                                "interior_ratio": (interior * K / (ms * 1e-3)) / (interior * K / (msb * 1e-3)),
                                "what": "FP32 batch with the sides FP32 takes (2^k or 3 * 2^k); interior_ratio = "
                                        "mixed / FP32 interior cell-steps/s",
-                               "roofline": roofline_of(ktb, batch_algorithmic_bytes(sizes_fp32), hbm, peak_kind,
-                                                       traffic_lookup=False)},
+                               "roofline": roofline_of(ktb, lambda k, n: alg_fb[k], hbm, peak_kind,
+                                                       traffic_lookup=False, note=concurrent),
+                               "step_bytes": step_bytes(sum(alg_fb.values()), cells_fp32, msb / K, hbm)},
         }
         if not args.no_e2e:
             line["e2e"] = {"value": e2e_a, "unit": "cell-steps/s", "h2d_bytes_per_step": 5 * cells * 4,
@@ -529,7 +554,9 @@ def te2048_side(capi, torch, args, dev, world, hbm, peak_kind):
     return {"workload": WORKLOAD, "precision": PREC_NOTE["fp32"], "value": NX * NY * args.steps / (ms * 1e-3),
             "ms_per_step": ms / args.steps, "unit": "cell-steps/s",
             "l2": "flushed before every timed step (256 MiB write)",
-            "roofline": roofline_of(kt, algorithmic_bytes(), hbm, peak_kind), "clocks": clk}
+            "roofline": roofline_of(kt, lambda k, n: algorithmic_bytes()[k] * n, hbm, peak_kind),
+            "step_bytes": step_bytes(sum(algorithmic_bytes().values()), NX * NY, ms / args.steps, hbm),
+            "clocks": clk}
 
 
 def run_reference_batch(args, world, rank):

@@ -75,7 +75,8 @@ typedef enum {
   PSATD_ERR_OOM = 3,          /* device allocation failed                             */
   PSATD_ERR_CUDA = 4,         /* a CUDA runtime call or launch failed                 */
   PSATD_ERR_TIMEOUT = 5,      /* a bounded device-side wait expired                   */
-  PSATD_ERR_NONFINITE = 6     /* PSATD_FLAG_CHECKED: NaN or Inf in a step's output   */
+  PSATD_ERR_NONFINITE = 6,    /* PSATD_FLAG_CHECKED: NaN or Inf in a step's output   */
+  PSATD_ERR_BOUNDS = 7        /* PSATD_FLAG_CHECKED: a pass's index check failed      */
 } psatd_status;
 
 typedef enum {
@@ -118,11 +119,16 @@ typedef enum { PSATD_FDTD_YEE = 0, PSATD_FDTD_CKC = 1 } psatd_fdtd_scheme;
  * c dt |k| < 2 over the propagated modes (the caller's choice of dt); J-form or
  * vacuum only (INVALID_ARG with the rho-form); any order (k or k_p). */
 #define PSATD_FLAG_PSTD 2
-/* PSATD_FLAG_CHECKED: after every step the output field arrays are scanned for
- * NaN and Inf (one more read of the outputs, on the plan's stream); a hit sets
- * the plan's device error word and the next psatd_plan_sync returns
- * PSATD_ERR_NONFINITE (and clears it).  PSATD plans, batches and local
- * decompositions; psatd_step_noalloc and fdtd_step refuse it. */
+/* PSATD_FLAG_CHECKED: the checked mode.  (1) Index checks: before its first
+ * access every CTA of every pass tests the element ranges it is about to read
+ * and write (caller arrays, spectra, coefficient rows) against the extents the
+ * plan knows; if any range falls outside, the CTA touches nothing and sets the
+ * plan's device error word, and the next sync returns PSATD_ERR_BOUNDS (a bug
+ * of this library, never of the caller's data).  (2) After every step the
+ * output field arrays are scanned for NaN and Inf (one more read of the
+ * outputs); a hit makes the next sync return PSATD_ERR_NONFINITE.  The sync
+ * clears the word.  PSATD plans, batches and local decompositions;
+ * psatd_step_noalloc and fdtd_step refuse it. */
 #define PSATD_FLAG_CHECKED 4
 /* PSATD_FLAG_TEST_STALL_MMA: a test hook of the failure path, for
  * PSATD_MIXED_FP16 / _BF16 plans only (INVALID_ARG otherwise).  The
@@ -132,6 +138,12 @@ typedef enum { PSATD_FDTD_YEE = 0, PSATD_FDTD_CKC = 1 } psatd_fdtd_scheme;
  * PSATD_ERR_TIMEOUT.  The step's output is not valid.  Never set it in
  * production use. */
 #define PSATD_FLAG_TEST_STALL_MMA 8
+/* PSATD_FLAG_TEST_SHORT_EXTENT: a test hook of the checked mode (with
+ * PSATD_FLAG_CHECKED only, INVALID_ARG otherwise): every pass is told that each
+ * array it touches is one element shorter than it is, so the index checks of
+ * the CTAs reaching the last element fail, those CTAs skip their accesses and
+ * psatd_plan_sync returns PSATD_ERR_BOUNDS.  The step's output is not valid. */
+#define PSATD_FLAG_TEST_SHORT_EXTENT 16
 
 /* Problem statement (the paper's arguments: grid sizes, cell sizes, dt, c, eps0). */
 typedef struct {
@@ -233,6 +245,7 @@ psatd_status psatd_step(psatd_plan plan, const psatd_fields* fields,
                         const psatd_sources* sources, int32_t nsteps);
 
 /* Synchronise the plan's stream and report any asynchronous CUDA error, or
+ * PSATD_ERR_BOUNDS when a checked plan's index check failed, or
  * PSATD_ERR_TIMEOUT when a tensor-core pass (PSATD_MIXED_FP16 / _BF16) gave up
  * a bounded wait for its MMAs since the last sync (the CTA then skipped its
  * remaining tensor-core stages and freed its TMEM; the step's output is not

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libpsatd.so")
 
 PSATD_OK = 0
 STATUS = {0: "PSATD_OK", 1: "PSATD_ERR_INVALID_ARG", 2: "PSATD_ERR_UNSUPPORTED", 3: "PSATD_ERR_OOM",
-          4: "PSATD_ERR_CUDA", 5: "PSATD_ERR_TIMEOUT", 6: "PSATD_ERR_NONFINITE"}
+          4: "PSATD_ERR_CUDA", 5: "PSATD_ERR_TIMEOUT", 6: "PSATD_ERR_NONFINITE", 7: "PSATD_ERR_BOUNDS"}
 PREC = {"fp64": 0, "fp32": 1, "mixed_bf16": 2, "mixed_fp16": 3}
 SRC = {"none": 0, "J": 1, "rho": 2}
 LAYOUT = {"3d6": 0, "2d6": 1, "te": 2, "tm": 3}
@@ -92,6 +92,7 @@ FLAG_AUTOTUNE = 1
 FLAG_PSTD = 2
 FLAG_CHECKED = 4
 FLAG_TEST_STALL_MMA = 8  # test hook of the failure path (mixed precisions): see include/psatd.h
+FLAG_TEST_SHORT_EXTENT = 16  # test hook of the checked mode's index checks: see include/psatd.h
 
 
 def load(path: str = LIB_PATH):
@@ -117,7 +118,7 @@ def _check(status, plan=None):
 
 
 def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, autotune=False, order=0,
-              scheme="psatd", checked=False, test_stall_mma=False):
+              scheme="psatd", checked=False, test_stall_mma=False, test_short_extent=False):
     """psatd_desc for grid ``n`` = (nx, ny[, nz]) and cell sizes ``d``."""
     nd = len(n)
     desc = psatd_desc()
@@ -132,7 +133,8 @@ def make_desc(n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, a
     if scheme not in ("psatd", "pstd"):
         raise ValueError("scheme must be 'psatd' or 'pstd'")
     desc.flags = ((FLAG_AUTOTUNE if autotune else 0) | (FLAG_PSTD if scheme == "pstd" else 0)
-                  | (FLAG_CHECKED if checked else 0) | (FLAG_TEST_STALL_MMA if test_stall_mma else 0))
+                  | (FLAG_CHECKED if checked else 0) | (FLAG_TEST_STALL_MMA if test_stall_mma else 0)
+                  | (FLAG_TEST_SHORT_EXTENT if test_short_extent else 0))
     desc.order = int(order)
     return desc
 
@@ -198,14 +200,16 @@ class Plan:
     """
 
     def __init__(self, n, d, dt, *, layout="te", prec="fp32", src="J", c=1.0, eps0=1.0, stream=None,
-                 autotune=False, order=0, scheme="psatd", checked=False, test_stall_mma=False):
+                 autotune=False, order=0, scheme="psatd", checked=False, test_stall_mma=False,
+                 test_short_extent=False):
         import torch
         lib = load()
         self.n, self.layout, self.prec, self.src = tuple(n), layout, prec, src
         self.shape = _grid_shape(n)
         self.dtype = _torch_dtype(prec)
         self.desc = make_desc(n, d, dt, layout=layout, prec=prec, src=src, c=c, eps0=eps0, autotune=autotune,
-                              order=order, scheme=scheme, checked=checked, test_stall_mma=test_stall_mma)
+                              order=order, scheme=scheme, checked=checked, test_stall_mma=test_stall_mma,
+                              test_short_extent=test_short_extent)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -71,6 +71,7 @@ struct psatd_plan_s {
   double* cw_d = nullptr;               // staggered Fornberg weights (p/2)
   void* gmat = nullptr;       // their split DFT matrices (kTcTail image, device)
   int* d_err = nullptr;       // device error word of the tensor-core passes
+  int64_t caller_elems = 0;   // elements of each caller array (checked mode's extents)
 };
 
 namespace {
@@ -122,8 +123,10 @@ psatd_status validate_desc(psatd_plan p, const psatd_desc* d, bool psatd_limits)
   if (d->ndim != layout_ndim(d->layout))
     return fail(p, PSATD_ERR_INVALID_ARG, "ndim %d does not match layout %d", d->ndim, d->layout);
   if ((d->flags & ~(psatd_limits ? (PSATD_FLAG_AUTOTUNE | PSATD_FLAG_PSTD | PSATD_FLAG_CHECKED |
-                                     PSATD_FLAG_TEST_STALL_MMA) : 0)) != 0)
+                                     PSATD_FLAG_TEST_STALL_MMA | PSATD_FLAG_TEST_SHORT_EXTENT) : 0)) != 0)
     return fail(p, PSATD_ERR_INVALID_ARG, "unknown flags");
+  if ((d->flags & PSATD_FLAG_TEST_SHORT_EXTENT) && !(d->flags & PSATD_FLAG_CHECKED))
+    return fail(p, PSATD_ERR_INVALID_ARG, "PSATD_FLAG_TEST_SHORT_EXTENT needs PSATD_FLAG_CHECKED");
   if ((d->flags & PSATD_FLAG_TEST_STALL_MMA) && d->prec != PSATD_MIXED_FP16 && d->prec != PSATD_MIXED_BF16)
     return fail(p, PSATD_ERR_INVALID_ARG, "PSATD_FLAG_TEST_STALL_MMA applies to the mixed precisions only");
   if ((d->flags & PSATD_FLAG_PSTD) && d->src == PSATD_SRC_J_RHO)
@@ -398,6 +401,12 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
   io.gmat = p->gmat;
   io.err = p->d_err;
   io.tc_ctl = (p->d.flags & PSATD_FLAG_TEST_STALL_MMA) ? kTcStallMma : 0;
+  // checked mode: the extents every pass checks its index ranges against (the
+  // test hook reports each array one element shorter than it is)
+  const bool chk = (p->d.flags & PSATD_FLAG_CHECKED) != 0;
+  const int64_t shrink = (p->d.flags & PSATD_FLAG_TEST_SHORT_EXTENT) ? 1 : 0;
+  const int64_t ext_user = chk ? p->caller_elems - shrink : 0, ext_spec = chk ? cs - shrink : 0;
+  io.chk_err = p->d_err;
   const size_t tail = TC ? (size_t)kTcTail : 0;  // tensor-core passes: matrices + mbarrier first
 
   // a0: z in 3D (strided), the patch in a 2D batch (offset table; spectra [c][patch][kx][y])
@@ -413,6 +422,8 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
       io.in[c] = in[c];
       io.out[c] = s1 + c * cs;
     }
+    io.in_ext = ext_user;
+    io.out_ext = ext_spec;
     TimedLaunch tl(p, K_FWD_X);
     e = fwd_T_any<R, TC>(Lx, true, g, p->st, io, p->tw[0], d3 ? ny * nx : 0, nx, d3 ? ny : nxh * ny, nz * ny,
                         d3 ? nullptr : p->d_off);
@@ -432,6 +443,8 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
       io.in[c] = s1 + c * cs;
       io.out[c] = s2 + c * cs;
     }
+    io.in_ext = ext_spec;
+    io.out_ext = ext_spec;
     TimedLaunch tl(p, K_FWD_Y);
     e = fwd_T_any<R, TC>((int)ny, false, g, p->st, io, p->tw[1], nz * ny, ny, ny * nz, nz);
     if (e != cudaSuccess) return cuda_fail(p, e, "fwd_y_c2c launch");
@@ -467,6 +480,8 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     a.gmat = p->gmat;
     a.err = p->d_err;
     a.tc_ctl = io.tc_ctl;
+    a.tab_ext = chk ? p->tab_e[0] * p->tab_e[1] * p->tab_e[2] - shrink : 0;
+    a.chk_err = p->d_err;
     a.stag = p->order > 0 ? 1 : 0;
     a.scheme = (p->d.flags & PSATD_FLAG_PSTD) ? 1 : 0;
     a.p_h = (R)(0.5 * p->d.dt * p->g0);
@@ -509,6 +524,8 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
       io.in[c] = s2 + c * cs;
       io.out[c] = s1 + c * cs;
     }
+    io.in_ext = ext_spec;
+    io.out_ext = ext_spec;
     TimedLaunch tl(p, K_INV_Y);
     e = inv_T_any<R, TC>((int)ny, false, g, p->st, io, p->tw[1], ny * nz, nz, nz * ny, ny);
     if (e != cudaSuccess) return cuda_fail(p, e, "inv_y_c2c launch");
@@ -523,6 +540,8 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
       io.in[c] = s1 + c * cs;
       io.out[c] = out[c];
     }
+    io.in_ext = ext_spec;
+    io.out_ext = ext_user;
     TimedLaunch tl(p, K_INV_X);
     e = inv_T_any<R, TC>(Lx, true, g, p->st, io, p->tw[0], d3 ? ny : nxh * ny, nz * ny, d3 ? ny * nx : 0, nx,
                         d3 ? nullptr : p->d_off);
@@ -830,6 +849,7 @@ static psatd_status plan_create_n(const psatd_desc* desc, void* cuda_stream, int
   p->nxh = p->nx / 2 + 1;
   p->npatch = npatch;
   p->cs = p->nxh * p->ny * p->nz * npatch;
+  p->caller_elems = p->nx * p->ny * p->nz * npatch;  // batches and local decompositions set their packed size
   cudaGetDevice(&p->device);
   // push pass shared memory (one line per CTA at least)
   {
@@ -1042,6 +1062,9 @@ psatd_status psatd_plan_sync(psatd_plan p) {
       cudaMemset(p->d_err, 0, sizeof(int));
       if (w & kErrMmaWait)
         return fail(p, PSATD_ERR_TIMEOUT, "a tensor-core pass gave up waiting for its MMAs (error word %d)", w);
+      if (w & kErrBounds)
+        return fail(p, PSATD_ERR_BOUNDS, "a pass's index check failed; its CTA skipped its accesses (error word %d)",
+                    w);
       return fail(p, PSATD_ERR_NONFINITE, "NaN or Inf in a step's output since the last sync (error word %d)", w);
     }
   }
@@ -1483,6 +1506,7 @@ extern "C" psatd_status psatd_batch_create(const psatd_desc* base, int32_t npatc
     psatd_plan p = nullptr;
     psatd_status s = plan_create_n(&d, cuda_stream, (int)offs.size(), &p);
     if (s == PSATD_OK) {
+      p->caller_elems = acc;  // the packed arrays of the whole batch
       s = alloc(p, reinterpret_cast<void**>(&p->d_off), offs.size() * sizeof(int64_t), "patch offsets");
       if (s == PSATD_OK) {
         cudaError_t e = cudaMemcpy(p->d_off, offs.data(), offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice);

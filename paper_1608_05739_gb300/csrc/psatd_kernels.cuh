@@ -28,6 +28,10 @@ struct LineIO {
   const void* gmat;  // tensor-core passes: split DFT matrices (kTcTail image)
   int* err;          // tensor-core passes: device error word
   int tc_ctl;        // tensor-core passes: control word (kTcStallMma test hook)
+  // checked mode (PSATD_FLAG_CHECKED): elements of every input / output array
+  // (0: unchecked) and the error word that a failed index check sets
+  int64_t in_ext, out_ext;
+  int* chk_err;
 };
 
 // k-space coefficient table entry (one per |m|-octant point), see tables.cu.
@@ -62,6 +66,8 @@ struct PushArgs {
   const void* gmat;  // tensor-core pass: split DFT matrices (kTcTail image)
   int* err;          // tensor-core pass: device error word
   int tc_ctl;        // tensor-core pass: control word (kTcStallMma test hook)
+  int64_t tab_ext;   // checked mode: coefficient-table entries (0: unchecked); spectra: n_in * cs
+  int* chk_err;      // checked mode: error word of a failed index check
   int scheme;        // 0: PSATD (analytic in time); 1: PSTD (leapfrog, p_h / p_e / p_j / inv_n)
   R p_h, p_e, p_j, inv_n;  // PSTD: dt g0 / 2, c^2 dt g0, dt / eps0, 1/N
   int stag;          // staggered order-p plan (PSATD-p): k_p and half-cell phases below
@@ -69,9 +75,20 @@ struct PushArgs {
   const void* ph[3];    // per axis, exp(-i pi m/n) for m = 0..n/2 (twiddle type)
 };
 
-// Error-word bit of the non-finite scan (PSATD_FLAG_CHECKED); the tensor-core
-// passes use kErrMmaWait (tc_dft.cuh).
+// Error-word bits of the checked mode (PSATD_FLAG_CHECKED): the non-finite scan
+// and the passes' index checks; the tensor-core passes use kErrMmaWait (tc_dft.cuh).
 constexpr int kErrNonfinite = 1 << 8;
+constexpr int kErrBounds = 1 << 9;
+
+// Index check of the checked mode: every thread tests the ends of the element
+// ranges it is about to touch against the extents the pass was given; the CTA
+// agrees (one barrier) and, when any range falls outside, sets kErrBounds and
+// the CTA touches nothing (it returns before its first access).
+__device__ __forceinline__ bool cta_out_of_bounds(bool bad, int* err) {
+  if (!__syncthreads_or(bad)) return false;
+  if (threadIdx.x == 0 && threadIdx.y == 0 && err) atomicOr(err, kErrBounds);
+  return true;
+}
 
 // Scan `n` elements of each of gridDim.y arrays (at p[y] + off[patch], patches
 // along gridDim.z; off == NULL: one array from p[y]) for NaN / Inf and set
@@ -115,6 +132,12 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_fwd_T(LineIO io,
   const int t = threadIdx.x, g = threadIdx.y;
   const int64_t b = (int64_t)blockIdx.x * TB + g;
   const int a0 = blockIdx.y, a1 = blockIdx.z;
+  if (io.in_ext) {  // checked mode: the row read and the transposed block written
+    const int64_t o0c = in_off ? in_off[a0] : a0 * in_sa0;
+    const int64_t in_end = o0c + b * in_sb + (R2C ? 2 * L : L);
+    const int64_t out_end = a0 * out_sa0 + (int64_t)blockIdx.x * TB + TB + (int64_t)(NK - 1) * out_sk;
+    if (cta_out_of_bounds(in_end > io.in_ext || out_end > io.out_ext || o0c < 0, io.chk_err)) return;
+  }
   __shared__ const void* twslot;
   if (t == 0 && g == 0) twslot = tw;
   TcCtx tc;
@@ -222,6 +245,12 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_inv_T(LineIO io,
   const int t = threadIdx.x, g = threadIdx.y;
   const int64_t b = (int64_t)blockIdx.x * TB + g;
   const int a0 = blockIdx.y, a1 = blockIdx.z;
+  if (io.in_ext) {  // checked mode: the transposed block read and the row written
+    const int64_t o0c = out_off ? out_off[a0] : a0 * out_sa0;
+    const int64_t in_end = a0 * in_sa0 + (int64_t)blockIdx.x * TB + TB + (int64_t)(NK - 1) * in_sk;
+    const int64_t out_end = o0c + b * out_sb + (C2R ? 2 * L : L);
+    if (cta_out_of_bounds(in_end > io.in_ext || out_end > io.out_ext || o0c < 0, io.chk_err)) return;
+  }
   __shared__ const void* twslot;
   if (t == 0 && g == 0) twslot = tw;
   TcCtx tc;
@@ -720,6 +749,13 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   const int t = threadIdx.x, g = threadIdx.y;
   const int line = blockIdx.x * blockDim.y + g;
   const bool valid = line < a.nlines;
+  if (a.tab_ext) {  // checked mode: the line's columns of every slot and its coefficient row
+    int mx_c, my_c, row_c;
+    line_modes(a, valid ? line : 0, mx_c, my_c, row_c);
+    const bool bad = (valid && (int64_t)(line + 1) * L > a.cs) ||
+                     (int64_t)(row_c + 1) * a.tab_row > a.tab_ext || row_c < 0;
+    if (cta_out_of_bounds(bad, a.chk_err)) return;
+  }
   C* base = reinterpret_cast<C*>(smem_raw + (TC ? kTcTail : 0));
   const int ss = (int)blockDim.y * L;  // slot stride (component-major)
   C* st = base + g * L;                // this line's slot 0; slot c at st + c * ss

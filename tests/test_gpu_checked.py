@@ -120,3 +120,43 @@ def test_expired_mma_wait_reports_timeout_and_frees_tmem(prec):
     Bg = np.stack([z, z, b[2].double().cpu().numpy()])
     err = rel_l2_fields(Eg, Bg, mask_layout(Eo, "te", "E"), mask_layout(Bo, "te", "B"))
     assert err < 4e-6, err
+
+
+BOUNDS = 7
+
+
+@pytest.mark.parametrize("prec,layout,shape", [("fp32", "te", (128, 256)), ("mixed_bf16", "te", (256, 256)),
+                                               ("fp64", "3d6", (16, 32, 32))])
+def test_index_checks_trip_on_short_extents_and_pass_otherwise(prec, layout, shape):
+    """The checked mode's index checks: told that every array is one element shorter
+    (the test hook), the CTAs reaching the last element skip their accesses and the
+    sync reports PSATD_ERR_BOUNDS; with the true extents the checked plan gives the
+    unchecked plan's bits."""
+    ensure_lib()
+    n = tuple(reversed(shape))
+    d = tuple([1.0] * len(shape))
+    dt = 0.4
+    g = torch.Generator(device="cuda").manual_seed(11)
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    pe, pb, pj = capi.PRESENT[layout]
+    mk = lambda p: [torch.randn(shape, device="cuda", generator=g, dtype=dtype) if p[i] else None for i in range(3)]
+    E, B, J = mk(pe), mk(pb), mk(pj)
+    clone = lambda F: [t.clone() if t is not None else None for t in F]
+    E1, B1, E2, B2 = clone(E), clone(B), clone(E), clone(B)
+    p0 = capi.Plan(n, d, dt, layout=layout, prec=prec, src="J")
+    p1 = capi.Plan(n, d, dt, layout=layout, prec=prec, src="J", checked=True)
+    p0.step(E1, B1, J, nsteps=2)
+    p1.step(E2, B2, J, nsteps=2)
+    p0.sync()
+    p1.sync()
+    for x, y in zip(E1 + B1, E2 + B2):
+        if x is not None:
+            assert torch.equal(x, y)
+    p2 = capi.Plan(n, d, dt, layout=layout, prec=prec, src="J", checked=True, test_short_extent=True)
+    p2.step(clone(E), clone(B), J)
+    with pytest.raises(capi.PsatdError) as ei:
+        p2.sync()
+    assert ei.value.status == BOUNDS
+    p2.sync()                            # reported once, then cleared
+    for p in (p0, p1, p2):
+        p.destroy()
