@@ -297,6 +297,7 @@ def time_batch(capi, torch, prec, sizes, Jhost, args, dev, stream, sample_clocks
     clk = clocks.stop() if clocks else None
     ms = e0.elapsed_time(e1)
     kt = b.kernel_times()
+    kt["_launches_per_step"] = (b.launches_per_step(), 0.0)
     b.set_timing(False)
     b.sync()  # raises if a tensor-core pass reported an expired wait
     if not bool(torch.isfinite(Ey).all()):
@@ -429,7 +430,7 @@ def run_batch_line(args, world, rank, local):
     ms, kt, clk, b, F = time_batch(capi, torch, prec, sizes, J, args, dev, stream, sample_clocks=True)
     value, t_max = replica_throughput(ms, cells, K, world, dev)
     gpu_fields = patch_fields(F[:3], sizes, offs, samp)
-    launches_per_step = sum(v[0] for v in kt.values())
+    launches_per_step = kt.pop("_launches_per_step")[0]
     # a longer series of the same call with its own clock record (at least ~2 s of steps)
     long_series = None
     n_long = int(math.ceil(2000.0 / (ms / K)))
@@ -446,10 +447,12 @@ def run_batch_line(args, world, rank, local):
     b.destroy()
     # plain FP32 on the same patches (same transform sizes), and on the sizes FP32 itself takes
     ms32, kt32, _, b32, F32 = time_batch(capi, torch, "fp32", sizes, J, args, dev, stream, sample_clocks=False)
+    lps32 = kt32.pop("_launches_per_step")[0]
     f32_fields = patch_fields(F32[:3], sizes, offs, samp)
     b32.destroy()
     del F32
     msb, ktb, _, bb, Fb = time_batch(capi, torch, "fp32", sizes_fp32, J32, args, dev, stream, sample_clocks=False)
+    lpsb = ktb.pop("_launches_per_step")[0]
     fb_fields = patch_fields(Fb[:3], sizes_fp32, offs32, samp32)
     bb.destroy()
     del Fb, F
@@ -461,7 +464,9 @@ def run_batch_line(args, world, rank, local):
         hbm, peak_kind = 6800.0, "fallback"
     alg_b = batch_algorithmic_bytes(sizes)
     alg_fb = batch_algorithmic_bytes(sizes_fp32)
-    concurrent = ("the size classes' kernels run side by side on the batch's branch streams, so each launch's "
+    concurrent = ("persistent passes: one launch per pass type (and length family) over every patch, so a "
+                  "launch's bytes are the whole batch's for that pass" if launches_per_step <= 6 else
+                  "the size classes' kernels run side by side on the batch's branch streams, so each launch's "
                   "duration includes time shared with other classes' kernels")
     roof = roofline_of(kt, lambda k, n: alg_b[k], hbm, peak_kind, traffic_lookup=False, note=concurrent)
 
@@ -480,6 +485,7 @@ def run_batch_line(args, world, rank, local):
                        "size_classes": len(set(sizes)),
                        "value_counts": "cells of the transformed patch domains (interior + widened guards)",
                        "run": "one psatd_batch_step(nsteps = steps) call: a CUDA graph of one step replayed",
+                       "launches_per_step": launches_per_step,
                        "l2": "not flushed: the inputs (%.2f GB) are 15x the 129 MB L2" % (5 * cells * 4 / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "interior_cell_steps_per_s": value * interior / cells,
@@ -494,6 +500,7 @@ def run_batch_line(args, world, rank, local):
             "same_patches": {"precision": PREC_NOTE["fp32"], "value": cells * K / (ms32 * 1e-3),
                              "ms_per_step": ms32 / K, "ratio": (cells * K / (ms * 1e-3)) / (cells * K / (ms32 * 1e-3)),
                              "what": "FP32 batch on the same power-of-two patch sides; ratio = mixed / FP32",
+                             "launches_per_step": lps32,
                              "roofline": roofline_of(kt32, lambda k, n: alg_b[k], hbm, peak_kind,
                                                      traffic_lookup=False, note=concurrent),
                              "step_bytes": step_bytes(sum(alg_b.values()), cells, ms32 / K, hbm)},
@@ -502,6 +509,7 @@ def run_batch_line(args, world, rank, local):
                                "interior_ratio": (interior * K / (ms * 1e-3)) / (interior * K / (msb * 1e-3)),
                                "what": "FP32 batch with the sides FP32 takes (2^k or 3 * 2^k); interior_ratio = "
                                        "mixed / FP32 interior cell-steps/s",
+                               "launches_per_step": lpsb,
                                "roofline": roofline_of(ktb, lambda k, n: alg_fb[k], hbm, peak_kind,
                                                        traffic_lookup=False, note=concurrent),
                                "step_bytes": step_bytes(sum(alg_fb.values()), cells_fp32, msb / K, hbm)},

@@ -289,9 +289,10 @@ psatd_status fdtd_step(const psatd_desc* desc, int32_t scheme, const psatd_field
  * sources of all patches are packed per component: one array per component
  * holding patch 0, patch 1, ... back to back (patch i at element offset
  * sum_{j<i} n[2j] n[2j+1]).
- * Patches of equal size form a class advanced with one launch per pass; each
- * step forks from the batch's stream into up to four internal streams that
- * run the classes side by side, and joins back.  A call with nsteps > 1 on a
+ * Patches of equal size form a class (own spectra and tables).  A step runs
+ * the persistent passes below where the sizes allow; else one launch per pass
+ * and class, forked from the batch's stream into up to four internal streams
+ * that run the classes side by side, and joined back.  A call with nsteps > 1 on a
  * non-default stream records one step of all classes into a CUDA graph
  * (re-recorded when the field/source pointers change) and replays it nsteps
  * times.  Guard cells are part of each patch
@@ -316,6 +317,24 @@ int64_t psatd_batch_cells(psatd_batch batch);
  * size class, an asynchronous CUDA error, PSATD_ERR_TIMEOUT (tensor-core waits)
  * or PSATD_ERR_NONFINITE (PSATD_FLAG_CHECKED) since the last sync. */
 psatd_status psatd_batch_sync(psatd_batch batch);
+
+/* Persistent passes (the default where they apply).  When every patch's line
+ * lengths allow it (FP32 or a mixed precision; x lines n[2i]/2 of 32..512
+ * points, or 48..384 = 3 * 2^k in FP32; last-axis lines n[2i+1] of 64..1024, or
+ * 96..768 = 3 * 2^k in FP32), a step is one launch per pass type (x forward,
+ * fused y pass, x inverse) and per length family (powers of two, 3 * 2^k): the
+ * CTAs of each launch stay resident and take the work of every patch from a
+ * device queue (an atomic counter; the last CTA to finish resets it), so the
+ * passes run in stream order with no wait inside a kernel.  Otherwise each step
+ * is one launch per pass and size class on the branch streams described above.
+ * psatd_batch_set_persistent(batch, 0) selects the per-class launches, 1 the
+ * persistent ones (UNSUPPORTED when the sizes do not allow them); results are
+ * the same bits either way.  psatd_batch_launches_per_step: kernel launches of
+ * one step in the current mode (without PSATD_FLAG_CHECKED's scans).  The
+ * first step after the field or source pointers change uploads the classes'
+ * argument tables (a synchronising copy, outside any graph capture). */
+psatd_status psatd_batch_set_persistent(psatd_batch batch, int32_t enable);
+int32_t psatd_batch_launches_per_step(psatd_batch batch);
 
 /* Per-kernel CUDA-event timing of the batch, as psatd_plan_set_timing /
  * psatd_kernel_times do for a plan, summed over the size classes: enable != 0

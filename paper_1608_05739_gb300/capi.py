@@ -74,6 +74,8 @@ EXPORTS = [
     ("psatd_batch_sync", ct.c_int, [ct.c_void_p]),
     ("psatd_batch_destroy", ct.c_int, [ct.c_void_p]),
     ("psatd_batch_set_timing", ct.c_int, [ct.c_void_p, ct.c_int32]),
+    ("psatd_batch_set_persistent", ct.c_int, [ct.c_void_p, ct.c_int32]),
+    ("psatd_batch_launches_per_step", ct.c_int32, [ct.c_void_p]),
     ("psatd_batch_kernel_times", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_char_p),
                                               ct.POINTER(ct.c_int64), ct.POINTER(ct.c_double)]),
     ("psatd_plan_autotune", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_char_p, ct.c_size_t]),
@@ -314,6 +316,13 @@ class Batch:
 
     def set_timing(self, enable=True):
         _check(load().psatd_batch_set_timing(self.handle, 1 if enable else 0))
+
+    def set_persistent(self, enable=True):
+        """Persistent passes (default where the sizes allow) or per-class launches."""
+        _check(load().psatd_batch_set_persistent(self.handle, 1 if enable else 0))
+
+    def launches_per_step(self):
+        return int(load().psatd_batch_launches_per_step(self.handle))
 
     def kernel_times(self):
         """{kernel name: (launches, total ms)} summed over the size classes."""

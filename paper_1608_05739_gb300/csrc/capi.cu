@@ -342,6 +342,7 @@ size_t tc_a3_bytes(psatd_plan p, int threads) {
 struct TimedLaunch {
   psatd_plan p;
   int slot;
+  cudaStream_t st;
   EventPair ep{};
   static void record(cudaEvent_t e, cudaStream_t st) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -350,7 +351,8 @@ struct TimedLaunch {
     else
       cudaEventRecord(e, st);
   }
-  TimedLaunch(psatd_plan pl, int s) : p(pl), slot(s) {
+  TimedLaunch(psatd_plan pl, int s) : TimedLaunch(pl, s, pl->st) {}
+  TimedLaunch(psatd_plan pl, int s, cudaStream_t stream) : p(pl), slot(s), st(stream) {
     if (!p->timing) return;
     if (!p->pool.empty()) {
       ep = p->pool.back();
@@ -359,11 +361,11 @@ struct TimedLaunch {
       cudaEventCreate(&ep.a);
       cudaEventCreate(&ep.b);
     }
-    record(ep.a, p->st);
+    record(ep.a, st);
   }
   ~TimedLaunch() {
     if (!p->timing) return;
-    record(ep.b, p->st);
+    record(ep.b, st);
     p->ev[slot].push_back(ep);
   }
 };
@@ -385,6 +387,54 @@ cudaError_t inv_T_any(int L, bool c2r, const PassGeom& g, cudaStream_t st, const
   if constexpr (std::is_same<R, float>::value && TC == 0)
     return launch_inv_T3<R>(L, c2r, g, st, io, tw, in_sa0, in_sk, out_sa0, out_sb, a0_off);
   return cudaErrorInvalidValue;
+}
+
+// Arguments of the fused pass of plan p over the spectra at sp (lines of Lline
+// points, nlines of them).
+template <typename R>
+PushArgs<R> make_push_args(psatd_plan p, void* sp, int Lline, int64_t nlines) {
+  PushArgs<R> a;
+  std::memset(&a, 0, sizeof a);
+  const bool chk = (p->d.flags & PSATD_FLAG_CHECKED) != 0;
+  const int64_t shrink = (p->d.flags & PSATD_FLAG_TEST_SHORT_EXTENT) ? 1 : 0;
+  a.spec = sp;
+  a.cs = p->cs;
+  a.tab = static_cast<const Coef<R>*>(p->tab);
+  a.nlines = (int)nlines;
+  a.n_in = p->n_in;
+  a.n_out = p->n_out;
+  a.form = p->form;
+  a.ndim = p->ndim;
+  a.nx_half = (int)(p->nx / 2);
+  a.lines_per_patch = (int)p->nxh;
+  a.ny = (int)p->ny;
+  a.tab_row = Lline / 2 + 1;
+  a.rx = (R)p->r[0];
+  a.ry = (R)p->r[1];
+  a.rz = (R)p->r[2];
+  const double c = p->d.c, ic = 1.0 / c;
+  a.c_h = (R)c;
+  a.c_l = (R)(c - (double)a.c_h);
+  a.ic_h = (R)ic;
+  a.ic_l = (R)(ic - (double)a.ic_h);
+  a.s_src = (R)(1.0 / (p->d.eps0 * c * p->g0));
+  a.s_a6 = (R)(1.0 / (p->d.eps0 * c * c * p->g0));
+  a.gmat = p->gmat;
+  a.err = p->d_err;
+  a.tc_ctl = (p->d.flags & PSATD_FLAG_TEST_STALL_MMA) ? kTcStallMma : 0;
+  a.tab_ext = chk ? p->tab_e[0] * p->tab_e[1] * p->tab_e[2] - shrink : 0;
+  a.chk_err = p->d_err;
+  a.stag = p->order > 0 ? 1 : 0;
+  a.scheme = (p->d.flags & PSATD_FLAG_PSTD) ? 1 : 0;
+  a.p_h = (R)(0.5 * p->d.dt * p->g0);
+  a.p_e = (R)(p->d.c * p->d.c * p->d.dt * p->g0);
+  a.p_j = (R)(p->d.dt / p->d.eps0);
+  a.inv_n = (R)(1.0 / ((double)p->nx * (double)p->ny * (double)p->nz));
+  for (int i = 0; i < 3; ++i) {
+    a.kp[i] = p->kp_d[i];
+    a.ph[i] = p->ph_d[i];
+  }
+  return a;
 }
 
 template <typename R, int TC>
@@ -454,44 +504,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
   }
   // fused last-axis pass
   {
-    PushArgs<R> a;
-    a.spec = sp;
-    a.cs = cs;
-    a.tab = static_cast<const Coef<R>*>(p->tab);
-    a.nlines = (int)nlines;
-    a.n_in = p->n_in;
-    a.n_out = p->n_out;
-    a.form = p->form;
-    a.ndim = p->ndim;
-    a.nx_half = (int)(nx / 2);
-    a.lines_per_patch = (int)nxh;
-    a.ny = (int)ny;
-    a.tab_row = Lline / 2 + 1;
-    a.rx = (R)p->r[0];
-    a.ry = (R)p->r[1];
-    a.rz = (R)p->r[2];
-    const double c = p->d.c, ic = 1.0 / c;
-    a.c_h = (R)c;
-    a.c_l = (R)(c - (double)a.c_h);
-    a.ic_h = (R)ic;
-    a.ic_l = (R)(ic - (double)a.ic_h);
-    a.s_src = (R)(1.0 / (p->d.eps0 * c * p->g0));
-    a.s_a6 = (R)(1.0 / (p->d.eps0 * c * c * p->g0));
-    a.gmat = p->gmat;
-    a.err = p->d_err;
-    a.tc_ctl = io.tc_ctl;
-    a.tab_ext = chk ? p->tab_e[0] * p->tab_e[1] * p->tab_e[2] - shrink : 0;
-    a.chk_err = p->d_err;
-    a.stag = p->order > 0 ? 1 : 0;
-    a.scheme = (p->d.flags & PSATD_FLAG_PSTD) ? 1 : 0;
-    a.p_h = (R)(0.5 * p->d.dt * p->g0);
-    a.p_e = (R)(p->d.c * p->d.c * p->d.dt * p->g0);
-    a.p_j = (R)(p->d.dt / p->d.eps0);
-    a.inv_n = (R)(1.0 / ((double)p->nx * (double)p->ny * (double)p->nz));
-    for (int i = 0; i < 3; ++i) {
-      a.kp[i] = p->kp_d[i];
-      a.ph[i] = p->ph_d[i];
-    }
+    PushArgs<R> a = make_push_args<R>(p, sp, Lline, nlines);
     const void* twl = p->tw[p->ndim == 3 ? 2 : 1];
     {
       const int tb = p->cfg_push_tb > 0 ? p->cfg_push_tb
@@ -1412,11 +1425,37 @@ struct psatd_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   const void* gkey[2 * kMaxComp] = {};
+  // Persistent mode (persist.cuh): per pass type and length family (0 powers of two,
+  // 1 the 3 * 2^k lengths) one launch over every class's work items.
+  bool persist_ok = false;   // every class has lengths the persistent passes take
+  bool persist = false;      // in use (default when persist_ok)
+  void* d_xf = nullptr;      // XClassArgs per class: x forward, x inverse
+  void* d_xi = nullptr;
+  void* d_push = nullptr;    // PushArgs<float> per class
+  void* d_tws = nullptr;     // fused-axis twiddle table per class
+  BatchItem* d_items = nullptr;
+  unsigned* d_ctr = nullptr;  // two counters per queue
+  struct Queue {
+    int pass;       // 0 x forward, 1 fused, 2 x inverse
+    int fam;
+    int64_t first;  // offset of its items in d_items
+    int n;
+    int grid;
+  };
+  std::vector<Queue> queues;
+  const void* pkey[2 * kMaxComp] = {};  // field / source pointers the x-pass arguments hold
+  bool pkey_set = false;
 };
 
 namespace {
 
 void batch_release(psatd_batch b) {
+  void* bufs[] = {b->d_xf, b->d_xi, b->d_push, b->d_tws, b->d_items, b->d_ctr};
+  for (void* q : bufs)
+    if (q) cudaFree(q);
+  b->d_xf = b->d_xi = b->d_push = b->d_tws = nullptr;
+  b->d_items = nullptr;
+  b->d_ctr = nullptr;
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->gexec = nullptr;
@@ -1434,7 +1473,220 @@ void batch_release(psatd_batch b) {
   b->cls.clear();
 }
 
+// ---- persistent mode
+bool persist_x_len(int L, bool tc) {
+  return (pow2(L) && L >= 32 && L <= 512) || (!tc && three_pow2(L) && L <= 384);
+}
+bool persist_y_len(int L, bool tc) {
+  return (pow2(L) && L >= 64 && L <= 1024) || (!tc && three_pow2(L) && L <= 768);
+}
+int fam_of(int L) { return pow2(L) ? 0 : 1; }
+// rows per item of a transposing pass and lines per item of the fused pass
+int persist_x_tb(int L) { return kPersistThreads / (L / row_ept(L)); }
+int persist_y_tb(int L, bool tc) { return kPersistThreads / (L / (pow2(L) ? (tc ? 16 : 8) : 12)); }
+
+// X-pass arguments of class plan p for the step's field / source pointers (as
+// run_step's first and last passes in 2D).
+XClassArgs make_x_args(psatd_plan p, bool fwd, const void* in[kMaxComp], void* out[kMaxComp]) {
+  XClassArgs a;
+  std::memset(&a, 0, sizeof a);
+  const bool chk = (p->d.flags & PSATD_FLAG_CHECKED) != 0;
+  const int64_t shrink = (p->d.flags & PSATD_FLAG_TEST_SHORT_EXTENT) ? 1 : 0;
+  const size_t csz = p->tc ? 8 : (p->f32 ? 8 : 16);
+  char* s1 = static_cast<char*>(p->spec1);
+  const int n = fwd ? p->n_in : p->n_out;
+  for (int c = 0; c < n; ++c) {
+    a.io.in[c] = fwd ? in[c] : static_cast<const void*>(s1 + c * p->cs * csz);
+    a.io.out[c] = fwd ? static_cast<void*>(s1 + c * p->cs * csz) : out[c];
+  }
+  a.io.gmat = p->gmat;
+  a.io.err = p->d_err;
+  a.io.tc_ctl = (p->d.flags & PSATD_FLAG_TEST_STALL_MMA) ? kTcStallMma : 0;
+  a.io.in_ext = chk ? (fwd ? p->caller_elems : p->cs) - shrink : 0;
+  a.io.out_ext = chk ? (fwd ? p->cs : p->caller_elems) - shrink : 0;
+  a.io.chk_err = p->d_err;
+  a.tw = p->tw[0];
+  if (fwd) {
+    a.s0 = 0;                 // in_sa0 (patch offsets from the table)
+    a.s1 = p->nx;             // in_sb
+    a.s2 = p->nxh * p->ny;    // out_sa0
+    a.s3 = p->ny;             // out_sk
+  } else {
+    a.s0 = p->nxh * p->ny;    // in_sa0
+    a.s1 = p->ny;             // in_sk
+    a.s2 = 0;                 // out_sa0
+    a.s3 = p->nx;             // out_sb
+  }
+  a.off = p->d_off;
+  a.nb = p->ny;
+  a.L = (int)(p->nx / 2);
+  return a;
+}
+
+// Build the persistent mode's tables (class arguments that do not depend on the
+// step's pointers, work items, queues); leaves b->persist_ok false when a class
+// has lengths the persistent passes do not take.
+psatd_status persist_setup(psatd_batch b) {
+  b->persist_ok = b->f32;
+  for (psatd_plan p : b->cls)
+    b->persist_ok = b->persist_ok && persist_x_len((int)(p->nx / 2), p->tc) && persist_y_len((int)p->ny, p->tc);
+  if (!b->persist_ok) return PSATD_OK;
+  const int ncls = (int)b->cls.size();
+  const bool tc = b->cls[0]->tc;
+  std::vector<PushArgs<float>> pa(ncls);
+  std::vector<const void*> tws(ncls);
+  for (int i = 0; i < ncls; ++i) {
+    psatd_plan p = b->cls[i];
+    pa[i] = make_push_args<float>(p, p->spec1, (int)p->ny, p->nxh * p->npatch);
+    tws[i] = p->tw[1];
+  }
+  // work items, one queue per (pass, family), classes largest first
+  std::vector<int> order(ncls);
+  for (int i = 0; i < ncls; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return b->cls[x]->nx * b->cls[x]->ny * b->cls[x]->npatch > b->cls[y]->nx * b->cls[y]->ny * b->cls[y]->npatch;
+  });
+  std::vector<BatchItem> items;
+  b->queues.clear();
+  for (int pass = 0; pass < 3; ++pass)
+    for (int fam = 0; fam < 2; ++fam) {
+      psatd_batch_s::Queue q{pass, fam, (int64_t)items.size(), 0, 0};
+      for (int ci : order) {
+        psatd_plan p = b->cls[ci];
+        if (pass == 1) {
+          const int L = (int)p->ny;
+          if (fam_of(L) != fam) continue;
+          const int tb = persist_y_tb(L, tc);
+          const int64_t nl = p->nxh * p->npatch;
+          for (int64_t blk = 0; blk < (nl + tb - 1) / tb; ++blk) items.push_back({ci, 0, 0, (int)blk});
+        } else {
+          const int L = (int)(p->nx / 2);
+          if (fam_of(L) != fam) continue;
+          const int tb = persist_x_tb(L);
+          const int nc = pass == 0 ? p->n_in : p->n_out;
+          const int64_t nblk = (p->ny + tb - 1) / tb;
+          for (int a0 = 0; a0 < p->npatch; ++a0)
+            for (int a1 = 0; a1 < nc; ++a1)
+              for (int64_t blk = 0; blk < nblk; ++blk) items.push_back({ci, a0, a1, (int)blk});
+        }
+      }
+      q.n = (int)(items.size() - q.first);
+      if (q.n) b->queues.push_back(q);
+    }
+  cudaError_t e;
+  auto dalloc = [&](void** ptr, size_t bytes) -> bool {
+    e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+      *ptr = nullptr;
+      cudaGetLastError();
+      return false;
+    }
+    return true;
+  };
+  if (!dalloc(&b->d_xf, ncls * sizeof(XClassArgs)) || !dalloc(&b->d_xi, ncls * sizeof(XClassArgs)) ||
+      !dalloc(&b->d_push, ncls * sizeof(PushArgs<float>)) || !dalloc(&b->d_tws, ncls * sizeof(void*)) ||
+      !dalloc(reinterpret_cast<void**>(&b->d_items), items.size() * sizeof(BatchItem)) ||
+      !dalloc(reinterpret_cast<void**>(&b->d_ctr), 2 * b->queues.size() * sizeof(unsigned)))
+    return fail(nullptr, PSATD_ERR_OOM, "batch persistent tables: %s", cudaGetErrorString(e));
+  e = cudaMemcpy(b->d_push, pa.data(), ncls * sizeof(PushArgs<float>), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->d_tws, tws.data(), ncls * sizeof(void*), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(b->d_ctr, 0, 2 * b->queues.size() * sizeof(unsigned));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch persistent tables");
+  // grids: the CTAs that stay resident together, at most the queue's chunks
+  int nsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int layout = b->cls[0]->layout, n_in = b->cls[0]->n_in;
+  const int tcv = tc ? (b->cls[0]->tc_bf16 ? 2 : 1) : 0;
+  for (auto& q : b->queues) {
+    int occ = 0;
+    PersistQueue pq{nullptr, 0, nullptr};
+    if (q.pass == 1) {
+      if (tcv == 2) e = launch_persist_push<float, 2, 0>(layout, n_in, 0, b->st, nullptr, nullptr, pq, &occ);
+      else if (tcv == 1) e = launch_persist_push<float, 1, 0>(layout, n_in, 0, b->st, nullptr, nullptr, pq, &occ);
+      else if (q.fam == 0) e = launch_persist_push<float, 0, 0>(layout, n_in, 0, b->st, nullptr, nullptr, pq, &occ);
+      else e = launch_persist_push<float, 0, 1>(layout, n_in, 0, b->st, nullptr, nullptr, pq, &occ);
+    } else {
+      const bool fwd = q.pass == 0;
+      if (tcv == 2) e = launch_persist_x<float, 2, 0>(fwd, 0, b->st, nullptr, pq, &occ);
+      else if (tcv == 1) e = launch_persist_x<float, 1, 0>(fwd, 0, b->st, nullptr, pq, &occ);
+      else if (q.fam == 0) e = launch_persist_x<float, 0, 0>(fwd, 0, b->st, nullptr, pq, &occ);
+      else e = launch_persist_x<float, 0, 1>(fwd, 0, b->st, nullptr, pq, &occ);
+    }
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "persistent pass occupancy");
+    const int chunks = (q.n + kPersistChunk - 1) / kPersistChunk;
+    q.grid = std::max(1, std::min(chunks, std::max(occ, 1) * nsm));
+  }
+  b->persist = true;
+  return PSATD_OK;
+}
+
+// Upload the x passes' class arguments when the step's pointers differ from the
+// last upload (stream-ordered on the batch's stream, outside any capture).
+psatd_status persist_upload(psatd_batch b, const void* in[kMaxComp], void* out[kMaxComp]) {
+  const void* key[2 * kMaxComp];
+  for (int i = 0; i < kMaxComp; ++i) {
+    key[i] = in[i];
+    key[kMaxComp + i] = out[i];
+  }
+  if (b->pkey_set && std::memcmp(key, b->pkey, sizeof key) == 0) return PSATD_OK;
+  const int ncls = (int)b->cls.size();
+  std::vector<XClassArgs> xf(ncls), xi(ncls);
+  for (int i = 0; i < ncls; ++i) {
+    xf[i] = make_x_args(b->cls[i], true, in, out);
+    xi[i] = make_x_args(b->cls[i], false, in, out);
+  }
+  cudaError_t e = cudaMemcpyAsync(b->d_xf, xf.data(), ncls * sizeof(XClassArgs), cudaMemcpyHostToDevice, b->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_xi, xi.data(), ncls * sizeof(XClassArgs), cudaMemcpyHostToDevice, b->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);  // the host tables are freed on return
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "batch argument upload");
+  std::memcpy(b->pkey, key, sizeof key);
+  b->pkey_set = true;
+  return PSATD_OK;
+}
+
+// One step of every class as one persistent launch per pass type and family.
+psatd_status batch_launch_persist(psatd_batch b, void* out[kMaxComp]) {
+  psatd_plan p0 = b->cls[0];
+  const bool tc = p0->tc;
+  const int tcv = tc ? (p0->tc_bf16 ? 2 : 1) : 0;
+  const int slot[3] = {K_FWD_X, K_PUSH, K_INV_X};
+  for (size_t qi = 0; qi < b->queues.size(); ++qi) {
+    const auto& q = b->queues[qi];
+    PersistQueue pq{b->d_items + q.first, q.n, b->d_ctr + 2 * qi};
+    cudaError_t e;
+    TimedLaunch tl(p0, slot[q.pass], b->st);
+    if (q.pass == 1) {
+      const PushArgs<float>* a = static_cast<const PushArgs<float>*>(b->d_push);
+      const void* const* tws = static_cast<const void* const*>(b->d_tws);
+      if (tcv == 2) e = launch_persist_push<float, 2, 0>(p0->layout, p0->n_in, q.grid, b->st, a, tws, pq);
+      else if (tcv == 1) e = launch_persist_push<float, 1, 0>(p0->layout, p0->n_in, q.grid, b->st, a, tws, pq);
+      else if (q.fam == 0) e = launch_persist_push<float, 0, 0>(p0->layout, p0->n_in, q.grid, b->st, a, tws, pq);
+      else e = launch_persist_push<float, 0, 1>(p0->layout, p0->n_in, q.grid, b->st, a, tws, pq);
+    } else {
+      const bool fwd = q.pass == 0;
+      const XClassArgs* a = static_cast<const XClassArgs*>(fwd ? b->d_xf : b->d_xi);
+      if (tcv == 2) e = launch_persist_x<float, 2, 0>(fwd, q.grid, b->st, a, pq);
+      else if (tcv == 1) e = launch_persist_x<float, 1, 0>(fwd, q.grid, b->st, a, pq);
+      else if (q.fam == 0) e = launch_persist_x<float, 0, 0>(fwd, q.grid, b->st, a, pq);
+      else e = launch_persist_x<float, 0, 1>(fwd, q.grid, b->st, a, pq);
+    }
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "persistent batch pass launch");
+  }
+  if (p0->d.flags & PSATD_FLAG_CHECKED)
+    for (psatd_plan p : b->cls) {
+      cudaError_t e = launch_nonfinite(p->f32, out, p->n_out, p->d_off, p->npatch, p->nx * p->ny * p->nz, p->d_err,
+                                       b->st);
+      if (e != cudaSuccess) return cuda_fail(nullptr, e, "non-finite scan launch");
+    }
+  return PSATD_OK;
+}
+
 psatd_status batch_launch_all(psatd_batch b, const void* in[kMaxComp], void* out[kMaxComp]) {
+  if (b->persist) return batch_launch_persist(b, out);
   const bool forked = !b->br.empty();
   cudaError_t e = cudaSuccess;
   if (forked) {
@@ -1526,6 +1778,14 @@ extern "C" psatd_status psatd_batch_create(const psatd_desc* base, int32_t npatc
     }
     b->cls.push_back(p);
   }
+  {  // persistent passes over every class, when all the classes' lengths allow them
+    psatd_status s = persist_setup(b);
+    if (s != PSATD_OK) {
+      batch_release(b);
+      delete b;
+      return s;
+    }
+  }
   // branch streams: up to 4, classes assigned largest first to the least loaded branch
   const int nbr = (int)std::min<size_t>(4, b->cls.size());
   if (nbr > 1) {
@@ -1571,6 +1831,7 @@ extern "C" psatd_status psatd_batch_step(psatd_batch b, const psatd_fields* fiel
     g_err = b->cls[0]->err;
     return s;
   }
+  if (b->persist && (s = persist_upload(b, in, out)) != PSATD_OK) return s;
   if (nsteps == 1 || b->st == nullptr) {  // the legacy stream cannot be captured
     for (int i = 0; i < nsteps; ++i)
       if ((s = batch_launch_all(b, in, out)) != PSATD_OK) return s;
@@ -1612,6 +1873,28 @@ extern "C" psatd_status psatd_batch_step(psatd_batch b, const psatd_fields* fiel
 }
 
 extern "C" int64_t psatd_batch_cells(psatd_batch b) { return b ? b->total_cells : 0; }
+
+extern "C" psatd_status psatd_batch_set_persistent(psatd_batch b, int32_t enable) {
+  if (!b) return fail(nullptr, PSATD_ERR_INVALID_ARG, "batch is NULL");
+  if (enable && !b->persist_ok)
+    return fail(nullptr, PSATD_ERR_UNSUPPORTED,
+                "persistent passes need FP32 or mixed precision and sides whose line lengths they take "
+                "(x: n/2 in 32..512 or 48..384 (3 * 2^k); last axis 64..1024 or 96..768)");
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "stream synchronise");
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  b->persist = enable != 0;
+  return PSATD_OK;
+}
+
+extern "C" int32_t psatd_batch_launches_per_step(psatd_batch b) {
+  if (!b) return 0;
+  if (b->persist) return (int32_t)b->queues.size();
+  return (int32_t)(b->cls.size() * (b->cls.empty() ? 0 : 3));
+}
 
 extern "C" psatd_status psatd_batch_sync(psatd_batch b) {
   if (!b) return fail(nullptr, PSATD_ERR_INVALID_ARG, "batch is NULL");

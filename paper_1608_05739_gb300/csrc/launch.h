@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "persist.cuh"
 #include "psatd_kernels.cuh"
 
 namespace psatd {
@@ -44,6 +45,16 @@ cudaError_t launch_inv_T3(int L, bool c2r, const PassGeom& g, cudaStream_t st, c
 template <typename R>
 cudaError_t launch_line_push3(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
                               const PushArgs<R>& a, const void* tw);
+
+// Persistent batch passes (persist.cuh): FAM 0 power-of-two lengths, 1 the 3 * 2^k
+// lengths (float, TC = 0).  `grid` CTAs of kPersistThreads threads; *occ (if not
+// NULL) receives the CTAs per SM the kernel can keep resident.
+template <typename R, int TC, int FAM>
+cudaError_t launch_persist_x(bool fwd, int grid, cudaStream_t st, const XClassArgs* cls, const PersistQueue& q,
+                             int* occ = nullptr);
+template <typename R, int TC, int FAM>
+cudaError_t launch_persist_push(int layout, int n_in, int grid, cudaStream_t st, const PushArgs<R>* cls,
+                                const void* const* tws, const PersistQueue& q, int* occ = nullptr);
 
 template <typename R>
 cudaError_t launch_fdtd(int ndim, int scheme, int64_t nx, int64_t ny, int64_t nz, const double* d,

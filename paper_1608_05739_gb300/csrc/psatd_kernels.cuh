@@ -117,33 +117,47 @@ struct RowThreads { static constexpr int value = RowEPT<L>::value == 24 ? 256 : 
 // TC: radix-16 stages on the tensor cores (1 split-FP16, 2 split-BF16); the
 // dynamic shared memory then starts with the kTcTail block and the A tiles
 // alias the line buffers.
-template <typename R, int L, bool R2C, int TC = 0>
-__global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_fwd_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
-                                               int64_t in_sa0, int64_t in_sb, int64_t out_sa0,
-                                               int64_t out_sk, int log_tb, const int64_t* __restrict__ in_off) {
+// Work of one CTA of a transposing pass: row block bx (rows bx TB .. bx TB + TB - 1,
+// TB = 1 << log_tb) of plane / patch a0 and component a1, thread (t, g) = (position
+// in its line, line in the block); rows b >= nb are idle (they transform zeros and
+// store nothing), so that a block may run past the rows of its patch.
+struct RowCta {
+  int bx, a0, a1, t, g, log_tb;
+  int64_t nb;
+};
+
+template <typename R, int L, bool R2C, int TC, bool PART>
+__device__ __forceinline__ void fwd_T_body(const LineIO& io, const typename Types<R>::W* __restrict__ tw,
+                                           int64_t in_sa0, int64_t in_sb, int64_t out_sa0, int64_t out_sk,
+                                           const int64_t* __restrict__ in_off, const RowCta& cta,
+                                           unsigned char* smem_raw, TcCtx& tc) {
   typedef typename Types<R>::C C;
   constexpr int EPT = RowEPT<L>::value;
   typedef FFTPlan<L, EPT> P;
   constexpr int T = P::kT;
   constexpr int NK = R2C ? L + 1 : L;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smem = reinterpret_cast<C*>(smem_raw + (TC ? kTcTail : 0));
+  const int log_tb = cta.log_tb;
   const int TB = 1 << log_tb;
-  const int t = threadIdx.x, g = threadIdx.y;
-  const int64_t b = (int64_t)blockIdx.x * TB + g;
-  const int a0 = blockIdx.y, a1 = blockIdx.z;
-  if (io.in_ext) {  // checked mode: the row read and the transposed block written
+  const int t = cta.t, g = cta.g;
+  const int64_t b0 = (int64_t)cta.bx * TB;
+  const int64_t b = b0 + g;
+  // PART: the block may run past the rows (nb) of its plane; else every row is valid
+  const bool valid = !PART || b < cta.nb;
+  const int rows = PART ? (int)(cta.nb - b0 < TB ? cta.nb - b0 : TB) : TB;  // valid rows of the block
+  const int a0 = cta.a0, a1 = cta.a1;
+  if (io.in_ext) {  // checked mode: the rows read and the transposed block written
     const int64_t o0c = in_off ? in_off[a0] : a0 * in_sa0;
-    const int64_t in_end = o0c + b * in_sb + (R2C ? 2 * L : L);
-    const int64_t out_end = a0 * out_sa0 + (int64_t)blockIdx.x * TB + TB + (int64_t)(NK - 1) * out_sk;
+    const int64_t in_end = valid ? o0c + b * in_sb + (R2C ? 2 * L : L) : 0;
+    const int64_t out_end = a0 * out_sa0 + b0 + rows + (int64_t)(NK - 1) * out_sk;
     if (cta_out_of_bounds(in_end > io.in_ext || out_end > io.out_ext || o0c < 0, io.chk_err)) return;
   }
   __shared__ const void* twslot;
   if (t == 0 && g == 0) twslot = tw;
-  TcCtx tc;
-  if constexpr (TC)  // split-BF16: the third A piece after the exchange region (line buffers or tile)
-    tc_setup(tc, smem_raw, io.gmat, smem_u32(smem), io.err, TC == 2,
-             smem_u32(smem + (R2C ? TB * L : L * (TB + 1))), io.tc_ctl);
+  if constexpr (TC) {  // the A tiles alias the line buffers; split-BF16's third piece follows them
+    tc.a_tile = smem_u32(smem);
+    tc.a_tile3 = smem_u32(smem + (R2C ? TB * L : L * (TB + 1)));
+  }
   ExBuf<C> ex{{smem + g * L, smem + g * L}, 0, &twslot, true};  // one exchange buffer per line
   if constexpr (!TC && T % 32 == 0)
     if (TB <= 8) {  // each line's warps synchronise among themselves between stages
@@ -160,7 +174,7 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_fwd_T(LineIO io,
     else
       row = static_cast<const C*>(io.in[a1]) + o0 + b * in_sb;
 #pragma unroll
-    for (int m = 0; m < EPT; ++m) v[m] = row[t + T * m];
+    for (int m = 0; m < EPT; ++m) v[m] = (!PART || valid) ? row[t + T * m] : mkc(R(0), R(0));
   }
   // twslot visible to every line (else the first exchange barrier publishes it, when it spans the CTA)
   if (P::kStages == 1 || ex.bar_n) __syncthreads();
@@ -184,8 +198,9 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_fwd_T(LineIO io,
     const int k0 = tid >> log_tb;  // in [0, T)
     const int xgg = (gg * (16 >> log_tb)) & 15 & (L - 1);
     const C* zr = smem + gg * L;
-    C* o = static_cast<C*>(io.out[a1]) + a0 * out_sa0 + (int64_t)blockIdx.x * TB + (int64_t)k0 * out_sk + gg;
+    C* o = static_cast<C*>(io.out[a1]) + a0 * out_sa0 + b0 + (int64_t)k0 * out_sk + gg;
     const int64_t ostep = (int64_t)T * out_sk;
+    if (!PART || gg < rows) {
 #pragma unroll
     for (int j0 = 0; j0 < EPT; j0 += 4) {
       typename Types<R>::W w[4];
@@ -208,6 +223,7 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_fwd_T(LineIO io,
       const C fo = mkc(R(0.5) * (z0.y - zm.y), R(-0.5) * (z0.x - zm.x));
       o[EPT * ostep] = csub(fe, fo);
     }
+    }
   } else {
     C* tile = smem;  // [NK][TB + 1], aliases the exchange buffers
     const int tp = TB + 1;
@@ -215,13 +231,25 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_fwd_T(LineIO io,
 #pragma unroll
     for (int m = 0; m < EPT; ++m) tile[(t + T * m) * tp + g] = v[m];
     __syncthreads();
-    C* ob = static_cast<C*>(io.out[a1]) + a0 * out_sa0 + (int64_t)blockIdx.x * TB;
+    C* ob = static_cast<C*>(io.out[a1]) + a0 * out_sa0 + b0;
     const int nthr = T * TB;
     for (int idx = g * T + t; idx < NK * TB; idx += nthr) {
       const int k = idx >> log_tb, gg = idx & (TB - 1);
-      ob[(int64_t)k * out_sk + gg] = tile[k * tp + gg];
+      if (!PART || gg < rows) ob[(int64_t)k * out_sk + gg] = tile[k * tp + gg];
     }
   }
+}
+
+template <typename R, int L, bool R2C, int TC = 0>
+__global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_fwd_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
+                                               int64_t in_sa0, int64_t in_sb, int64_t out_sa0,
+                                               int64_t out_sk, int log_tb, const int64_t* __restrict__ in_off) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TcCtx tc;
+  if constexpr (TC) tc_setup(tc, smem_raw, io.gmat, 0u, io.err, TC == 2, 0u, io.tc_ctl);
+  const RowCta cta{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)threadIdx.x, (int)threadIdx.y, log_tb,
+                   (int64_t)gridDim.x << log_tb};
+  fwd_T_body<R, L, R2C, TC, false>(io, tw, in_sa0, in_sb, out_sa0, out_sk, in_off, cta, smem_raw, tc);
   if constexpr (TC) tc_teardown(tc);
 }
 
@@ -230,33 +258,38 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_fwd_T(LineIO io,
 // in[a1] + a0*in_sa0 + k*in_sk + b, inverse FFT along k, write the lines
 // contiguously to out[a1] + a0*out_sa0 + b*out_sb.  C2R: L+1 Hermitian bins
 // in, real rows of length 2L out (unnormalised).
-template <typename R, int L, bool C2R, int TC = 0>
-__global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_inv_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
-                                               int64_t in_sa0, int64_t in_sk, int64_t out_sa0,
-                                               int64_t out_sb, int log_tb, const int64_t* __restrict__ out_off) {
+template <typename R, int L, bool C2R, int TC, bool PART>
+__device__ __forceinline__ void inv_T_body(const LineIO& io, const typename Types<R>::W* __restrict__ tw,
+                                           int64_t in_sa0, int64_t in_sk, int64_t out_sa0, int64_t out_sb,
+                                           const int64_t* __restrict__ out_off, const RowCta& cta,
+                                           unsigned char* smem_raw, TcCtx& tc) {
   typedef typename Types<R>::C C;
   constexpr int EPT = RowEPT<L>::value;
   typedef FFTPlan<L, EPT> P;
   constexpr int T = P::kT;
   constexpr int NK = C2R ? L + 1 : L;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   C* smem = reinterpret_cast<C*>(smem_raw + (TC ? kTcTail : 0));
+  const int log_tb = cta.log_tb;
   const int TB = 1 << log_tb;
-  const int t = threadIdx.x, g = threadIdx.y;
-  const int64_t b = (int64_t)blockIdx.x * TB + g;
-  const int a0 = blockIdx.y, a1 = blockIdx.z;
-  if (io.in_ext) {  // checked mode: the transposed block read and the row written
+  const int t = cta.t, g = cta.g;
+  const int64_t b0 = (int64_t)cta.bx * TB;
+  const int64_t b = b0 + g;
+  // PART: the block may run past the rows (nb) of its plane; else every row is valid
+  const bool valid = !PART || b < cta.nb;
+  const int rows = PART ? (int)(cta.nb - b0 < TB ? cta.nb - b0 : TB) : TB;  // valid rows of the block
+  const int a0 = cta.a0, a1 = cta.a1;
+  if (io.in_ext) {  // checked mode: the transposed block read and the rows written
     const int64_t o0c = out_off ? out_off[a0] : a0 * out_sa0;
-    const int64_t in_end = a0 * in_sa0 + (int64_t)blockIdx.x * TB + TB + (int64_t)(NK - 1) * in_sk;
-    const int64_t out_end = o0c + b * out_sb + (C2R ? 2 * L : L);
+    const int64_t in_end = a0 * in_sa0 + b0 + rows + (int64_t)(NK - 1) * in_sk;
+    const int64_t out_end = valid ? o0c + b * out_sb + (C2R ? 2 * L : L) : 0;
     if (cta_out_of_bounds(in_end > io.in_ext || out_end > io.out_ext || o0c < 0, io.chk_err)) return;
   }
   __shared__ const void* twslot;
   if (t == 0 && g == 0) twslot = tw;
-  TcCtx tc;
-  if constexpr (TC)
-    tc_setup(tc, smem_raw, io.gmat, smem_u32(smem), io.err, TC == 2,
-             smem_u32(smem + (C2R ? TB * L : L * (TB + 1))), io.tc_ctl);
+  if constexpr (TC) {
+    tc.a_tile = smem_u32(smem);
+    tc.a_tile3 = smem_u32(smem + (C2R ? TB * L : L * (TB + 1)));
+  }
   C v[EPT];
   if constexpr (C2R) {
     // Z[k] = Fe + i Fo, Fe = X[k] + X*[L-k], Fo = (X[k] - X*[L-k]) conj(W_N^k), read straight
@@ -271,8 +304,10 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_inv_T(LineIO io,
     const int p0 = tid >> log_tb;  // in [0, T)
     const int xgg = (gg * (16 >> log_tb)) & 15 & (L - 1);
     C* zr = smem + gg * L;
-    const C* ib = static_cast<const C*>(io.in[a1]) + a0 * in_sa0 + (int64_t)blockIdx.x * TB + gg;
+    const bool gvalid = !PART || gg < rows;
+    const C* ib = static_cast<const C*>(io.in[a1]) + a0 * in_sa0 + b0 + gg;
     constexpr int NP = EPT / 2;  // 4 or 8 pairs, taken four at a time
+    const C zero = mkc(R(0), R(0));
 #pragma unroll
     for (int j0 = 0; j0 < NP; j0 += 4) {
       C xk[4], xm[4];
@@ -280,8 +315,8 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_inv_T(LineIO io,
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int pp = p0 + (j0 + j) * T;
-        xk[j] = ib[(int64_t)pp * in_sk];
-        xm[j] = ib[(int64_t)(L - pp) * in_sk];
+        xk[j] = gvalid ? ib[(int64_t)pp * in_sk] : zero;
+        xm[j] = gvalid ? ib[(int64_t)(L - pp) * in_sk] : zero;
         w[j] = __ldg(&wn[pp]);
       }
 #pragma unroll
@@ -296,7 +331,7 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_inv_T(LineIO io,
       }
     }
     if (p0 == 0) {  // pp = L/2: X[L/2] pairs with itself
-      const C x = ib[(int64_t)(L / 2) * in_sk];
+      const C x = gvalid ? ib[(int64_t)(L / 2) * in_sk] : zero;
       const C fe = cadd(x, cconj(x));
       const C fo = twmul_conj(csub(x, cconj(x)), __ldg(&wn[L / 2]));
       zr[(L / 2) ^ xgg] = cadd(fe, cmul_pi(fo));
@@ -311,13 +346,14 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_inv_T(LineIO io,
     const int tp = TB + 1;
     {
       // L * TB values over T * TB threads: EPT each, all loads issued before the stores
-      const C* ib = static_cast<const C*>(io.in[a1]) + a0 * in_sa0 + (int64_t)blockIdx.x * TB;
+      const C* ib = static_cast<const C*>(io.in[a1]) + a0 * in_sa0 + b0;
       const int nthr = T * TB;
       C tv[EPT];
 #pragma unroll
       for (int j = 0; j < EPT; ++j) {
         const int idx = g * T + t + j * nthr;
-        tv[j] = ib[(int64_t)(idx >> log_tb) * in_sk + (idx & (TB - 1))];
+        tv[j] = (!PART || (idx & (TB - 1)) < rows) ? ib[(int64_t)(idx >> log_tb) * in_sk + (idx & (TB - 1))]
+                                                   : mkc(R(0), R(0));
       }
 #pragma unroll
       for (int j = 0; j < EPT; ++j) {
@@ -337,6 +373,7 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_inv_T(LineIO io,
       ex.bar_n = T;
     }
   block_fft_inv<R, L, EPT, TC>(v, ex, tw, t, &tc);
+  if (PART && !valid) return;
   C* row;
   const int64_t o0 = out_off ? out_off[a0] : a0 * out_sa0;  // per-patch offsets of a batch
   if constexpr (C2R)
@@ -345,6 +382,18 @@ __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_inv_T(LineIO io,
     row = static_cast<C*>(io.out[a1]) + o0 + b * out_sb;
 #pragma unroll
   for (int m = 0; m < EPT; ++m) row[t + T * m] = v[m];
+}
+
+template <typename R, int L, bool C2R, int TC = 0>
+__global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_inv_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
+                                               int64_t in_sa0, int64_t in_sk, int64_t out_sa0,
+                                               int64_t out_sb, int log_tb, const int64_t* __restrict__ out_off) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TcCtx tc;
+  if constexpr (TC) tc_setup(tc, smem_raw, io.gmat, 0u, io.err, TC == 2, 0u, io.tc_ctl);
+  const RowCta cta{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)threadIdx.x, (int)threadIdx.y, log_tb,
+                   (int64_t)gridDim.x << log_tb};
+  inv_T_body<R, L, C2R, TC, false>(io, tw, in_sa0, in_sk, out_sa0, out_sb, out_off, cta, smem_raw, tc);
   if constexpr (TC) tc_teardown(tc);
 }
 
@@ -737,17 +786,17 @@ __device__ __forceinline__ void push_line_modes(typename Types<R>::C* st, int ss
 // touch each thread's own positions.
 // EPT: elements per thread, 8 (radix-8 stages) or 16 (radix-16 stages; the
 // only choice of the tensor-core variant).
-template <typename R, int L, int LAYOUT, int TC = 0, int EPT = PushEPT<L, TC>::value>
-__global__ void __launch_bounds__(FFTPlan<L, EPT>::kT > 256 ? FFTPlan<L, EPT>::kT : 256)
-k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
+// Body of one CTA of the fused pass: line block bx (lines bx tb .. bx tb + tb - 1,
+// line g of the block handled by the threads g T .. g T + T - 1, t their position).
+template <typename R, int L, int LAYOUT, int TC, int EPT>
+__device__ __forceinline__ void line_push_body(const PushArgs<R>& a, const typename Types<R>::W* __restrict__ tw,
+                                               int bx, int t, int g, int tb, unsigned char* smem_raw, TcCtx& tc) {
   typedef typename Types<R>::C C;
   static_assert(!TC || EPT == 16, "tensor-core stages are radix 16");
   typedef FFTPlan<L, EPT> P;
   constexpr int T = P::kT;
   constexpr int CXL = P::kLastCX;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int t = threadIdx.x, g = threadIdx.y;
-  const int line = blockIdx.x * blockDim.y + g;
+  const int line = bx * tb + g;
   const bool valid = line < a.nlines;
   if (a.tab_ext) {  // checked mode: the line's columns of every slot and its coefficient row
     int mx_c, my_c, row_c;
@@ -757,15 +806,13 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
     if (cta_out_of_bounds(bad, a.chk_err)) return;
   }
   C* base = reinterpret_cast<C*>(smem_raw + (TC ? kTcTail : 0));
-  const int ss = (int)blockDim.y * L;  // slot stride (component-major)
+  const int ss = tb * L;               // slot stride (component-major)
   C* st = base + g * L;                // this line's slot 0; slot c at st + c * ss
   C* bufB = base + a.n_in * ss + g * L;
   C* spec = static_cast<C*>(a.spec);
   __shared__ const void* twslot;
   if (t == 0 && g == 0) twslot = tw;
-  TcCtx tc;
-  if constexpr (TC)  // split-BF16's third A piece: set per component below
-    tc_setup(tc, smem_raw, a.gmat, smem_u32(base + a.n_in * ss), a.err, TC == 2, smem_u32(base), a.tc_ctl);
+  if constexpr (TC) tc.a_tile = smem_u32(base + a.n_in * ss);  // split-BF16's third A piece: per component below
 
   int mxi, myi, rowi;
   line_modes(a, valid ? line : 0, mxi, myi, rowi);
@@ -840,6 +887,16 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
       for (int m = 0; m < EPT; ++m) dst[t + T * m] = v[m];
     }
   }
+}
+
+template <typename R, int L, int LAYOUT, int TC = 0, int EPT = PushEPT<L, TC>::value>
+__global__ void __launch_bounds__(FFTPlan<L, EPT>::kT > 256 ? FFTPlan<L, EPT>::kT : 256)
+k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TcCtx tc;
+  if constexpr (TC) tc_setup(tc, smem_raw, a.gmat, 0u, a.err, TC == 2, 0u, a.tc_ctl);
+  line_push_body<R, L, LAYOUT, TC, EPT>(a, tw, (int)blockIdx.x, (int)threadIdx.x, (int)threadIdx.y, (int)blockDim.y,
+                                        smem_raw, tc);
   if constexpr (TC) tc_teardown(tc);
 }
 

@@ -116,3 +116,61 @@ def test_batch_kernel_times_of_a_graph_replay(prec):
         out.append(F[:3])
     for x, y in zip(*out):
         assert torch.equal(x, y)
+
+
+PERSIST_SIZES = {
+    "fp32": [(64, 64), (128, 96), (192, 128), (256, 256), (1024, 768), (96, 1024), (512, 384), (64, 64)],
+    "mixed_fp16": [(64, 64), (128, 128), (256, 512), (1024, 1024), (512, 64), (128, 128)],
+    "mixed_bf16": [(64, 64), (128, 128), (256, 512), (1024, 1024), (512, 64), (128, 128)],
+}
+
+
+@pytest.mark.parametrize("prec,layout", [("fp32", "te"), ("fp32", "tm"), ("fp32", "2d6"), ("mixed_fp16", "te"),
+                                         ("mixed_bf16", "te"), ("mixed_bf16", "2d6")])
+def test_persistent_passes_equal_per_class_launches(prec, layout):
+    """One persistent launch per pass type and length family over every patch (the
+    default where the sizes allow) gives the bits of the per-class launches, in a
+    graph replay of several steps, and matches the oracle on a patch of each family."""
+    import torch
+    ensure_lib()
+    sizes = PERSIST_SIZES[prec]
+    tot = sum(a * b for a, b in sizes)
+    g = torch.Generator(device="cuda").manual_seed(21)
+    pe, pb, pj = capi.PRESENT[layout]
+    mk = lambda p: [torch.randn(tot, device="cuda", generator=g) if p[i] else None for i in range(3)]
+    E0, B0, J = mk(pe), mk(pb), mk(pj)
+    host0 = ([t.double().cpu().numpy() if t is not None else None for t in E0],
+             [t.double().cpu().numpy() if t is not None else None for t in B0],
+             [t.double().cpu().numpy() if t is not None else None for t in J])
+    out = []
+    for persistent in (True, False):
+        E = [t.clone() if t is not None else None for t in E0]
+        B = [t.clone() if t is not None else None for t in B0]
+        stream = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        b = capi.Batch(sizes, (1.0, 1.0), 0.5, layout=layout, prec=prec, src="J", stream=stream)
+        fams_x = len({(nx // 2) & (nx // 2 - 1) == 0 for nx, _ in sizes})
+        fams_y = len({ny & (ny - 1) == 0 for _, ny in sizes})
+        assert b.launches_per_step() == 2 * fams_x + fams_y      # persistent by default
+        b.set_persistent(persistent)
+        with torch.cuda.stream(stream):
+            b.step(E, B, J, nsteps=3)
+        b.sync()
+        b.destroy()
+        out.append(E + B)
+    for x, y in zip(*out):
+        if x is not None:
+            assert torch.equal(x, y)
+    # the oracle on the first patch and the largest one
+    offs = np.concatenate([[0], np.cumsum([a * c for a, c in sizes])])
+    area = [a * c for a, c in sizes]
+    for i in {0, int(np.argmax(area))}:
+        nx, ny = sizes[i]
+        cut = lambda arrs: np.stack([a[offs[i]:offs[i + 1]].reshape(ny, nx) if a is not None else np.zeros((ny, nx))
+                                     for a in arrs])
+        Eo, Bo = orc.psatd_step(cut(host0[0]), cut(host0[1]), cut(host0[2]), d=(1.0, 1.0), dt=0.5, form="J",
+                                nsteps=3)
+        Eg = cut([t.double().cpu().numpy() if t is not None else None for t in out[0][:3]])
+        Bg = cut([t.double().cpu().numpy() if t is not None else None for t in out[0][3:]])
+        tol = 4e-6 if prec == "fp32" else 8e-6
+        assert rel_l2_fields(Eg, Bg, mask_layout(Eo, layout, "E"), mask_layout(Bo, layout, "B")) < tol, i
