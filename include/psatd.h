@@ -246,8 +246,9 @@ psatd_status psatd_step(psatd_plan plan, const psatd_fields* fields,
 
 /* Synchronise the plan's stream and report any asynchronous CUDA error, or
  * PSATD_ERR_BOUNDS when a checked plan's index check failed, or
- * PSATD_ERR_TIMEOUT when a tensor-core pass (PSATD_MIXED_FP16 / _BF16) gave up
- * a bounded wait for its MMAs since the last sync (the CTA then skipped its
+ * PSATD_ERR_TIMEOUT when a bounded device-side wait gave up since the last
+ * sync: the fused pass's wait for its bulk-copied inputs, or a tensor-core
+ * pass's (PSATD_MIXED_FP16 / _BF16) wait for its MMAs (the CTA then skipped its
  * remaining tensor-core stages and freed its TMEM; the step's output is not
  * valid), or PSATD_ERR_NONFINITE when a checked plan (PSATD_FLAG_CHECKED)
  * saw NaN or Inf in a step's output since the last sync; the word is cleared. */

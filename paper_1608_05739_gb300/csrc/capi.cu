@@ -917,9 +917,9 @@ static psatd_status plan_create_n(const psatd_desc* desc, void* cuda_stream, int
   }
   if (a == PSATD_OK && p->order > 0)
     a = alloc(p, reinterpret_cast<void**>(&p->cw_d), (size_t)(p->order / 2) * sizeof(double), "stencil weights");
-  const bool need_err = p->tc || (desc->flags & PSATD_FLAG_CHECKED);
-  if (a == PSATD_OK && need_err) a = alloc(p, reinterpret_cast<void**>(&p->d_err), sizeof(int), "error word");
-  if (a == PSATD_OK && need_err) {
+  // the device error word (expired bounded waits, checked mode)
+  if (a == PSATD_OK) a = alloc(p, reinterpret_cast<void**>(&p->d_err), sizeof(int), "error word");
+  if (a == PSATD_OK) {
     cudaError_t e = cudaMemset(p->d_err, 0, sizeof(int));
     if (e != cudaSuccess) a = cuda_fail(p, e, "error word clear");
   }
@@ -1075,6 +1075,8 @@ psatd_status psatd_plan_sync(psatd_plan p) {
       cudaMemset(p->d_err, 0, sizeof(int));
       if (w & kErrMmaWait)
         return fail(p, PSATD_ERR_TIMEOUT, "a tensor-core pass gave up waiting for its MMAs (error word %d)", w);
+      if (w & kErrStageWait)
+        return fail(p, PSATD_ERR_TIMEOUT, "the fused pass gave up waiting for its staged inputs (error word %d)", w);
       if (w & kErrBounds)
         return fail(p, PSATD_ERR_BOUNDS, "a pass's index check failed; its CTA skipped its accesses (error word %d)",
                     w);

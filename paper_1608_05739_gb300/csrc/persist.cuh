@@ -134,8 +134,12 @@ __global__ void __launch_bounds__(kPersistThreads, 4) k_persist_push(const PushA
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int slot;
   __shared__ __align__(16) PushArgs<R> A;
+  __shared__ __align__(8) uint64_t stage_mbar;
+  StageCtx sc;
+  stage_init(sc, &stage_mbar, cls[0].err ? cls[0].err : cls[0].chk_err);
   TcCtx tc;
   if constexpr (TC) tc_setup(tc, smem_raw, cls[0].gmat, 0u, cls[0].err, TC == 2, 0u, cls[0].tc_ctl);
+  // (the queue's first take has a block barrier before any use of the stage mbarrier)
   constexpr int EPT = FAM ? 12 : (TC ? 16 : 8);
   for (;;) {
     const int i0 = persist_take(q, &slot);
@@ -153,7 +157,7 @@ __global__ void __launch_bounds__(kPersistThreads, 4) k_persist_push(const PushA
     constexpr int T = LL / EPT;                                                                            \
     line_push_body<R, LL, LAYOUT, TC, EPT>(A, static_cast<const W*>(tws[it.cls]), it.blk,                 \
                                            (int)threadIdx.x % T, (int)threadIdx.x / T, kPersistThreads / T, \
-                                           smem_raw, tc);                                                  \
+                                           smem_raw, tc, sc);                                              \
   }
       PSATD_PERSIST_Y_LENGTHS(FAM, PSATD_Y_CASE)
 #undef PSATD_Y_CASE

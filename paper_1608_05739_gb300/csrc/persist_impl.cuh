@@ -5,11 +5,14 @@
 
 namespace psatd {
 
+// Opt the kernel in to its dynamic shared memory (always: its static shared
+// memory, the class arguments, adds to the request), and report its occupancy.
 template <typename K>
 static cudaError_t persist_launch(K kern, size_t smem, int grid, cudaStream_t st, int* occ) {
+  (void)grid;
+  (void)st;
   cudaError_t e;
-  if (smem > 48 * 1024 &&
-      (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return e;
   if (occ) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, kPersistThreads, smem);

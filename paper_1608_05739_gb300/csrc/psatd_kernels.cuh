@@ -701,12 +701,33 @@ __device__ __forceinline__ void stag_axis(const PushArgs<R>& a, int ax, int m, R
   w = m < 0 ? wconj(p) : p;
 }
 
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+// Bulk asynchronous copy global -> this CTA's shared memory (16-byte aligned
+// addresses, a multiple of 16 bytes) completing on an mbarrier's transaction count.
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.wait_all;\n" ::: "memory");
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// Error-word bit of an expired wait for the fused pass's staged inputs.
+constexpr int kErrStageWait = 2;
+
+// Staging state of the fused pass: the mbarrier its bulk copies complete on and
+// the parity of that mbarrier's next phase (one phase per line block).
+struct StageCtx {
+  uint32_t mbar;
+  uint32_t phase;
+  int* err;
+};
+// Set up by one thread of the kernel before its first barrier.
+__device__ __forceinline__ void stage_init(StageCtx& sc, uint64_t* mbar_word, int* err) {
+  sc.mbar = smem_u32(mbar_word);
+  sc.phase = 0u;
+  sc.err = err;
+  if (threadIdx.x == 0 && threadIdx.y == 0) mbar_init(sc.mbar, 1);
 }
 
 // The push of the EPT modes l = t + T m of one line, in the slots at positions
@@ -790,7 +811,8 @@ __device__ __forceinline__ void push_line_modes(typename Types<R>::C* st, int ss
 // line g of the block handled by the threads g T .. g T + T - 1, t their position).
 template <typename R, int L, int LAYOUT, int TC, int EPT>
 __device__ __forceinline__ void line_push_body(const PushArgs<R>& a, const typename Types<R>::W* __restrict__ tw,
-                                               int bx, int t, int g, int tb, unsigned char* smem_raw, TcCtx& tc) {
+                                               int bx, int t, int g, int tb, unsigned char* smem_raw, TcCtx& tc,
+                                               StageCtx& sc) {
   typedef typename Types<R>::C C;
   static_assert(!TC || EPT == 16, "tensor-core stages are radix 16");
   typedef FFTPlan<L, EPT> P;
@@ -831,19 +853,38 @@ __device__ __forceinline__ void line_push_body(const PushArgs<R>& a, const typen
     const int l = t + T * m;
     asm volatile("prefetch.global.L2 [%0];" ::"l"(trow + ((l <= L / 2) ? l : L - l)));
   }
-  // stage every input slot of this line (cp.async, 16-byte chunks)
+  // stage every input slot of the block's lines: one bulk copy per line and
+  // slot, issued by one thread, completing on the stage mbarrier; lines past
+  // the last are zero-filled.  The barrier before the issue orders every earlier
+  // access to this shared memory (the previous line block's, in a persistent
+  // CTA) before the copies, the proxy fence the generic stores among them.
   {
-    constexpr int CH = (L * (int)sizeof(C)) / 16;  // chunks per slot
-    for (int c = 0; c < a.n_in; ++c) {
-      const char* src = reinterpret_cast<const char*>(spec + c * a.cs + (int64_t)line * L);
-      char* dst = reinterpret_cast<char*>(st + c * ss);
-      for (int i = t; i < CH; i += T) {
-        if (valid) cp_async16(dst + 16 * i, src + 16 * i);
-        else reinterpret_cast<float4*>(dst)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!valid) {
+      constexpr int CH = (L * (int)sizeof(C)) / 16;  // 16-byte chunks per slot
+      for (int c = 0; c < a.n_in; ++c) {
+        float4* dst = reinterpret_cast<float4*>(st + c * ss);
+        for (int i = t; i < CH; i += T) dst[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
-    cp_async_wait_all();
+    const int line0 = bx * tb;
+    const int nv = a.nlines - line0 < tb ? a.nlines - line0 : tb;  // valid lines of the block
     __syncthreads();
+    if (t == 0 && g == 0) {
+      constexpr uint32_t bytes = (uint32_t)(L * sizeof(C));
+      fence_async_smem();
+      mbar_arrive_expect_tx(sc.mbar, (uint32_t)(nv * a.n_in) * bytes);
+      for (int gl = 0; gl < nv; ++gl)
+        for (int c = 0; c < a.n_in; ++c)
+          bulk_copy_g2s(smem_u32(base + c * ss + gl * L), spec + c * a.cs + (int64_t)(line0 + gl) * L, bytes,
+                        sc.mbar);
+    }
+    // bounded wait; on expiry the error word is set and one more bounded wait
+    // lets copies still in flight land before the buffers are used
+    if (!mbar_wait(sc.mbar, sc.phase, kWaitIters)) {
+      if (sc.err) atomicOr(sc.err, kErrStageWait);
+      mbar_wait(sc.mbar, sc.phase, kWaitIters);
+    }
+    sc.phase ^= 1u;
   }
   C v[EPT];
   for (int c = 0; c < a.n_in; ++c) {
@@ -893,10 +934,14 @@ template <typename R, int L, int LAYOUT, int TC = 0, int EPT = PushEPT<L, TC>::v
 __global__ void __launch_bounds__(FFTPlan<L, EPT>::kT > 256 ? FFTPlan<L, EPT>::kT : 256)
 k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t stage_mbar;
+  StageCtx sc;
+  stage_init(sc, &stage_mbar, a.err ? a.err : a.chk_err);
   TcCtx tc;
-  if constexpr (TC) tc_setup(tc, smem_raw, a.gmat, 0u, a.err, TC == 2, 0u, a.tc_ctl);
+  if constexpr (TC) tc_setup(tc, smem_raw, a.gmat, 0u, a.err, TC == 2, 0u, a.tc_ctl);  // has a block barrier
+  else __syncthreads();  // the stage mbarrier is initialised
   line_push_body<R, L, LAYOUT, TC, EPT>(a, tw, (int)blockIdx.x, (int)threadIdx.x, (int)threadIdx.y, (int)blockDim.y,
-                                        smem_raw, tc);
+                                        smem_raw, tc, sc);
   if constexpr (TC) tc_teardown(tc);
 }
 
