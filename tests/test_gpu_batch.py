@@ -109,7 +109,9 @@ def test_batch_kernel_times_of_a_graph_replay(prec):
         if timed:
             kt = b.kernel_times()
             assert set(kt) == {"fwd_x_r2c", "line_fft_push", "inv_x_c2r"}, kt
-            assert all(v[0] == 3 and v[1] > 0 for v in kt.values()), kt   # three size classes, one step's launches
+            # one step's launches (the last replay's): one per pass in the persistent mode these sizes allow
+            assert all(v[0] >= 1 and v[1] > 0 for v in kt.values()), kt
+            assert sum(v[0] for v in kt.values()) == b.launches_per_step() == 3, kt
             b.set_timing(False)
         b.sync()
         b.destroy()
