@@ -390,9 +390,10 @@ def run_batch_line(args, world, rank, local):
     from paper_1608_05739_gb300 import build as bld
     from paper_1608_05739_gb300 import capi, synth
 
-    sizes, interior = synth.batch_patch_sizes(512, BATCH_SEED, mixed_ok=False)
-    sizes_fp32, _ = synth.batch_patch_sizes(512, BATCH_SEED, mixed_ok=True)
-    requested = synth.batch_requested_cells(512, BATCH_SEED)
+    npatch = args.patches
+    sizes, interior = synth.batch_patch_sizes(npatch, BATCH_SEED, mixed_ok=False)
+    sizes_fp32, _ = synth.batch_patch_sizes(npatch, BATCH_SEED, mixed_ok=True)
+    requested = synth.batch_requested_cells(npatch, BATCH_SEED)
     cells, cells_fp32 = sum(a * b for a, b in sizes), sum(a * b for a, b in sizes_fp32)
     offs = np.concatenate([[0], np.cumsum([a * b for a, b in sizes])]).astype(np.int64)
     offs32 = np.concatenate([[0], np.cumsum([a * b for a, b in sizes_fp32])]).astype(np.int64)
@@ -434,7 +435,7 @@ def run_batch_line(args, world, rank, local):
     # a longer series of the same call with its own clock record (at least ~2 s of steps)
     long_series = None
     n_long = int(math.ceil(2000.0 / (ms / K)))
-    if n_long > K:
+    if n_long > K and not args.no_long_series:
         ms_l, _, clk_l, b_l, _ = time_batch(capi, torch, prec, sizes, J, args, dev, stream, sample_clocks=True,
                                             nsteps=n_long)
         b_l.destroy()
@@ -479,7 +480,7 @@ def run_batch_line(args, world, rank, local):
             "metric": METRIC, "value": value, "unit": "cell-steps/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": t_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[prec], "data": "synthetic",
-            "config": {"workload": BATCH_WORKLOAD, "patches": 512, "precision": PREC_NOTE[prec],
+            "config": {"workload": BATCH_WORKLOAD, "patches": npatch, "precision": PREC_NOTE[prec],
                        "patch_sides": "powers of two (the tensor-core passes' lengths)",
                        "cells": cells, "interior_cells": interior, "requested_domain_cells": requested,
                        "size_classes": len(set(sizes)),
@@ -789,6 +790,9 @@ def main():
     ap.add_argument("--no-comparator", action="store_true", help="skip timing the cuFFT comparator")
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the end-to-end legs (profiling runs: only the timed steps' kernels)")
+    ap.add_argument("--patches", type=int, default=512,
+                    help="batch512: patches of the batch (the first N of the 512-patch recipe; profiling runs)")
+    ap.add_argument("--no-long-series", action="store_true", help="batch512: skip the >= 2 s clock series")
     ap.add_argument("--workload", default="batch512",
                     choices=["batch512", "te2048", "3d256", "3d512", "fdtd-yee", "fdtd-ckc", "local", "cost3d",
                              "small128", "batch512-side"],
