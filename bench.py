@@ -266,7 +266,7 @@ def batch_algorithmic_bytes(sizes):
     return tot
 
 
-def time_batch(capi, torch, prec, sizes, Jhost, args, dev, stream, sample_clocks, nsteps=None):
+def time_batch(capi, torch, prec, sizes, Jhost, args, dev, stream, sample_clocks, nsteps=None, persistent=None):
     """A batch at precision `prec`: W untimed steps (one call: the step graph is
     recorded and replayed), then one psatd_batch_step(nsteps = K) call between
     CUDA events on the batch's stream.  Per-kernel event pairs are recorded in the
@@ -274,6 +274,8 @@ def time_batch(capi, torch, prec, sizes, Jhost, args, dev, stream, sample_clocks
     batch, (Ex, Ey, Bz, Jx, Jy))."""
     K = nsteps or args.steps
     b = capi.Batch(sizes, (BATCH_DX, BATCH_DX), BATCH_DT, layout="te", prec=prec, src="J", stream=stream)
+    if persistent is not None:
+        b.set_persistent(persistent)
     tot = b.total
     Ex, Ey, Bz = (torch.zeros(tot, device=dev) for _ in range(3))
     Jx = torch.from_numpy(Jhost[0]).to(dev)
@@ -441,6 +443,18 @@ def run_batch_line(args, world, rank, local):
         b_l.destroy()
         long_series = {"steps": n_long, "ms_per_step": ms_l / n_long, "value": cells * n_long / (ms_l * 1e-3),
                        "clocks": clk_l}
+    # the same batch and precision with the other launch mode (persistent passes or per-class launches)
+    other = None
+    if not args.no_side_precision:
+        persistent_now = launches_per_step <= 6
+        ms_o, kt_o, _, b_o, F_o = time_batch(capi, torch, prec, sizes, J, args, dev, stream, sample_clocks=False,
+                                             persistent=not persistent_now)
+        lps_o = kt_o.pop("_launches_per_step")[0]
+        b_o.destroy()
+        del F_o
+        other = {"mode": "per-class launches on branch streams" if persistent_now else "persistent passes",
+                 "ms_per_step": ms_o / K, "value": cells * K / (ms_o * 1e-3), "launches_per_step": lps_o,
+                 "per_kernel_ms_summed": {k: v[1] for k, v in kt_o.items()}}
     e2e_a = e2e_b = None
     e2e_steps = max(3, min(K, 20))
     if not args.no_e2e:
@@ -497,6 +511,9 @@ def run_batch_line(args, world, rank, local):
         }
         if long_series:
             line["long_series"] = long_series
+        line["config"]["mode"] = "persistent passes" if launches_per_step <= 6 else "per-class launches"
+        if other is not None:
+            line["other_mode"] = other
         line["vs_plain_fp32"] = {
             "same_patches": {"precision": PREC_NOTE["fp32"], "value": cells * K / (ms32 * 1e-3),
                              "ms_per_step": ms32 / K, "ratio": (cells * K / (ms * 1e-3)) / (cells * K / (ms32 * 1e-3)),

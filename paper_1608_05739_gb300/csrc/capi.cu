@@ -1476,15 +1476,16 @@ void batch_release(psatd_batch b) {
 }
 
 // ---- persistent mode
+// the lengths of the persistent passes' case lists (persist.cuh)
 bool persist_x_len(int L, bool tc) {
-  return (pow2(L) && L >= 32 && L <= 512) || (!tc && three_pow2(L) && L <= 384);
+  return (pow2(L) && L >= 32 && L <= 512) || (!tc && three_pow2(L) && L >= 48 && L <= 384);
 }
 bool persist_y_len(int L, bool tc) {
-  return (pow2(L) && L >= 64 && L <= 1024) || (!tc && three_pow2(L) && L <= 768);
+  return (pow2(L) && L >= 64 && L <= 1024) || (!tc && three_pow2(L) && L >= 48 && L <= 768);
 }
 int fam_of(int L) { return pow2(L) ? 0 : 1; }
 // rows per item of a transposing pass and lines per item of the fused pass
-int persist_x_tb(int L) { return kPersistThreads / (L / row_ept(L)); }
+int persist_x_tb(int L) { return kPersistXThreads / (L / row_ept(L)); }
 int persist_y_tb(int L, bool tc) { return kPersistThreads / (L / (pow2(L) ? (tc ? 16 : 8) : 12)); }
 
 // X-pass arguments of class plan p for the step's field / source pointers (as

@@ -1,6 +1,6 @@
 // persist.cuh -- persistent batch passes: one launch per pass type runs the work
 // of every size class of a batch of 2D patches (the paper's local-FFT subdomains,
-// Sec. II.A.3).  Each CTA of kPersistThreads threads takes work items from a
+// Sec. II.A.3).  Each CTA takes work items from a
 // device queue (an atomic counter, kPersistChunk items per take) until it is
 // empty; an item is one CTA's worth of the standalone pass (a block of rows of
 // one component of one patch, or a block of lines of the fused pass), whose
@@ -13,7 +13,8 @@
 
 namespace psatd {
 
-constexpr int kPersistThreads = 128;
+constexpr int kPersistThreads = 128;   // fused pass: one 128-row MMA group per CTA in the tensor-core variant
+constexpr int kPersistXThreads = 256;  // transposing passes: 8 to 128 rows per item, two MMA groups
 constexpr int kPersistChunk = 4;
 
 // One work item: size class, patch within the class and component (transposing
@@ -74,12 +75,12 @@ __device__ __forceinline__ void copy_to_shared(T* dst, const T* src) {
   else { CASE(48) CASE(96) CASE(192) CASE(384) }
 #define PSATD_PERSIST_Y_LENGTHS(FAM, CASE) \
   if constexpr (FAM == 0) { CASE(64) CASE(128) CASE(256) CASE(512) CASE(1024) } \
-  else { CASE(96) CASE(192) CASE(384) CASE(768) }
+  else { CASE(48) CASE(96) CASE(192) CASE(384) CASE(768) }
 
 template <int L>
 struct PersistRows {
   static constexpr int T = L / RowEPT<L>::value;
-  static constexpr int TB = kPersistThreads / T;
+  static constexpr int TB = kPersistXThreads / T;
   static constexpr int LOG_TB = ilog2(TB);
 };
 
@@ -90,7 +91,7 @@ struct PersistRows {
 // the fused pass 128 (the tensor-core variant is held to two CTAs per SM by
 // its shared memory anyway).
 template <typename R, int TC, int FAM, bool FWD>
-__global__ void __launch_bounds__(kPersistThreads, FAM ? 4 : 8) k_persist_x(const XClassArgs* __restrict__ cls, PersistQueue q) {
+__global__ void __launch_bounds__(kPersistXThreads, FAM ? 2 : 4) k_persist_x(const XClassArgs* __restrict__ cls, PersistQueue q) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int slot;
   __shared__ __align__(16) XClassArgs A;
@@ -106,8 +107,10 @@ __global__ void __launch_bounds__(kPersistThreads, FAM ? 4 : 8) k_persist_x(cons
       copy_to_shared(&A, &cls[it.cls]);
       __syncthreads();
       typedef typename Types<R>::W W;
+      bool matched = false;
 #define PSATD_X_CASE(LL)                                                                                        \
   if (A.L == LL) {                                                                                              \
+    matched = true;                                                                                             \
     typedef PersistRows<LL> G;                                                                                  \
     const RowCta cta{it.blk, it.a0, it.a1, (int)threadIdx.x % G::T, (int)threadIdx.x / G::T, G::LOG_TB, A.nb}; \
     if constexpr (FWD)                                                                                          \
@@ -119,6 +122,8 @@ __global__ void __launch_bounds__(kPersistThreads, FAM ? 4 : 8) k_persist_x(cons
   }
       PSATD_PERSIST_X_LENGTHS(FAM, PSATD_X_CASE)
 #undef PSATD_X_CASE
+      // a length without a case (the host admits none) is reported, not skipped silently
+      if (!matched && threadIdx.x == 0 && A.io.chk_err) atomicOr(A.io.chk_err, kErrBounds);
     }
   }
   persist_finish(q);
@@ -133,7 +138,6 @@ __global__ void __launch_bounds__(kPersistThreads, 4) k_persist_push(const PushA
                                                                   PersistQueue q) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int slot;
-  __shared__ __align__(16) PushArgs<R> A;
   __shared__ __align__(8) uint64_t stage_mbar;
   StageCtx sc;
   stage_init(sc, &stage_mbar, cls[0].err ? cls[0].err : cls[0].chk_err);
@@ -147,13 +151,13 @@ __global__ void __launch_bounds__(kPersistThreads, 4) k_persist_push(const PushA
     const int i1 = i0 + kPersistChunk < q.n_items ? i0 + kPersistChunk : q.n_items;
     for (int i = i0; i < i1; ++i) {
       const BatchItem it = q.items[i];
-      __syncthreads();
-      copy_to_shared(&A, &cls[it.cls]);
-      __syncthreads();
+      const PushArgs<R>& A = cls[it.cls];
       const int Lc = 2 * (A.tab_row - 1);
       typedef typename Types<R>::W W;
+      bool matched = false;
 #define PSATD_Y_CASE(LL)                                                                                   \
   if (Lc == LL) {                                                                                          \
+    matched = true;                                                                                        \
     constexpr int T = LL / EPT;                                                                            \
     line_push_body<R, LL, LAYOUT, TC, EPT>(A, static_cast<const W*>(tws[it.cls]), it.blk,                 \
                                            (int)threadIdx.x % T, (int)threadIdx.x / T, kPersistThreads / T, \
@@ -161,6 +165,7 @@ __global__ void __launch_bounds__(kPersistThreads, 4) k_persist_push(const PushA
   }
       PSATD_PERSIST_Y_LENGTHS(FAM, PSATD_Y_CASE)
 #undef PSATD_Y_CASE
+      if (!matched && threadIdx.x == 0 && A.chk_err) atomicOr(A.chk_err, kErrBounds);
     }
   }
   persist_finish(q);
@@ -172,8 +177,8 @@ __global__ void __launch_bounds__(kPersistThreads, 4) k_persist_push(const PushA
 template <typename R, int TC, int FAM>
 constexpr size_t persist_x_smem() {
   // TB lines of L values, plus split-BF16's third A piece (one per 128 threads)
-  return (TC ? kTcTail : 0) + (size_t)kPersistThreads * (FAM ? 24 : 16) * sizeof(typename Types<R>::C) +
-         (TC == 2 ? TcGeom<16>::kAPiece : 0);
+  return (TC ? kTcTail : 0) + (size_t)kPersistXThreads * (FAM ? 24 : 16) * sizeof(typename Types<R>::C) +
+         (TC == 2 ? (kPersistXThreads / 128) * TcGeom<16>::kAPiece : 0);
 }
 template <typename R, int TC, int FAM>
 constexpr size_t persist_push_smem(int n_in) {

@@ -8,14 +8,12 @@ namespace psatd {
 // Opt the kernel in to its dynamic shared memory (always: its static shared
 // memory, the class arguments, adds to the request), and report its occupancy.
 template <typename K>
-static cudaError_t persist_launch(K kern, size_t smem, int grid, cudaStream_t st, int* occ) {
-  (void)grid;
-  (void)st;
+static cudaError_t persist_launch(K kern, int threads, size_t smem, int* occ) {
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
     return e;
   if (occ) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, kPersistThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, threads, smem);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -26,9 +24,9 @@ cudaError_t launch_persist_x(bool fwd, int grid, cudaStream_t st, const XClassAr
                              int* occ) {
   const size_t smem = persist_x_smem<R, TC, FAM>();
   auto kern = fwd ? k_persist_x<R, TC, FAM, true> : k_persist_x<R, TC, FAM, false>;
-  cudaError_t e = persist_launch(kern, smem, grid, st, occ);
+  cudaError_t e = persist_launch(kern, kPersistXThreads, smem, occ);
   if (e != cudaSuccess || grid <= 0) return e;
-  kern<<<grid, kPersistThreads, smem, st>>>(cls, q);
+  kern<<<grid, kPersistXThreads, smem, st>>>(cls, q);
   return cudaGetLastError();
 }
 
@@ -43,7 +41,7 @@ cudaError_t launch_persist_push(int layout, int n_in, int grid, cudaStream_t st,
     case 3: kern = k_persist_push<R, TC, FAM, 3>; break;
     default: return cudaErrorInvalidValue;
   }
-  cudaError_t e = persist_launch(kern, smem, grid, st, occ);
+  cudaError_t e = persist_launch(kern, kPersistThreads, smem, occ);
   if (e != cudaSuccess || grid <= 0) return e;
   kern<<<grid, kPersistThreads, smem, st>>>(cls, tws, q);
   return cudaGetLastError();

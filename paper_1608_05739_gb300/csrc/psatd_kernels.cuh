@@ -110,6 +110,13 @@ __global__ void k_nonfinite(NfPtrs ptrs, const int64_t* __restrict__ off, int64_
 template <typename R, int L>
 struct RowThreads { static constexpr int value = RowEPT<L>::value == 24 ? 256 : sizeof(R) == 4 ? 512 : 256; };
 
+// XOR mask of row r's buffer in the transposed stores and reads (TB = 1 << log_tb
+// rows): rows spread over the 16 eight-byte bank pairs (at most 16 rows: one row
+// per pair; more: two or more rows per pair); it stays inside the line for L < 16.
+__device__ __forceinline__ int row_xor(int r, int log_tb, int L) {
+  return (log_tb <= 4 ? r * (16 >> log_tb) : r) & 15 & (L - 1);
+}
+
 // ---------------------------------------------------------------- pass 1 / 2
 // Forward FFT along the contiguous axis of TB consecutive lines b, written out
 // with b contiguous: out[a1] + a0*out_sa0 + k*out_sk + b.  R2C: the input rows
@@ -186,7 +193,7 @@ __device__ __forceinline__ void fwd_T_body(const LineIO& io, const typename Type
     // (XOR-ed by a row-dependent mask so that the column-wise reads hit distinct banks),
     // then each thread produces whole output elements (k, row) and stores them.
     C* zb = ex.next();
-    const int xg = (g * (16 >> log_tb)) & 15 & (L - 1);  // stays inside the line for L < 16
+    const int xg = row_xor(g, log_tb, L);  // stays inside the line for L < 16
 #pragma unroll
     for (int m = 0; m < EPT; ++m) zb[(t + T * m) ^ xg] = v[m];
     __syncthreads();
@@ -196,7 +203,7 @@ __device__ __forceinline__ void fwd_T_body(const LineIO& io, const typename Type
     const int tid = g * T + t;
     const int gg = tid & (TB - 1);
     const int k0 = tid >> log_tb;  // in [0, T)
-    const int xgg = (gg * (16 >> log_tb)) & 15 & (L - 1);
+    const int xgg = row_xor(gg, log_tb, L);
     const C* zr = smem + gg * L;
     C* o = static_cast<C*>(io.out[a1]) + a0 * out_sa0 + b0 + (int64_t)k0 * out_sk + gg;
     const int64_t ostep = (int64_t)T * out_sk;
@@ -302,7 +309,7 @@ __device__ __forceinline__ void inv_T_body(const LineIO& io, const typename Type
     const int tid = g * T + t;
     const int gg = tid & (TB - 1);
     const int p0 = tid >> log_tb;  // in [0, T)
-    const int xgg = (gg * (16 >> log_tb)) & 15 & (L - 1);
+    const int xgg = row_xor(gg, log_tb, L);
     C* zr = smem + gg * L;
     const bool gvalid = !PART || gg < rows;
     const C* ib = static_cast<const C*>(io.in[a1]) + a0 * in_sa0 + b0 + gg;
@@ -337,7 +344,7 @@ __device__ __forceinline__ void inv_T_body(const LineIO& io, const typename Type
       zr[(L / 2) ^ xgg] = cadd(fe, cmul_pi(fo));
     }
     __syncthreads();
-    const int xg = (g * (16 >> log_tb)) & 15 & (L - 1);
+    const int xg = row_xor(g, log_tb, L);
     const C* zb = smem + g * L;
 #pragma unroll
     for (int m = 0; m < EPT; ++m) v[m] = zb[(t + T * m) ^ xg];
@@ -810,9 +817,11 @@ __device__ __forceinline__ void push_line_modes(typename Types<R>::C* st, int ss
 // Body of one CTA of the fused pass: line block bx (lines bx tb .. bx tb + tb - 1,
 // line g of the block handled by the threads g T .. g T + T - 1, t their position).
 template <typename R, int L, int LAYOUT, int TC, int EPT>
-__device__ __forceinline__ void line_push_body(const PushArgs<R>& a, const typename Types<R>::W* __restrict__ tw,
+__device__ __forceinline__ void line_push_body(const PushArgs<R>& a_in, const typename Types<R>::W* __restrict__ tw,
                                                int bx, int t, int g, int tb, unsigned char* smem_raw, TcCtx& tc,
                                                StageCtx& sc) {
+  // a private copy: its scalars stay in registers through the shared-memory stores of the transforms
+  const PushArgs<R> a = a_in;
   typedef typename Types<R>::C C;
   static_assert(!TC || EPT == 16, "tensor-core stages are radix 16");
   typedef FFTPlan<L, EPT> P;
