@@ -319,18 +319,19 @@ int64_t psatd_batch_cells(psatd_batch batch);
  * or PSATD_ERR_NONFINITE (PSATD_FLAG_CHECKED) since the last sync. */
 psatd_status psatd_batch_sync(psatd_batch batch);
 
-/* Persistent passes (the default where they apply).  When every patch's line
- * lengths allow it (FP32 or a mixed precision; x lines n[2i]/2 of 32..512
- * points, or 48..384 = 3 * 2^k in FP32; last-axis lines n[2i+1] of 64..1024, or
- * 96..768 = 3 * 2^k in FP32), a step is one launch per pass type (x forward,
- * fused y pass, x inverse) and per length family (powers of two, 3 * 2^k): the
- * CTAs of each launch stay resident and take the work of every patch from a
- * device queue (an atomic counter; the last CTA to finish resets it), so the
- * passes run in stream order with no wait inside a kernel.  Otherwise each step
- * is one launch per pass and size class on the branch streams described above.
- * psatd_batch_set_persistent(batch, 0) selects the per-class launches, 1 the
- * persistent ones (UNSUPPORTED when the sizes do not allow them); results are
- * the same bits either way.  psatd_batch_launches_per_step: kernel launches of
+/* Persistent passes (selectable; per-class launches are the default).  When
+ * every patch's line lengths allow it (FP32 or a mixed precision; x lines
+ * n[2i]/2 of 32..512 points, or 48..384 = 3 * 2^k in FP32; last-axis lines
+ * n[2i+1] of 64..1024, or 48..768 = 3 * 2^k in FP32), psatd_batch_set_persistent
+ * (batch, 1) makes a step one launch per pass type (x forward, fused y pass, x
+ * inverse) and per length family (powers of two, 3 * 2^k): the CTAs of each
+ * launch stay resident and take the work of every patch from a device queue (an
+ * atomic counter; the last CTA to finish resets it), so the passes run in stream
+ * order with no wait inside a kernel.  psatd_batch_set_persistent(batch, 0)
+ * returns to one launch per pass and size class on the branch streams described
+ * above, which keeps a class's spectra in L2 between its passes and measured
+ * faster; UNSUPPORTED when the sizes do not allow the persistent passes.  The
+ * results are the same bits either way.  psatd_batch_launches_per_step: kernel launches of
  * one step in the current mode (without PSATD_FLAG_CHECKED's scans).  The
  * first step after the field or source pointers change uploads the classes'
  * argument tables (a synchronising copy, outside any graph capture). */

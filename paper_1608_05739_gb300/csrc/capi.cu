@@ -1622,7 +1622,10 @@ psatd_status persist_setup(psatd_batch b) {
     const int chunks = (q.n + kPersistChunk - 1) / kPersistChunk;
     q.grid = std::max(1, std::min(chunks, std::max(occ, 1) * nsm));
   }
-  b->persist = true;
+  // not the default: measured slower on the 512-patch workload (split-BF16 9.39 against 5.73 ms per
+  // step, FP32 2.74 against 2.69), as a pass over the whole batch streams every class's spectra
+  // through HBM where per-class launches run a class's three passes while its spectra are in L2
+  b->persist = false;
   return PSATD_OK;
 }
 

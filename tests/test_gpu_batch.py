@@ -84,8 +84,9 @@ def test_batch_graph_replay_equals_single_calls():
     assert rel_l2_fields(_patch(E1, 4), _patch(B1, 4), mask_layout(Eo, "te", "E"), mask_layout(Bo, "te", "B")) < 1e-5
 
 
-@pytest.mark.parametrize("prec", ["fp32", "mixed_bf16"])
-def test_batch_kernel_times_of_a_graph_replay(prec):
+@pytest.mark.parametrize("prec,persistent", [("fp32", False), ("fp32", True), ("mixed_bf16", False),
+                                             ("mixed_bf16", True)])
+def test_batch_kernel_times_of_a_graph_replay(prec, persistent):
     """Batch timing with a multi-step call: the event pairs are recorded inside the
     step graph, each replay times the launches again, and the results stay those of
     an untimed run (bitwise)."""
@@ -101,6 +102,7 @@ def test_batch_kernel_times_of_a_graph_replay(prec):
         stream = torch.cuda.Stream()
         torch.cuda.synchronize()
         b = capi.Batch(sizes, (1.0, 1.0), 0.5, layout="te", prec=prec, src="J", stream=stream)
+        b.set_persistent(persistent)
         if timed:
             b.set_timing(True)
         with torch.cuda.stream(stream):
@@ -109,9 +111,9 @@ def test_batch_kernel_times_of_a_graph_replay(prec):
         if timed:
             kt = b.kernel_times()
             assert set(kt) == {"fwd_x_r2c", "line_fft_push", "inv_x_c2r"}, kt
-            # one step's launches (the last replay's): one per pass in the persistent mode these sizes allow
+            # one step's launches (the last replay's): one per pass and class, or one per pass (persistent)
             assert all(v[0] >= 1 and v[1] > 0 for v in kt.values()), kt
-            assert sum(v[0] for v in kt.values()) == b.launches_per_step() == 3, kt
+            assert sum(v[0] for v in kt.values()) == b.launches_per_step() == (3 if persistent else 9), kt
             b.set_timing(False)
         b.sync()
         b.destroy()
@@ -152,10 +154,12 @@ def test_persistent_passes_equal_per_class_launches(prec, layout):
         stream = torch.cuda.Stream()
         torch.cuda.synchronize()
         b = capi.Batch(sizes, (1.0, 1.0), 0.5, layout=layout, prec=prec, src="J", stream=stream)
-        fams_x = len({(nx // 2) & (nx // 2 - 1) == 0 for nx, _ in sizes})
-        fams_y = len({ny & (ny - 1) == 0 for _, ny in sizes})
-        assert b.launches_per_step() == 2 * fams_x + fams_y      # persistent by default
+        assert b.launches_per_step() == 3 * len(set(sizes))      # per-class launches by default
         b.set_persistent(persistent)
+        if persistent:
+            fams_x = len({(nx // 2) & (nx // 2 - 1) == 0 for nx, _ in sizes})
+            fams_y = len({ny & (ny - 1) == 0 for _, ny in sizes})
+            assert b.launches_per_step() == 2 * fams_x + fams_y
         with torch.cuda.stream(stream):
             b.step(E, B, J, nsteps=3)
         b.sync()
