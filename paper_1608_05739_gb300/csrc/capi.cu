@@ -94,6 +94,8 @@ psatd_status cuda_fail(psatd_plan p, cudaError_t e, const char* what) {
 bool pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 // 3 * 2^k with k >= 4: the mixed-radix lengths of the FP32 passes (radix-3 first stage)
 bool three_pow2(int64_t v) { return v >= 48 && v % 3 == 0 && pow2(v / 3); }
+// 5 * 2^k with k >= 4: the radix-5 lengths of the FP32 passes
+bool five_pow2(int64_t v) { return v >= 80 && v % 5 == 0 && pow2(v / 5); }
 bool pos_finite(double v) { return std::isfinite(v) && v > 0; }
 
 int layout_ndim(int layout) { return layout == PSATD_FIELDS_3D6 ? 3 : 2; }
@@ -153,14 +155,17 @@ psatd_status validate_desc(psatd_plan p, const psatd_desc* d, bool psatd_limits)
     if (d->n[i] < 2) return fail(p, PSATD_ERR_INVALID_ARG, "n[%d] = %lld too small", i, (long long)d->n[i]);
   if (psatd_limits) {
     // x is transformed as a complex line of nx/2 points, y and z as lines of n points:
-    // powers of two, or 3 * 2^k (FP32 only) from 48 to 3072 points per line
+    // powers of two, or (FP32 only) 3 * 2^k from 48 to 3072 or 5 * 2^k from 80 to 1280 points per line
     const bool mixed_ok = d->prec == PSATD_FP32;
     for (int i = 0; i < nd; ++i) {
       const int64_t L = i == 0 ? d->n[0] / 2 : d->n[i];
       const bool ok = (i > 0 || d->n[0] % 2 == 0) &&
-                      ((pow2(L) && L >= 8 && d->n[i] <= 4096) || (mixed_ok && three_pow2(L) && d->n[i] <= 3072));
+                      ((pow2(L) && L >= 8 && d->n[i] <= 4096) || (mixed_ok && three_pow2(L) && d->n[i] <= 3072) ||
+                       (mixed_ok && five_pow2(L) && L <= 1280));
       if (!ok) {
-        const char* alt = !mixed_ok ? "" : i == 0 ? " or 6 * 2^k in [96, 3072]" : " or 3 * 2^k in [48, 3072]";
+        const char* alt = !mixed_ok ? ""
+                          : i == 0 ? ", 6 * 2^k in [96, 3072] or 10 * 2^k in [160, 2560]"
+                                   : ", 3 * 2^k in [48, 3072] or 5 * 2^k in [80, 1280]";
         return fail(p, PSATD_ERR_UNSUPPORTED, "n[%d] must be a power of two in [%d, 4096]%s", i, i == 0 ? 16 : 8, alt);
       }
     }
@@ -267,7 +272,7 @@ psatd_status alloc(psatd_plan p, void** ptr, size_t bytes, const char* what) {
 }
 
 // threads per CTA a transposing pass may launch (the kernels' launch bounds)
-int row_maxthr(int L, bool f32) { return row_ept(L) == 24 || !f32 ? 256 : 512; }
+int row_maxthr(int L, bool f32) { return row_ept(L) >= 20 || !f32 ? 256 : 512; }
 // lines per CTA for a transposing pass of length L over `nb` lines (a divisor
 // of nb; at most 16 lines: the row-dependent XOR of the transposed store
 // spreads 16 lines over the banks, 32 would read one bank twice; the
@@ -376,16 +381,20 @@ template <typename R, int TC>
 cudaError_t fwd_T_any(int L, bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io, const void* tw,
                       int64_t in_sa0, int64_t in_sb, int64_t out_sa0, int64_t out_sk, const int64_t* a0_off = nullptr) {
   if (pow2(L)) return launch_fwd_T<R, TC>(L, r2c, g, st, io, tw, in_sa0, in_sb, out_sa0, out_sk, a0_off);
-  if constexpr (std::is_same<R, float>::value && TC == 0)
-    return launch_fwd_T3<R>(L, r2c, g, st, io, tw, in_sa0, in_sb, out_sa0, out_sk, a0_off);
+  if constexpr (std::is_same<R, float>::value && TC == 0) {
+    if (three_pow2(L)) return launch_fwd_T3<R>(L, r2c, g, st, io, tw, in_sa0, in_sb, out_sa0, out_sk, a0_off);
+    return launch_fwd_T5<R>(L, r2c, g, st, io, tw, in_sa0, in_sb, out_sa0, out_sk, a0_off);
+  }
   return cudaErrorInvalidValue;
 }
 template <typename R, int TC>
 cudaError_t inv_T_any(int L, bool c2r, const PassGeom& g, cudaStream_t st, const LineIO& io, const void* tw,
                       int64_t in_sa0, int64_t in_sk, int64_t out_sa0, int64_t out_sb, const int64_t* a0_off = nullptr) {
   if (pow2(L)) return launch_inv_T<R, TC>(L, c2r, g, st, io, tw, in_sa0, in_sk, out_sa0, out_sb, a0_off);
-  if constexpr (std::is_same<R, float>::value && TC == 0)
-    return launch_inv_T3<R>(L, c2r, g, st, io, tw, in_sa0, in_sk, out_sa0, out_sb, a0_off);
+  if constexpr (std::is_same<R, float>::value && TC == 0) {
+    if (three_pow2(L)) return launch_inv_T3<R>(L, c2r, g, st, io, tw, in_sa0, in_sk, out_sa0, out_sb, a0_off);
+    return launch_inv_T5<R>(L, c2r, g, st, io, tw, in_sa0, in_sk, out_sa0, out_sb, a0_off);
+  }
   return cudaErrorInvalidValue;
 }
 
@@ -512,9 +521,10 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
       const size_t per_line = ((size_t)p->n_in + 1) * (size_t)Lline * csz;  // split-BF16's third piece: in a slot
       const dim3 grid((unsigned)((nlines + tb - 1) / tb));
       TimedLaunch tl(p, K_PUSH);
-      if (p->push_ept == 12) {
+      if (p->push_ept == 12 || p->push_ept == 20) {
         if constexpr (std::is_same<R, float>::value && TC == 0)
-          e = launch_line_push3<R>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl);
+          e = p->push_ept == 12 ? launch_line_push3<R>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl)
+                                : launch_line_push5<R>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl);
         else
           e = cudaErrorInvalidValue;
       } else if (p->push_ept == 16) {
@@ -678,8 +688,10 @@ TuneSpace tune_space(psatd_plan p) {
       ts.rows[k].push_back(lg);
     }
   }
-  for (int ept : {8, 16, 12}) {
-    if ((p->tc && ept != 16) || ts.Ll < ept || (ept == 12) == pow2(ts.Ll)) continue;
+  for (int ept : {8, 16, 12, 20}) {
+    // powers of two: radix-8 or radix-16 stages (tensor cores: 16); 3 * 2^k: 12; 5 * 2^k: 20
+    const bool allowed = pow2(ts.Ll) ? (ept == 8 || ept == 16) && (!p->tc || ept == 16) : ept == push_ept(ts.Ll);
+    if (!allowed || ts.Ll < ept) continue;
     const int T = ts.Ll / ept;
     const size_t per_line = ((size_t)p->n_in + 1) * (size_t)ts.Ll * csz;
     for (int tb = 1; tb * T <= (T > 256 ? T : 256); tb *= 2) {
@@ -1017,8 +1029,8 @@ psatd_status psatd_plan_set_launch(psatd_plan p, const int32_t cfg[6]) {
     c.log_tb[k] = cfg[k];
   }
   if (cfg[5] >= 0) {
-    if (cfg[5] != 8 && cfg[5] != 16 && cfg[5] != 12)
-      return fail(p, PSATD_ERR_INVALID_ARG, "cfg[5] must be 8, 16, 12 or -1");
+    if (cfg[5] != 8 && cfg[5] != 16 && cfg[5] != 12 && cfg[5] != 20)
+      return fail(p, PSATD_ERR_INVALID_ARG, "cfg[5] must be 8, 16, 12, 20 or -1");
     c.push_ept = cfg[5];
   }
   bool ok = false;

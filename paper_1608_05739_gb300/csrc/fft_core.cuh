@@ -3,9 +3,10 @@
 // A length-L transform is computed by T = L/EPT threads; thread t holds the EPT
 // elements x[t + T*m], m < EPT, in registers before and after the transform
 // (natural order in both domains).  Lengths: powers of two 8..4096 with 8 or
-// 16 elements per thread (a radix-2/4/8 first stage, then radix-EPT stages), or
+// 16 elements per thread (a radix-2/4/8 first stage, then radix-EPT stages),
 // 3 * 2^k, 48..3072, with 24 (radix 3, then 2/4, then 8) or 12 (prime-factor
-// radix 12, then 2, then 4) -- FFTPlan below.  Between stages the data go
+// radix 12, then 2, then 4), or 5 * 2^k, 80..1280, with 20 (radix 5, then 2,
+// then 4) -- FFTPlan below.  Between stages the data go
 // through shared memory in rows of 16 elements whose columns are XOR-swizzled
 // per exchange (free of bank conflicts for each stage's write pattern).
 //
@@ -243,6 +244,40 @@ __device__ __forceinline__ void dft3(C& a0, C& a1, C& a2) {
   a2 = csub(m, s);
 }
 
+// Radix-5 DFT in place.  With t1 = a1 + a4, t2 = a2 + a3, t3 = a1 - a4,
+// t4 = a2 - a3 and c_j = cos(2 pi j/5), s_j = sin(2 pi j/5):
+//   X0 = a0 + t1 + t2,  m1 = a0 + c1 t1 + c2 t2,  m2 = a0 + c2 t1 + c1 t2,
+//   n1 = s1 t3 + s2 t4,  n2 = s2 t3 - s1 t4,
+//   forward (W = exp(-2 pi i/5)): X1,4 = m1 -+ i n1, X2,3 = m2 -+ i n2;
+//   adjoint (the conjugate constants): X1,4 = m1 +- i n1, X2,3 = m2 +- i n2.
+// The four constants multiply as hi + lo pairs in float.
+constexpr double kC51 = 0.30901699437494742410;   // cos(2 pi/5)
+constexpr double kC52 = -0.80901699437494742410;  // cos(4 pi/5)
+constexpr double kS51 = 0.95105651629515357212;   // sin(2 pi/5)
+constexpr double kS52 = 0.58778525229247312917;   // sin(4 pi/5)
+template <int K> __device__ __forceinline__ float k5_mul(float v) {
+  constexpr double c = K == 0 ? kC51 : K == 1 ? kC52 : K == 2 ? kS51 : kS52;
+  constexpr float h = (float)c, l = (float)(c - (double)(float)c);
+  return fmaf(v, h, v * l);
+}
+template <int K> __device__ __forceinline__ double k5_mul(double v) {
+  return v * (K == 0 ? kC51 : K == 1 ? kC52 : K == 2 ? kS51 : kS52);
+}
+template <bool ADJ, class C>
+__device__ __forceinline__ void dft5(C* a) {
+  const C t1 = cadd(a[1], a[4]), t2 = cadd(a[2], a[3]), t3 = csub(a[1], a[4]), t4 = csub(a[2], a[3]);
+  const C m1 = mkc(a[0].x + k5_mul<0>(t1.x) + k5_mul<1>(t2.x), a[0].y + k5_mul<0>(t1.y) + k5_mul<1>(t2.y));
+  const C m2 = mkc(a[0].x + k5_mul<1>(t1.x) + k5_mul<0>(t2.x), a[0].y + k5_mul<1>(t1.y) + k5_mul<0>(t2.y));
+  const C n1 = mkc(k5_mul<2>(t3.x) + k5_mul<3>(t4.x), k5_mul<2>(t3.y) + k5_mul<3>(t4.y));
+  const C n2 = mkc(k5_mul<3>(t3.x) - k5_mul<2>(t4.x), k5_mul<3>(t3.y) - k5_mul<2>(t4.y));
+  const C in1 = ADJ ? cmul_pi(n1) : cmul_mi(n1), in2 = ADJ ? cmul_pi(n2) : cmul_mi(n2);
+  a[0] = cadd(a[0], cadd(t1, t2));
+  a[1] = cadd(m1, in1);
+  a[4] = csub(m1, in1);
+  a[2] = cadd(m2, in2);
+  a[3] = csub(m2, in2);
+}
+
 // Radix-12 DFT in place, natural order in and out, as the prime-factor
 // (Good-Thomas) split 12 = 3 x 4: with n = (4 n1 + 3 n2) mod 12 and
 // k = (4 k1 + 9 k2) mod 12, W12^(n k) = W3^(n1 k1) W4^(n2 k2), so radix-3 DFTs
@@ -294,6 +329,8 @@ template <int RS, bool ADJ, class C>
 __device__ __forceinline__ void butterfly(C* a) {
   if constexpr (RS == 3) {
     dft3<ADJ>(a[0], a[1], a[2]);
+  } else if constexpr (RS == 5) {
+    dft5<ADJ>(a);
   } else if constexpr (RS == 12) {
     dft12<ADJ>(a);
   } else if constexpr (RS == 2) {
@@ -319,29 +356,34 @@ __host__ __device__ constexpr bool is_pow2(int v) { return v > 0 && (v & (v - 1)
 // Lengths 3 * 2^k (k >= 4) are mixed-radix: 24 elements per thread in the
 // transposing passes, 12 in the fused pass (whose shared memory per line is
 // fixed, so that fewer elements per thread keep more threads on an SM).
+// Lengths 5 * 2^k (k >= 4): 20 elements per thread in every pass.
+__host__ __device__ constexpr int odd_factor(int v) { return is_pow2(v) ? 1 : (v % 3 == 0 ? 3 : 5); }
 template <int L>
-struct RowEPT { static constexpr int value = !is_pow2(L) ? 24 : L >= 16 ? 16 : 8; };
+struct RowEPT { static constexpr int value = odd_factor(L) == 3 ? 24 : odd_factor(L) == 5 ? 20 : L >= 16 ? 16 : 8; };
 // The fused pass keeps 8 elements per thread: with 16 a 2048-point line has
 // half the threads and, its shared memory being fixed per line, the SM half
 // the warps (measured slower).  The tensor-core variant (TC) takes 16, so that
 // its stages are radix-16 DFT-matrix contractions.
 template <int L, int TC = 0>
-struct PushEPT { static constexpr int value = !is_pow2(L) ? 12 : TC ? 16 : 8; };
+struct PushEPT { static constexpr int value = odd_factor(L) == 3 ? 12 : odd_factor(L) == 5 ? 20 : TC ? 16 : 8; };
 
 // Power-of-two L: a radix-2/4/8 first stage when log2 L is not a multiple of
 // log2 EPT, then radix-EPT stages.  Mixed L = 3 * 2^k: with EPT = 24 a radix-3
 // first stage, a radix-2 or radix-4 stage when k is not a multiple of 3, then
 // radix-8 stages; with EPT = 12 a radix-12 first stage (prime-factor 3 x 4),
-// a radix-2 stage when k is odd, then radix-4 stages.  Every radix divides EPT.
+// a radix-2 stage when k is odd, then radix-4 stages.  Mixed L = 5 * 2^k
+// (EPT = 20): a radix-5 first stage, a radix-2 stage when k is odd, then
+// radix-4 stages.  Every radix divides EPT.
 template <int L, int EPT = 8>
 struct FFTPlan {
   static constexpr int kEPT = EPT;
-  static constexpr bool kMixed = !is_pow2(L);
-  static constexpr int kLog = kMixed ? ilog2(L / 3) : ilog2(L);  // log2 of the power-of-two part
-  static constexpr int kHeadLog = (kMixed && EPT == 12) ? 2 : 0;  // power of two taken by the first stage
-  static constexpr int kB = kMixed ? (EPT == 12 ? 2 : 3) : ilog2(EPT);
+  static constexpr int kF = odd_factor(L);  // 1, 3 or 5
+  static constexpr bool kMixed = kF > 1;
+  static constexpr int kLog = ilog2(L / kF);  // log2 of the power-of-two part
+  static constexpr int kHeadLog = (kF == 3 && EPT == 12) ? 2 : 0;  // power of two taken by the first stage
+  static constexpr int kB = kF == 5 ? 2 : kMixed ? (EPT == 12 ? 2 : 3) : ilog2(EPT);
   static constexpr int kRem = (kLog - kHeadLog) % kB;
-  static constexpr int kR0 = kMixed ? 3 << kHeadLog : kRem ? (1 << kRem) : EPT;
+  static constexpr int kR0 = kMixed ? kF << kHeadLog : kRem ? (1 << kRem) : EPT;
   static constexpr int kStages = kMixed ? 1 + (kRem ? 1 : 0) + (kLog - kHeadLog) / kB
                                         : kRem ? kLog / kB + 1 : kLog / kB;
   static constexpr int kT = L / EPT;
@@ -371,9 +413,10 @@ struct FFTPlan {
   // swizzle of the last exchange: forward output / inverse input positions
   // sw<kLastCX>(t + T m) are each touched by their own thread only
   static constexpr int kLastCX = (kStages >= 2) ? swz(kStages - 2) : 0;
-  static_assert(kMixed ? (L == 3 * (1 << kLog) && (EPT == 24 || EPT == 12) && kLog >= 4)
-                       : (L >= EPT && EPT != 24 && EPT != 12),
-                "L must be a power of two >= EPT, or 3 * 2^k (k >= 4) with EPT = 12 or 24");
+  static_assert(kF == 3   ? (L == 3 * (1 << kLog) && (EPT == 24 || EPT == 12) && kLog >= 4)
+                : kF == 5 ? (L == 5 * (1 << kLog) && EPT == 20 && kLog >= 4)
+                          : (L >= EPT && EPT != 24 && EPT != 12 && EPT != 20),
+                "L must be a power of two >= EPT, 3 * 2^k (k >= 4) with EPT = 12 or 24, or 5 * 2^k with EPT 20");
 };
 
 // element i of an exchange buffer, rows of 16 elements (128 B) XOR-swizzled

@@ -46,6 +46,19 @@ template <typename R>
 cudaError_t launch_line_push3(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
                               const PushArgs<R>& a, const void* tw);
 
+// the same passes for the mixed lengths L = 5 * 2^k (80..1280), float only
+template <typename R>
+cudaError_t launch_fwd_T5(int L, bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io, const void* tw,
+                          int64_t in_sa0, int64_t in_sb, int64_t out_sa0, int64_t out_sk,
+                          const int64_t* a0_off = nullptr);
+template <typename R>
+cudaError_t launch_inv_T5(int L, bool c2r, const PassGeom& g, cudaStream_t st, const LineIO& io, const void* tw,
+                          int64_t in_sa0, int64_t in_sk, int64_t out_sa0, int64_t out_sb,
+                          const int64_t* a0_off = nullptr);
+template <typename R>
+cudaError_t launch_line_push5(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
+                              const PushArgs<R>& a, const void* tw);
+
 // Persistent batch passes (persist.cuh): FAM 0 power-of-two lengths, 1 the 3 * 2^k
 // lengths (float, TC = 0).  `grid` CTAs of kPersistThreads threads; *occ (if not
 // NULL) receives the CTAs per SM the kernel can keep resident.

@@ -118,6 +118,40 @@ static cudaError_t push_L(int layout, dim3 grid, int tb, size_t smem, cudaStream
     default: return cudaErrorInvalidValue;               \
   }
 
+// Mixed lengths 5 * 2^k (FP32, no tensor-core stages).
+#define PSATD_L5_SWITCH(FN, ...)                         \
+  switch (L) {                                           \
+    case 80: return FN<R, 0, 80>(__VA_ARGS__);           \
+    case 160: return FN<R, 0, 160>(__VA_ARGS__);         \
+    case 320: return FN<R, 0, 320>(__VA_ARGS__);         \
+    case 640: return FN<R, 0, 640>(__VA_ARGS__);         \
+    case 1280: return FN<R, 0, 1280>(__VA_ARGS__);       \
+    default: return cudaErrorInvalidValue;               \
+  }
+
+template <typename R>
+cudaError_t launch_fwd_T5(int L, bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io, const void* tw,
+                          int64_t in_sa0, int64_t in_sb, int64_t out_sa0, int64_t out_sk, const int64_t* a0_off) {
+  PSATD_L5_SWITCH(fwd_T_L, r2c, g, st, io, tw, in_sa0, in_sb, out_sa0, out_sk, a0_off)
+}
+template <typename R>
+cudaError_t launch_inv_T5(int L, bool c2r, const PassGeom& g, cudaStream_t st, const LineIO& io, const void* tw,
+                          int64_t in_sa0, int64_t in_sk, int64_t out_sa0, int64_t out_sb, const int64_t* a0_off) {
+  PSATD_L5_SWITCH(inv_T_L, c2r, g, st, io, tw, in_sa0, in_sk, out_sa0, out_sb, a0_off)
+}
+template <typename R>
+cudaError_t launch_line_push5(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
+                              const PushArgs<R>& a, const void* tw) {
+  switch (L) {
+    case 80: return push_L<R, 0, 20, 80>(layout, grid, tb, smem, st, a, tw);
+    case 160: return push_L<R, 0, 20, 160>(layout, grid, tb, smem, st, a, tw);
+    case 320: return push_L<R, 0, 20, 320>(layout, grid, tb, smem, st, a, tw);
+    case 640: return push_L<R, 0, 20, 640>(layout, grid, tb, smem, st, a, tw);
+    case 1280: return push_L<R, 0, 20, 1280>(layout, grid, tb, smem, st, a, tw);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <typename R>
 cudaError_t launch_fwd_T3(int L, bool r2c, const PassGeom& g, cudaStream_t st, const LineIO& io, const void* tw,
                           int64_t in_sa0, int64_t in_sb, int64_t out_sa0, int64_t out_sk, const int64_t* a0_off) {

@@ -108,7 +108,7 @@ __global__ void k_nonfinite(NfPtrs ptrs, const int64_t* __restrict__ off, int64_
 // Threads per CTA a transposing pass of length L may use (the register budget
 // of 24 elements per thread halves it for the mixed lengths).
 template <typename R, int L>
-struct RowThreads { static constexpr int value = RowEPT<L>::value == 24 ? 256 : sizeof(R) == 4 ? 512 : 256; };
+struct RowThreads { static constexpr int value = RowEPT<L>::value >= 20 ? 256 : sizeof(R) == 4 ? 512 : 256; };
 
 // XOR mask of row r's buffer in the transposed stores and reads (TB = 1 << log_tb
 // rows): rows spread over the 16 eight-byte bank pairs (at most 16 rows: one row
@@ -313,21 +313,22 @@ __device__ __forceinline__ void inv_T_body(const LineIO& io, const typename Type
     C* zr = smem + gg * L;
     const bool gvalid = !PART || gg < rows;
     const C* ib = static_cast<const C*>(io.in[a1]) + a0 * in_sa0 + b0 + gg;
-    constexpr int NP = EPT / 2;  // 4 or 8 pairs, taken four at a time
+    constexpr int NP = EPT / 2;  // 4 to 12 pairs, taken four (or two) at a time
+    constexpr int GP = NP % 4 == 0 ? 4 : 2;
     const C zero = mkc(R(0), R(0));
 #pragma unroll
-    for (int j0 = 0; j0 < NP; j0 += 4) {
-      C xk[4], xm[4];
-      typename Types<R>::W w[4];
+    for (int j0 = 0; j0 < NP; j0 += GP) {
+      C xk[GP], xm[GP];
+      typename Types<R>::W w[GP];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < GP; ++j) {
         const int pp = p0 + (j0 + j) * T;
         xk[j] = gvalid ? ib[(int64_t)pp * in_sk] : zero;
         xm[j] = gvalid ? ib[(int64_t)(L - pp) * in_sk] : zero;
         w[j] = __ldg(&wn[pp]);
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < GP; ++j) {
         const int pp = p0 + (j0 + j) * T;
         const C xmc = cconj(xm[j]);
         const C fe = cadd(xk[j], xmc);

@@ -35,10 +35,12 @@ struct Radices {
 static Radices plan_radices(int L, int ept) {
   Radices R{};
   auto lg = [](int v) { int k = 0; while ((1 << k) < v) ++k; return k; };
-  if (L & (L - 1)) {  // 3 * 2^k: radix 3, (2|4), 8, ... (ept 24) or radix 12, (2), 4, ... (ept 12)
-    const int head = ept == 12 ? 2 : 0, b = ept == 12 ? 2 : 3;
-    const int k = lg(L / 3) - head, rem = k % b;
-    R.r[R.n++] = 3 << head;
+  if (L & (L - 1)) {  // 3 * 2^k: radix 3, (2|4), 8, ... (ept 24) or radix 12, (2), 4, ... (ept 12);
+                      // 5 * 2^k: radix 5, (2), 4, ... (ept 20)
+    const int f = L % 3 == 0 ? 3 : 5;
+    const int head = (f == 3 && ept == 12) ? 2 : 0, b = (f == 5 || ept == 12) ? 2 : 3;
+    const int k = lg(L / f) - head, rem = k % b;
+    R.r[R.n++] = f << head;
     if (rem) R.r[R.n++] = 1 << rem;
     for (int i = 0; i < k / b; ++i) R.r[R.n++] = 1 << b;
   } else {

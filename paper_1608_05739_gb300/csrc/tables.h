@@ -9,8 +9,10 @@ namespace psatd {
 // thread of the kernels that read it; table of at most 2L entries
 cudaError_t launch_twiddles(void* out, int L, int ept, bool r2c, bool f32, cudaStream_t st);
 // elements per thread of the transposing passes (RowEPT in fft_core.cuh) and of the fused pass
-inline int row_ept(int L) { return !is_pow2(L) ? 24 : L >= 16 ? 16 : 8; }
-inline int push_ept(int L, bool tc = false) { return !is_pow2(L) ? 12 : tc ? 16 : 8; }
+inline int row_ept(int L) { return odd_factor(L) == 3 ? 24 : odd_factor(L) == 5 ? 20 : L >= 16 ? 16 : 8; }
+inline int push_ept(int L, bool tc = false) {
+  return odd_factor(L) == 3 ? 12 : odd_factor(L) == 5 ? 20 : tc ? 16 : 8;
+}
 // split-FP16 (or split-BF16) radix-16 DFT matrices of both directions, tensor-core operand layout
 cudaError_t launch_tc_dftmat(void* out, bool bf16, cudaStream_t st);
 // kp: per-axis order-p wavenumber tables (units of g0, n_i/2+1 entries) of a

@@ -273,8 +273,10 @@ def batch_patch_domains(npatch=512, seed=1612):
 
 def transform_lengths(mixed_ok=True):
     """Transform lengths of the batch's patch sides: powers of two, and with
-    ``mixed_ok`` also 3 * 2^k from 96 up (the lengths the FP32 passes take)."""
-    return sorted([1 << k for k in range(4, 13)] + ([3 << k for k in range(5, 11)] if mixed_ok else []))
+    ``mixed_ok`` also 3 * 2^k from 96 and 5 * 2^k from 160 up (the lengths the
+    FP32 passes take on both axes: x lines of n/2 points, y lines of n)."""
+    return sorted([1 << k for k in range(4, 13)] +
+                  ([3 << k for k in range(5, 11)] + [5 << k for k in range(5, 9)] if mixed_ok else []))
 
 
 def batch_patch_sizes(npatch=512, seed=1612, mixed_ok=True, lengths=None):

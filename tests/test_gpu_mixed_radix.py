@@ -1,7 +1,8 @@
-"""GPU parity of the mixed-radix line lengths L = 3 * 2^k (FP32): every pass
-(R2C x rows of nx/2 points, C2C y lines in 3D, the fused last-axis pass, the
-inverses) transforms such lines with a radix-3 first stage, then radix-2/4 and
-radix-8 stages.  The method does not restrict the grid to powers of two; these
+"""GPU parity of the mixed-radix line lengths L = 3 * 2^k and 5 * 2^k (FP32):
+every pass (R2C x rows of nx/2 points, C2C y lines in 3D, the fused last-axis
+pass, the inverses) transforms such lines with a radix-3 first stage, then
+radix-2/4 and radix-8 stages, or a radix-5 first stage, then radix-2 and
+radix-4 stages.  The method does not restrict the grid to powers of two; these
 lengths matter for the local FFTs of Sec. II.A.3, whose extended patches are
 an interior plus two guard regions (e.g. 16 + 2 * 16 = 48 cells).
 
@@ -39,6 +40,11 @@ CASES_2D = [
     ((64, 3072), "te", "none"),     # longest x rows (1536 points, R2C)
     ((192, 256), "2d6", "J"),       # power-of-two x, mixed y
     ((128, 384), "tm", "none"),     # mixed x, power-of-two y
+    ((80, 160), "te", "J"),         # smallest 5 * 2^k lengths on both axes (80, 80)
+    ((320, 192), "2d6", "rho"),     # 96-point x rows, 320-point lines
+    ((1280, 64), "te", "J"),        # longest 5 * 2^k fused-pass line
+    ((64, 2560), "tm", "none"),     # longest 5 * 2^k x rows (1280 points, R2C)
+    ((160, 384), "te", "J"),        # 3 * 2^k x rows, 5 * 2^k lines
 ]
 
 
@@ -53,7 +59,8 @@ def test_mixed_lengths_2d_match_oracle(shape, layout, src):
     assert rel_l2_fields(Eg, Bg, Eo, Bo) < TOL * n
 
 
-@pytest.mark.parametrize("shape", [(48, 96, 192), (64, 48, 128), (96, 64, 96), (48, 48, 96)])
+@pytest.mark.parametrize("shape", [(48, 96, 192), (64, 48, 128), (96, 64, 96), (48, 48, 96), (80, 160, 64),
+                                   (96, 80, 320)])
 @pytest.mark.parametrize("src", ["J", "rho"])
 def test_mixed_lengths_3d_match_oracle(shape, src):
     """(nz, ny, nx): the C2C y pass and the fused z pass on mixed and
@@ -116,7 +123,7 @@ def test_local_patches_of_96_by_48_cells():
 def test_batch_of_mixed_and_power_of_two_patches():
     import torch
     ensure_lib()
-    sizes = [(96, 48), (64, 64), (192, 96), (96, 48), (128, 384)]
+    sizes = [(96, 48), (64, 64), (192, 96), (96, 48), (128, 384), (160, 80), (320, 640), (192, 160)]
     d, dt = (1.0, 1.0), 0.5
     per = [_inputs((ny, nx), "te", 1100 + 10 * i)[:3] for i, (nx, ny) in enumerate(sizes)]
     pe, pb, pj = capi.PRESENT["te"]
