@@ -135,12 +135,15 @@ def test_mixed_fp16_shape_limits(lib, n, why):
 
 @pytest.mark.parametrize("n,prec", [
     ((96, 64), "fp64"), ((64, 48), "mixed_fp16"), ((96, 96), "mixed_bf16"),   # 3 * 2^k lengths: FP32 only
+    ((160, 64), "fp64"), ((64, 80), "mixed_bf16"),                            # 5 * 2^k lengths: FP32 only
     ((6144, 64), "fp32"),                    # x rows of 3072 points: the R2C pass stops at 1536
-    ((64, 6144), "fp32"), ((64, 24), "fp32"), ((72, 64), "fp32"), ((64, 80), "fp32"),
+    ((64, 6144), "fp32"), ((64, 24), "fp32"), ((72, 64), "fp32"), ((64, 112), "fp32"),
+    ((64, 2560), "fp32"), ((64, 40), "fp32"),  # 5 * 2^k lines: 80 to 1280 points
 ])
 def test_mixed_radix_length_limits(lib, n, prec):
-    """Lines of 3 * 2^k points (48 to 3072; x rows are nx/2 points) are FP32-only;
-    other lengths and other precisions are refused before any allocation."""
+    """Lines of 3 * 2^k points (48 to 3072) and 5 * 2^k points (80 to 1280; x rows
+    are nx/2 points) are FP32-only; other lengths and other precisions are refused
+    before any allocation."""
     d = capi.make_desc(n, (1.0, 1.0), 0.5, layout="te", prec=prec, src="J")
     st, h = _create(lib, d)
     assert st == 2 and h.value is None
