@@ -20,7 +20,7 @@ def test_batch_patch_sizes_are_transform_lengths_covering_the_patch():
     sizes, interior = synth.batch_patch_sizes(512, 1612, mixed_ok=True)
     again, interior2 = synth.batch_patch_sizes(512, 1612, mixed_ok=True)
     assert sizes == again and interior == interior2 and len(sizes) == 512
-    ok = {1 << k for k in range(4, 13)} | {3 << k for k in range(5, 11)}
+    ok = {1 << k for k in range(4, 13)} | {3 << k for k in range(5, 11)} | {5 << k for k in range(5, 9)}
     g = synth.rng(1612)
     for nx, ny in sizes:
         n = g.integers(64, 513, size=2)
