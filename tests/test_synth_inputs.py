@@ -20,7 +20,7 @@ def test_batch_patch_sizes_are_transform_lengths_covering_the_patch():
     sizes, interior = synth.batch_patch_sizes(512, 1612, mixed_ok=True)
     again, interior2 = synth.batch_patch_sizes(512, 1612, mixed_ok=True)
     assert sizes == again and interior == interior2 and len(sizes) == 512
-    ok = {1 << k for k in range(4, 13)} | {3 << k for k in range(5, 11)} | {5 << k for k in range(5, 9)}
+    ok = {1 << k for k in range(4, 13)} | {3 << k for k in range(5, 11)}
     g = synth.rng(1612)
     for nx, ny in sizes:
         n = g.integers(64, 513, size=2)
@@ -32,6 +32,9 @@ def test_batch_patch_sizes_are_transform_lengths_covering_the_patch():
     pow2, _ = synth.batch_patch_sizes(512, 1612, mixed_ok=False)
     assert all(a & (a - 1) == 0 and b & (b - 1) == 0 for a, b in pow2)
     assert sum(a * b for a, b in sizes) < sum(a * b for a, b in pow2)
+    five, _ = synth.batch_patch_sizes(512, 1612, mixed_ok=True, five=True)
+    assert any(a % 5 == 0 or b % 5 == 0 for a, b in five)
+    assert sum(a * b for a, b in five) < sum(a * b for a, b in sizes)
 
 
 def test_large_3d_inputs_continuity_gauss_and_divergence():
