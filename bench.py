@@ -266,7 +266,8 @@ def batch_algorithmic_bytes(sizes):
     return tot
 
 
-def time_batch(capi, torch, prec, sizes, Jhost, args, dev, stream, sample_clocks, nsteps=None, persistent=None):
+def time_batch(capi, torch, prec, sizes, Jhost, args, dev, stream, sample_clocks, nsteps=None, persistent=None,
+               forked=True):
     """A batch at precision `prec`: W untimed steps (one call: the step graph is
     recorded and replayed), then one psatd_batch_step(nsteps = K) call between
     CUDA events on the batch's stream.  Per-kernel event pairs are recorded in the
@@ -276,6 +277,8 @@ def time_batch(capi, torch, prec, sizes, Jhost, args, dev, stream, sample_clocks
     b = capi.Batch(sizes, (BATCH_DX, BATCH_DX), BATCH_DT, layout="te", prec=prec, src="J", stream=stream)
     if persistent is not None:
         b.set_persistent(persistent)
+    if not forked:
+        b.set_branches(False)
     tot = b.total
     Ex, Ey, Bz = (torch.zeros(tot, device=dev) for _ in range(3))
     Jx = torch.from_numpy(Jhost[0]).to(dev)
@@ -434,6 +437,13 @@ def run_batch_line(args, world, rank, local):
     value, t_max = replica_throughput(ms, cells, K, world, dev)
     gpu_fields = patch_fields(F[:3], sizes, offs, samp)
     launches_per_step = kt.pop("_launches_per_step")[0]
+    # the roofline's timed region: the same batch and call with the size classes one after
+    # another on the batch's stream, so that each launch's event time is its own
+    ms_s, kt_s, _, b_s, F_s = time_batch(capi, torch, prec, sizes, J, args, dev, stream, sample_clocks=False,
+                                         forked=False)
+    kt_s.pop("_launches_per_step")
+    b_s.destroy()
+    del F_s
     # a longer series of the same call with its own clock record (at least ~2 s of steps)
     long_series = None
     n_long = int(math.ceil(2000.0 / (ms / K)))
@@ -483,7 +493,10 @@ def run_batch_line(args, world, rank, local):
                   "launch's bytes are the whole batch's for that pass" if launches_per_step <= 6 else
                   "the size classes' kernels run side by side on the batch's branch streams, so each launch's "
                   "duration includes time shared with other classes' kernels")
-    roof = roofline_of(kt, lambda k, n: alg_b[k], hbm, peak_kind, traffic_lookup=False, note=concurrent)
+    roof = roofline_of(kt_s, lambda k, n: alg_b[k], hbm, peak_kind, traffic_lookup=False,
+                       note="the size classes one after another (%.3f ms per step; %.3f forked, the line's value): each "
+                            "launch's own duration; the pass's launches over every class of one step" % (ms_s / K, ms / K))
+    roof["forked_per_kernel_ms_summed"] = {k: v[1] for k, v in kt.items()}
 
     side = None
     if not args.no_side_precision and rank == 0:

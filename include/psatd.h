@@ -338,6 +338,12 @@ psatd_status psatd_batch_sync(psatd_batch batch);
 psatd_status psatd_batch_set_persistent(psatd_batch batch, int32_t enable);
 int32_t psatd_batch_launches_per_step(psatd_batch batch);
 
+/* Per-class launches on the branch streams (forked != 0, the default) or all on
+ * the batch's own stream one class after another (forked = 0: no kernel of one
+ * class overlaps another's, so per-launch event times are the kernels' own).
+ * Synchronises the batch's streams; the same bits either way. */
+psatd_status psatd_batch_set_branches(psatd_batch batch, int32_t forked);
+
 /* Per-kernel CUDA-event timing of the batch, as psatd_plan_set_timing /
  * psatd_kernel_times do for a plan, summed over the size classes: enable != 0
  * records an event pair around every launch of every class (the recorded step

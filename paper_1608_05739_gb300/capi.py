@@ -76,6 +76,7 @@ EXPORTS = [
     ("psatd_batch_set_timing", ct.c_int, [ct.c_void_p, ct.c_int32]),
     ("psatd_batch_set_persistent", ct.c_int, [ct.c_void_p, ct.c_int32]),
     ("psatd_batch_launches_per_step", ct.c_int32, [ct.c_void_p]),
+    ("psatd_batch_set_branches", ct.c_int, [ct.c_void_p, ct.c_int32]),
     ("psatd_batch_kernel_times", ct.c_int32, [ct.c_void_p, ct.c_int32, ct.POINTER(ct.c_char_p),
                                               ct.POINTER(ct.c_int64), ct.POINTER(ct.c_double)]),
     ("psatd_plan_autotune", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_char_p, ct.c_size_t]),
@@ -323,6 +324,10 @@ class Batch:
 
     def launches_per_step(self):
         return int(load().psatd_batch_launches_per_step(self.handle))
+
+    def set_branches(self, forked=True):
+        """Size classes on the branch streams (default) or one after another on the batch's stream."""
+        _check(load().psatd_batch_set_branches(self.handle, 1 if forked else 0))
 
     def kernel_times(self):
         """{kernel name: (launches, total ms)} summed over the size classes."""

@@ -1435,6 +1435,8 @@ struct psatd_batch_s {
   std::vector<cudaStream_t> br;
   cudaEvent_t fork = nullptr;
   std::vector<cudaEvent_t> join;
+  std::vector<int> branch_of;   // branch stream of each class when forked
+  bool fork_on = true;          // psatd_batch_set_branches: forked (true) or one stream
   int64_t total_cells = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -1705,7 +1707,7 @@ psatd_status batch_launch_persist(psatd_batch b, void* out[kMaxComp]) {
 
 psatd_status batch_launch_all(psatd_batch b, const void* in[kMaxComp], void* out[kMaxComp]) {
   if (b->persist) return batch_launch_persist(b, out);
-  const bool forked = !b->br.empty();
+  const bool forked = !b->br.empty() && b->fork_on;
   cudaError_t e = cudaSuccess;
   if (forked) {
     e = cudaEventRecord(b->fork, b->st);
@@ -1825,6 +1827,7 @@ extern "C" psatd_status psatd_batch_create(const psatd_desc* base, int32_t npatc
     }
     std::vector<int> order(b->cls.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    b->branch_of.assign(b->cls.size(), 0);
     auto cells = [&](int i) { return b->cls[i]->nx * b->cls[i]->ny * b->cls[i]->npatch; };
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cells(a) > cells(c); });
     std::vector<int64_t> load(nbr, 0);
@@ -1832,6 +1835,7 @@ extern "C" psatd_status psatd_batch_create(const psatd_desc* base, int32_t npatc
       const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
       load[k] += cells(i);
       b->cls[i]->st = b->br[k];
+      b->branch_of[i] = k;
     }
   }
   *out = b;
@@ -1905,6 +1909,22 @@ extern "C" psatd_status psatd_batch_set_persistent(psatd_batch b, int32_t enable
   b->gexec = nullptr;
   b->graph = nullptr;
   b->persist = enable != 0;
+  return PSATD_OK;
+}
+
+extern "C" psatd_status psatd_batch_set_branches(psatd_batch b, int32_t forked) {
+  if (!b) return fail(nullptr, PSATD_ERR_INVALID_ARG, "batch is NULL");
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  for (cudaStream_t st : b->br)
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "stream synchronise");
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  b->fork_on = forked != 0;
+  for (size_t i = 0; i < b->cls.size(); ++i)
+    b->cls[i]->st = (b->fork_on && !b->br.empty()) ? b->br[b->branch_of[i]] : b->st;
   return PSATD_OK;
 }
 

@@ -181,3 +181,28 @@ def test_persistent_passes_equal_per_class_launches(prec, layout):
         Bg = cut([t.double().cpu().numpy() if t is not None else None for t in out[0][3:]])
         tol = 4e-6 if prec == "fp32" else 8e-6
         assert rel_l2_fields(Eg, Bg, mask_layout(Eo, layout, "E"), mask_layout(Bo, layout, "B")) < tol, i
+
+
+def test_serialised_classes_give_the_forked_bits():
+    """psatd_batch_set_branches(0) runs the size classes one after another on the
+    batch's stream (the bench's roofline run): the same bits as the forked default."""
+    import torch
+    ensure_lib()
+    sizes = [(256, 128), (128, 96), (192, 256), (512, 64), (128, 96)]
+    tot = sum(a * b for a, b in sizes)
+    g = torch.Generator(device="cuda").manual_seed(31)
+    init = [torch.randn(tot, device="cuda", generator=g) for _ in range(5)]
+    out = []
+    for forked in (True, False):
+        F = [t.clone() for t in init]
+        stream = torch.cuda.Stream()
+        torch.cuda.synchronize()
+        b = capi.Batch(sizes, (1.0, 1.0), 0.5, layout="te", prec="fp32", src="J", stream=stream)
+        b.set_branches(forked)
+        with torch.cuda.stream(stream):
+            b.step([F[0], F[1], None], [None, None, F[2]], [F[3], F[4], None], nsteps=3)
+        b.sync()
+        b.destroy()
+        out.append(F[:3])
+    for x, y in zip(*out):
+        assert torch.equal(x, y)
