@@ -213,7 +213,7 @@ psatd_status psatd_coeffs_init(psatd_plan plan);
  *   the fused pass's radix schedule (radix-8 or radix-16 stages, i.e. 8 or 16
  *   elements per thread; radix 16 only for the mixed precisions; for 3 * 2^k
  *   lengths only 12 elements per thread: a radix-12 first stage, then radix
- *   2 and 4) with its lines per CTA.
+ *   2 and 4) with its lines per CTA and component groups (below).
  * Results do not depend on the choice (same arithmetic, same order per line).
  * `report` (may be NULL) receives a one-line summary of the times, the chosen
  * ones marked '*', truncated to report_len - 1 bytes.  Synchronous.
@@ -234,6 +234,26 @@ psatd_status psatd_plan_autotune(psatd_plan plan, int32_t reps, char* report, si
  * cfg[5] changes, so it needs psatd_coeffs_init first.                    */
 psatd_status psatd_plan_set_launch(psatd_plan plan, const int32_t cfg[6]);
 psatd_status psatd_plan_get_launch(psatd_plan plan, int32_t cfg[6]);
+
+/* Component groups of the fused pass (a launch shape, like cfg[4]): with G > 1
+ * each line gets G thread groups that forward- and inverse-transform its
+ * components in turn (group j: components j, j + G, ...; their own exchange
+ * buffer and barrier each), meeting for the per-mode push; shared memory per
+ * line grows from (n_in + 1) to (n_in + G) line buffers.  G = 1 is the plain
+ * pass.  Valid: 1 always; 2 or 4 for PSATD_FP32 plans whose fused-axis lines
+ * have a multiple of 32 threads (length / elements per thread), at most 512
+ * threads and 15 groups per CTA, an even number of modes per thread, and the
+ * shared memory within the device's limit.  -1: the built-in choice, 2 where
+ * lines have at least 64 threads and the one-group pass keeps fewer than 12
+ * warps per SM resident (shared memory: many components on long lines, e.g.
+ * 1024-point 3D rho-form lines), else 1.  Results
+ * are bitwise the same for every G (each transform and each mode's update
+ * runs the same arithmetic).  set: INVALID_ARG when the shape is not valid
+ * for the plan's current lines per CTA and elements per thread (a later
+ * psatd_plan_set_launch that makes it invalid falls back to 1).  get: the G
+ * the next step uses.                                                     */
+psatd_status psatd_plan_set_push_groups(psatd_plan plan, int32_t groups);
+psatd_status psatd_plan_get_push_groups(psatd_plan plan, int32_t* groups);
 
 /* Advance E, B by nsteps PSATD steps (nsteps >= 1).  `sources` may be NULL
  * for PSATD_SRC_NONE and must not be NULL otherwise.  Per step: forward
@@ -343,6 +363,13 @@ int32_t psatd_batch_launches_per_step(psatd_batch batch);
  * class overlaps another's, so per-launch event times are the kernels' own).
  * Synchronises the batch's streams; the same bits either way. */
 psatd_status psatd_batch_set_branches(psatd_batch batch, int32_t forked);
+
+/* Component groups of every size class's fused pass (psatd_plan_set_push_groups):
+ * each class takes `groups` (2 or 4) where its shape admits them and one group
+ * otherwise; 1 everywhere; -1 the built-in choice.  The per-class launches use
+ * it (the persistent passes keep one group).  Synchronises the batch's streams;
+ * the same bits either way.  INVALID_ARG for other values. */
+psatd_status psatd_batch_set_push_groups(psatd_batch batch, int32_t groups);
 
 /* Per-kernel CUDA-event timing of the batch, as psatd_plan_set_timing /
  * psatd_kernel_times do for a plan, summed over the size classes: enable != 0

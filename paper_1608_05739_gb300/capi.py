@@ -82,6 +82,9 @@ EXPORTS = [
     ("psatd_plan_autotune", ct.c_int, [ct.c_void_p, ct.c_int32, ct.c_char_p, ct.c_size_t]),
     ("psatd_plan_set_launch", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32)]),
     ("psatd_plan_get_launch", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32)]),
+    ("psatd_plan_set_push_groups", ct.c_int, [ct.c_void_p, ct.c_int32]),
+    ("psatd_batch_set_push_groups", ct.c_int, [ct.c_void_p, ct.c_int32]),
+    ("psatd_plan_get_push_groups", ct.c_int, [ct.c_void_p, ct.POINTER(ct.c_int32)]),
     ("psatd_local_create", ct.c_int, [ct.POINTER(psatd_desc), ct.c_int32, ct.c_int32, ct.c_int32, ct.c_void_p,
                                       ct.POINTER(ct.c_void_p)]),
     ("psatd_local_step", ct.c_int, [ct.c_void_p, ct.POINTER(psatd_fields), ct.POINTER(psatd_sources), ct.c_int32]),
@@ -241,6 +244,16 @@ class Plan:
         arr = (ct.c_int32 * 6)(*[int(v) for v in cfg])
         _check(load().psatd_plan_set_launch(self.handle, arr), self.handle)
 
+    def get_push_groups(self):
+        """Component groups the fused pass's next launch uses."""
+        g = ct.c_int32(0)
+        _check(load().psatd_plan_get_push_groups(self.handle, ct.byref(g)), self.handle)
+        return g.value
+
+    def set_push_groups(self, groups):
+        """psatd_plan_set_push_groups: 1, 2 or 4 component groups (-1: the built-in choice)."""
+        _check(load().psatd_plan_set_push_groups(self.handle, int(groups)), self.handle)
+
     def autotune(self, reps=5):
         """psatd_plan_autotune: time the launch shapes, keep the fastest; returns the report."""
         buf = ct.create_string_buffer(4096)
@@ -319,11 +332,15 @@ class Batch:
         _check(load().psatd_batch_set_timing(self.handle, 1 if enable else 0))
 
     def set_persistent(self, enable=True):
-        """Persistent passes (default where the sizes allow) or per-class launches."""
+        """Persistent passes (where the sizes allow) or per-class launches (the default)."""
         _check(load().psatd_batch_set_persistent(self.handle, 1 if enable else 0))
 
     def launches_per_step(self):
         return int(load().psatd_batch_launches_per_step(self.handle))
+
+    def set_push_groups(self, groups):
+        """psatd_batch_set_push_groups: component groups of each class's fused pass where valid."""
+        _check(load().psatd_batch_set_push_groups(self.handle, int(groups)))
 
     def set_branches(self, forked=True):
         """Size classes on the branch streams (default) or one after another on the batch's stream."""

@@ -65,6 +65,9 @@ struct psatd_plan_s {
   int cfg_log_tb[4] = {-1, -1, -1, -1};
   int cfg_push_tb = -1;
   int push_ept = 8;
+  int cfg_push_groups = -1;   // component groups of the fused pass (-1: the built-in choice)
+  int maxsm = 0;              // opt-in shared memory per block of the plan's device
+  int sm_bytes = 0;           // shared memory per SM of the plan's device
   int order = 0;                        // 0: nodes, exact k; p: staggered PSATD-p
   double* kp_d[3] = {nullptr, nullptr, nullptr};  // per axis k_p / g0 (n_i/2+1 entries)
   void* ph_d[3] = {nullptr, nullptr, nullptr};    // per axis half-cell phases (twiddle type)
@@ -334,6 +337,41 @@ int push_lines_per_cta(int L, int n_in, int64_t nlines, bool tc, bool f32, int e
   return tb;
 }
 
+// Component groups of the fused pass (psatd_kernels.cuh): 1, or 2 / 4 thread
+// groups per line taking the components in turn, for FP32 plans without
+// tensor-core stages whose lines have a multiple of 32 threads (named barriers
+// per group: at most 15 per CTA; at most 512 threads; an even number of modes
+// per thread in the push).
+bool push_groups_ok(int L, int ept, int tb, int G, bool tc, bool f32) {
+  if (G == 1) return true;
+  if (tc || !f32 || (G != 2 && G != 4) || L < ept) return false;
+  const int T = L / ept;
+  return T % 32 == 0 && (ept / G) % 2 == 0 && T * tb * G <= 512 && tb * G <= 15;
+}
+// shared memory of the fused pass: per line the n_in slots and one second
+// exchange buffer per group (split-BF16's third A piece sits in a slot)
+size_t push_smem(int n_in, int L, int tb, int G, size_t csz) {
+  return (size_t)tb * ((size_t)n_in + (size_t)G) * (size_t)L * csz;
+}
+// The built-in choice (measured on GB300 against the plain pass): two groups
+// where lines have at least 64 threads and the plain pass keeps fewer than 12
+// warps per SM resident for lack of shared memory (3D rho-form and 2D
+// six-component J-form lines of 1024 points: 8 warps, 12 % faster with two
+// groups); one group otherwise (the 2048^2 TE grid, 256^3, the 512-patch
+// batch ran fastest with one).  sm_bytes: shared memory per SM.
+int push_groups_default(int L, int ept, int tb, int n_in, bool tc, bool f32, size_t csz, int maxsm, int sm_bytes) {
+  if (tc || !f32 || L < ept || sm_bytes <= 0) return 1;
+  const int T = L / ept;
+  if (T < 64) return 1;
+  const size_t smem1 = push_smem(n_in, L, tb, 1, csz) + 1024;  // + the per-CTA reservation
+  int ctas = (int)((size_t)sm_bytes / smem1);
+  ctas = std::min(ctas, std::min(2048 / (T * tb), 32));
+  if (ctas * T * tb / 32 >= 12) return 1;
+  if (push_groups_ok(L, ept, tb, 2, tc, f32) && (maxsm <= 0 || push_smem(n_in, L, tb, 2, csz) <= (size_t)maxsm))
+    return 2;
+  return 1;
+}
+
 // split-BF16 passes: shared memory of the third A piece of `threads` threads
 // (one 128-row piece per 128 threads), after the pass's exchange region
 size_t tc_a3_bytes(psatd_plan p, int threads) {
@@ -518,20 +556,24 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
     {
       const int tb = p->cfg_push_tb > 0 ? p->cfg_push_tb
                                         : push_lines_per_cta(Lline, p->n_in, nlines, TC, p->f32, p->push_ept);
-      const size_t per_line = ((size_t)p->n_in + 1) * (size_t)Lline * csz;  // split-BF16's third piece: in a slot
+      int G = p->cfg_push_groups > 0
+                  ? p->cfg_push_groups
+                  : push_groups_default(Lline, p->push_ept, tb, p->n_in, TC, p->f32, csz, p->maxsm, p->sm_bytes);
+      if (!push_groups_ok(Lline, p->push_ept, tb, G, TC, p->f32)) G = 1;
+      const size_t smem = tail + push_smem(p->n_in, Lline, tb, G, csz);
       const dim3 grid((unsigned)((nlines + tb - 1) / tb));
       TimedLaunch tl(p, K_PUSH);
       if (p->push_ept == 12 || p->push_ept == 20) {
         if constexpr (std::is_same<R, float>::value && TC == 0)
-          e = p->push_ept == 12 ? launch_line_push3<R>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl)
-                                : launch_line_push5<R>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl);
+          e = p->push_ept == 12 ? launch_line_push3<R>(Lline, p->layout, grid, tb, G, smem, p->st, a, twl)
+                                : launch_line_push5<R>(Lline, p->layout, grid, tb, G, smem, p->st, a, twl);
         else
           e = cudaErrorInvalidValue;
       } else if (p->push_ept == 16) {
-        e = launch_line_push<R, TC, 16>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl);
+        e = launch_line_push<R, TC, 16>(Lline, p->layout, grid, tb, G, smem, p->st, a, twl);
       } else {
         if constexpr (TC) e = cudaErrorInvalidValue;
-        else e = launch_line_push<R, false, 8>(Lline, p->layout, grid, tb, tail + tb * per_line, p->st, a, twl);
+        else e = launch_line_push<R, false, 8>(Lline, p->layout, grid, tb, G, smem, p->st, a, twl);
       }
       if (e != cudaSuccess) return cuda_fail(p, e, "line_fft_push launch");
     }
@@ -602,7 +644,7 @@ psatd_status check_tc_shape(psatd_plan p, int maxsm) {
   }
   const int64_t nlines = p->ndim == 3 ? p->nxh * p->ny : p->nxh * p->npatch;
   const int tb = push_lines_per_cta(Ll, p->n_in, nlines, true, true, 16);
-  const size_t smem = (size_t)kTcTail + (size_t)tb * ((size_t)p->n_in + 1) * (size_t)Ll * 8;
+  const size_t smem = (size_t)kTcTail + push_smem(p->n_in, Ll, tb, 1, 8);
   if (maxsm > 0 && smem > (size_t)maxsm)
     return fail(nullptr, PSATD_ERR_UNSUPPORTED, "mixed precision: last-axis length %d needs %zu bytes of shared memory",
                 Ll, smem);
@@ -621,6 +663,7 @@ psatd_status check_tc_shape(psatd_plan p, int maxsm) {
 struct TuneCfg {
   int log_tb[4];
   int push_tb, push_ept;
+  int push_groups = -1;
 };
 struct TuneKey {
   int prec, layout, form, npatch, order, flags;
@@ -643,6 +686,7 @@ void apply_cfg(psatd_plan p, const TuneCfg& c) {
   for (int i = 0; i < 4; ++i) p->cfg_log_tb[i] = c.log_tb[i];
   p->cfg_push_tb = c.push_tb;
   p->push_ept = c.push_ept;
+  p->cfg_push_groups = c.push_groups;
 }
 
 psatd_status regen_push_twiddles(psatd_plan p) {
@@ -655,10 +699,13 @@ psatd_status regen_push_twiddles(psatd_plan p) {
 
 // Valid launch shapes of every knob: rows[k] = log2(lines per CTA) of
 // transposing pass k (empty if the pass does not exist), push = (elements per
-// thread, lines per CTA) of the fused pass.
+// thread, lines per CTA, component groups) of the fused pass.
+struct PushShape {
+  int ept, tb, groups;
+};
 struct TuneSpace {
   std::vector<int> rows[4];
-  std::vector<std::pair<int, int>> push;
+  std::vector<PushShape> push;
   int rowL[4];
   int Ll;
 };
@@ -693,12 +740,14 @@ TuneSpace tune_space(psatd_plan p) {
     const bool allowed = pow2(ts.Ll) ? (ept == 8 || ept == 16) && (!p->tc || ept == 16) : ept == push_ept(ts.Ll);
     if (!allowed || ts.Ll < ept) continue;
     const int T = ts.Ll / ept;
-    const size_t per_line = ((size_t)p->n_in + 1) * (size_t)ts.Ll * csz;
     for (int tb = 1; tb * T <= (T > 256 ? T : 256); tb *= 2) {
       if (p->tc && (tb * T) % 128 != 0) continue;
-      if (maxsm > 0 && tail + tb * per_line > (size_t)maxsm) continue;
       if (tb > 1 && tb / 2 >= nlines) break;
-      ts.push.push_back({ept, tb});
+      for (int G : {1, 2, 4}) {
+        if (!push_groups_ok(ts.Ll, ept, tb, G, p->tc, p->f32)) continue;
+        if (maxsm > 0 && tail + push_smem(p->n_in, ts.Ll, tb, G, csz) > (size_t)maxsm) continue;
+        ts.push.push_back({ept, tb, G});
+      }
     }
   }
   return ts;
@@ -709,7 +758,7 @@ psatd_status autotune(psatd_plan p, int reps, std::string* report) {
   const size_t rsz = p->f32 ? 4 : 8;
   TuneSpace ts = tune_space(p);
   std::vector<int>* rows = ts.rows;
-  std::vector<std::pair<int, int>>& push = ts.push;
+  std::vector<PushShape>& push = ts.push;
   const int* rowL = ts.rowL;
   const int Ll = ts.Ll;
   const bool rowOn[4] = {true, p->ndim == 3, p->ndim == 3, true};
@@ -756,12 +805,13 @@ psatd_status autotune(psatd_plan p, int reps, std::string* report) {
   for (size_t r = 0; r < rounds && st == PSATD_OK; ++r) {
     for (int k = 0; k < 4; ++k)
       if (!rows[k].empty()) p->cfg_log_tb[k] = rows[k][std::min(r, rows[k].size() - 1)];
-    const auto pc = push[std::min(r, push.size() - 1)];
-    if (pc.first != p->push_ept) {
-      p->push_ept = pc.first;
+    const PushShape pc = push[std::min(r, push.size() - 1)];
+    if (pc.ept != p->push_ept) {
+      p->push_ept = pc.ept;
       if ((st = regen_push_twiddles(p)) != PSATD_OK) break;
     }
-    p->cfg_push_tb = pc.second;
+    p->cfg_push_tb = pc.tb;
+    p->cfg_push_groups = pc.groups;
     if ((st = step_once(p, in, out)) != PSATD_OK) break;  // warm-up
     cudaStreamSynchronize(p->st);
     for (auto& v : p->ev) {
@@ -797,6 +847,7 @@ psatd_status autotune(psatd_plan p, int reps, std::string* report) {
   if (st != PSATD_OK) {
     for (int k = 0; k < 4; ++k) p->cfg_log_tb[k] = -1;
     p->cfg_push_tb = -1;
+    p->cfg_push_groups = -1;
     if (p->push_ept != saved_ept) {
       p->push_ept = saved_ept;
       regen_push_twiddles(p);
@@ -821,14 +872,15 @@ psatd_status autotune(psatd_plan p, int reps, std::string* report) {
     }
   }
   size_t b = std::min_element(tpush.begin(), tpush.end()) - tpush.begin();
-  best.push_ept = push[b].first;
-  best.push_tb = push[b].second;
+  best.push_ept = push[b].ept;
+  best.push_tb = push[b].tb;
+  best.push_groups = push[b].groups;
   if (report) {
     std::snprintf(buf, sizeof buf, "push L=%d:", Ll);
     *report += buf;
     for (size_t i = 0; i < push.size(); ++i) {
-      std::snprintf(buf, sizeof buf, " radix%d tb=%d %.4fms%s", push[i].first, push[i].second, tpush[i],
-                    i == b ? "*" : "");
+      std::snprintf(buf, sizeof buf, " radix%d tb=%d g=%d %.4fms%s", push[i].ept, push[i].tb, push[i].groups,
+                    tpush[i], i == b ? "*" : "");
       *report += buf;
     }
   }
@@ -880,9 +932,11 @@ static psatd_status plan_create_n(const psatd_desc* desc, void* cuda_stream, int
   {
     const int L = (int)(p->ndim == 3 ? p->nz : p->ny);
     const size_t csz = p->f32 ? 8 : 16;
-    const size_t need = ((size_t)p->n_in + 1) * (size_t)L * csz;
+    const size_t need = push_smem(p->n_in, L, 1, 1, csz);
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+    p->maxsm = maxsm;
+    cudaDeviceGetAttribute(&p->sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, p->device);
     if (maxsm > 0 && need > (size_t)maxsm) {
       psatd_status r = fail(nullptr, PSATD_ERR_UNSUPPORTED,
                             "last-axis length %d with %d components needs %zu bytes of shared memory (> %d)", L,
@@ -1034,12 +1088,48 @@ psatd_status psatd_plan_set_launch(psatd_plan p, const int32_t cfg[6]) {
     c.push_ept = cfg[5];
   }
   bool ok = false;
-  for (auto& pt : ts.push) ok |= pt.first == c.push_ept && (cfg[4] < 0 || pt.second == cfg[4]);
+  for (auto& pt : ts.push) ok |= pt.ept == c.push_ept && (cfg[4] < 0 || pt.tb == cfg[4]);
   if (!ok) return fail(p, PSATD_ERR_INVALID_ARG, "fused pass: %d elements per thread and %d lines per CTA not valid",
                        c.push_ept, cfg[4]);
   c.push_tb = cfg[4];
+  c.push_groups = p->cfg_push_groups;  // kept; psatd_plan_set_push_groups checks it against the new shape
   apply_cfg(p, c);
   return regen_push_twiddles(p);
+}
+
+psatd_status psatd_plan_set_push_groups(psatd_plan p, int32_t groups) {
+  if (!p) return fail(nullptr, PSATD_ERR_INVALID_ARG, "plan is NULL");
+  if (groups < 0) {
+    p->cfg_push_groups = -1;
+    return PSATD_OK;
+  }
+  const int64_t nlines = p->ndim == 3 ? p->nxh * p->ny : p->nxh * p->npatch;
+  const int Ll = (int)(p->ndim == 3 ? p->nz : p->ny);
+  const int tb = p->cfg_push_tb > 0 ? p->cfg_push_tb : push_lines_per_cta(Ll, p->n_in, nlines, p->tc, p->f32, p->push_ept);
+  int maxsm = 0;
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+  const size_t csz = p->f32 ? 8 : 16;
+  const size_t smem = (p->tc ? (size_t)kTcTail : 0) + push_smem(p->n_in, Ll, tb, groups, csz);
+  if (!push_groups_ok(Ll, p->push_ept, tb, groups, p->tc, p->f32) || (maxsm > 0 && smem > (size_t)maxsm))
+    return fail(p, PSATD_ERR_INVALID_ARG,
+                "fused pass: %d component groups not valid with %d-point lines, %d elements per thread, "
+                "%d lines per CTA and this precision",
+                groups, Ll, p->push_ept, tb);
+  p->cfg_push_groups = groups;
+  return PSATD_OK;
+}
+
+psatd_status psatd_plan_get_push_groups(psatd_plan p, int32_t* groups) {
+  if (!p || !groups) return fail(p, PSATD_ERR_INVALID_ARG, "plan or groups is NULL");
+  const int64_t nlines = p->ndim == 3 ? p->nxh * p->ny : p->nxh * p->npatch;
+  const int Ll = (int)(p->ndim == 3 ? p->nz : p->ny);
+  const int tb = p->cfg_push_tb > 0 ? p->cfg_push_tb : push_lines_per_cta(Ll, p->n_in, nlines, p->tc, p->f32, p->push_ept);
+  int G = p->cfg_push_groups > 0 ? p->cfg_push_groups
+                                 : push_groups_default(Ll, p->push_ept, tb, p->n_in, p->tc, p->f32, p->f32 ? 8 : 16,
+                                                       p->maxsm, p->sm_bytes);
+  if (!push_groups_ok(Ll, p->push_ept, tb, G, p->tc, p->f32)) G = 1;
+  *groups = G;
+  return PSATD_OK;
 }
 
 psatd_status psatd_plan_get_launch(psatd_plan p, int32_t cfg[6]) {
@@ -1343,7 +1433,9 @@ extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_f
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int L = (int)(p.ndim == 3 ? p.nz : p.ny);
-    const size_t smem = ((size_t)p.n_in + 1) * (size_t)L * csz;
+    const size_t smem = push_smem(p.n_in, L, 1, 1, csz);
+    p.maxsm = maxsm;
+    cudaDeviceGetAttribute(&p.sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (maxsm > 0 && smem > (size_t)maxsm)
       return fail(nullptr, PSATD_ERR_UNSUPPORTED, "last-axis length %d needs %zu bytes of shared memory", L, smem);
   }
@@ -1444,7 +1536,7 @@ struct psatd_batch_s {
   // Persistent mode (persist.cuh): per pass type and length family (0 powers of two,
   // 1 the 3 * 2^k lengths) one launch over every class's work items.
   bool persist_ok = false;   // every class has lengths the persistent passes take
-  bool persist = false;      // in use (default when persist_ok)
+  bool persist = false;      // in use (psatd_batch_set_persistent; off by default)
   void* d_xf = nullptr;      // XClassArgs per class: x forward, x inverse
   void* d_xi = nullptr;
   void* d_push = nullptr;    // PushArgs<float> per class
@@ -1909,6 +2001,23 @@ extern "C" psatd_status psatd_batch_set_persistent(psatd_batch b, int32_t enable
   b->gexec = nullptr;
   b->graph = nullptr;
   b->persist = enable != 0;
+  return PSATD_OK;
+}
+
+extern "C" psatd_status psatd_batch_set_push_groups(psatd_batch b, int32_t groups) {
+  if (!b) return fail(nullptr, PSATD_ERR_INVALID_ARG, "batch is NULL");
+  if (groups == 0 || groups > 4 || groups == 3)
+    return fail(nullptr, PSATD_ERR_INVALID_ARG, "component groups must be 1, 2, 4 or -1 (got %d)", groups);
+  cudaError_t e = cudaStreamSynchronize(b->st);
+  for (cudaStream_t st : b->br)
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "stream synchronise");
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  for (psatd_plan p : b->cls)
+    if (groups < 0 || psatd_plan_set_push_groups(p, groups) != PSATD_OK) p->cfg_push_groups = groups < 0 ? -1 : 1;
   return PSATD_OK;
 }
 

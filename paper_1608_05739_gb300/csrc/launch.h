@@ -30,7 +30,7 @@ cudaError_t launch_inv_T(int L, bool c2r, const PassGeom& g, cudaStream_t st, co
                          int64_t out_sb, const int64_t* a0_off = nullptr);
 // EPT: 8 or 16 elements per thread (radix-8 / radix-16 stages); TC needs 16.
 template <typename R, int TC, int EPT>
-cudaError_t launch_line_push(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
+cudaError_t launch_line_push(int L, int layout, dim3 grid, int tb, int groups, size_t smem, cudaStream_t st,
                              const PushArgs<R>& a, const void* tw);
 
 // the same passes for the mixed lengths L = 3 * 2^k (48..3072; R2C / C2R up to 1536), float only
@@ -43,7 +43,7 @@ cudaError_t launch_inv_T3(int L, bool c2r, const PassGeom& g, cudaStream_t st, c
                           int64_t in_sa0, int64_t in_sk, int64_t out_sa0, int64_t out_sb,
                           const int64_t* a0_off = nullptr);
 template <typename R>
-cudaError_t launch_line_push3(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
+cudaError_t launch_line_push3(int L, int layout, dim3 grid, int tb, int groups, size_t smem, cudaStream_t st,
                               const PushArgs<R>& a, const void* tw);
 
 // the same passes for the mixed lengths L = 5 * 2^k (80..1280), float only
@@ -56,7 +56,7 @@ cudaError_t launch_inv_T5(int L, bool c2r, const PassGeom& g, cudaStream_t st, c
                           int64_t in_sa0, int64_t in_sk, int64_t out_sa0, int64_t out_sb,
                           const int64_t* a0_off = nullptr);
 template <typename R>
-cudaError_t launch_line_push5(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
+cudaError_t launch_line_push5(int L, int layout, dim3 grid, int tb, int groups, size_t smem, cudaStream_t st,
                               const PushArgs<R>& a, const void* tw);
 
 // Persistent batch passes (persist.cuh): FAM 0 power-of-two lengths, 1 the 3 * 2^k

@@ -60,19 +60,32 @@ static cudaError_t inv_T_L(bool c2r, const PassGeom& g, cudaStream_t st, const L
 }
 
 template <typename R, int TC, int EPT, int L>
-static cudaError_t push_L(int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
+static cudaError_t push_L(int layout, dim3 grid, int tb, int groups, size_t smem, cudaStream_t st,
                           const PushArgs<R>& a, const void* tw) {
   typedef typename Types<R>::W W;
   if constexpr (L < EPT) {
     return cudaErrorInvalidValue;
   } else {
-    const dim3 block(FFTPlan<L, EPT>::kT, tb);
+    const dim3 block(FFTPlan<L, EPT>::kT, tb, groups);
+    // component groups: their own instantiation, for whole-warp lines in FP32 without
+    // tensor-core stages (the host admits groups > 1 nowhere else)
+    constexpr bool kGrpOk = !TC && sizeof(R) == 4 && FFTPlan<L, EPT>::kT % 32 == 0;
+    if (groups > 1 && !kGrpOk) return cudaErrorInvalidValue;
     cudaError_t e;
-#define PSATD_PUSH_CASE(LAY)                                                   \
-  case LAY: {                                                                  \
-    auto kern = k_line_push<R, L, LAY, TC, EPT>;                               \
+#define PSATD_PUSH_LAUNCH(LAY, GRP)                                            \
+  {                                                                            \
+    auto kern = k_line_push<R, L, LAY, TC, EPT, GRP>;                          \
     if ((e = set_smem(kern, smem)) != cudaSuccess) return e;                   \
     kern<<<grid, block, smem, st>>>(a, static_cast<const W*>(tw));             \
+  }
+#define PSATD_PUSH_CASE(LAY)                                                   \
+  case LAY: {                                                                  \
+    if constexpr (kGrpOk) {                                                    \
+      if (groups > 1) PSATD_PUSH_LAUNCH(LAY, true)                             \
+      else PSATD_PUSH_LAUNCH(LAY, false)                                       \
+    } else {                                                                   \
+      PSATD_PUSH_LAUNCH(LAY, false)                                            \
+    }                                                                          \
     break;                                                                     \
   }
     switch (layout) {
@@ -84,6 +97,7 @@ static cudaError_t push_L(int layout, dim3 grid, int tb, size_t smem, cudaStream
         return cudaErrorInvalidValue;
     }
 #undef PSATD_PUSH_CASE
+#undef PSATD_PUSH_LAUNCH
     return cudaGetLastError();
   }
 }
@@ -140,14 +154,14 @@ cudaError_t launch_inv_T5(int L, bool c2r, const PassGeom& g, cudaStream_t st, c
   PSATD_L5_SWITCH(inv_T_L, c2r, g, st, io, tw, in_sa0, in_sk, out_sa0, out_sb, a0_off)
 }
 template <typename R>
-cudaError_t launch_line_push5(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
+cudaError_t launch_line_push5(int L, int layout, dim3 grid, int tb, int groups, size_t smem, cudaStream_t st,
                               const PushArgs<R>& a, const void* tw) {
   switch (L) {
-    case 80: return push_L<R, 0, 20, 80>(layout, grid, tb, smem, st, a, tw);
-    case 160: return push_L<R, 0, 20, 160>(layout, grid, tb, smem, st, a, tw);
-    case 320: return push_L<R, 0, 20, 320>(layout, grid, tb, smem, st, a, tw);
-    case 640: return push_L<R, 0, 20, 640>(layout, grid, tb, smem, st, a, tw);
-    case 1280: return push_L<R, 0, 20, 1280>(layout, grid, tb, smem, st, a, tw);
+    case 80: return push_L<R, 0, 20, 80>(layout, grid, tb, groups, smem, st, a, tw);
+    case 160: return push_L<R, 0, 20, 160>(layout, grid, tb, groups, smem, st, a, tw);
+    case 320: return push_L<R, 0, 20, 320>(layout, grid, tb, groups, smem, st, a, tw);
+    case 640: return push_L<R, 0, 20, 640>(layout, grid, tb, groups, smem, st, a, tw);
+    case 1280: return push_L<R, 0, 20, 1280>(layout, grid, tb, groups, smem, st, a, tw);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -163,16 +177,16 @@ cudaError_t launch_inv_T3(int L, bool c2r, const PassGeom& g, cudaStream_t st, c
   PSATD_L3_SWITCH(inv_T_L, c2r, g, st, io, tw, in_sa0, in_sk, out_sa0, out_sb, a0_off)
 }
 template <typename R>
-cudaError_t launch_line_push3(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
+cudaError_t launch_line_push3(int L, int layout, dim3 grid, int tb, int groups, size_t smem, cudaStream_t st,
                               const PushArgs<R>& a, const void* tw) {
   switch (L) {
-    case 48: return push_L<R, 0, 12, 48>(layout, grid, tb, smem, st, a, tw);
-    case 96: return push_L<R, 0, 12, 96>(layout, grid, tb, smem, st, a, tw);
-    case 192: return push_L<R, 0, 12, 192>(layout, grid, tb, smem, st, a, tw);
-    case 384: return push_L<R, 0, 12, 384>(layout, grid, tb, smem, st, a, tw);
-    case 768: return push_L<R, 0, 12, 768>(layout, grid, tb, smem, st, a, tw);
-    case 1536: return push_L<R, 0, 12, 1536>(layout, grid, tb, smem, st, a, tw);
-    case 3072: return push_L<R, 0, 12, 3072>(layout, grid, tb, smem, st, a, tw);
+    case 48: return push_L<R, 0, 12, 48>(layout, grid, tb, groups, smem, st, a, tw);
+    case 96: return push_L<R, 0, 12, 96>(layout, grid, tb, groups, smem, st, a, tw);
+    case 192: return push_L<R, 0, 12, 192>(layout, grid, tb, groups, smem, st, a, tw);
+    case 384: return push_L<R, 0, 12, 384>(layout, grid, tb, groups, smem, st, a, tw);
+    case 768: return push_L<R, 0, 12, 768>(layout, grid, tb, groups, smem, st, a, tw);
+    case 1536: return push_L<R, 0, 12, 1536>(layout, grid, tb, groups, smem, st, a, tw);
+    case 3072: return push_L<R, 0, 12, 3072>(layout, grid, tb, groups, smem, st, a, tw);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -192,30 +206,30 @@ cudaError_t launch_inv_T(int L, bool c2r, const PassGeom& g, cudaStream_t st, co
 }
 
 template <typename R, int TC, int EPT>
-static cudaError_t push_L_e(int layout, dim3 grid, int tb, size_t smem, cudaStream_t st, const PushArgs<R>& a,
-                            const void* tw, int L) {
+static cudaError_t push_L_e(int layout, dim3 grid, int tb, int groups, size_t smem, cudaStream_t st,
+                            const PushArgs<R>& a, const void* tw, int L) {
 #define PUSH_E(LL) push_L<R, TC, EPT, LL>
   switch (L) {
-    case 8: if constexpr (!TC) return PUSH_E(8)(layout, grid, tb, smem, st, a, tw);
+    case 8: if constexpr (!TC) return PUSH_E(8)(layout, grid, tb, groups, smem, st, a, tw);
             else return cudaErrorInvalidValue;
-    case 16: return PUSH_E(16)(layout, grid, tb, smem, st, a, tw);
-    case 32: return PUSH_E(32)(layout, grid, tb, smem, st, a, tw);
-    case 64: return PUSH_E(64)(layout, grid, tb, smem, st, a, tw);
-    case 128: return PUSH_E(128)(layout, grid, tb, smem, st, a, tw);
-    case 256: return PUSH_E(256)(layout, grid, tb, smem, st, a, tw);
-    case 512: return PUSH_E(512)(layout, grid, tb, smem, st, a, tw);
-    case 1024: return PUSH_E(1024)(layout, grid, tb, smem, st, a, tw);
-    case 2048: return PUSH_E(2048)(layout, grid, tb, smem, st, a, tw);
-    case 4096: return PUSH_E(4096)(layout, grid, tb, smem, st, a, tw);
+    case 16: return PUSH_E(16)(layout, grid, tb, groups, smem, st, a, tw);
+    case 32: return PUSH_E(32)(layout, grid, tb, groups, smem, st, a, tw);
+    case 64: return PUSH_E(64)(layout, grid, tb, groups, smem, st, a, tw);
+    case 128: return PUSH_E(128)(layout, grid, tb, groups, smem, st, a, tw);
+    case 256: return PUSH_E(256)(layout, grid, tb, groups, smem, st, a, tw);
+    case 512: return PUSH_E(512)(layout, grid, tb, groups, smem, st, a, tw);
+    case 1024: return PUSH_E(1024)(layout, grid, tb, groups, smem, st, a, tw);
+    case 2048: return PUSH_E(2048)(layout, grid, tb, groups, smem, st, a, tw);
+    case 4096: return PUSH_E(4096)(layout, grid, tb, groups, smem, st, a, tw);
     default: return cudaErrorInvalidValue;
   }
 #undef PUSH_E
 }
 
 template <typename R, int TC, int EPT>
-cudaError_t launch_line_push(int L, int layout, dim3 grid, int tb, size_t smem, cudaStream_t st,
+cudaError_t launch_line_push(int L, int layout, dim3 grid, int tb, int groups, size_t smem, cudaStream_t st,
                              const PushArgs<R>& a, const void* tw) {
-  return push_L_e<R, TC, EPT>(layout, grid, tb, smem, st, a, tw, L);
+  return push_L_e<R, TC, EPT>(layout, grid, tb, groups, smem, st, a, tw, L);
 }
 
 }  // namespace psatd

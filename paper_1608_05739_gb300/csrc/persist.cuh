@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kPersistThreads, 4) k_persist_push(const PushA
     constexpr int T = LL / EPT;                                                                            \
     line_push_body<R, LL, LAYOUT, TC, EPT>(A, static_cast<const W*>(tws[it.cls]), it.blk,                 \
                                            (int)threadIdx.x % T, (int)threadIdx.x / T, kPersistThreads / T, \
-                                           smem_raw, tc, sc);                                              \
+                                           0, 1, smem_raw, tc, sc);                                        \
   }
       PSATD_PERSIST_Y_LENGTHS(FAM, PSATD_Y_CASE)
 #undef PSATD_Y_CASE

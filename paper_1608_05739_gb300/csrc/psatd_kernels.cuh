@@ -742,10 +742,12 @@ __device__ __forceinline__ void stage_init(StageCtx& sc, uint64_t* mbar_word, in
 // sw<kLastCX>(l): PSATD reads the coefficient table (two modes per iteration,
 // both loads issued together), PSTD none; staggered plans rotate every slot
 // value to its Yee position and back around the update.
+// With G component groups (grp < G) the thread takes the modes m = grp + G i
+// (EPT / G of them, an even count) and the other groups' threads t the rest.
 template <typename R, int L, int LAYOUT, int EPT, bool STAG, bool PSTD>
 __device__ __forceinline__ void push_line_modes(typename Types<R>::C* st, int ss, const PushArgs<R>& a,
-                                                const Coef<R>* trow, int t, int mxi, int myi, R kpx, R kpy,
-                                                typename Types<R>::W phx, typename Types<R>::W phy) {
+                                                const Coef<R>* trow, int t, int grp, int G, int mxi, int myi,
+                                                R kpx, R kpy, typename Types<R>::W phx, typename Types<R>::W phy) {
   typedef typename Types<R>::W Wt;
   typedef FFTPlan<L, EPT> P;
   constexpr int T = P::kT;
@@ -756,17 +758,18 @@ __device__ __forceinline__ void push_line_modes(typename Types<R>::C* st, int ss
     if constexpr (!PSTD) return trow[(l <= L / 2) ? l : L - l];  // |m| along the line axis
     else return Coef<R>{};
   };
-  Coef<R> qn[2] = {coef(t), coef(t + T)};
+  const int nm = EPT / G;
+  Coef<R> qn[2] = {coef(t + T * grp), coef(t + T * (grp + G))};
 #pragma unroll 1
-  for (int m0 = 0; m0 < EPT; m0 += 2) {
+  for (int m0 = 0; m0 < nm; m0 += 2) {
     const Coef<R> q[2] = {qn[0], qn[1]};
-    if (m0 + 2 < EPT) {
-      qn[0] = coef(t + T * (m0 + 2));
-      qn[1] = coef(t + T * (m0 + 3));
+    if (m0 + 2 < nm) {
+      qn[0] = coef(t + T * (grp + G * (m0 + 2)));
+      qn[1] = coef(t + T * (grp + G * (m0 + 3)));
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int l = t + T * (m0 + h);
+      const int l = t + T * (grp + G * (m0 + h));
       CoefReg<R> f;
       f.C_h = q[h].C_h; f.C_l = q[h].C_l; f.S_h = q[h].S_h; f.S_l = q[h].S_l;
       f.A1 = q[h].A1; f.A4 = q[h].A4; f.B1 = q[h].B1; f.B2 = q[h].B2;
@@ -815,12 +818,24 @@ __device__ __forceinline__ void push_line_modes(typename Types<R>::C* st, int ss
 // touch each thread's own positions.
 // EPT: elements per thread, 8 (radix-8 stages) or 16 (radix-16 stages; the
 // only choice of the tensor-core variant).
+// Component groups (G > 1, T a multiple of 32, no tensor-core stages): each
+// line has G x T threads; group grp transforms the input components c = grp,
+// grp + G, ... and the output components c = G - 1 - grp, 2G - 1 - grp, ...
+// (the groups with an extra forward transform get one fewer inverse one), with
+// its own second exchange buffer per line and its own named barrier (id
+// 1 + g G + grp over its T threads), so that the groups run side by side; the
+// whole CTA meets at a block barrier before and after the push, in which the
+// groups split each thread position's modes.  G = 1 is the plain pass (block
+// barriers throughout, as the tensor-core stages need).
 // Body of one CTA of the fused pass: line block bx (lines bx tb .. bx tb + tb - 1,
-// line g of the block handled by the threads g T .. g T + T - 1, t their position).
-template <typename R, int L, int LAYOUT, int TC, int EPT>
+// line g of the block handled by the threads g T .. g T + T - 1 of each
+// component group, t their position).
+// GRP: the component-group variant (a kernel of its own, so that the plain pass
+// compiles with G = 1 as a constant).
+template <typename R, int L, int LAYOUT, int TC, int EPT, bool GRP = false>
 __device__ __forceinline__ void line_push_body(const PushArgs<R>& a_in, const typename Types<R>::W* __restrict__ tw,
-                                               int bx, int t, int g, int tb, unsigned char* smem_raw, TcCtx& tc,
-                                               StageCtx& sc) {
+                                               int bx, int t, int g, int tb, int grp, int G, unsigned char* smem_raw,
+                                               TcCtx& tc, StageCtx& sc) {
   // a private copy: its scalars stay in registers through the shared-memory stores of the transforms
   const PushArgs<R> a = a_in;
   typedef typename Types<R>::C C;
@@ -828,6 +843,11 @@ __device__ __forceinline__ void line_push_body(const PushArgs<R>& a_in, const ty
   typedef FFTPlan<L, EPT> P;
   constexpr int T = P::kT;
   constexpr int CXL = P::kLastCX;
+  static_assert(!GRP || (!TC && T % 32 == 0), "component groups need whole-warp lines and no tensor-core stages");
+  if constexpr (!GRP) {  // the plain pass
+    grp = 0;
+    G = 1;
+  }
   const int line = bx * tb + g;
   const bool valid = line < a.nlines;
   if (a.tab_ext) {  // checked mode: the line's columns of every slot and its coefficient row
@@ -840,10 +860,18 @@ __device__ __forceinline__ void line_push_body(const PushArgs<R>& a_in, const ty
   C* base = reinterpret_cast<C*>(smem_raw + (TC ? kTcTail : 0));
   const int ss = tb * L;               // slot stride (component-major)
   C* st = base + g * L;                // this line's slot 0; slot c at st + c * ss
-  C* bufB = base + a.n_in * ss + g * L;
+  C* bufB = base + a.n_in * ss + (grp * tb + g) * L;  // this group's second exchange buffer
   C* spec = static_cast<C*>(a.spec);
   __shared__ const void* twslot;
-  if (t == 0 && g == 0) twslot = tw;
+  if (t == 0 && g == 0 && grp == 0) twslot = tw;
+  // exchange barrier of this line's group: the block's (G = 1), else a named one.
+  // Only kernels whose lines have whole warps (T a multiple of 32) contain the
+  // named barrier at all: its thread count must be a multiple of the warp size.
+  int bar_id = 0, bar_n = 0;
+  if constexpr (GRP) {
+    bar_id = 1 + g * G + grp;
+    bar_n = T;
+  }
   if constexpr (TC) tc.a_tile = smem_u32(base + a.n_in * ss);  // split-BF16's third A piece: per component below
 
   int mxi, myi, rowi;
@@ -859,7 +887,7 @@ __device__ __forceinline__ void line_push_body(const PushArgs<R>& a_in, const ty
   // the push needs EPT coefficient entries per thread: start bringing them
   // into L2 now, so that its loads do not wait on DRAM one mode after another
 #pragma unroll
-  for (int m = 0; m < EPT; ++m) {
+  for (int m = grp; m < EPT; m += G) {
     const int l = t + T * m;
     asm volatile("prefetch.global.L2 [%0];" ::"l"(trow + ((l <= L / 2) ? l : L - l)));
   }
@@ -873,13 +901,13 @@ __device__ __forceinline__ void line_push_body(const PushArgs<R>& a_in, const ty
       constexpr int CH = (L * (int)sizeof(C)) / 16;  // 16-byte chunks per slot
       for (int c = 0; c < a.n_in; ++c) {
         float4* dst = reinterpret_cast<float4*>(st + c * ss);
-        for (int i = t; i < CH; i += T) dst[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = t + grp * T; i < CH; i += G * T) dst[i] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     const int line0 = bx * tb;
     const int nv = a.nlines - line0 < tb ? a.nlines - line0 : tb;  // valid lines of the block
     __syncthreads();
-    if (t == 0 && g == 0) {
+    if (t == 0 && g == 0 && grp == 0) {
       constexpr uint32_t bytes = (uint32_t)(L * sizeof(C));
       fence_async_smem();
       mbar_arrive_expect_tx(sc.mbar, (uint32_t)(nv * a.n_in) * bytes);
@@ -897,12 +925,12 @@ __device__ __forceinline__ void line_push_body(const PushArgs<R>& a_in, const ty
     sc.phase ^= 1u;
   }
   C v[EPT];
-  for (int c = 0; c < a.n_in; ++c) {
+  for (int c = grp; c < a.n_in; c += G) {
     C* sl = st + c * ss;
 #pragma unroll
     for (int m = 0; m < EPT; ++m) v[m] = sl[t + T * m];
-    __syncthreads();  // the slot becomes an exchange buffer
-    ExBuf<C> ex{{sl, bufB}, 0, &twslot, false};
+    ExBuf<C> ex{{sl, bufB}, 0, &twslot, false, bar_id, bar_n};
+    ex.sync();  // the slot becomes an exchange buffer
     if constexpr (TC) tc.a_tile3 = smem_u32(base + c * ss);
     if constexpr (TC == 0 && (EPT == 8 || EPT == 12))
       block_fft_fwd_pf<R, L, EPT>(v, ex, t);
@@ -911,22 +939,28 @@ __device__ __forceinline__ void line_push_body(const PushArgs<R>& a_in, const ty
 #pragma unroll
     for (int m = 0; m < EPT; ++m) sl[sw<CXL>(t + T * m)] = v[m];
   }
+  if (G > 1) __syncthreads();  // every group's spectra are in their slots
 
   // push every mode of the line (each thread its own positions); one loop per
   // (staggered?, PSTD?) combination, chosen once per CTA
   if (a.scheme == 0) {
-    if (a.stag) push_line_modes<R, L, LAYOUT, EPT, true, false>(st, ss, a, trow, t, mxi, myi, kpx, kpy, phx, phy);
-    else push_line_modes<R, L, LAYOUT, EPT, false, false>(st, ss, a, trow, t, mxi, myi, kpx, kpy, phx, phy);
+    if (a.stag)
+      push_line_modes<R, L, LAYOUT, EPT, true, false>(st, ss, a, trow, t, grp, G, mxi, myi, kpx, kpy, phx, phy);
+    else
+      push_line_modes<R, L, LAYOUT, EPT, false, false>(st, ss, a, trow, t, grp, G, mxi, myi, kpx, kpy, phx, phy);
   } else {
-    if (a.stag) push_line_modes<R, L, LAYOUT, EPT, true, true>(st, ss, a, trow, t, mxi, myi, kpx, kpy, phx, phy);
-    else push_line_modes<R, L, LAYOUT, EPT, false, true>(st, ss, a, trow, t, mxi, myi, kpx, kpy, phx, phy);
+    if (a.stag)
+      push_line_modes<R, L, LAYOUT, EPT, true, true>(st, ss, a, trow, t, grp, G, mxi, myi, kpx, kpy, phx, phy);
+    else
+      push_line_modes<R, L, LAYOUT, EPT, false, true>(st, ss, a, trow, t, grp, G, mxi, myi, kpx, kpy, phx, phy);
   }
+  if (G > 1) __syncthreads();  // every mode is pushed
 
-  for (int c = 0; c < a.n_out; ++c) {
+  for (int c = G - 1 - grp; c < a.n_out; c += G) {
     C* sl = st + c * ss;
 #pragma unroll
     for (int m = 0; m < EPT; ++m) v[m] = sl[sw<CXL>(t + T * m)];
-    ExBuf<C> ex{{sl, bufB}, 0, &twslot, false};
+    ExBuf<C> ex{{sl, bufB}, 0, &twslot, false, bar_id, bar_n};
     if constexpr (TC) tc.a_tile3 = smem_u32(base + c * ss);
     if constexpr (TC == 0 && (EPT == 8 || EPT == 12))
       block_fft_inv_pf<R, L, EPT>(v, ex, t);
@@ -940,8 +974,10 @@ __device__ __forceinline__ void line_push_body(const PushArgs<R>& a_in, const ty
   }
 }
 
-template <typename R, int L, int LAYOUT, int TC = 0, int EPT = PushEPT<L, TC>::value>
-__global__ void __launch_bounds__(FFTPlan<L, EPT>::kT > 256 ? FFTPlan<L, EPT>::kT : 256)
+// Block (T, lines per CTA, component groups); the group variant (GRP) takes up
+// to 512 threads, the plain pass 256 (or T).
+template <typename R, int L, int LAYOUT, int TC = 0, int EPT = PushEPT<L, TC>::value, bool GRP = false>
+__global__ void __launch_bounds__(GRP ? 512 : (FFTPlan<L, EPT>::kT > 256 ? FFTPlan<L, EPT>::kT : 256))
 k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t stage_mbar;
@@ -950,8 +986,8 @@ k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {
   TcCtx tc;
   if constexpr (TC) tc_setup(tc, smem_raw, a.gmat, 0u, a.err, TC == 2, 0u, a.tc_ctl);  // has a block barrier
   else __syncthreads();  // the stage mbarrier is initialised
-  line_push_body<R, L, LAYOUT, TC, EPT>(a, tw, (int)blockIdx.x, (int)threadIdx.x, (int)threadIdx.y, (int)blockDim.y,
-                                        smem_raw, tc, sc);
+  line_push_body<R, L, LAYOUT, TC, EPT, GRP>(a, tw, (int)blockIdx.x, (int)threadIdx.x, (int)threadIdx.y,
+                                             (int)blockDim.y, (int)threadIdx.z, (int)blockDim.z, smem_raw, tc, sc);
   if constexpr (TC) tc_teardown(tc);
 }
 

@@ -4,6 +4,6 @@
 #include "launch_impl.cuh"
 
 namespace psatd {
-template cudaError_t launch_line_push<double, false, 16>(int, int, dim3, int, size_t, cudaStream_t,
+template cudaError_t launch_line_push<double, false, 16>(int, int, dim3, int, int, size_t, cudaStream_t,
                                                    const PushArgs<double>&, const void*);
 }  // namespace psatd

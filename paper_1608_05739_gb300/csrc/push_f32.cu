@@ -2,7 +2,7 @@
 #include "launch_impl.cuh"
 
 namespace psatd {
-template cudaError_t launch_line_push<float, false, 8>(int, int, dim3, int, size_t, cudaStream_t,
+template cudaError_t launch_line_push<float, false, 8>(int, int, dim3, int, int, size_t, cudaStream_t,
                                               const PushArgs<float>&, const void*);
 
 }  // namespace psatd

@@ -3,6 +3,6 @@
 #include "launch_impl.cuh"
 
 namespace psatd {
-template cudaError_t launch_line_push<float, 2, 16>(int, int, dim3, int, size_t, cudaStream_t,
+template cudaError_t launch_line_push<float, 2, 16>(int, int, dim3, int, int, size_t, cudaStream_t,
                                                     const PushArgs<float>&, const void*);
 }  // namespace psatd
