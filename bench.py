@@ -346,10 +346,12 @@ def batch_e2e(torch, b, Jhost, stream, nsteps):
     return out[0], out[1]
 
 
-def roofline_of(ktimes, bytes_of, hbm, peak_kind, traffic_lookup=True, note=None):
+def roofline_of(ktimes, bytes_of, hbm, peak_kind, traffic_lookup=True, note=None, traffic_prefix=""):
     """Roofline object of the kernel with the largest summed time: the algorithmic
     bytes of its timed launches (bytes_of(kernel, launches)) over their summed
-    CUDA-event time, against `hbm`."""
+    CUDA-event time, against `hbm`.  `traffic`: the stored ncu DRAM bytes per launch
+    of that kernel (entry `traffic_prefix` + kernel name in profiles/dram_traffic.json)
+    while the CUDA sources are unchanged since the capture, else null."""
     if not ktimes:
         return None
     dom = max(ktimes, key=lambda k: ktimes[k][1])
@@ -360,7 +362,7 @@ def roofline_of(ktimes, bytes_of, hbm, peak_kind, traffic_lookup=True, note=None
     if traffic_lookup:
         try:
             tr = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
-            ent = tr.get(dom)
+            ent = tr.get(traffic_prefix + dom)
             if ent and ent.get("source_hash") == source_hash():
                 traffic = ent["bytes_per_launch"]
         except Exception:
@@ -493,7 +495,9 @@ def run_batch_line(args, world, rank, local):
                   "launch's bytes are the whole batch's for that pass" if launches_per_step <= 6 else
                   "the size classes' kernels run side by side on the batch's branch streams, so each launch's "
                   "duration includes time shared with other classes' kernels")
-    roof = roofline_of(kt_s, lambda k, n: alg_b[k], hbm, peak_kind, traffic_lookup=False,
+    roof = roofline_of(kt_s, lambda k, n: alg_b[k], hbm, peak_kind,
+                       traffic_lookup=(prec == "mixed_bf16" and len(sizes) == 512),
+                       traffic_prefix="batch_",
                        note="the size classes one after another (%.3f ms per step; %.3f forked, the line's value): each "
                             "launch's own duration; the pass's launches over every class of one step" % (ms_s / K, ms / K))
     roof["forked_per_kernel_ms_summed"] = {k: v[1] for k, v in kt.items()}
