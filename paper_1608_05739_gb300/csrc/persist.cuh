@@ -85,13 +85,14 @@ struct PersistRows {
 };
 
 // Transposing x pass (forward R2C or inverse C2R) over every class of the queue.
-// Register caps of the persistent passes (CTAs of kPersistThreads threads that
-// must stay resident together), as their standalone kernels: the transposing
-// passes 64 registers (128 for the 3 * 2^k lengths, 24 elements per thread);
-// the fused pass 128 (the tensor-core variant is held to two CTAs per SM by
-// its shared memory anyway).
+// Register caps of the persistent passes (CTAs that must stay resident together),
+// as their standalone kernels: the SIMT transposing passes 64 registers (128 for
+// the 3 * 2^k lengths, 24 elements per thread), the tensor-core ones 128 (at 64
+// their 16-element rows and split pieces went to the stack); the SIMT fused pass
+// 128, the tensor-core one up to 255 (two CTAs per SM, as its shared memory allows
+// anyway; with every line length in one kernel it spilled at 128).
 template <typename R, int TC, int FAM, bool FWD>
-__global__ void __launch_bounds__(kPersistXThreads, FAM ? 2 : 4) k_persist_x(const XClassArgs* __restrict__ cls, PersistQueue q) {
+__global__ void __launch_bounds__(kPersistXThreads, (FAM || TC) ? 2 : 4) k_persist_x(const XClassArgs* __restrict__ cls, PersistQueue q) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int slot;
   __shared__ __align__(16) XClassArgs A;
@@ -133,7 +134,7 @@ __global__ void __launch_bounds__(kPersistXThreads, FAM ? 2 : 4) k_persist_x(con
 // Fused last-axis pass over every class of the queue (PushArgs per class; the
 // line length is 2 (tab_row - 1)).
 template <typename R, int TC, int FAM, int LAYOUT>
-__global__ void __launch_bounds__(kPersistThreads, 4) k_persist_push(const PushArgs<R>* __restrict__ cls,
+__global__ void __launch_bounds__(kPersistThreads, TC ? 2 : 4) k_persist_push(const PushArgs<R>* __restrict__ cls,
                                                                   const void* const* __restrict__ tws,
                                                                   PersistQueue q) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

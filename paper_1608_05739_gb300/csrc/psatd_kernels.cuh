@@ -247,6 +247,9 @@ __device__ __forceinline__ void fwd_T_body(const LineIO& io, const typename Type
   }
 }
 
+// Launch bounds: two CTAs of the largest block per SM (at most 64 registers a
+// thread).  The tensor-core variants then keep part of each row on the stack,
+// but measured faster so than with 128 registers and half the resident warps.
 template <typename R, int L, bool R2C, int TC = 0>
 __global__ void __launch_bounds__(RowThreads<R, L>::value, 2) k_fwd_T(LineIO io, const typename Types<R>::W* __restrict__ tw,
                                                int64_t in_sa0, int64_t in_sb, int64_t out_sa0,
