@@ -240,7 +240,10 @@ psatd_status psatd_plan_get_launch(psatd_plan plan, int32_t cfg[6]);
  * components in turn (group j: components j, j + G, ...; their own exchange
  * buffer and barrier each), meeting for the per-mode push; shared memory per
  * line grows from (n_in + 1) to (n_in + G) line buffers.  G = 1 is the plain
- * pass.  Valid: 1 always; 2 or 4 for PSATD_FP32 plans whose fused-axis lines
+ * pass.  Tensor-core plans (PSATD_MIXED_*): 2 only, two 128-row groups that
+ * transform component pairs in lockstep and share every tensor-core round
+ * (measured slower than one group on GB300; kept as a launch shape).
+ * Valid otherwise: 1 always; 2 or 4 for PSATD_FP32 plans whose fused-axis lines
  * have a multiple of 32 threads (length / elements per thread), at most 512
  * threads and 15 groups per CTA, an even number of modes per thread, and the
  * shared memory within the device's limit.  -1: the built-in choice, 2 where

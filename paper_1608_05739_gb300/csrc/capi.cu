@@ -342,16 +342,22 @@ int push_lines_per_cta(int L, int n_in, int64_t nlines, bool tc, bool f32, int e
 // tensor-core stages whose lines have a multiple of 32 threads (named barriers
 // per group: at most 15 per CTA; at most 512 threads; an even number of modes
 // per thread in the push).
+// Tensor-core plans take G = 2 only: component pairs in lockstep, one 128-row
+// MMA group each (256 threads).
 bool push_groups_ok(int L, int ept, int tb, int G, bool tc, bool f32) {
   if (G == 1) return true;
-  if (tc || !f32 || (G != 2 && G != 4) || L < ept) return false;
+  if (L < ept) return false;
   const int T = L / ept;
+  if (tc) return G == 2 && ept == 16 && T * tb == 128;
+  if (!f32 || (G != 2 && G != 4)) return false;
   return T % 32 == 0 && (ept / G) % 2 == 0 && T * tb * G <= 512 && tb * G <= 15;
 }
 // shared memory of the fused pass: per line the n_in slots and one second
-// exchange buffer per group (split-BF16's third A piece sits in a slot)
-size_t push_smem(int n_in, int L, int tb, int G, size_t csz) {
-  return (size_t)tb * ((size_t)n_in + (size_t)G) * (size_t)L * csz;
+// exchange buffer per group (split-BF16's third A piece sits in a slot); the
+// tensor-core pairs exchange in their own slots and keep the one spare buffer
+// for the third A pieces
+size_t push_smem(int n_in, int L, int tb, int G, size_t csz, bool tc = false) {
+  return (size_t)tb * ((size_t)n_in + (size_t)(tc ? 1 : G)) * (size_t)L * csz;
 }
 // The built-in choice (measured on GB300 against the plain pass): two groups
 // where lines have at least 64 threads and the plain pass keeps fewer than 12
@@ -560,7 +566,7 @@ psatd_status run_step(psatd_plan p, const void* in[kMaxComp], void* out[kMaxComp
                   ? p->cfg_push_groups
                   : push_groups_default(Lline, p->push_ept, tb, p->n_in, TC, p->f32, csz, p->maxsm, p->sm_bytes);
       if (!push_groups_ok(Lline, p->push_ept, tb, G, TC, p->f32)) G = 1;
-      const size_t smem = tail + push_smem(p->n_in, Lline, tb, G, csz);
+      const size_t smem = tail + push_smem(p->n_in, Lline, tb, G, csz, TC);
       const dim3 grid((unsigned)((nlines + tb - 1) / tb));
       TimedLaunch tl(p, K_PUSH);
       if (p->push_ept == 12 || p->push_ept == 20) {
@@ -745,7 +751,7 @@ TuneSpace tune_space(psatd_plan p) {
       if (tb > 1 && tb / 2 >= nlines) break;
       for (int G : {1, 2, 4}) {
         if (!push_groups_ok(ts.Ll, ept, tb, G, p->tc, p->f32)) continue;
-        if (maxsm > 0 && tail + push_smem(p->n_in, ts.Ll, tb, G, csz) > (size_t)maxsm) continue;
+        if (maxsm > 0 && tail + push_smem(p->n_in, ts.Ll, tb, G, csz, p->tc) > (size_t)maxsm) continue;
         ts.push.push_back({ept, tb, G});
       }
     }
@@ -1109,7 +1115,7 @@ psatd_status psatd_plan_set_push_groups(psatd_plan p, int32_t groups) {
   int maxsm = 0;
   cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
   const size_t csz = p->f32 ? 8 : 16;
-  const size_t smem = (p->tc ? (size_t)kTcTail : 0) + push_smem(p->n_in, Ll, tb, groups, csz);
+  const size_t smem = (p->tc ? (size_t)kTcTail : 0) + push_smem(p->n_in, Ll, tb, groups, csz, p->tc);
   if (!push_groups_ok(Ll, p->push_ept, tb, groups, p->tc, p->f32) || (maxsm > 0 && smem > (size_t)maxsm))
     return fail(p, PSATD_ERR_INVALID_ARG,
                 "fused pass: %d component groups not valid with %d-point lines, %d elements per thread, "

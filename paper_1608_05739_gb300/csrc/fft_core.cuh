@@ -465,10 +465,13 @@ __device__ __forceinline__ const typename Types<R>::W* stage_tw(const ExBuf<C>& 
 // keeps W_L^(r k L/(Ns R)) at [tw_off(s) + (r-1) Ns + k], k < Ns, 1 <= r < R,
 // so the threads of a warp read consecutive entries.
 
-// One forward stage.
+// One forward stage.  act = false: the thread only takes part in the stage's
+// barriers (and tensor-core rounds), touching no exchange memory (a component
+// group with no component to transform while the other group has one).
 template <typename R, int L, int EPT, int S, int TC>
 __device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
-                                          const typename Types<R>::W* __restrict__ tw, int t, TcCtx* tc) {
+                                          const typename Types<R>::W* __restrict__ tw, int t, TcCtx* tc,
+                                          bool act = true) {
   typedef typename Types<R>::C C;
   typedef FFTPlan<L, EPT> P;
   constexpr int RS = P::radix(S), NS = P::span(S), Q = EPT / RS, T = P::kT;
@@ -485,16 +488,18 @@ __device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[EPT], ExBuf<
 #pragma unroll
     for (int r = 0; r < RS; ++r) a[r] = v[q + r * Q];
     if constexpr (NS > 1) {
-      const typename Types<R>::W* tws = stage_tw<R>(ex) + P::tw_off(S) + k;
+      if (act) {
+        const typename Types<R>::W* tws = stage_tw<R>(ex) + P::tw_off(S) + k;
 #pragma unroll
-      for (int r = 1; r < RS; ++r) a[r] = twmul(a[r], __ldg(&tws[(r - 1) * NS]));
+        for (int r = 1; r < RS; ++r) a[r] = twmul(a[r], __ldg(&tws[(r - 1) * NS]));
+      }
     }
-    if constexpr (TC && RS == 16) tc_dft<16, false, TC == 2>(a, *tc);
-    else butterfly<RS, false>(a);
+    if constexpr (TC && RS == 16) tc_dft<16, false, TC == 2>(a, *tc, act);
+    else if (act) butterfly<RS, false>(a);
     if constexpr (LAST) {
 #pragma unroll
       for (int r = 0; r < RS; ++r) v[q + r * Q] = a[r];
-    } else {
+    } else if (act) {
       const int base = (j - k) * RS + k;
 #pragma unroll
       for (int r = 0; r < RS; ++r) buf[sw<CX>(base + r * NS)] = a[r];
@@ -502,15 +507,18 @@ __device__ __forceinline__ void fwd_stage(typename Types<R>::C (&v)[EPT], ExBuf<
   }
   if constexpr (!LAST) {
     ex.sync();
+    if (act) {
 #pragma unroll
-    for (int m = 0; m < EPT; ++m) v[m] = buf[sw<CX>(t + T * m)];
+      for (int m = 0; m < EPT; ++m) v[m] = buf[sw<CX>(t + T * m)];
+    }
   }
 }
 
 // Adjoint of fwd_stage<S>.
 template <typename R, int L, int EPT, int S, int TC>
 __device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
-                                          const typename Types<R>::W* __restrict__ tw, int t, TcCtx* tc) {
+                                          const typename Types<R>::W* __restrict__ tw, int t, TcCtx* tc,
+                                          bool act = true) {
   typedef typename Types<R>::C C;
   typedef FFTPlan<L, EPT> P;
   constexpr int RS = P::radix(S), NS = P::span(S), Q = EPT / RS, T = P::kT;
@@ -519,8 +527,10 @@ __device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[EPT], ExBuf<
   C* buf = nullptr;
   if constexpr (!FIRST) {
     buf = ex.next();
+    if (act) {
 #pragma unroll
-    for (int m = 0; m < EPT; ++m) buf[sw<CX>(t + T * m)] = v[m];
+      for (int m = 0; m < EPT; ++m) buf[sw<CX>(t + T * m)] = v[m];
+    }
     ex.sync();
   }
   asm volatile("" : "+r"(t)::"memory");  // stage boundary (see fwd_stage)
@@ -532,17 +542,22 @@ __device__ __forceinline__ void inv_stage(typename Types<R>::C (&v)[EPT], ExBuf<
     if constexpr (FIRST) {
 #pragma unroll
       for (int r = 0; r < RS; ++r) a[r] = v[q + r * Q];
-    } else {
+    } else if (act) {
       const int base = (j - k) * RS + k;
 #pragma unroll
       for (int r = 0; r < RS; ++r) a[r] = buf[sw<CX>(base + r * NS)];
-    }
-    if constexpr (TC && RS == 16) tc_dft<16, true, TC == 2>(a, *tc);
-    else butterfly<RS, true>(a);
-    if constexpr (NS > 1) {
-      const typename Types<R>::W* tws = stage_tw<R>(ex) + P::tw_off(S) + k;
+    } else {
 #pragma unroll
-      for (int r = 1; r < RS; ++r) a[r] = twmul_conj(a[r], __ldg(&tws[(r - 1) * NS]));
+      for (int r = 0; r < RS; ++r) a[r] = v[q + r * Q];
+    }
+    if constexpr (TC && RS == 16) tc_dft<16, true, TC == 2>(a, *tc, act);
+    else if (act) butterfly<RS, true>(a);
+    if constexpr (NS > 1) {
+      if (act) {
+        const typename Types<R>::W* tws = stage_tw<R>(ex) + P::tw_off(S) + k;
+#pragma unroll
+        for (int r = 1; r < RS; ++r) a[r] = twmul_conj(a[r], __ldg(&tws[(r - 1) * NS]));
+      }
     }
 #pragma unroll
     for (int r = 0; r < RS; ++r) v[q + r * Q] = a[r];
@@ -630,27 +645,29 @@ __device__ __forceinline__ void fft_fwd_pf_seq(typename Types<R>::C (&v)[EPT], E
 
 template <typename R, int L, int EPT, int TC, int... S>
 __device__ __forceinline__ void fft_fwd_seq(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
-                                            const typename Types<R>::W* tw, int t, TcCtx* tc,
+                                            const typename Types<R>::W* tw, int t, TcCtx* tc, bool act,
                                             std::integer_sequence<int, S...>) {
-  (fwd_stage<R, L, EPT, S, TC>(v, ex, tw, t, tc), ...);
+  (fwd_stage<R, L, EPT, S, TC>(v, ex, tw, t, tc, act), ...);
 }
 template <typename R, int L, int EPT, int TC, int... S>
 __device__ __forceinline__ void fft_inv_seq(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
-                                            const typename Types<R>::W* tw, int t, TcCtx* tc,
+                                            const typename Types<R>::W* tw, int t, TcCtx* tc, bool act,
                                             std::integer_sequence<int, S...>) {
-  (inv_stage<R, L, EPT, FFTPlan<L, EPT>::kStages - 1 - S, TC>(v, ex, tw, t, tc), ...);
+  (inv_stage<R, L, EPT, FFTPlan<L, EPT>::kStages - 1 - S, TC>(v, ex, tw, t, tc, act), ...);
 }
 
 // Forward DFT of length L: v holds x[t + T m] on entry, X[t + T m] on exit
 // (T = L/EPT, m < EPT).  Every thread of the block must call it (block-wide
 // barriers inside); the exchanges alternate between the two buffers of `ex`.
 // TC: the radix-16 stages run on the tensor cores (tc_dft.cuh, context *tc):
-// 1 split-FP16, 2 split-BF16.
+// 1 split-FP16, 2 split-BF16.  act = false: barriers and tensor-core rounds
+// only (see fwd_stage).
 template <typename R, int L, int EPT, int TC = 0>
 __device__ __forceinline__ void block_fft_fwd(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
-                                              const typename Types<R>::W* tw, int t, TcCtx* tc = nullptr) {
+                                              const typename Types<R>::W* tw, int t, TcCtx* tc = nullptr,
+                                              bool act = true) {
   static_assert(!TC || sizeof(R) == 4, "tensor-core stages take float data");
-  fft_fwd_seq<R, L, EPT, TC>(v, ex, tw, t, tc, std::make_integer_sequence<int, FFTPlan<L, EPT>::kStages>{});
+  fft_fwd_seq<R, L, EPT, TC>(v, ex, tw, t, tc, act, std::make_integer_sequence<int, FFTPlan<L, EPT>::kStages>{});
 }
 // Adjoint of fwd_stage_pf's stage S: the stage's twiddles are loaded before its
 // exchange barrier (they are applied after the butterfly).
@@ -718,9 +735,10 @@ __device__ __forceinline__ void block_fft_fwd_pf(typename Types<R>::C (&v)[EPT],
 // Unnormalised inverse DFT (adjoint of block_fft_fwd).
 template <typename R, int L, int EPT, int TC = 0>
 __device__ __forceinline__ void block_fft_inv(typename Types<R>::C (&v)[EPT], ExBuf<typename Types<R>::C>& ex,
-                                              const typename Types<R>::W* tw, int t, TcCtx* tc = nullptr) {
+                                              const typename Types<R>::W* tw, int t, TcCtx* tc = nullptr,
+                                              bool act = true) {
   static_assert(!TC || sizeof(R) == 4, "tensor-core stages take float data");
-  fft_inv_seq<R, L, EPT, TC>(v, ex, tw, t, tc, std::make_integer_sequence<int, FFTPlan<L, EPT>::kStages>{});
+  fft_inv_seq<R, L, EPT, TC>(v, ex, tw, t, tc, act, std::make_integer_sequence<int, FFTPlan<L, EPT>::kStages>{});
 }
 
 }  // namespace psatd

@@ -67,9 +67,9 @@ static cudaError_t push_L(int layout, dim3 grid, int tb, int groups, size_t smem
     return cudaErrorInvalidValue;
   } else {
     const dim3 block(FFTPlan<L, EPT>::kT, tb, groups);
-    // component groups: their own instantiation, for whole-warp lines in FP32 without
-    // tensor-core stages (the host admits groups > 1 nowhere else)
-    constexpr bool kGrpOk = !TC && sizeof(R) == 4 && FFTPlan<L, EPT>::kT % 32 == 0;
+    // component groups: their own instantiation, for whole-warp lines in FP32 and
+    // for the tensor-core pairs (the host admits groups > 1 nowhere else)
+    constexpr bool kGrpOk = TC ? EPT == 16 : (sizeof(R) == 4 && FFTPlan<L, EPT>::kT % 32 == 0);
     if (groups > 1 && !kGrpOk) return cudaErrorInvalidValue;
     cudaError_t e;
 #define PSATD_PUSH_LAUNCH(LAY, GRP)                                            \

@@ -846,7 +846,7 @@ __device__ __forceinline__ void line_push_body(const PushArgs<R>& a_in, const ty
   typedef FFTPlan<L, EPT> P;
   constexpr int T = P::kT;
   constexpr int CXL = P::kLastCX;
-  static_assert(!GRP || (!TC && T % 32 == 0), "component groups need whole-warp lines and no tensor-core stages");
+  static_assert(!GRP || TC || T % 32 == 0, "SIMT component groups need whole-warp lines");
   if constexpr (!GRP) {  // the plain pass
     grp = 0;
     G = 1;
@@ -871,7 +871,7 @@ __device__ __forceinline__ void line_push_body(const PushArgs<R>& a_in, const ty
   // Only kernels whose lines have whole warps (T a multiple of 32) contain the
   // named barrier at all: its thread count must be a multiple of the warp size.
   int bar_id = 0, bar_n = 0;
-  if constexpr (GRP) {
+  if constexpr (GRP && !TC) {
     bar_id = 1 + g * G + grp;
     bar_n = T;
   }
@@ -928,19 +928,46 @@ __device__ __forceinline__ void line_push_body(const PushArgs<R>& a_in, const ty
     sc.phase ^= 1u;
   }
   C v[EPT];
-  for (int c = grp; c < a.n_in; c += G) {
-    C* sl = st + c * ss;
+  if constexpr (TC && GRP) {
+    // Tensor-core component pairs: the two groups (128 rows each) transform the
+    // components c0 and c0 + 1 in lockstep, so that every tensor-core round (block
+    // barriers, one issuing thread, one commit) serves both; a group with no
+    // component in the last pair only takes part in the barriers and rounds.  Each
+    // component exchanges in its own slot (one buffer), its A_h / A_m tiles sit in
+    // that slot at the round (group j's at tc.a_tile + j x tile size = slot c0 + j:
+    // the slot stride of 128 rows of 16 complex values equals the tile size) and
+    // both third pieces in the spare region; the shared memory is the one-group
+    // pass's, with twice its threads.
+    tc.a_tile3 = smem_u32(base + a.n_in * ss);
+    for (int c0 = 0; c0 < a.n_in; c0 += 2) {
+      const int c = c0 + grp;
+      const bool act = c < a.n_in;
+      C* sl = st + (act ? c : c0) * ss;
 #pragma unroll
-    for (int m = 0; m < EPT; ++m) v[m] = sl[t + T * m];
-    ExBuf<C> ex{{sl, bufB}, 0, &twslot, false, bar_id, bar_n};
-    ex.sync();  // the slot becomes an exchange buffer
-    if constexpr (TC) tc.a_tile3 = smem_u32(base + c * ss);
-    if constexpr (TC == 0 && (EPT == 8 || EPT == 12))
-      block_fft_fwd_pf<R, L, EPT>(v, ex, t);
-    else
-      block_fft_fwd<R, L, EPT, TC>(v, ex, tw, t, &tc);
+      for (int m = 0; m < EPT; ++m) v[m] = act ? sl[t + T * m] : mkc(R(0), R(0));
+      ExBuf<C> ex{{sl, sl}, 0, &twslot, true};
+      tc.a_tile = smem_u32(base + c0 * ss);
+      block_fft_fwd<R, L, EPT, TC>(v, ex, tw, t, &tc, act);
+      if (act) {
 #pragma unroll
-    for (int m = 0; m < EPT; ++m) sl[sw<CXL>(t + T * m)] = v[m];
+        for (int m = 0; m < EPT; ++m) sl[sw<CXL>(t + T * m)] = v[m];
+      }
+    }
+  } else {
+    for (int c = grp; c < a.n_in; c += G) {
+      C* sl = st + c * ss;
+#pragma unroll
+      for (int m = 0; m < EPT; ++m) v[m] = sl[t + T * m];
+      ExBuf<C> ex{{sl, bufB}, 0, &twslot, false, bar_id, bar_n};
+      ex.sync();  // the slot becomes an exchange buffer
+      if constexpr (TC) tc.a_tile3 = smem_u32(base + c * ss);
+      if constexpr (TC == 0 && (EPT == 8 || EPT == 12))
+        block_fft_fwd_pf<R, L, EPT>(v, ex, t);
+      else
+        block_fft_fwd<R, L, EPT, TC>(v, ex, tw, t, &tc);
+#pragma unroll
+      for (int m = 0; m < EPT; ++m) sl[sw<CXL>(t + T * m)] = v[m];
+    }
   }
   if (G > 1) __syncthreads();  // every group's spectra are in their slots
 
@@ -959,6 +986,24 @@ __device__ __forceinline__ void line_push_body(const PushArgs<R>& a_in, const ty
   }
   if (G > 1) __syncthreads();  // every mode is pushed
 
+  if constexpr (TC && GRP) {  // output pairs in lockstep, as the input pairs above
+    for (int c0 = 0; c0 < a.n_out; c0 += 2) {
+      const int c = c0 + grp;
+      const bool act = c < a.n_out;
+      C* sl = st + (act ? c : c0) * ss;
+#pragma unroll
+      for (int m = 0; m < EPT; ++m) v[m] = act ? sl[sw<CXL>(t + T * m)] : mkc(R(0), R(0));
+      ExBuf<C> ex{{sl, sl}, 0, &twslot, true};
+      tc.a_tile = smem_u32(base + c0 * ss);
+      block_fft_inv<R, L, EPT, TC>(v, ex, tw, t, &tc, act);
+      if (act && valid) {
+        C* dst = spec + c * a.cs + (int64_t)line * L;
+#pragma unroll
+        for (int m = 0; m < EPT; ++m) dst[t + T * m] = v[m];
+      }
+    }
+    return;
+  }
   for (int c = G - 1 - grp; c < a.n_out; c += G) {
     C* sl = st + c * ss;
 #pragma unroll
@@ -978,7 +1023,7 @@ __device__ __forceinline__ void line_push_body(const PushArgs<R>& a_in, const ty
 }
 
 // Block (T, lines per CTA, component groups); the group variant (GRP) takes up
-// to 512 threads, the plain pass 256 (or T).
+// to 512 threads (the tensor-core pairs 256), the plain pass 256 (or T).
 template <typename R, int L, int LAYOUT, int TC = 0, int EPT = PushEPT<L, TC>::value, bool GRP = false>
 __global__ void __launch_bounds__(GRP ? 512 : (FFTPlan<L, EPT>::kT > 256 ? FFTPlan<L, EPT>::kT : 256))
 k_line_push(PushArgs<R> a, const typename Types<R>::W* __restrict__ tw) {

@@ -187,7 +187,7 @@ __host__ __device__ constexpr int tc_tmem_cols(int nthreads) {
 
 // One radix-RS DFT (forward, or adjoint for ADJ) of the RS values a[] of every
 // thread's butterfly, on the tensor cores.  Every thread of the CTA calls it
-// (block barriers inside); blockDim.x * blockDim.y is a multiple of 128.  The
+// (block barriers inside); the block's thread count is a multiple of 128.  The
 // A tiles alias exchange space that holds no live data at a stage boundary.
 // BF16: split-BF16 operands (else split-FP16).
 // Failure path: a thread whose completion wait runs out sets the CTA's abort
@@ -196,12 +196,14 @@ __host__ __device__ constexpr int tc_tmem_cols(int nthreads) {
 // barrier, so every thread sees the same value: once it is set, no thread
 // splits, issues, waits or reads TMEM again, and tc_teardown makes one last
 // bounded wait for the outstanding commit before it frees the TMEM columns.
+// act = false: the thread writes no operand (its 128-row group has no data this
+// round; its rows of the MMAs read whatever the tile holds and are not used).
 template <int RS, bool ADJ, bool BF16>
-__device__ __forceinline__ void tc_dft(float2 (&a)[RS], TcCtx& tc) {
+__device__ __forceinline__ void tc_dft(float2 (&a)[RS], TcCtx& tc, bool act = true) {
   typedef TcGeom<RS> G;
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
   const int grp = tid >> 7, row = tid & 127;
-  const int ngrp = (blockDim.x * blockDim.y) >> 7;
+  const int ngrp = (blockDim.x * blockDim.y * blockDim.z) >> 7;
 
   // row scale 2^k with max |component| * 2^k in [2^14, 2^15)
   float mx = 0.f;
@@ -216,7 +218,7 @@ __device__ __forceinline__ void tc_dft(float2 (&a)[RS], TcCtx& tc) {
 
   __syncthreads();  // every exchange read of the previous stage is done
   const bool aborted = *tc.abort != 0;
-  if (!aborted) {
+  if (!aborted && act) {
     const uint32_t base = tc.a_tile + grp * G::kATile + (row >> 3) * G::kSBO + (row & 7) * 16;
     const uint32_t base3 = tc.a_tile3 + grp * G::kAPiece + (row >> 3) * G::kSBO + (row & 7) * 16;
 #pragma unroll
@@ -332,8 +334,8 @@ constexpr int kTcTail = 2 * TcGeom<16>::kGDir + 1024;
 // ctl: the pass's control word (kTcStallMma).  Contains a block barrier.
 __device__ __forceinline__ void tc_setup(TcCtx& tc, unsigned char* tail, const void* gmat, uint32_t a_tile,
                                          int* err, int bf16, uint32_t a_tile3, int ctl) {
-  const int nthr = blockDim.x * blockDim.y;
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
   constexpr int kG = 2 * TcGeom<16>::kGDir;
   for (int i = tid; i < kG / 16; i += nthr)
     reinterpret_cast<uint4*>(tail)[i] = __ldg(static_cast<const uint4*>(gmat) + i);
@@ -366,8 +368,8 @@ __device__ __forceinline__ void tc_setup(TcCtx& tc, unsigned char* tail, const v
 // After an expired wait (abort word set) the last commit may still be
 // outstanding: warp 0 first waits for it once more (bounded), then frees.
 __device__ __forceinline__ void tc_teardown(const TcCtx& tc) {
-  const int nthr = blockDim.x * blockDim.y;
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  const int tid = (threadIdx.z * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
   tc_fence_before();
   __syncthreads();
   if (tid < 32) {

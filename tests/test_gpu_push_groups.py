@@ -2,7 +2,8 @@
 
 With G > 1 each line's input components are forward-transformed, and its
 output components inverse-transformed, by G thread groups in turn, which meet
-only for the per-mode push.  Every transform and every mode's update runs the
+only for the per-mode push (tensor-core plans: two groups in lockstep, one
+128-row MMA group each, sharing every tensor-core round).  Every transform and every mode's update runs the
 same arithmetic in the same order as with one group, so the fields must be
 bitwise identical for every valid G; one G > 1 case per shape is also checked
 against the FP64 oracle.  Shapes: 2D TE (lines of 256 and 2048 points), 2D
@@ -99,16 +100,15 @@ def test_groups_over_many_steps_stay_bitwise():
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
-@pytest.mark.parametrize("prec,shape,ept", [
-    ("fp64", (256, 64), None),          # FP64 plans keep one group
-    ("mixed_bf16", (512, 128), None),   # tensor-core stages synchronise the whole CTA
-    ("fp32", (128, 64), None),          # 128-point lines: 16 threads a line
-    ("fp32", (384, 64), None),          # 12 elements per thread: no four groups (odd modes per thread)
+@pytest.mark.parametrize("prec,shape,bad", [
+    ("fp64", (256, 64), [2, 4]),          # FP64 plans keep one group
+    ("mixed_bf16", (512, 128), [4]),      # tensor-core stages: pairs only
+    ("fp32", (128, 64), [2, 4]),          # 128-point lines: 16 threads a line
+    ("fp32", (384, 64), [4]),             # 12 elements per thread: no four groups (odd modes per thread)
 ])
-def test_invalid_groups_are_refused(prec, shape, ept):
+def test_invalid_groups_are_refused(prec, shape, bad):
     ensure_lib()
     plan = capi.Plan(tuple(reversed(shape)), (1.0, 1.0), 0.5, layout="te", prec=prec, src="J")
-    bad = [4] if shape == (384, 64) else [2, 4]
     for G in bad:
         with pytest.raises(capi.PsatdError):
             plan.set_push_groups(G)
@@ -161,3 +161,57 @@ def test_batch_groups_give_the_same_bits():
             assert np.array_equal(a, c)
     with pytest.raises(capi.PsatdError):
         capi.Batch(sizes, (1.0, 1.0), 0.5, layout="te", prec="fp32", src="J").set_push_groups(3)
+
+
+# tensor-core pairs: (array shape, layout, source form); odd and even component counts
+TC_CASES = [
+    ((512, 128), "te", "J"),       # 5 inputs, 3 outputs: the last pair of each has one component
+    ((64, 128), "2d6", "rho"),     # 11 inputs, 6 outputs
+    ((1024, 128), "tm", "none"),   # 3 inputs, 3 outputs
+    ((128, 256), "te", "J"),       # 128-point lines: 8 threads a line, 16 lines per group
+]
+
+
+@pytest.mark.parametrize("prec", ["mixed_bf16", "mixed_fp16"])
+@pytest.mark.parametrize("shape,layout,src", TC_CASES)
+def test_tensor_core_pairs_give_the_same_bits(shape, layout, src, prec):
+    ensure_lib()
+    d, dt = (1.0, 0.9), 0.4
+    E, B, J, r0, r1 = _inputs(shape, layout, 311)
+    out = []
+    for G in (1, 2):
+        plan = capi.Plan(tuple(reversed(shape)), d, dt, layout=layout, prec=prec, src=src)
+        plan.set_push_groups(G)
+        assert plan.get_push_groups() == G
+        out.append(psatd_gpu(shape, d, dt, E, B, J, r0, r1, layout=layout, prec=prec, src=src, plan=plan, nsteps=3))
+        plan.destroy()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    Eo, Bo = orc.psatd_step(E, B, J if src != "none" else None, r0 if src == "rho" else None,
+                            r1 if src == "rho" else None, d=d, dt=dt, form=src, nsteps=3)
+    assert rel_l2_fields(out[1][0], out[1][1], mask_layout(Eo, layout, "E"), mask_layout(Bo, layout, "B")) < 2e-5
+
+
+def test_tensor_core_pairs_in_a_batch():
+    """Split-BF16 batch of mixed sizes (tensor-core sides): pairs in every class give the
+    one-group bits over a multi-step graph replay."""
+    import torch
+    ensure_lib()
+    sizes = [(256, 512), (128, 256), (512, 128), (128, 1024), (256, 512)]
+    tot = sum(a * b for a, b in sizes)
+    g = torch.Generator().manual_seed(9)
+    J = [torch.randn(tot, generator=g).cuda() * 0.01 for _ in range(2)]
+    E0 = [torch.randn(tot, generator=g).cuda() for _ in range(3)]
+    stream = torch.cuda.Stream()
+    res = []
+    for G in (1, 2):
+        b = capi.Batch(sizes, (1.0, 1.0), 0.5, layout="te", prec="mixed_bf16", src="J", stream=stream)
+        b.set_push_groups(G)
+        E = [x.clone() for x in E0]
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            b.step([E[0], E[1], None], [None, None, E[2]], [J[0], J[1], None], nsteps=4)
+        b.sync()
+        res.append([x.cpu().numpy() for x in E])
+        b.destroy()
+    for a, c in zip(res[0], res[1]):
+        assert np.array_equal(a, c)
