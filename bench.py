@@ -271,10 +271,14 @@ def time_batch(capi, torch, prec, sizes, Jhost, args, dev, stream, sample_clocks
     """A batch at precision `prec`: W untimed steps (one call: the step graph is
     recorded and replayed), then one psatd_batch_step(nsteps = K) call between
     CUDA events on the batch's stream.  Per-kernel event pairs are recorded in the
-    graph (their times are the last replay's).  Returns (ms, kernel times, clocks,
-    batch, (Ex, Ey, Bz, Jx, Jy))."""
+    graph (their times are the last replay's).  The mixed-precision batch is
+    autotuned per size class at creation (its shapes are then cached for the
+    process); the FP32 batch keeps the built-in shapes, which ran faster for it
+    (each class is tuned alone, while the batch runs the classes side by side).
+    Returns (ms, kernel times, clocks, batch, (Ex, Ey, Bz, Jx, Jy))."""
     K = nsteps or args.steps
-    b = capi.Batch(sizes, (BATCH_DX, BATCH_DX), BATCH_DT, layout="te", prec=prec, src="J", stream=stream)
+    b = capi.Batch(sizes, (BATCH_DX, BATCH_DX), BATCH_DT, layout="te", prec=prec, src="J", stream=stream,
+                   autotune=(prec != "fp32"))
     if persistent is not None:
         b.set_persistent(persistent)
     if not forked:
@@ -517,6 +521,8 @@ def run_batch_line(args, world, rank, local):
                        "size_classes": len(set(sizes)),
                        "value_counts": "cells of the transformed patch domains (interior + widened guards)",
                        "run": "one psatd_batch_step(nsteps = steps) call: a CUDA graph of one step replayed",
+                       "launch_shapes": ("autotuned per size class at batch creation (lines per CTA of every pass, "
+                                         "component groups of the fused pass)" if prec != "fp32" else "built-in"),
                        "launches_per_step": launches_per_step,
                        "l2": "not flushed: the inputs (%.2f GB) are 15x the 129 MB L2" % (5 * cells * 4 / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -535,6 +541,8 @@ def run_batch_line(args, world, rank, local):
             "same_patches": {"precision": PREC_NOTE["fp32"], "value": cells * K / (ms32 * 1e-3),
                              "ms_per_step": ms32 / K, "ratio": (cells * K / (ms * 1e-3)) / (cells * K / (ms32 * 1e-3)),
                              "what": "FP32 batch on the same power-of-two patch sides; ratio = mixed / FP32",
+                             "launch_shapes": "built-in (faster for FP32 in this batch than per-class autotuned "
+                                              "shapes, which are tuned with each class alone)",
                              "launches_per_step": lps32,
                              "roofline": roofline_of(kt32, lambda k, n: alg_b[k], hbm, peak_kind,
                                                      traffic_lookup=False, note=concurrent),
