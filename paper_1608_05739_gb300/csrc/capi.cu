@@ -15,6 +15,8 @@
 #include <vector>
 
 #include "../../include/psatd.h"
+#include <nvtx3/nvToolsExt.h>
+
 #include "farfield.h"
 #include "launch.h"
 #include "local.h"
@@ -32,6 +34,15 @@ const char* kSlotNames[K_NSLOTS] = {"fwd_x_r2c", "fwd_y_c2c", "line_fft_push", "
 
 struct EventPair {
   cudaEvent_t a, b;
+};
+
+// NVTX range for the profilers' timelines (a no-op unless a tool is attached):
+// one per public step call and one per pass launch, named like the timing slots.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 }  // namespace
@@ -392,6 +403,7 @@ struct TimedLaunch {
   psatd_plan p;
   int slot;
   cudaStream_t st;
+  NvtxRange range;
   EventPair ep{};
   static void record(cudaEvent_t e, cudaStream_t st) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -401,7 +413,7 @@ struct TimedLaunch {
       cudaEventRecord(e, st);
   }
   TimedLaunch(psatd_plan pl, int s) : TimedLaunch(pl, s, pl->st) {}
-  TimedLaunch(psatd_plan pl, int s, cudaStream_t stream) : p(pl), slot(s), st(stream) {
+  TimedLaunch(psatd_plan pl, int s, cudaStream_t stream) : p(pl), slot(s), st(stream), range(kSlotNames[s]) {
     if (!p->timing) return;
     if (!p->pool.empty()) {
       ep = p->pool.back();
@@ -1155,6 +1167,7 @@ psatd_status psatd_plan_get_launch(psatd_plan p, int32_t cfg[6]) {
 }
 
 psatd_status psatd_step(psatd_plan p, const psatd_fields* fields, const psatd_sources* sources, int32_t nsteps) {
+  NvtxRange range("psatd_step");
   if (!p) return fail(nullptr, PSATD_ERR_INVALID_ARG, "plan is NULL");
   if (nsteps < 1) return fail(p, PSATD_ERR_INVALID_ARG, "nsteps must be >= 1 (got %d)", nsteps);
   if (!p->coeffs_ready) return fail(p, PSATD_ERR_INVALID_ARG, "psatd_coeffs_init was not called");
@@ -1237,6 +1250,7 @@ int32_t psatd_kernel_times(psatd_plan p, int32_t n_slots, const char** names, in
 
 psatd_status fdtd_step(const psatd_desc* desc, int32_t scheme, const psatd_fields* fields,
                        const psatd_sources* sources, int32_t nsteps, void* cuda_stream) {
+  NvtxRange range("fdtd_step");
   psatd_status s = validate_desc(nullptr, desc, false);
   if (s != PSATD_OK) return s;
   if (scheme != PSATD_FDTD_YEE && scheme != PSATD_FDTD_CKC)
@@ -1388,6 +1402,7 @@ bool current_ctx_id(unsigned long long* id) {
 
 extern "C" psatd_status psatd_step_noalloc(const psatd_desc* desc, const psatd_fields* fields,
                                            const psatd_sources* sources, int32_t nsteps, void* cuda_stream) {
+  NvtxRange range("psatd_step_noalloc");
   psatd_status s = validate_desc(nullptr, desc, true);
   if (s != PSATD_OK) return s;
   if (nsteps < 1) return fail(nullptr, PSATD_ERR_INVALID_ARG, "nsteps must be >= 1 (got %d)", nsteps);
@@ -1942,6 +1957,7 @@ extern "C" psatd_status psatd_batch_create(const psatd_desc* base, int32_t npatc
 
 extern "C" psatd_status psatd_batch_step(psatd_batch b, const psatd_fields* fields, const psatd_sources* sources,
                                          int32_t nsteps) {
+  NvtxRange range("psatd_batch_step");
   if (!b) return fail(nullptr, PSATD_ERR_INVALID_ARG, "batch is NULL");
   if (nsteps < 1) return fail(nullptr, PSATD_ERR_INVALID_ARG, "nsteps must be >= 1 (got %d)", nsteps);
   const void* in[kMaxComp] = {};
@@ -2186,6 +2202,7 @@ extern "C" psatd_status psatd_local_create(const psatd_desc* global, int32_t px,
 
 extern "C" psatd_status psatd_local_step(psatd_local L, const psatd_fields* fields, const psatd_sources* sources,
                                          int32_t nsteps) {
+  NvtxRange range("psatd_local_step");
   if (!L) return fail(nullptr, PSATD_ERR_INVALID_ARG, "local decomposition is NULL");
   psatd_plan p = L->plan;
   if (nsteps < 1) return fail(p, PSATD_ERR_INVALID_ARG, "nsteps must be >= 1 (got %d)", nsteps);
