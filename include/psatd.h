@@ -178,11 +178,13 @@ typedef struct psatd_plan_s* psatd_plan;
 int32_t psatd_abi_version(void);
 
 /* Create a PSATD plan for `desc` on `cuda_stream`.
- * Supported (this build): every n[i] a power of two, 16 <= n[0] <= 4096,
+ * Supported sizes: every n[i] a power of two, 16 <= n[0] <= 4096,
  * 8 <= n[1], n[2] <= 4096; with PSATD_FP32 also the mixed-radix lengths
  * n[0] = 6 * 2^k in [96, 3072] (x rows of n[0]/2 = 3 * 2^(k-1) points) and
- * n[1], n[2] = 3 * 2^k in [48, 3072], on any axis and combined freely with
- * powers of two (radix-3 first stage); PSATD_FP64, PSATD_FP32,
+ * n[1], n[2] = 3 * 2^k in [48, 3072] (radix-3 first stage), and
+ * n[0] = 10 * 2^k in [160, 2560], n[1], n[2] = 5 * 2^k in [80, 1280] (radix-5
+ * first stage), on any axis and combined freely with powers of two;
+ * PSATD_FP64, PSATD_FP32,
  * PSATD_MIXED_FP16 or _BF16; flags from PSATD_FLAG_*.  A last axis of n
  * points needs (n_in + 1) * n * 8 (FP32) or 16 (FP64) bytes of shared memory
  * per CTA (UNSUPPORTED beyond the device's opt-in limit).
